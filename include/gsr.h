@@ -1,0 +1,337 @@
+/*
+ * gsr.h - C ABI of the GB300 (sm_103a) 3DGS rasterizer and SkipGS gate.
+ *
+ * The calls follow the paper's statement of the problem:
+ *   Sec. 3 (Preliminaries), Eq. (gaussian), (cov), (proj), (blend), (alpha),
+ *   (loss); Sec. 3.1-3.3 and Algorithm 1 (SkipGS gating) with Eq. (view-ema),
+ *   (deviation), (gate), (rhocum), (rhocum_check), (rhohat), (rhomincalib).
+ *
+ * Conventions shared by every call
+ *   - Every function returns gs_status (GS_OK = 0).  Argument checks run on the
+ *     host before anything is launched and return GS_ERR_INVALID_ARG or
+ *     GS_ERR_WORKSPACE; a failed launch returns GS_ERR_CUDA.
+ *   - Work is enqueued asynchronously on the given stream; the call does not
+ *     synchronise.  Failures found on the device (pair capacity exceeded, a
+ *     non-finite loss given to the gate) are written into the caller's device
+ *     word `dev_status` (0 = no error; the first error wins) and the kernel
+ *     skips the affected work.  Read it after synchronising.
+ *   - All memory is owned by the caller: every pointer is a device pointer
+ *     unless marked "host", arrays are dense, row-major, float32 unless stated.
+ *     The library allocates no device memory; scratch space is passed in as a
+ *     workspace whose size the matching *_workspace_size call returns.
+ *   - No call reads back from the device, so every call can be captured into
+ *     a CUDA graph; sizes that depend on data (the number of Gaussian x tile
+ *     pairs) stay on the device.
+ *
+ * Layouts
+ *   - Parameters of N Gaussians (gs_params): means [N,3], log_scales [N,3]
+ *     (per-axis standard deviation s = exp(log_scale), Eq. cov), quats [N,4]
+ *     (w,x,y,z; normalised inside), opacity_logit [N] (opacity =
+ *     sigmoid(logit)), sh [N,K,3] with K = (sh_degree+1)^2 real SH
+ *     coefficients per colour channel.  gs_param_layout gives the offsets of
+ *     these groups inside one flat buffer (59 floats per Gaussian at degree 3
+ *     plus alignment padding; means | log_scales | quats | opacity_logit | sh),
+ *     the layout the optimizer step works on.  quats, and sh when 3K is a
+ *     multiple of 4, must be 16-byte aligned.
+ *   - Views: an array of gs_camera in device memory.  View v's tiles occupy
+ *     global tile ids [tile_offset, tile_offset + tiles_x * tiles_y) and its
+ *     pixels the image range starting at pix_offset, stored planar
+ *     [3][height][width].  gs_camera_layout fills both offsets.
+ *   - Projected Gaussians (gs_projected), per view and Gaussian, at index
+ *     v * N + i: a 12-float record rec = (mean2d.x, mean2d.y, u00, u01, u11,
+ *     opacity, r, g, b, depth, radius, 0), where U = [[u00, u01], [0, u11]] is
+ *     the upper Cholesky factor of the conic Q = Sigma2D^-1 (Q = U^T U);
+ *     rect = tile rectangle (x0, y0, x1, y1) inclusive; tiles_touched = its
+ *     tile count (0 = culled).
+ *   - Pixel centres are at (i + 0.5, j + 0.5); the principal point (cx, cy) is
+ *     in the same continuous coordinates.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,  /* a pointer, size or configuration value is invalid */
+    GS_ERR_WORKSPACE = 2,    /* the workspace is missing or smaller than required */
+    GS_ERR_CUDA = 3,         /* a CUDA runtime call failed (launch or capture) */
+    GS_ERR_CAPACITY = 4,     /* device: more Gaussian x tile pairs than pair_capacity */
+    GS_ERR_NONFINITE = 5,    /* device: the gate was given a NaN or infinite loss */
+    GS_ERR_UNSUPPORTED = 6   /* a configuration this build does not provide */
+} gs_status;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *gs_status_string(int status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int gs_version(void);
+
+/* ---------------------------------------------------------------- types */
+
+/* Pinhole camera of one view, Eq. (proj): world -> camera x_c = R x + t
+ * (x right, y down, z forward); fx, fy, cx, cy in pixels; znear: Gaussians with
+ * z <= znear are culled.  tile_offset / pix_offset: see Layouts above. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;
+    int32_t tile_offset;
+    int64_t pix_offset;
+} gs_camera;
+
+/* Rasterizer constants.  lowpass: isotropic dilation added to Sigma2D (px^2);
+ * alpha_max (0.99), alpha_min (1/255) and t_min (1e-4): Eq. (alpha) clamp, the
+ * cut-off below which a Gaussian is skipped at a pixel, and the transmittance
+ * floor (a pixel stops before a Gaussian that would take T below it);
+ * bg: background colour added with the final transmittance; tile: 8, 16 or
+ * 32 (pixels per tile side); batch: Gaussians staged in shared memory per step
+ * (64, 128 or 256); sh_degree: 0..3. */
+typedef struct {
+    float lowpass, alpha_max, alpha_min, t_min;
+    float bg[3];
+    int32_t tile;
+    int32_t batch;
+    int32_t sh_degree;
+} gs_raster_config;
+
+typedef struct {
+    const float *means, *log_scales, *quats, *opacity_logit, *sh;
+    int64_t n;
+    int32_t sh_degree;
+} gs_params;
+
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logit, *sh;
+} gs_grads;
+
+typedef struct {
+    float *rec;              /* [V*N][12] */
+    int32_t *rect;           /* [V*N][4]  */
+    int32_t *tiles_touched;  /* [V*N]     */
+} gs_projected;
+
+/* State the forward pass saves for the backward pass (caller-owned):
+ *   T_final [total pixels]: transmittance after the pixel's last contributor;
+ *   n_last  [total pixels]: 1 + position, in its tile's list, of the pixel's
+ *            last contributor (0 = none);
+ *   ckpt    [ckpt_slots][tile*tile]: transmittance of every pixel at the
+ *            start of each staging batch the forward pass processed (per-tile
+ *            transmittance checkpoints); gs_ckpt_slots gives ckpt_slots. */
+typedef struct {
+    float *T_final;
+    int32_t *n_last;
+    float *ckpt;
+    int64_t ckpt_slots;
+} gs_fwd_saved;
+
+/* --------------------------------------------------------------- layout */
+
+/* Offsets (in floats) of the parameter groups inside one flat buffer for N
+ * Gaussians: out[0..5] = means, log_scales, quats, opacity_logit, sh, end.
+ * Each group starts on a 256-byte boundary (padding floats between groups are
+ * ignored by the kernels and stay zero under the optimizer). */
+gs_status gs_param_layout(int64_t n, int32_t sh_degree, int64_t *out6 /* host */);
+
+/* Fills tile_offset and pix_offset of n_views host-side cameras for `tile`,
+ * and returns the total tile and pixel counts (host pointers). */
+gs_status gs_camera_layout(gs_camera *cams /* host */, int32_t n_views, int32_t tile,
+                           int64_t *total_tiles, int64_t *total_pixels);
+
+/* Number of per-tile transmittance checkpoint slots needed for pair_capacity
+ * pairs over total_tiles tiles at staging batch `batch`. */
+int64_t gs_ckpt_slots(int64_t pair_capacity, int64_t total_tiles, int32_t batch);
+
+/* ------------------------------------------------------------ projection */
+
+/* Eq. (cov) and Eq. (proj) for n_views views: Sigma = R S S^T R^T, camera
+ * transform, EWA Jacobian J (x/z, y/z clamped to 1.3x the half field of view),
+ * Sigma2D = J W Sigma W^T J^T + lowpass I, conic factor U, mean2D, depth,
+ * opacity = sigmoid(logit), colour = max(0, sum_k f_k Y_k(d) + 0.5) for the
+ * direction d from the camera centre (real SH, Condon-Shortley phase), and
+ * the conservative tile rectangle of the region where alpha' >= alpha_min
+ * can hold: |p - mean2D| <= r with r^2 = 2 lambda_max(Sigma2D) ln(opacity /
+ * alpha_min), inflated for float32 rounding. */
+gs_status gs_project(const gs_params *params /* host */, const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg /* host */, gs_projected out,
+                     int32_t *dev_status, cudaStream_t stream);
+
+/* ------------------------------------------------------ binning and sort */
+
+/* Scratch bytes gs_bin_sort needs for n Gaussians x n_views views and
+ * pair_capacity pairs. */
+size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capacity, int64_t total_tiles);
+
+/* Tile binning + depth order ("depth-sorted Gaussians overlapping a pixel",
+ * Sec. 3): every (Gaussian, tile of its rectangle) pair, ordered by
+ * (global tile id, float32 bits of depth, Gaussian index) - the stable sort
+ * of the 64-bit keys (tile << 32 | depth bits) in emission order.  Writes
+ * vals[pair] = Gaussian index, ranges[tile] = [start, end) (empty = [0,0)),
+ * *dev_pair_count, and - if keys is not NULL - the 64-bit keys.  More pairs
+ * than pair_capacity: GS_ERR_CAPACITY in dev_status, ranges left empty
+ * (only the tile geometry of cams is read). */
+gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n, int64_t total_tiles, const gs_raster_config *cfg /* host */,
+                      void *workspace, size_t workspace_bytes, uint64_t *keys, uint32_t *vals,
+                      int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count,
+                      int32_t *dev_status, cudaStream_t stream);
+
+/* --------------------------------------------------------------- forward */
+
+/* Eq. (blend) and Eq. (alpha): per tile, Gaussians staged `batch` at a time in
+ * shared memory; per pixel front to back alpha' = min(alpha_max, o exp(-1/2
+ * dp^T Q dp)), skip alpha' < alpha_min, stop before a Gaussian with
+ * T (1 - alpha') < t_min, C += c alpha' T, T *= 1 - alpha'; C += T bg.
+ * image: planar float [3][H][W] per view at pix_offset.  Saves state for
+ * gs_render_bwd. */
+gs_status gs_render_fwd(const gs_projected *proj /* host */, int64_t n, const uint32_t *vals,
+                        const uint32_t *ranges, const gs_camera *cams, int32_t n_views,
+                        int64_t total_tiles, const gs_raster_config *cfg /* host */, float *image, gs_fwd_saved saved, int32_t *dev_status, cudaStream_t stream);
+
+/* ------------------------------------------------------------------ loss */
+
+/* Scratch bytes of gs_loss for these views (host cameras; width, height and
+ * pix_offset are read). */
+size_t gs_loss_workspace_size(const gs_camera *cams_host, int32_t n_views);
+
+/* Eq. (loss): L_v = (1 - lambda) mean|C - C_hat| + lambda (1 - mean SSIM) per
+ * view (11x11 Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2, zero
+ * padding, 'same' size, means over 3HW).  cams_host: the views' cameras in
+ * host memory (only width, height and pix_offset are read).  image: as
+ * written by gs_render_fwd; target: same layout, or - when target_offsets is
+ * given - view slot v's target starts at target + target_offsets[view_ids[v]]
+ * (floats; view_ids in device memory).  Writes
+ * loss_per_view[n_views] (the gate's input) and keeps the SSIM partial
+ * derivatives in the workspace for gs_loss_backward.  If dL_dimage is not NULL
+ * the gradient is written too (as gs_loss_backward would). */
+gs_status gs_loss(const float *image, const float *target, const int64_t *target_offsets,
+                  const gs_camera *cams_host, const int32_t *view_ids, int32_t n_views, float lambda_ssim,
+                  void *workspace, size_t workspace_bytes, float *loss_per_view, float *dL_dimage,
+                  cudaStream_t stream);
+
+/* dL/dimage from the state gs_loss left in the workspace (same arguments). */
+gs_status gs_loss_backward(const float *image, const float *target, const int64_t *target_offsets,
+                           const gs_camera *cams_host, const int32_t *view_ids, int32_t n_views,
+                           float lambda_ssim, void *workspace, size_t workspace_bytes, float *dL_dimage,
+                           cudaStream_t stream);
+
+/* -------------------------------------------------------------- backward */
+
+size_t gs_render_bwd_workspace_size(int64_t n, int32_t n_views);
+
+/* Analytic adjoint of gs_render_fwd and gs_project (the paper's
+ * differentiable rasterizer, Sec. 3).  Per tile, pixels walk their list back
+ * to front from their last contributor, rebuilding T from the per-batch
+ * checkpoints; per-pair gradients of (mean2D, conic, opacity, colour) are
+ * reduced across the warp with shuffles, across the block in shared memory,
+ * and added to a per-view, per-Gaussian buffer with vector float atomics;
+ * a per-Gaussian pass then chains them to the parameters.  view_gate
+ * (nullable, device u8[n_views]): views with 0 contribute nothing.  grads are
+ * overwritten (accumulate = 0) or added to (accumulate = 1); views are summed. */
+gs_status gs_render_bwd(const gs_params *params /* host */, const gs_projected *proj /* host */,
+                        const uint32_t *vals, const uint32_t *ranges, const gs_camera *cams,
+                        int32_t n_views, int64_t total_tiles,
+                        const gs_raster_config *cfg /* host */, gs_fwd_saved saved, const float *dL_dimage,
+                        const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
+                        size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream);
+
+/* ----------------------------------------------------------------- Adam */
+
+/* Adam (Kingma & Ba, bias-corrected), the optimizer step of Algorithm 1.
+ * lr[6]: means, log_scales, quats, opacity, SH DC, SH higher bands. */
+typedef struct {
+    float lr[6];
+    float beta1, beta2, eps;
+} gs_adam_config;
+
+/* One fused update of every scalar of the flat parameter buffer (layout of
+ * gs_param_layout): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr m_hat / (sqrt(v_hat) + eps); zero_grad != 0 also sets g = 0.
+ * dev_step (int64, device) counts executed steps and is incremented.
+ * dev_do_step (nullable, int32 device): when it holds 0 nothing changes. */
+gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t n, int32_t sh_degree,
+                       const gs_adam_config *cfg /* host */, const int32_t *dev_do_step, int64_t *dev_step,
+                       int32_t zero_grad, cudaStream_t stream);
+
+/* ----------------------------------------------------------- SkipGS gate */
+
+/* Gate hyperparameters (Sec. 4.1): W = 500, beta = 0.95, eps = 1e-8,
+ * rho_lo = 0.5.  rho_lo < 0 selects the ablation without budget control
+ * (Table 4). */
+typedef struct {
+    int32_t W;
+    double beta, eps, rho_lo;
+    int32_t n_views;
+} gs_gate_config;
+
+/* Bytes of device state for a gate over n_views training views. */
+size_t skipgs_gate_state_size(int32_t n_views);
+
+/* Initialise the state (Algorithm 1: EMA table empty, rho_min = rho_lo, b = 0). */
+gs_status skipgs_gate_init(const gs_gate_config *cfg /* host */, void *dev_state, cudaStream_t stream);
+
+/* Algorithm 1, per loss in order (reading: each one is its own iteration t):
+ * deviation score s = L / (EMA + eps) or +inf without history (Eq. deviation),
+ * skip test g = [s > 1] (Eq. gate); during warmup (t <= W) the test is recorded
+ * for views with history and g is forced to 1; at t = W + 1 rho_min = rho_lo +
+ * (1 - rho_lo) rho_hat (Eq. rhohat, rhomincalib); after warmup g is forced to 1
+ * when b / max(t-1, 1) < rho_min (Eq. rhocum_check); b += g.  All arithmetic
+ * in binary64 with one rounding per operation.  Writes g[n] (u8) and, if
+ * given, *dev_any = OR of g (int32) and the graph conditional `cond` (host
+ * pointer to a handle created for the graph being captured; NULL outside a
+ * graph).  A non-finite loss: g = 0, state untouched, GS_ERR_NONFINITE. */
+gs_status skipgs_gate_decide(void *dev_state, const int32_t *dev_view_ids, const float *dev_losses, int32_t n,
+                             uint8_t *dev_g, int32_t *dev_any, const cudaGraphConditionalHandle *cond,
+                             int32_t *dev_status, cudaStream_t stream);
+
+/* Eq. (view-ema), unconditional after the decision: EMA_v = beta EMA_v +
+ * (1 - beta) L, or L on the view's first observation. */
+gs_status skipgs_gate_update(void *dev_state, const int32_t *dev_view_ids, const float *dev_losses, int32_t n,
+                             cudaStream_t stream);
+
+/* Copies the scalar part of the state to host memory for inspection:
+ * out[0..6] = t, b, n_w, n_w1, calibrated, errors, n_views (int64, host) and
+ * rho_min (double, host).  Synchronises the stream. */
+gs_status skipgs_gate_read(const void *dev_state, int64_t *out7 /* host */, double *rho_min /* host */,
+                           cudaStream_t stream);
+
+/* ------------------------------------------------------------ step graph */
+
+/* Small helpers that build one refinement step as a CUDA graph whose backward
+ * branch is a conditional IF node set on the device by skipgs_gate_decide.
+ * Capture is stream capture: between gs_graph_begin and gs_graph_end only gs_*
+ * calls (and other capturable work) may be issued on `stream`. */
+typedef struct gs_graph_s *gs_graph;
+
+gs_status gs_graph_begin(cudaStream_t stream);
+/* Creates a conditional handle in the graph being captured on `stream`
+ * (default value 0). */
+gs_status gs_graph_cond_create(cudaStream_t stream, cudaGraphConditionalHandle *out /* host */);
+/* Adds an IF node on `cond` after the work captured so far on `stream`, and
+ * starts capturing `body_stream` into its body. */
+gs_status gs_graph_if_begin(cudaStream_t stream, cudaGraphConditionalHandle cond, cudaStream_t body_stream);
+/* Ends the body capture; later work on `stream` runs after the IF node. */
+gs_status gs_graph_if_end(cudaStream_t stream, cudaStream_t body_stream);
+gs_status gs_graph_end(cudaStream_t stream, gs_graph *out /* host */);
+gs_status gs_graph_launch(gs_graph graph, cudaStream_t stream);
+gs_status gs_graph_destroy(gs_graph graph);
+
+/* Device-side view selection for graph replay: view_ids[k] =
+ * seq[(*iter * n + k) mod seq_len] for k < n, then *iter += 1 (int64, device).
+ * If pose_src and slots are given, slots[k].R and slots[k].t are set to the
+ * pose of pose_src[view_ids[k]] (intrinsics, size and offsets of the slot are
+ * kept), so a captured step renders the selected views. */
+gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
+                          const gs_camera *pose_src, gs_camera *slots, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H */

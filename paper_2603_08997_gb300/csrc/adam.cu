@@ -1,0 +1,100 @@
+// gs_adam_step: Adam (Kingma & Ba, bias-corrected) over the flat parameter
+// buffer, the optimizer step Algorithm 1 runs only when g = 1.
+// HBM-bound: 16 B read (p, g, m, v) and 12-16 B written per scalar.
+#include "common.cuh"
+
+using namespace gsr;
+
+namespace {
+
+struct Groups {
+    int64_t o_scales, o_quats, o_opac, o_sh, total;
+    int K3;
+};
+
+__device__ __forceinline__ int group_of(int64_t e, const Groups &G) {
+    if (e < G.o_scales) return 0;
+    if (e < G.o_quats) return 1;
+    if (e < G.o_opac) return 2;
+    if (e < G.o_sh) return 3;
+    return ((e - G.o_sh) % G.K3) < 3 ? 4 : 5;
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
+                                                   float *__restrict__ v, Groups G, gs_adam_config cfg,
+                                                   const int32_t *do_step, const int64_t *step, int zero_grad) {
+    if (do_step && *do_step == 0) return;
+    __shared__ float s_lr[6];
+    __shared__ float s_ibc2;
+    if (threadIdx.x == 0) {
+        const double t = (double)(*step + 1);
+        const double bc1 = 1.0 - pow((double)cfg.beta1, t);
+        const double bc2 = 1.0 - pow((double)cfg.beta2, t);
+        for (int k = 0; k < 6; ++k) s_lr[k] = (float)((double)cfg.lr[k] / bc1);
+        s_ibc2 = (float)(1.0 / sqrt(bc2));
+    }
+    __syncthreads();
+    const float b1 = cfg.beta1, b2 = cfg.beta2, eps = cfg.eps;
+    const float ib1 = 1.f - b1, ib2 = 1.f - b2, ibc2 = s_ibc2;
+    const int64_t nvec = G.total / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nvec; c += stride) {
+        float4 pp = reinterpret_cast<float4 *>(p)[c];
+        const float4 gg = reinterpret_cast<const float4 *>(g)[c];
+        float4 mm = reinterpret_cast<float4 *>(m)[c];
+        float4 vv = reinterpret_cast<float4 *>(v)[c];
+        float *pe = &pp.x, *me = &mm.x, *ve = &vv.x;
+        const float *ge = &gg.x;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float lr = s_lr[group_of(4 * c + u, G)];
+            me[u] = b1 * me[u] + ib1 * ge[u];
+            ve[u] = b2 * ve[u] + ib2 * ge[u] * ge[u];
+            pe[u] -= lr * me[u] / (sqrtf(ve[u]) * ibc2 + eps);
+        }
+        reinterpret_cast<float4 *>(p)[c] = pp;
+        reinterpret_cast<float4 *>(m)[c] = mm;
+        reinterpret_cast<float4 *>(v)[c] = vv;
+        if (zero_grad) reinterpret_cast<float4 *>(g)[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // scalar tail
+    for (int64_t e = 4 * nvec + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < G.total; e += stride) {
+        const float lr = s_lr[group_of(e, G)];
+        const float ge = g[e];
+        const float me = b1 * m[e] + ib1 * ge;
+        const float ve = b2 * v[e] + ib2 * ge * ge;
+        m[e] = me;
+        v[e] = ve;
+        p[e] -= lr * me / (sqrtf(ve) * ibc2 + eps);
+        if (zero_grad) g[e] = 0.f;
+    }
+}
+
+__global__ void adam_count_kernel(const int32_t *do_step, int64_t *step) {
+    if (!do_step || *do_step) *step += 1;
+}
+
+}  // namespace
+
+extern "C" gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t n, int32_t sh_degree,
+                                  const gs_adam_config *cfg, const int32_t *dev_do_step, int64_t *dev_step,
+                                  int32_t zero_grad, cudaStream_t stream) {
+    if (!params || !grads || !m || !v || !cfg || !dev_step || n < 0 || sh_degree < 0 || sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    if (((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) & 15) return GS_ERR_INVALID_ARG;
+    if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
+        return GS_ERR_INVALID_ARG;
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    int64_t o[6];
+    param_offsets(n, sh_degree, o);
+    Groups G{o[1], o[2], o[3], o[4], o[5], 3 * K};
+    if (n > 0) {
+        int64_t blocks = ceil_div(G.total / 4 + 1, 256);
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(params, grads, m, v, G, *cfg, dev_do_step, dev_step, zero_grad);
+        GS_TRY_LAUNCH();
+    }
+    adam_count_kernel<<<1, 1, 0, stream>>>(dev_do_step, dev_step);
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}

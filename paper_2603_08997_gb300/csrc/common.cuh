@@ -1,0 +1,221 @@
+// Internal helpers shared by the sm_103a kernels of libgsr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsr.h"
+
+#define GS_TRY_LAUNCH()                                       \
+    do {                                                      \
+        if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA; \
+    } while (0)
+
+#define GS_TRY(call)                                          \
+    do {                                                      \
+        if ((call) != cudaSuccess) return GS_ERR_CUDA;        \
+    } while (0)
+
+namespace gsr {
+
+constexpr int kRecFloats = 12;   // packed projected record (see gsr.h)
+constexpr int kG2d = 12;         // per-Gaussian 2D gradient slots: dmean(2) dconic(3) dopac(1) drgb(3) pad(3)
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Offsets (floats) of the parameter groups in the flat buffer: means,
+// log_scales, quats, opacity_logit, sh, end.  Each group starts on a 256-byte
+// boundary so every group can be read with 16-byte vector loads.
+__host__ __device__ inline void param_offsets(int64_t n, int sh_degree, int64_t *o) {
+    const int64_t K = (int64_t)(sh_degree + 1) * (sh_degree + 1);
+    auto al = [](int64_t x) { return (x + 63) / 64 * 64; };
+    o[0] = 0;
+    o[1] = al(3 * n);
+    o[2] = al(o[1] + 3 * n);
+    o[3] = al(o[2] + 4 * n);
+    o[4] = al(o[3] + n);
+    o[5] = al(o[4] + 3 * K * n);
+}
+
+// First error wins.
+__device__ inline void set_status(int32_t *st, int32_t code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+// The view a global tile id belongs to (views are few; linear search).
+__device__ inline int view_of_tile(const gs_camera *cams, int n_views, int64_t tile) {
+    int v = 0;
+    while (v + 1 < n_views && cams[v + 1].tile_offset <= tile) ++v;
+    return v;
+}
+
+// Eq. (alpha) at one pixel, evaluated through the conic's Cholesky factor U
+// (Q = U^T U): dp^T Q dp = |U dp|^2 with z0 = u00 dx + u01 dy, z1 = u11 dy.
+// A sum of squares keeps the float32 rounding error near eps * sqrt(cond(Q)).
+// Explicit round-to-nearest intrinsics pin every operation, so the forward and
+// backward kernels obtain bit-identical alphas and contributor sets.
+struct AlphaEval {
+    float alpha, G, dx, dy, z0, z1;
+    bool clamped;
+};
+
+__device__ __forceinline__ AlphaEval eval_alpha(float4 a, float4 b, float px, float py, float alpha_max) {
+    AlphaEval r;
+    r.dx = __fsub_rn(px, a.x);
+    r.dy = __fsub_rn(py, a.y);
+    r.z0 = __fmaf_rn(a.z, r.dx, __fmul_rn(a.w, r.dy));
+    r.z1 = __fmul_rn(b.x, r.dy);
+    const float q = __fmaf_rn(r.z0, r.z0, __fmul_rn(r.z1, r.z1));
+    r.G = __expf(__fmul_rn(-0.5f, q));
+    const float og = __fmul_rn(b.y, r.G);
+    r.clamped = og > alpha_max;
+    r.alpha = r.clamped ? alpha_max : og;
+    return r;
+}
+
+// Real spherical harmonics (Condon-Shortley phase) up to degree 3 at a unit
+// direction (x, y, z), basis order k = l*l + l + m.  Constants are the
+// normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0)
+// folded with the polynomial coefficients of each basis function.
+namespace sh {
+constexpr float c0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float c1 = 0.48860251190291992f;   // sqrt(3) / (2 sqrt(pi))
+constexpr float c2a = 1.0925484305920792f;   // sqrt(15) / (2 sqrt(pi))
+constexpr float c2b = 0.31539156525252005f;  // sqrt(5) / (4 sqrt(pi))
+constexpr float c2c = 0.54627421529603959f;  // sqrt(15) / (4 sqrt(pi))
+constexpr float c3a = 0.59004358992664352f;  // sqrt(35/2) / (4 sqrt(pi))
+constexpr float c3b = 2.8906114426405538f;   // sqrt(105) / (2 sqrt(pi))
+constexpr float c3c = 0.45704579946446572f;  // sqrt(21/2) / (4 sqrt(pi))
+constexpr float c3d = 0.37317633259011546f;  // sqrt(7) / (4 sqrt(pi))
+constexpr float c3e = 1.4453057213202769f;   // sqrt(105) / (4 sqrt(pi))
+}  // namespace sh
+
+// Y[0..K) at direction (x,y,z).
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y) {
+    Y[0] = sh::c0;
+    if (deg < 1) return;
+    Y[1] = -sh::c1 * y;
+    Y[2] = sh::c1 * z;
+    Y[3] = -sh::c1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = sh::c2a * x * y;
+    Y[5] = -sh::c2a * y * z;
+    Y[6] = sh::c2b * (2.f * zz - xx - yy);
+    Y[7] = -sh::c2a * x * z;
+    Y[8] = sh::c2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -sh::c3a * y * (3.f * xx - yy);
+    Y[10] = sh::c3b * x * y * z;
+    Y[11] = -sh::c3c * y * (4.f * zz - xx - yy);
+    Y[12] = sh::c3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -sh::c3c * x * (4.f * zz - xx - yy);
+    Y[14] = sh::c3e * z * (xx - yy);
+    Y[15] = -sh::c3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of each basis polynomial above with respect to (x, y, z), taken as
+// free variables (the caller projects onto the sphere's tangent plane).
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float (*dY)[3]) {
+    dY[0][0] = dY[0][1] = dY[0][2] = 0.f;
+    if (deg < 1) return;
+    dY[1][0] = 0.f; dY[1][1] = -sh::c1; dY[1][2] = 0.f;
+    dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = sh::c1;
+    dY[3][0] = -sh::c1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    dY[4][0] = sh::c2a * y; dY[4][1] = sh::c2a * x; dY[4][2] = 0.f;
+    dY[5][0] = 0.f; dY[5][1] = -sh::c2a * z; dY[5][2] = -sh::c2a * y;
+    dY[6][0] = -2.f * sh::c2b * x; dY[6][1] = -2.f * sh::c2b * y; dY[6][2] = 4.f * sh::c2b * z;
+    dY[7][0] = -sh::c2a * z; dY[7][1] = 0.f; dY[7][2] = -sh::c2a * x;
+    dY[8][0] = 2.f * sh::c2c * x; dY[8][1] = -2.f * sh::c2c * y; dY[8][2] = 0.f;
+    if (deg < 3) return;
+    dY[9][0] = -sh::c3a * 6.f * x * y; dY[9][1] = -sh::c3a * (3.f * xx - 3.f * yy); dY[9][2] = 0.f;
+    dY[10][0] = sh::c3b * y * z; dY[10][1] = sh::c3b * x * z; dY[10][2] = sh::c3b * x * y;
+    dY[11][0] = sh::c3c * 2.f * x * y; dY[11][1] = -sh::c3c * (4.f * zz - xx - 3.f * yy); dY[11][2] = -sh::c3c * 8.f * y * z;
+    dY[12][0] = -sh::c3d * 6.f * x * z; dY[12][1] = -sh::c3d * 6.f * y * z; dY[12][2] = sh::c3d * (6.f * zz - 3.f * xx - 3.f * yy);
+    dY[13][0] = -sh::c3c * (4.f * zz - 3.f * xx - yy); dY[13][1] = sh::c3c * 2.f * x * y; dY[13][2] = -sh::c3c * 8.f * x * z;
+    dY[14][0] = sh::c3e * 2.f * x * z; dY[14][1] = -sh::c3e * 2.f * y * z; dY[14][2] = sh::c3e * (xx - yy);
+    dY[15][0] = -sh::c3a * (3.f * xx - 3.f * yy); dY[15][1] = sh::c3a * 6.f * x * y; dY[15][2] = 0.f;
+}
+
+// a*b - c*d with one rounding error (Kahan's FMA-based difference of products).
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return f + e;
+}
+
+// Forward projection state of one Gaussian for one camera (Eq. cov, Eq. proj).
+struct ProjState {
+    bool culled;
+    float qn[4], qinv;      // normalised quaternion, 1/|q|
+    float R[9];             // rotation of the Gaussian
+    float s[3];             // standard deviations
+    float p[3];             // camera-space centre
+    int clamp_x, clamp_y;   // J built from x/z, y/z clamped (+1/-1 side) or not (0)
+    float txz, tyz;         // the (clamped) x/z, y/z used in J
+    float T[6];             // J W (2x3)
+    float M[6];             // J W R S (2x3); Sigma2D = M M^T + lowpass I
+    float s00, s01, s11;    // Sigma2D
+    float det;
+    float mean2d[2];
+    float o;
+};
+
+// Camera centre -R^T t.
+__device__ __forceinline__ void cam_center(const gs_camera &c, float *cp) {
+    for (int i = 0; i < 3; ++i) cp[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
+}
+
+__device__ __forceinline__ void project_state(const float *mu, const float *ls, float4 q, float logit,
+                                              const gs_camera &c, float lowpass, ProjState &g) {
+    g.culled = false;
+    for (int i = 0; i < 3; ++i) g.p[i] = c.R[3 * i] * mu[0] + c.R[3 * i + 1] * mu[1] + c.R[3 * i + 2] * mu[2] + c.t[i];
+    const float x = g.p[0], y = g.p[1], z = g.p[2];
+    if (!(z > c.znear)) { g.culled = true; return; }
+    const float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    g.qinv = 1.0f / sqrtf(qq);
+    const float w = q.x * g.qinv, qx = q.y * g.qinv, qy = q.z * g.qinv, qz = q.w * g.qinv;
+    g.qn[0] = w; g.qn[1] = qx; g.qn[2] = qy; g.qn[3] = qz;
+    g.R[0] = 1.f - 2.f * (qy * qy + qz * qz); g.R[1] = 2.f * (qx * qy - w * qz); g.R[2] = 2.f * (qx * qz + w * qy);
+    g.R[3] = 2.f * (qx * qy + w * qz); g.R[4] = 1.f - 2.f * (qx * qx + qz * qz); g.R[5] = 2.f * (qy * qz - w * qx);
+    g.R[6] = 2.f * (qx * qz - w * qy); g.R[7] = 2.f * (qy * qz + w * qx); g.R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    for (int i = 0; i < 3; ++i) g.s[i] = expf(ls[i]);
+    const float iz = 1.0f / z;
+    const float limx = 1.3f * (0.5f * (float)c.width) / c.fx;
+    const float limy = 1.3f * (0.5f * (float)c.height) / c.fy;
+    const float xz = x * iz, yz = y * iz;
+    g.clamp_x = xz > limx ? 1 : (xz < -limx ? -1 : 0);
+    g.clamp_y = yz > limy ? 1 : (yz < -limy ? -1 : 0);
+    g.txz = g.clamp_x ? (float)g.clamp_x * limx : xz;
+    g.tyz = g.clamp_y ? (float)g.clamp_y * limy : yz;
+    // J = [[fx/z, 0, -fx txz/z], [0, fy/z, -fy tyz/z]]; T = J W
+    const float j00 = c.fx * iz, j02 = -c.fx * g.txz * iz, j11 = c.fy * iz, j12 = -c.fy * g.tyz * iz;
+    for (int k = 0; k < 3; ++k) {
+        g.T[k] = j00 * c.R[k] + j02 * c.R[6 + k];
+        g.T[3 + k] = j11 * c.R[3 + k] + j12 * c.R[6 + k];
+    }
+    // M = T R S
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k)
+            g.M[3 * r + k] = (g.T[3 * r] * g.R[k] + g.T[3 * r + 1] * g.R[3 + k] + g.T[3 * r + 2] * g.R[6 + k]) * g.s[k];
+    const float *m0 = g.M, *m1 = g.M + 3;
+    const float n0 = m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2];
+    const float n1 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+    g.s00 = n0 + lowpass;
+    g.s11 = n1 + lowpass;
+    g.s01 = m0[0] * m1[0] + m0[1] * m1[1] + m0[2] * m1[2];
+    // det(M M^T + l I) = |m0 x m1|^2 + l (|m0|^2 + |m1|^2) + l^2 (Cauchy-Binet), all terms >= 0
+    const float cx_ = diff_prod(m0[1], m1[2], m0[2], m1[1]);
+    const float cy_ = diff_prod(m0[2], m1[0], m0[0], m1[2]);
+    const float cz_ = diff_prod(m0[0], m1[1], m0[1], m1[0]);
+    g.det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + lowpass * (n0 + n1) + lowpass * lowpass;
+    if (!(g.det > 0.f) || !(g.s11 > 0.f)) { g.culled = true; return; }
+    g.mean2d[0] = c.fx * xz + c.cx;
+    g.mean2d[1] = c.fy * yz + c.cy;
+    g.o = 1.0f / (1.0f + expf(-logit));
+}
+
+}  // namespace gsr

@@ -1,0 +1,124 @@
+// Step-graph helpers: one refinement step captured as a CUDA graph whose
+// backward branch (Algorithm 1, "if g = 1: backward; optimizer step") is an IF
+// conditional node that skipgs_gate_decide sets on the device.  Built with
+// stream capture plus cudaStreamBeginCaptureToGraph for the IF body.
+#include <new>
+
+#include "common.cuh"
+
+using namespace gsr;
+
+struct gs_graph_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+__global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t *iter, int n, int32_t *view_ids,
+                                    const gs_camera *pose_src, gs_camera *slots) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t it = *iter;
+    for (int k = 0; k < n; ++k) {
+        const int64_t idx = (it * n + k) % seq_len;
+        const int32_t vid = seq[idx];
+        view_ids[k] = vid;
+        if (pose_src && slots) {
+            for (int a = 0; a < 9; ++a) slots[k].R[a] = pose_src[vid].R[a];
+            for (int a = 0; a < 3; ++a) slots[k].t[a] = pose_src[vid].t[a];
+        }
+    }
+    *iter = it + 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_graph_begin(cudaStream_t stream) {
+    if (!stream) return GS_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+    GS_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+    return GS_OK;
+}
+
+gs_status gs_graph_cond_create(cudaStream_t stream, cudaGraphConditionalHandle *out) {
+    if (!stream || !out) return GS_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus status;
+    cudaGraph_t graph;
+    GS_TRY(cudaStreamGetCaptureInfo(stream, &status, nullptr, &graph, nullptr, nullptr, nullptr));
+    if (status != cudaStreamCaptureStatusActive) return GS_ERR_INVALID_ARG;
+    GS_TRY(cudaGraphConditionalHandleCreate(out, graph, 0, cudaGraphCondAssignDefault));
+    return GS_OK;
+}
+
+gs_status gs_graph_if_begin(cudaStream_t stream, cudaGraphConditionalHandle cond, cudaStream_t body_stream) {
+    if (!stream || !body_stream || stream == body_stream) return GS_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus status;
+    cudaGraph_t graph;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    GS_TRY(cudaStreamGetCaptureInfo(stream, &status, nullptr, &graph, &deps, &edata, &ndeps));
+    if (status != cudaStreamCaptureStatusActive) return GS_ERR_INVALID_ARG;
+    cudaGraphNodeParams params = {};
+    params.type = cudaGraphNodeTypeConditional;
+    params.conditional.handle = cond;
+    params.conditional.type = cudaGraphCondTypeIf;
+    params.conditional.size = 1;
+    cudaGraphNode_t node;
+    GS_TRY(cudaGraphAddNode(&node, graph, deps, edata, ndeps, &params));
+    GS_TRY(cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = params.conditional.phGraph_out[0];
+    GS_TRY(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    return GS_OK;
+}
+
+gs_status gs_graph_if_end(cudaStream_t stream, cudaStream_t body_stream) {
+    if (!stream || !body_stream) return GS_ERR_INVALID_ARG;
+    cudaGraph_t body;
+    GS_TRY(cudaStreamEndCapture(body_stream, &body));
+    return GS_OK;
+}
+
+gs_status gs_graph_end(cudaStream_t stream, gs_graph *out) {
+    if (!stream || !out) return GS_ERR_INVALID_ARG;
+    cudaGraph_t graph;
+    GS_TRY(cudaStreamEndCapture(stream, &graph));
+    cudaGraphExec_t exec;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return GS_ERR_CUDA;
+    }
+    gs_graph_s *g = new (std::nothrow) gs_graph_s{graph, exec};
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return GS_ERR_CUDA;
+    }
+    *out = g;
+    return GS_OK;
+}
+
+gs_status gs_graph_launch(gs_graph graph, cudaStream_t stream) {
+    if (!graph) return GS_ERR_INVALID_ARG;
+    GS_TRY(cudaGraphLaunch(graph->exec, stream));
+    return GS_OK;
+}
+
+gs_status gs_graph_destroy(gs_graph graph) {
+    if (!graph) return GS_ERR_INVALID_ARG;
+    cudaGraphExecDestroy(graph->exec);
+    cudaGraphDestroy(graph->graph);
+    delete graph;
+    return GS_OK;
+}
+
+gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
+                          const gs_camera *pose_src, gs_camera *slots, cudaStream_t stream) {
+    if (!seq || seq_len <= 0 || !iter || n <= 0 || !view_ids) return GS_ERR_INVALID_ARG;
+    select_views_kernel<<<1, 32, 0, stream>>>(seq, seq_len, iter, n, view_ids, pose_src, slots);
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,322 @@
+// gs_loss / gs_loss_backward: Eq. (loss), L = (1 - lambda) L1 + lambda (1 - SSIM).
+//
+// SSIM uses an 11x11 Gaussian window (sigma 1.5, separable), zero padding,
+// C1 = 0.01^2, C2 = 0.03^2.  One CTA computes a 32x16 output tile: it stages
+// the tile plus a 5-pixel halo of image and target in shared memory, filters
+// rows then columns, and evaluates the SSIM map.  Window sums are taken of
+// values shifted by the tile's centre value (exact for a window whose weights
+// sum to 1, padded pixels included), which keeps the variance terms
+// E[x^2] - E[x]^2 well conditioned in float32.
+//
+// The forward kernel also stores, per pixel and channel, the three partial
+// derivatives of the SSIM map that the gradient needs:
+//   P1 = dm/dmu_x - 2 mu_x dm/dsxx - mu_y dm/dsxy,  P2 = dm/dsxx,  P3 = dm/dsxy,
+// so that d mean(m)/dx = (F(P1) + 2 x F(P2) + y F(P3)) / n with F the same
+// window filter.  The gradient kernel only runs when a backward pass does
+// (in the refinement step it sits inside the gate's conditional branch).
+// Per-view sums are reduced in a fixed order, so the loss is deterministic.
+#include "common.cuh"
+
+using namespace gsr;
+
+namespace {
+
+constexpr int LTW = 32, LTH = 16, HALO = 5, LW = LTW + 2 * HALO, LH = LTH + 2 * HALO;
+constexpr float SSIM_C1 = 0.0001f;  // (0.01)^2
+constexpr float SSIM_C2 = 0.0009f;  // (0.03)^2
+
+// Normalised 1D Gaussian window, sigma 1.5: w[t] = exp(-(t-5)^2 / 4.5) / sum,
+// passed by value (kernel parameters), so no upload precedes a graph capture.
+struct Win {
+    float w[11];
+};
+
+Win window_host() {
+    Win r;
+    double s = 0.0, g[11];
+    for (int t = 0; t < 11; ++t) {
+        const double d = t - 5.0;
+        g[t] = exp(-d * d / 4.5);
+        s += g[t];
+    }
+    for (int t = 0; t < 11; ++t) r.w[t] = (float)(g[t] / s);
+    return r;
+}
+
+__device__ __forceinline__ const float *target_base(const float *target, const int64_t *target_offsets,
+                                                    const int32_t *view_ids, int v, int64_t pix_offset) {
+    if (target_offsets && view_ids) return target + target_offsets[view_ids[v]];
+    return target + 3 * pix_offset;
+}
+
+__global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__ img, const float *__restrict__ target,
+                                                       const int64_t *__restrict__ target_offsets,
+                                                       const int32_t *__restrict__ view_ids, int v,
+                                                       int64_t pix_offset, int W, int H, Win win,
+                                                       float *__restrict__ dmaps, double2 *__restrict__ partials) {
+    __shared__ float sx[LH][LW];
+    __shared__ float sy[LH][LW];
+    __shared__ float hs[5][LH][LTW];
+    __shared__ double red[2][8];
+    const float *tgt = target_base(target, target_offsets, view_ids, v, pix_offset);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int bx0 = blockIdx.x * LTW, by0 = blockIdx.y * LTH;
+    const int64_t hw = (int64_t)W * H;
+    const int ccx = min(bx0 + LTW / 2, W - 1), ccy = min(by0 + LTH / 2, H - 1);
+    float ssim_acc = 0.f, l1_acc = 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+        const float *X = img + ch * hw, *Yp = tgt + ch * hw;
+        const float shx = X[(int64_t)ccy * W + ccx], shy = Yp[(int64_t)ccy * W + ccx];
+        for (int idx = tid; idx < LH * LW; idx += 256) {
+            const int r = idx / LW, c = idx % LW;
+            const int gx = bx0 + c - HALO, gy = by0 + r - HALO;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const int64_t p = (int64_t)gy * W + gx;
+            sx[r][c] = (in ? X[p] : 0.f) - shx;
+            sy[r][c] = (in ? Yp[p] : 0.f) - shy;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < LH * LTW; idx += 256) {
+            const int r = idx / LTW, c = idx % LTW;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+            for (int t = 0; t < 11; ++t) {
+                const float w = win.w[t], xv = sx[r][c + t], yv = sy[r][c + t];
+                a0 += w * xv;
+                a1 += w * yv;
+                a2 += w * xv * xv;
+                a3 += w * yv * yv;
+                a4 += w * xv * yv;
+            }
+            hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2; hs[3][r][c] = a3; hs[4][r][c] = a4;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int r = threadIdx.y + 8 * half, c = threadIdx.x;
+            const int gx = bx0 + c, gy = by0 + r;
+            if (gx < W && gy < H) {
+                float m0 = 0.f, m1 = 0.f, e2 = 0.f, f2 = 0.f, exy = 0.f;
+#pragma unroll
+                for (int t = 0; t < 11; ++t) {
+                    const float w = win.w[t];
+                    m0 += w * hs[0][r + t][c];
+                    m1 += w * hs[1][r + t][c];
+                    e2 += w * hs[2][r + t][c];
+                    f2 += w * hs[3][r + t][c];
+                    exy += w * hs[4][r + t][c];
+                }
+                const float sxx = e2 - m0 * m0, syy = f2 - m1 * m1, sxy = exy - m0 * m1;
+                const float mx = m0 + shx, my = m1 + shy;
+                const float A1 = 2.f * mx * my + SSIM_C1, A2 = 2.f * sxy + SSIM_C2;
+                const float B1 = mx * mx + my * my + SSIM_C1, B2 = sxx + syy + SSIM_C2;
+                const float iD = 1.f / (B1 * B2);
+                const float m = A1 * A2 * iD;
+                const float P2 = -m / B2;
+                const float P3 = 2.f * A1 * iD;
+                const float dmu = (2.f * my * A2 - 2.f * mx * m * B2) * iD;
+                const float P1 = dmu - 2.f * mx * P2 - my * P3;
+                const int64_t p = (int64_t)gy * W + gx;
+                dmaps[(0 * 3 + ch) * hw + p] = P1;
+                dmaps[(1 * 3 + ch) * hw + p] = P2;
+                dmaps[(2 * 3 + ch) * hw + p] = P3;
+                ssim_acc += m;
+                l1_acc += fabsf(X[p] - Yp[p]);
+            }
+        }
+        __syncthreads();
+    }
+    double s0 = ssim_acc, s1 = l1_acc;
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    }
+    if (threadIdx.x == 0) { red[0][threadIdx.y] = s0; red[1][threadIdx.y] = s1; }
+    __syncthreads();
+    if (tid == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < 8; ++w) { t0 += red[0][w]; t1 += red[1][w]; }
+        partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(t0, t1);
+    }
+}
+
+// Per view: fixed-order sum of the block partials -> loss.
+__global__ void loss_reduce_kernel(const double2 *__restrict__ partials, int nblocks, double n, float lambda,
+                                   float *__restrict__ loss_out) {
+    __shared__ double s0[256], s1[256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 256) {
+        const double2 p = partials[i];
+        a += p.x;
+        b += p.y;
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s0[threadIdx.x] += s0[threadIdx.x + off];
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double ssim = s0[0] / n, l1 = s1[0] / n;
+        *loss_out = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
+    }
+}
+
+__global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__ img, const float *__restrict__ target,
+                                                       const int64_t *__restrict__ target_offsets,
+                                                       const int32_t *__restrict__ view_ids, int v,
+                                                       int64_t pix_offset, int W, int H, float lambda, Win win,
+                                                       const float *__restrict__ dmaps, float *__restrict__ grad) {
+    __shared__ float sp[3][LH][LW];
+    __shared__ float hs[3][LH][LTW];
+    const float *tgt = target_base(target, target_offsets, view_ids, v, pix_offset);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int bx0 = blockIdx.x * LTW, by0 = blockIdx.y * LTH;
+    const int64_t hw = (int64_t)W * H;
+    const float inv_n = 1.f / (3.f * (float)hw);
+    for (int ch = 0; ch < 3; ++ch) {
+        for (int idx = tid; idx < LH * LW; idx += 256) {
+            const int r = idx / LW, c = idx % LW;
+            const int gx = bx0 + c - HALO, gy = by0 + r - HALO;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const int64_t p = (int64_t)gy * W + gx;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sp[q][r][c] = in ? dmaps[(q * 3 + ch) * hw + p] : 0.f;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < LH * LTW; idx += 256) {
+            const int r = idx / LTW, c = idx % LTW;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int t = 0; t < 11; ++t) {
+                const float w = win.w[t];
+                a0 += w * sp[0][r][c + t];
+                a1 += w * sp[1][r][c + t];
+                a2 += w * sp[2][r][c + t];
+            }
+            hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int r = threadIdx.y + 8 * half, c = threadIdx.x;
+            const int gx = bx0 + c, gy = by0 + r;
+            if (gx < W && gy < H) {
+                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+#pragma unroll
+                for (int t = 0; t < 11; ++t) {
+                    const float w = win.w[t];
+                    f0 += w * hs[0][r + t][c];
+                    f1 += w * hs[1][r + t][c];
+                    f2 += w * hs[2][r + t][c];
+                }
+                const int64_t p = (int64_t)gy * W + gx;
+                const float xv = img[ch * hw + p], yv = tgt[ch * hw + p];
+                const float dssim = (f0 + 2.f * xv * f1 + yv * f2) * inv_n;
+                const float diff = xv - yv;
+                const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                grad[ch * hw + p] = (1.f - lambda) * sgn * inv_n - lambda * dssim;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct LossLayout {
+    size_t dmaps_off, partials_off, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool loss_layout(const gs_camera *cams, int n_views, LossLayout &L, int64_t *block_off /* n_views+1, nullable */) {
+    int64_t pixels = 0, blocks = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (cams[v].width <= 0 || cams[v].height <= 0) return false;
+        if (block_off) block_off[v] = blocks;
+        pixels = pixels > cams[v].pix_offset + (int64_t)cams[v].width * cams[v].height
+                     ? pixels
+                     : cams[v].pix_offset + (int64_t)cams[v].width * cams[v].height;
+        blocks += ceil_div(cams[v].width, LTW) * ceil_div(cams[v].height, LTH);
+    }
+    if (block_off) block_off[n_views] = blocks;
+    L.dmaps_off = 0;
+    L.partials_off = align256(sizeof(float) * 9 * (size_t)pixels);
+    L.total = L.partials_off + align256(sizeof(double2) * (size_t)blocks);
+    return true;
+}
+
+gs_status check_loss_args(const float *image, const float *target, const gs_camera *cams_host, int32_t n_views,
+                          void *workspace, size_t workspace_bytes, LossLayout &L) {
+    if (!image || !target || !cams_host || n_views <= 0) return GS_ERR_INVALID_ARG;
+    if (!loss_layout(cams_host, n_views, L, nullptr)) return GS_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255)) return GS_ERR_WORKSPACE;
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gs_loss_workspace_size(const gs_camera *cams_host, int32_t n_views) {
+    if (!cams_host || n_views <= 0) return 0;
+    LossLayout L;
+    if (!loss_layout(cams_host, n_views, L, nullptr)) return 0;
+    return L.total;
+}
+
+gs_status gs_loss(const float *image, const float *target, const int64_t *target_offsets, const gs_camera *cams_host,
+                  const int32_t *view_ids, int32_t n_views, float lambda_ssim, void *workspace,
+                  size_t workspace_bytes, float *loss_per_view, float *dL_dimage, cudaStream_t stream) {
+    LossLayout L;
+    gs_status st = check_loss_args(image, target, cams_host, n_views, workspace, workspace_bytes, L);
+    if (st != GS_OK) return st;
+    if (!loss_per_view) return GS_ERR_INVALID_ARG;
+    if ((target_offsets == nullptr) != (view_ids == nullptr)) return GS_ERR_INVALID_ARG;
+    const Win win = window_host();
+    float *dmaps = reinterpret_cast<float *>((char *)workspace + L.dmaps_off);
+    double2 *partials = reinterpret_cast<double2 *>((char *)workspace + L.partials_off);
+    int64_t boff = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera &c = cams_host[v];
+        const dim3 grid((unsigned)ceil_div(c.width, LTW), (unsigned)ceil_div(c.height, LTH));
+        ssim_fwd_kernel<<<grid, dim3(32, 8), 0, stream>>>(image + 3 * c.pix_offset, target, target_offsets, view_ids, v,
+                                                          c.pix_offset, c.width, c.height, win,
+                                                          dmaps + 9 * c.pix_offset, partials + boff);
+        GS_TRY_LAUNCH();
+        loss_reduce_kernel<<<1, 256, 0, stream>>>(partials + boff, (int)(grid.x * grid.y),
+                                                  3.0 * (double)c.width * c.height, lambda_ssim, loss_per_view + v);
+        GS_TRY_LAUNCH();
+        boff += (int64_t)grid.x * grid.y;
+    }
+    if (dL_dimage)
+        return gs_loss_backward(image, target, target_offsets, cams_host, view_ids, n_views, lambda_ssim, workspace,
+                                workspace_bytes, dL_dimage, stream);
+    return GS_OK;
+}
+
+gs_status gs_loss_backward(const float *image, const float *target, const int64_t *target_offsets,
+                           const gs_camera *cams_host, const int32_t *view_ids, int32_t n_views, float lambda_ssim,
+                           void *workspace, size_t workspace_bytes, float *dL_dimage, cudaStream_t stream) {
+    LossLayout L;
+    gs_status st = check_loss_args(image, target, cams_host, n_views, workspace, workspace_bytes, L);
+    if (st != GS_OK) return st;
+    if (!dL_dimage) return GS_ERR_INVALID_ARG;
+    if ((target_offsets == nullptr) != (view_ids == nullptr)) return GS_ERR_INVALID_ARG;
+    const Win win = window_host();
+    const float *dmaps = reinterpret_cast<const float *>((char *)workspace + L.dmaps_off);
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera &c = cams_host[v];
+        const dim3 grid((unsigned)ceil_div(c.width, LTW), (unsigned)ceil_div(c.height, LTH));
+        ssim_bwd_kernel<<<grid, dim3(32, 8), 0, stream>>>(image + 3 * c.pix_offset, target, target_offsets, view_ids, v,
+                                                          c.pix_offset, c.width, c.height, lambda_ssim, win,
+                                                          dmaps + 9 * c.pix_offset, dL_dimage + 3 * c.pix_offset);
+        GS_TRY_LAUNCH();
+    }
+    return GS_OK;
+}
+
+}  // extern "C"

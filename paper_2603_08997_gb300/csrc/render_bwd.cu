@@ -1,0 +1,431 @@
+// gs_render_bwd: analytic adjoint of gs_render_fwd and gs_project.
+//
+// Raster adjoint (one CTA per tile, one thread per pixel).  With
+// A_k = sum_{j>k} c_j a_j T_j + T_end bg (the colour behind contributor k),
+// Eq. (blend) gives dC/dc_k = a_k T_k and dC/da_k = c_k T_k - A_k / (1 - a_k).
+// Batches are visited last to first and each pixel walks back from its last
+// contributor, so A_k is a plain suffix sum.  T is rebuilt by
+// T_k = T_{k+1} / (1 - a_k), re-anchored at every batch boundary on the
+// transmittance checkpoint the forward pass stored, so division error never
+// spans more than one batch.  The alphas come from the same bit-exact
+// evaluation as the forward pass, so the contributor set is identical.
+//
+// Per pair the 9 gradients (mean2D 2, conic 3, opacity 1, colour 3) are
+// reduced across the warp with a halving shuffle tree (12 shuffles for 9
+// values), summed per Gaussian in shared memory, and added once per
+// (Gaussian, tile) to a per-view buffer with float4 vector atomics.
+//
+// Projection adjoint: one thread per Gaussian chains those 2D gradients
+// through Eq. (proj), Eq. (cov), the SH colour and the sigmoid to the
+// parameters, summing the views.
+#include "common.cuh"
+
+using namespace gsr;
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Reduces v[0..9) over the warp.  On return the even lane L with valid index
+// `idx` holds the warp total of v[idx]; other lanes get idx = -1.
+__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane, int &idx) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+    float a[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float lo = v[i];
+        const float hi = (5 + i < 9) ? v[5 + i] : 0.f;
+        a[i] = (h16 ? hi : lo) + __shfl_xor_sync(FULL, h16 ? lo : hi, 16);
+    }
+    float b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = a[i];
+        const float hi = (3 + i < 5) ? a[3 + i] : 0.f;
+        b[i] = (h8 ? hi : lo) + __shfl_xor_sync(FULL, h8 ? lo : hi, 8);
+    }
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float lo = b[i];
+        const float hi = (2 + i < 3) ? b[2 + i] : 0.f;
+        c[i] = (h4 ? hi : lo) + __shfl_xor_sync(FULL, h4 ? lo : hi, 4);
+    }
+    float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(FULL, h2 ? c[0] : c[1], 2);
+    d += __shfl_xor_sync(FULL, d, 1);
+    const int jb = (h4 ? 2 : 0) + (h2 ? 1 : 0);
+    const int ja = (h8 ? 3 : 0) + jb;
+    const int j = (h16 ? 5 : 0) + ja;
+    idx = ((lane & 1) == 0 && jb < 3 && ja < 5 && j < 9) ? j : -1;
+    return d;
+}
+
+template <int TILE, int BATCH>
+__global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
+    const float4 *__restrict__ rec, int64_t n, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
+    const gs_camera *__restrict__ cams, int n_views, gs_raster_config cfg, const float *__restrict__ T_final,
+    const int32_t *__restrict__ n_last, const float *__restrict__ ckpt, int64_t ckpt_slots,
+    const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d) {
+    constexpr int NT = TILE * TILE;
+    __shared__ float4 s_a[BATCH];
+    __shared__ float4 s_b[BATCH];
+    __shared__ float s_c[BATCH];
+    __shared__ uint32_t s_g[BATCH];
+    __shared__ float s_acc[BATCH][9];
+    __shared__ int s_max;
+    const int64_t tile = blockIdx.x;
+    const int v = view_of_tile(cams, n_views, tile);
+    if (view_gate && !view_gate[v]) return;
+    const gs_camera &cam = cams[v];
+    const int tiles_x = (cam.width + TILE - 1) / TILE;
+    const int64_t lt = tile - cam.tile_offset;
+    const int tx = (int)(lt % tiles_x), ty = (int)(lt / tiles_x);
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int x = tx * TILE + lx, y = ty * TILE + ly;
+    const bool inside = x < cam.width && y < cam.height;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int lane = threadIdx.x & 31;
+    const uint2 rg = ranges[tile];
+    const int64_t slot0 = (int64_t)(rg.x / BATCH) + tile;
+    const float4 *recv = rec + (int64_t)v * n * 3;
+    const float amax = cfg.alpha_max, amin = cfg.alpha_min;
+
+    int my_last = 0;
+    float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, T_end = 0.f;
+    if (inside) {
+        const int64_t hw = (int64_t)cam.width * cam.height;
+        const int64_t pix = (int64_t)y * cam.width + x;
+        my_last = n_last[cam.pix_offset + pix];
+        T_end = T_final[cam.pix_offset + pix];
+        const float *g = dL_dimage + 3 * cam.pix_offset;
+        dC0 = g[pix];
+        dC1 = g[hw + pix];
+        dC2 = g[2 * hw + pix];
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    if (my_last > 0) atomicMax(&s_max, my_last);
+    __syncthreads();
+    const int max_last = s_max;
+    float A0 = T_end * cfg.bg[0], A1 = T_end * cfg.bg[1], A2 = T_end * cfg.bg[2];
+
+    for (int b = (max_last + BATCH - 1) / BATCH - 1; b >= 0; --b) {
+        __syncthreads();
+        const int64_t b0 = (int64_t)rg.x + (int64_t)b * BATCH;
+        const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
+        for (int k = threadIdx.x; k < cnt; k += NT) {
+            const uint32_t g = vals[b0 + k];
+            const float4 *r = recv + (int64_t)g * 3;
+            s_a[k] = r[0];
+            s_b[k] = r[1];
+            s_c[k] = r[2].x;
+            s_g[k] = g;
+        }
+        for (int k = threadIdx.x; k < BATCH * 9; k += NT) (&s_acc[0][0])[k] = 0.f;
+        __syncthreads();
+        const int lo = b * BATCH;
+        int jstart = -1;
+        float T = 0.f;
+        if (my_last > lo + cnt) {
+            jstart = cnt - 1;
+            const int64_t slot = slot0 + b + 1;
+            T = slot < ckpt_slots ? ckpt[slot * NT + threadIdx.x] : 0.f;
+        } else if (my_last > lo) {
+            jstart = my_last - 1 - lo;
+            T = T_end;
+        }
+        const int wj = __reduce_max_sync(FULL, jstart);
+        for (int j = wj; j >= 0; --j) {
+            float gv[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) gv[q] = 0.f;
+            bool contrib = false;
+            if (j <= jstart) {
+                const float4 sa = s_a[j], sb = s_b[j];
+                const AlphaEval ae = eval_alpha(sa, sb, px, py, amax);
+                if (ae.alpha >= amin) {
+                    contrib = true;
+                    const float om = __fsub_rn(1.f, ae.alpha);
+                    const float Tk = __fdiv_rn(T, om);
+                    const float wgt = ae.alpha * Tk;
+                    const float c0 = sb.z, c1 = sb.w, c2 = s_c[j];
+                    gv[6] = dC0 * wgt;
+                    gv[7] = dC1 * wgt;
+                    gv[8] = dC2 * wgt;
+                    const float inv = 1.f / om;
+                    const float da = dC0 * (c0 * Tk - A0 * inv) + dC1 * (c1 * Tk - A1 * inv) + dC2 * (c2 * Tk - A2 * inv);
+                    A0 += c0 * wgt;
+                    A1 += c1 * wgt;
+                    A2 += c2 * wgt;
+                    T = Tk;
+                    if (!ae.clamped) {
+                        gv[5] = da * ae.G;                   // dL/d opacity
+                        const float dG = da * sb.y;          // dL/dG
+                        const float gG = dG * ae.G;
+                        gv[0] = gG * sa.z * ae.z0;                       // dL/d mean2D.x = G dG (Q dp)_x
+                        gv[1] = gG * (sa.w * ae.z0 + sb.x * ae.z1);     // dL/d mean2D.y
+                        const float dq = -0.5f * gG;                     // dL/d(dp^T Q dp)
+                        gv[2] = dq * ae.dx * ae.dx;
+                        gv[3] = 2.f * dq * ae.dx * ae.dy;
+                        gv[4] = dq * ae.dy * ae.dy;
+                    }
+                }
+            }
+            if (__any_sync(FULL, contrib)) {
+                int idx;
+                const float tot = warp_reduce9(gv, lane, idx);
+                if (idx >= 0 && tot != 0.f) atomicAdd(&s_acc[j][idx], tot);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += NT) {
+            const float *a = s_acc[k];
+            bool nz = false;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) nz |= a[q] != 0.f;
+            if (!nz) continue;
+            float4 *dst = g2d + ((int64_t)v * n + s_g[k]) * 3;
+            atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
+            atomicAdd(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
+            atomicAdd(&dst[2].x, a[8]);
+        }
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(128) proj_bwd_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
+                                                       const uint8_t *__restrict__ view_gate, gs_raster_config cfg,
+                                                       const float4 *__restrict__ g2d, gs_grads gr, int accumulate) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int64_t n = prm.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mu[3] = {prm.means[3 * i], prm.means[3 * i + 1], prm.means[3 * i + 2]};
+    const float ls[3] = {prm.log_scales[3 * i], prm.log_scales[3 * i + 1], prm.log_scales[3 * i + 2]};
+    const float4 q4 = reinterpret_cast<const float4 *>(prm.quats)[i];
+    const float logit = prm.opacity_logit[i];
+    const float *f = prm.sh + i * (3 * K);
+    float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
+    float df[3 * K];
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) df[k] = 0.f;
+
+    for (int v = 0; v < n_views; ++v) {
+        if (view_gate && !view_gate[v]) continue;
+        const float4 *gp = g2d + ((int64_t)v * n + i) * 3;
+        const float4 ga = gp[0], gb = gp[1];
+        const float gc = gp[2].x;
+        const float gd[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc};
+        bool nz = false;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) nz |= gd[q] != 0.f;
+        if (!nz) continue;
+        const gs_camera &c = cams[v];
+        ProjState g;
+        project_state(mu, ls, q4, logit, c, cfg.lowpass, g);
+        if (g.culled) continue;
+        // opacity = sigmoid(logit)
+        dlogit += gd[5] * g.o * (1.f - g.o);
+        // colour = max(0, sum_k f_k Y_k(d) + 0.5), d = (mu - campos) / |mu - campos|
+        float cp[3];
+        cam_center(c, cp);
+        float dv[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
+        const float inv_n = 1.0f / sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        const float d[3] = {dv[0] * inv_n, dv[1] * inv_n, dv[2] * inv_n};
+        float Y[16], dY[16][3];
+        sh_basis(DEG, d[0], d[1], d[2], Y);
+        sh_basis_grad(DEG, d[0], d[1], d[2], dY);
+        float ddir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float pre = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) pre += f[3 * k + ch] * Y[k];
+            if (!(pre > 0.f)) continue;
+            const float dc = gd[6 + ch];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                df[3 * k + ch] += dc * Y[k];
+                const float fk = f[3 * k + ch] * dc;
+                ddir[0] += fk * dY[k][0];
+                ddir[1] += fk * dY[k][1];
+                ddir[2] += fk * dY[k][2];
+            }
+        }
+        const float dd = ddir[0] * d[0] + ddir[1] * d[1] + ddir[2] * d[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - d[a] * dd) * inv_n;
+        // conic Q = Sigma2D^-1 -> dL/dSigma2D = -Q GQ Q (full symmetric matrices)
+        const float idet = 1.f / g.det;
+        const float Qa = g.s11 * idet, Qb = -g.s01 * idet, Qc = g.s00 * idet;
+        const float Ga = gd[2], Gb = 0.5f * gd[3], Gc = gd[4];
+        // tmp = GQ Q
+        const float t00 = Ga * Qa + Gb * Qb, t01 = Ga * Qb + Gb * Qc;
+        const float t10 = Gb * Qa + Gc * Qb, t11 = Gb * Qb + Gc * Qc;
+        const float S00 = -(Qa * t00 + Qb * t10), S01 = -(Qa * t01 + Qb * t11), S11 = -(Qb * t01 + Qc * t11);
+        // Sigma2D = M M^T + l I -> dL/dM = 2 S M
+        float dM[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dM[k] = 2.f * (S00 * g.M[k] + S01 * g.M[3 + k]);
+            dM[3 + k] = 2.f * (S01 * g.M[k] + S11 * g.M[3 + k]);
+        }
+        // M = T R S: dT = dM (R S)^T, Gp = T^T dM, dR_jk = Gp_jk s_k, ds_k = sum_j Gp_jk R_jk
+        float dT[6];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dT[3 * r + j] = dM[3 * r] * g.R[3 * j] * g.s[0] + dM[3 * r + 1] * g.R[3 * j + 1] * g.s[1] +
+                                dM[3 * r + 2] * g.R[3 * j + 2] * g.s[2];
+        float dR[9];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float gp_ = g.T[j] * dM[k] + g.T[3 + j] * dM[3 + k];
+                dR[3 * j + k] = gp_ * g.s[k];
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float ds = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) ds += (g.T[j] * dM[k] + g.T[3 + j] * dM[3 + k]) * g.R[3 * j + k];
+            dls[k] += ds * g.s[k];
+        }
+        // T = J W: dJ = dT W^T (only J00, J02, J11, J12 are non-zero)
+        const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
+        const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
+        const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
+        const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
+        const float z = g.p[2], iz = 1.f / z, iz2 = iz * iz;
+        float dp[3] = {0.f, 0.f, 0.f};
+        dp[2] += -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2;
+        if (g.clamp_x == 0) {
+            dp[0] += -dJ02 * c.fx * iz2;
+            dp[2] += dJ02 * 2.f * c.fx * g.txz * iz2;
+        } else {
+            dp[2] += dJ02 * c.fx * g.txz * iz2;
+        }
+        if (g.clamp_y == 0) {
+            dp[1] += -dJ12 * c.fy * iz2;
+            dp[2] += dJ12 * 2.f * c.fy * g.tyz * iz2;
+        } else {
+            dp[2] += dJ12 * c.fy * g.tyz * iz2;
+        }
+        // mean2D = (fx x/z + cx, fy y/z + cy)
+        dp[0] += gd[0] * c.fx * iz;
+        dp[1] += gd[1] * c.fy * iz;
+        dp[2] += -(gd[0] * c.fx * g.p[0] + gd[1] * c.fy * g.p[1]) * iz2;
+        // p = W mu + t
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dmu[a] += c.R[a] * dp[0] + c.R[3 + a] * dp[1] + c.R[6 + a] * dp[2];
+        // R(qn): partial derivatives of the rotation matrix entries
+        const float w = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
+        float dqn[4];
+        dqn[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+        dqn[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - w * dR[5] + qz * dR[6] + w * dR[7] -
+                        2.f * qx * dR[8]);
+        dqn[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + w * dR[2] + qx * dR[3] + qz * dR[5] - w * dR[6] + qz * dR[7] -
+                        2.f * qy * dR[8]);
+        dqn[3] = 2.f * (-2.f * qz * dR[0] - w * dR[1] + qx * dR[2] + w * dR[3] - 2.f * qz * dR[4] + qy * dR[5] +
+                        qx * dR[6] + qy * dR[7]);
+        const float qd = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) dq[a] += (dqn[a] - g.qn[a] * qd) * g.qinv;
+    }
+    if (accumulate) {
+        for (int a = 0; a < 3; ++a) { gr.means[3 * i + a] += dmu[a]; gr.log_scales[3 * i + a] += dls[a]; }
+        for (int a = 0; a < 4; ++a) gr.quats[4 * i + a] += dq[a];
+        gr.opacity_logit[i] += dlogit;
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) gr.sh[i * 3 * K + k] += df[k];
+    } else {
+        for (int a = 0; a < 3; ++a) { gr.means[3 * i + a] = dmu[a]; gr.log_scales[3 * i + a] = dls[a]; }
+        reinterpret_cast<float4 *>(gr.quats)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        gr.opacity_logit[i] = dlogit;
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) gr.sh[i * 3 * K + k] = df[k];
+    }
+}
+
+template <int TILE>
+gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
+                     const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                     const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate, float4 *g2d) {
+    const dim3 grid((unsigned)total_tiles);
+    switch (batch) {
+        case 64:
+            render_bwd_kernel<TILE, 64><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
+                                                                         s.T_final, s.n_last, s.ckpt, s.ckpt_slots, dL,
+                                                                         gate, g2d);
+            break;
+        case 128:
+            render_bwd_kernel<TILE, 128><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
+                                                                          s.T_final, s.n_last, s.ckpt, s.ckpt_slots,
+                                                                          dL, gate, g2d);
+            break;
+        case 256:
+            render_bwd_kernel<TILE, 256><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
+                                                                          s.T_final, s.n_last, s.ckpt, s.ckpt_slots,
+                                                                          dL, gate, g2d);
+            break;
+        default:
+            return GS_ERR_UNSUPPORTED;
+    }
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gs_render_bwd_workspace_size(int64_t n, int32_t n_views) {
+    if (n < 0 || n_views <= 0) return 0;
+    return sizeof(float) * kG2d * (size_t)(n > 0 ? n : 1) * (size_t)n_views;
+}
+
+gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
+                        const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                        const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                        const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
+                        size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    if (!params || !proj || !cfg || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0)
+        return GS_ERR_INVALID_ARG;
+    if (params->n < 0 || params->n >= ((int64_t)1 << 31) || params->sh_degree < 0 || params->sh_degree > 3 ||
+        cfg->sh_degree != params->sh_degree)
+        return GS_ERR_INVALID_ARG;
+    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
+    if (!grads.means || !grads.log_scales || !grads.quats || !grads.opacity_logit || !grads.sh) return GS_ERR_INVALID_ARG;
+    if (((uintptr_t)grads.quats & 15) || ((uintptr_t)params->quats & 15) || ((uintptr_t)proj->rec & 15))
+        return GS_ERR_INVALID_ARG;
+    const int64_t n = params->n;
+    if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
+    if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
+    if (n == 0) return GS_OK;
+    float4 *g2d = reinterpret_cast<float4 *>(workspace);
+    GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
+    const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    gs_status st;
+    switch (cfg->tile) {
+        case 8: st = launch_bwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        case 16: st = launch_bwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        case 32: st = launch_bwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        default: return GS_ERR_INVALID_ARG;
+    }
+    if (st != GS_OK) return st;
+    const unsigned blocks = (unsigned)ceil_div(n, 128);
+    switch (params->sh_degree) {
+        case 0: proj_bwd_kernel<0><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
+        case 1: proj_bwd_kernel<1><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
+        case 2: proj_bwd_kernel<2><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
+        default: proj_bwd_kernel<3><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
+    }
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}
+
+}  // extern "C"

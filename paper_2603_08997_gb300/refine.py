@@ -1,0 +1,142 @@
+"""Post-densification refinement loop with the SkipGS gate (Algorithm 1).
+
+One iteration: select the view of this iteration (device-side, from the
+pre-drawn view sequence) -> project -> bin/sort -> render -> loss (value) ->
+gate decision -> [loss gradient -> raster and projection adjoint -> Adam]
+only when g = 1 -> per-view EMA update.
+
+`step_graph` replays the iteration as one CUDA graph: the bracketed branch is
+an IF conditional node that the gate kernel sets on the device, so no value
+crosses to the host inside the loop.  `step_eager` issues the same calls
+directly, with the branch predicated on the device flag.  With gated=False
+the branch always runs (the vanilla always-backward loop).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import gsr
+from .raster import AdamState, Gate, GaussianModel, RasterSettings, Renderer, Views
+
+
+class RefinementLoop:
+    def __init__(self, model: GaussianModel, train_cams: list, targets: torch.Tensor, view_seq,
+                 settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
+                 eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None):
+        self.model = model
+        self.s = settings or RasterSettings()
+        self.gated = bool(gated)
+        dev = model.flat.device
+        self.n_train = len(train_cams)
+        self.slot = Views([train_cams[0]], self.s.tile, dev)
+        self.poses = Views(train_cams, self.s.tile, dev)
+        self.renderer = Renderer(model.n, model.sh_degree, self.slot, self.s, pair_capacity, dev)
+        t = targets.contiguous()
+        self.targets = t.view(-1)
+        per = t[0].numel()
+        self.target_offsets = torch.arange(self.n_train, dtype=torch.int64, device=dev) * per
+        self.seq = torch.as_tensor(np.asarray(view_seq, np.int32), device=dev)
+        self.iter = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.view_ids = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.g = torch.zeros(1, dtype=torch.uint8, device=dev)
+        self.any = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.gate = Gate(self.n_train, W, beta, eps, rho_lo, dev)
+        self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
+        self.params = model.c_params()
+        self.grads = model.c_grads(self.adam.grad)
+        self.stream = torch.cuda.Stream(device=dev)
+        self.body_stream = torch.cuda.Stream(device=dev)
+        self.graph = None
+        self.loss_log = None
+
+    # ---- pieces of one iteration
+    def _front(self, s):
+        gsr.call("gs_select_views", gsr.ptr(self.seq), int(self.seq.numel()), gsr.ptr(self.iter), 1,
+                 gsr.ptr(self.view_ids), gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), gsr.stream_handle(s))
+        self.renderer.forward(self.params, s)
+        self.renderer.compute_loss(self.targets, self.target_offsets, self.view_ids, with_grad=False, stream=s)
+
+    def _back(self, s, predicated: bool):
+        r = self.renderer
+        r.loss_backward(self.targets, self.target_offsets, self.view_ids, stream=s)
+        r.backward(self.params, self.grads, view_gate=self.g if predicated else None, accumulate=False, stream=s)
+        self.adam.step(do_step=self.any if predicated else None, stream=s)
+
+    def _update(self, s):
+        self.gate.update(self.view_ids, self.renderer.loss, stream=s)
+
+    # ---- eager
+    def step_eager(self) -> None:
+        s = self.stream
+        self._front(s)
+        self.gate.decide(self.view_ids, self.renderer.loss, self.g, self.any, stream=s)
+        self._back(s, predicated=self.gated)
+        self._update(s)
+
+    # ---- graph
+    def capture(self) -> None:
+        s, b = self.stream, self.body_stream
+        hs, hb = gsr.stream_handle(s), gsr.stream_handle(b)
+        torch.cuda.synchronize()
+        gsr.call("gs_graph_begin", hs)
+        try:
+            self._front(s)
+            if self.gated:
+                cond = C.c_uint64()
+                gsr.call("gs_graph_cond_create", hs, C.byref(cond))
+                self.gate.decide(self.view_ids, self.renderer.loss, self.g, self.any, cond=cond.value, stream=s)
+                gsr.call("gs_graph_if_begin", hs, cond, hb)
+                self._back(b, predicated=False)
+                gsr.call("gs_graph_if_end", hs, hb)
+            else:
+                self.gate.decide(self.view_ids, self.renderer.loss, self.g, self.any, stream=s)
+                self._back(s, predicated=False)
+            self._update(s)
+        finally:
+            g = C.c_void_p()
+            code = gsr.lib().gs_graph_end(hs, C.byref(g))
+        gsr.check("gs_graph_end", code)
+        self.graph = g
+
+    def step_graph(self) -> None:
+        if self.graph is None:
+            self.capture()
+        gsr.call("gs_graph_launch", self.graph, gsr.stream_handle(self.stream))
+
+    def close(self) -> None:
+        if self.graph is not None:
+            gsr.lib().gs_graph_destroy(self.graph)
+            self.graph = None
+
+    # ---- state
+    def reset(self, flat_params: torch.Tensor) -> None:
+        """Back to iteration 0 from the given parameters (device-side copies)."""
+        with torch.cuda.stream(self.stream):
+            self.model.flat.copy_(flat_params)
+            self.adam.m.zero_()
+            self.adam.v.zero_()
+            self.adam.grad.zero_()
+            self.adam.step_count.zero_()
+            self.iter.zero_()
+        self.gate.reset(self.stream)
+
+    def evaluate(self, view_ids=None) -> np.ndarray:
+        """Loss of every training view (or the given ones) with the current parameters."""
+        ids = range(self.n_train) if view_ids is None else view_ids
+        seq = torch.as_tensor(np.asarray(list(ids), np.int32), device=self.model.flat.device)
+        it = torch.zeros(1, dtype=torch.int64, device=seq.device)
+        vid = torch.zeros(1, dtype=torch.int32, device=seq.device)
+        out = torch.zeros(seq.numel(), dtype=torch.float32, device=seq.device)
+        s = self.stream
+        with torch.cuda.stream(s):
+            for k in range(seq.numel()):
+                gsr.call("gs_select_views", gsr.ptr(seq), int(seq.numel()), gsr.ptr(it), 1, gsr.ptr(vid),
+                         gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), gsr.stream_handle(s))
+                self.renderer.forward(self.params, s)
+                self.renderer.compute_loss(self.targets, self.target_offsets, vid, stream=s)
+                out[k:k + 1].copy_(self.renderer.loss)
+        s.synchronize()
+        return out.cpu().numpy()

@@ -266,3 +266,36 @@ def case_c5(seed: int = 0, n: int = 6_000_000, n_views: int = 4):
     scene = scene_ball(n, seed, sh_degree=3, opacity_std=1.5)
     cams = ring_cameras(n_views, 1920, 1080, seed + 2)
     return scene, cams
+
+
+def projected_records(n: int, width: int, height: int, seed: int = 0, tie_frac: float = 0.2,
+                      sigma_range=(0.6, 6.0), aniso=(1.0, 8.0), cull_frac: float = 0.05) -> dict:
+    """Random screen-space Gaussians, the input of the binning and compositing
+    stages, for stage-wise parity tests.
+
+    Returns float32 centres (mean2d, may lie outside the image), covariance
+    eigen-structure (sigma1 >= sigma2 in pixels, angle theta), opacity, colour,
+    depth (about tie_frac of them repeat another Gaussian's depth exactly), a
+    pixel-space box [x0, x1] x [y0, y1] of half-width 3.5 sigma1 around the
+    centre, and a culled flag for about cull_frac of them."""
+    rng = np.random.default_rng(seed)
+    mean2d = np.stack([rng.uniform(-0.1 * width, 1.1 * width, n), rng.uniform(-0.1 * height, 1.1 * height, n)], 1)
+    s1 = np.exp(rng.uniform(np.log(sigma_range[0]), np.log(sigma_range[1]), n))
+    s2 = s1 / rng.uniform(aniso[0], aniso[1], n)
+    theta = rng.uniform(0.0, np.pi, n)
+    opacity = rng.uniform(0.02, 1.0, n)
+    rgb = rng.uniform(0.0, 1.0, (n, 3))
+    depth = rng.uniform(0.5, 20.0, n).astype(F32)
+    ties = rng.random(n) < tie_frac
+    src = rng.integers(0, n, n)
+    depth[ties] = depth[src[ties]]
+    half = 3.5 * s1
+    box = np.stack([mean2d[:, 0] - half, mean2d[:, 0] + half, mean2d[:, 1] - half, mean2d[:, 1] + half], 1)
+    culled = rng.random(n) < cull_frac
+    return dict(mean2d=mean2d.astype(F32), sigma1=s1.astype(F32), sigma2=s2.astype(F32), theta=theta.astype(F32),
+                opacity=opacity.astype(F32), rgb=rgb.astype(F32), depth=depth, box=box.astype(F32), culled=culled)
+
+
+def dl_dimage(width: int, height: int, seed: int = 0) -> np.ndarray:
+    """A random upstream gradient dL/dimage [3,H,W] (a linear functional of the image)."""
+    return np.random.default_rng(seed).normal(0.0, 1.0, (3, height, width)).astype(F32)

@@ -1,0 +1,78 @@
+"""The C-ABI library builds for sm_103a, loads on the host and exports every
+entry point include/gsr.h declares; host-side argument checks reject bad
+input without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b((?:gs|skipgs)_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_08997_gb300 import build, gsr
+    build.build()
+    return gsr.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_loss", "gs_adam_step",
+                     "skipgs_gate_decide", "skipgs_gate_update"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_2603_08997_gb300 import gsr
+    assert set(declared_functions()) <= set(gsr.exported_symbols())
+
+
+def test_host_side_checks(lib):
+    from paper_2603_08997_gb300 import gsr
+    assert lib.gs_version() >= 100
+    assert gsr.status_string(gsr.GS_ERR_CAPACITY) == "GS_ERR_CAPACITY"
+    out = (C.c_int64 * 6)()
+    assert lib.gs_param_layout(10, 3, out) == 0
+    assert [out[i] % 64 for i in range(6)] == [0] * 6 and out[5] >= 59 * 10
+    assert lib.gs_param_layout(10, 4, out) == gsr.GS_ERR_INVALID_ARG
+    cams = (gsr.gs_camera * 2)()
+    cams[0].width, cams[0].height, cams[1].width, cams[1].height = 33, 17, 16, 16
+    tt, tp = C.c_int64(), C.c_int64()
+    assert lib.gs_camera_layout(cams, 2, 16, C.byref(tt), C.byref(tp)) == 0
+    assert (tt.value, tp.value) == (3 * 2 + 1, 33 * 17 + 256)
+    assert cams[1].tile_offset == 6 and cams[1].pix_offset == 33 * 17
+    assert lib.gs_camera_layout(cams, 2, 12, C.byref(tt), C.byref(tp)) == gsr.GS_ERR_INVALID_ARG
+    # invalid arguments are refused before any launch
+    assert lib.gs_project(None, None, 1, None, gsr.gs_projected(), None, None) == gsr.GS_ERR_INVALID_ARG
+    assert lib.skipgs_gate_decide(None, None, None, 1, None, None, None, None, None) == gsr.GS_ERR_INVALID_ARG
+    assert lib.gs_ckpt_slots(1000, 10, 256) == 1000 // 256 + 10 + 1
+    assert lib.skipgs_gate_state_size(200) >= 200 * 9
+    cfg = gsr.gs_gate_config()
+    cfg.W, cfg.beta, cfg.eps, cfg.rho_lo, cfg.n_views = 10, 1.5, 1e-8, 0.5, 4
+    assert lib.skipgs_gate_init(C.byref(cfg), C.c_void_p(16), None) == gsr.GS_ERR_INVALID_ARG
+
+
+def test_workspace_too_small_is_refused(lib):
+    from paper_2603_08997_gb300 import gsr
+    proj = gsr.gs_projected(16, 16, 16)
+    rc = gsr.gs_raster_config()
+    rc.tile, rc.batch = 16, 256
+    need = lib.gs_bin_sort_workspace_size(100, 1, 1000, 4)
+    code = lib.gs_bin_sort(C.byref(proj), C.c_void_p(256), 1, 100, 4, C.byref(rc), C.c_void_p(256), need - 1,
+                           None, C.c_void_p(256), 1000, C.c_void_p(256), C.c_void_p(256), None, None)
+    assert code == gsr.GS_ERR_WORKSPACE

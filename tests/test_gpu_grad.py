@@ -1,0 +1,148 @@
+"""GPU loss, backward and Adam against the FP64 oracle.
+
+Tolerances: loss within 1e-5 relative; gradients per parameter group within
+1e-4 normwise relative error with cosine >= 0.9999; Adam within 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle.adam import AdamConfig, adam_step
+from paper_2603_08997_gb300 import raster
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logit", "sh")
+
+
+def _setup(scene, cam, tile=16, batch=256):
+    gpu_util.lib()
+    views = raster.Views([cam], tile)
+    r = raster.Renderer(scene.n, scene.sh_degree, views, raster.RasterSettings(tile=tile, batch=batch))
+    model = raster.GaussianModel.from_scene(scene)
+    return r, model
+
+
+def test_loss_multi_view():
+    sizes = [(64, 64), (97, 41), (33, 120)]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    gpu_util.lib()
+    views = raster.Views(cams, 16)
+    r = raster.Renderer(10, 0, views)
+    rng = np.random.default_rng(0)
+    imgs = [rng.uniform(0, 1, (3, h, w)).astype(np.float32) for w, h in sizes]
+    tgts = [np.clip(i + rng.normal(0, 0.1, i.shape), 0, 1).astype(np.float32) for i in imgs]
+    r.image.copy_(torch.from_numpy(np.concatenate([i.ravel() for i in imgs])))
+    tgt = torch.from_numpy(np.concatenate([t.ravel() for t in tgts])).cuda()
+    r.compute_loss(tgt, with_grad=True)
+    torch.cuda.synchronize()
+    for v in range(3):
+        L, dL = oracle.loss_and_grad(imgs[v], tgts[v])
+        assert abs(float(r.loss[v].item()) - L) <= 1e-5 * abs(L)
+        g = r.views.image_view(r.dL_dimage, v).cpu().numpy()
+        assert gpu_util.rel_err(g, dL) < 1e-4
+
+
+def _check_grads(gg, og, tol=1e-4):
+    for k in GROUPS:
+        a, b = gg[k], og[k]
+        if np.linalg.norm(b) == 0:
+            assert np.linalg.norm(a) == 0
+            continue
+        assert gpu_util.rel_err(a, b) < tol, (k, gpu_util.rel_err(a, b))
+        assert gpu_util.cosine(a, b) > 0.9999, (k, gpu_util.cosine(a, b))
+
+
+@pytest.mark.parametrize("seed,deg", [(3, 3), (7, 1), (11, 0), (5, 2)])
+def test_backward_linear_functional_tiny(seed, deg):
+    scene, cam = synth.scene_tiny(40, seed=seed, sh_degree=deg)
+    dl = synth.dl_dimage(cam.width, cam.height, seed)
+    r, model = _setup(scene, cam)
+    adam = raster.AdamState(model)
+    r.forward(model.c_params())
+    r.backward(model.c_params(), model.c_grads(adam.grad), dL_dimage=torch.from_numpy(dl.ravel()).cuda())
+    torch.cuda.synchronize()
+    rc = oracle.RasterConfig()
+    f = oracle.forward(scene, cam, rc)
+    og = oracle.backward(scene, cam, rc, f, dl.astype(np.float64))
+    _check_grads(gpu_util.gpu_grads(model, adam.grad), og)
+
+
+@pytest.mark.parametrize("tile,batch", [(16, 256), (8, 64), (32, 128)])
+def test_backward_full_loss_c1(tile, batch):
+    scene, cam, target = synth.case_c1()
+    r, model = _setup(scene, cam, tile, batch)
+    adam = raster.AdamState(model)
+    r.forward(model.c_params())
+    r.compute_loss(torch.from_numpy(target.ravel()).cuda(), with_grad=True)
+    r.backward(model.c_params(), model.c_grads(adam.grad))
+    torch.cuda.synchronize()
+    rc = oracle.RasterConfig(tile=tile)
+    f = oracle.forward(scene, cam, rc)
+    L, dL = oracle.loss_and_grad(f["image"], target)
+    assert abs(float(r.loss.item()) - L) <= 1e-5 * L
+    og = oracle.backward(scene, cam, rc, f, dL)
+    _check_grads(gpu_util.gpu_grads(model, adam.grad), og)
+
+
+def test_backward_c2_like():
+    scene, tscene, cam, noise = synth.case_c2(n=40_000)
+    rc = oracle.RasterConfig()
+    target = oracle.forward(tscene, cam, rc)["image"] + noise
+    r, model = _setup(scene, cam)
+    adam = raster.AdamState(model)
+    r.forward(model.c_params())
+    r.compute_loss(torch.from_numpy(target.astype(np.float32).ravel()).cuda(), with_grad=True)
+    r.backward(model.c_params(), model.c_grads(adam.grad))
+    torch.cuda.synchronize()
+    f = oracle.forward(scene, cam, rc)
+    L, dL = oracle.loss_and_grad(f["image"], target.astype(np.float32))
+    assert abs(float(r.loss.item()) - L) <= 1e-5 * L
+    og = oracle.backward(scene, cam, rc, f, dL)
+    _check_grads(gpu_util.gpu_grads(model, adam.grad), og)
+
+
+def test_adam_against_oracle():
+    gpu_util.lib()
+    scene, _ = synth.scene_tiny(37, seed=1, sh_degree=3)
+    model = raster.GaussianModel.from_scene(scene)
+    cfg = AdamConfig()
+    adam = raster.AdamState(model, lr=cfg.lrs(), beta1=cfg.beta1, beta2=cfg.beta2, eps=cfg.eps)
+    rng = np.random.default_rng(4)
+    o = model.offsets
+    n, K = scene.n, scene.sh.shape[1]
+    p = {k: getattr(scene, k).astype(np.float64).ravel() for k in GROUPS}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    vv = {k: np.zeros_like(v) for k, v in p.items()}
+    lr = {"means": cfg.lr_means, "log_scales": cfg.lr_log_scales, "quats": cfg.lr_quats,
+          "opacity_logit": cfg.lr_opacity}
+    sh_lr = np.where((np.arange(3 * K * n) % (3 * K)) < 3, cfg.lr_sh_dc, cfg.lr_sh_rest)
+    do = torch.zeros(1, dtype=torch.int32, device="cuda")
+    step = 0
+    for it, on in enumerate([1, 1, 0, 1, 1, 0, 0, 1]):
+        g = {k: rng.normal(size=v.shape) * 10.0 ** rng.uniform(-5, 0, v.shape) for k, v in p.items()}
+        gv = model.group_views(adam.grad)
+        for k in GROUPS:
+            gv[k].copy_(torch.from_numpy(g[k].astype(np.float32).reshape(gv[k].shape)))
+        do.fill_(on)
+        adam.step(do_step=do, zero_grad=True)
+        if on:
+            for k in GROUPS:
+                gk = g[k].astype(np.float32).astype(np.float64)
+                p[k], m[k], vv[k], _ = adam_step(p[k], gk, m[k], vv[k], step, sh_lr if k == "sh" else lr[k], cfg)
+            step += 1
+    torch.cuda.synchronize()
+    assert int(adam.step_count.item()) == step
+    got = gpu_util.gpu_grads(model, model.flat)
+    for k in GROUPS:
+        np.testing.assert_allclose(got[k].ravel(), p[k], rtol=2e-6, atol=1e-7)
+    assert float(adam.grad.abs().max().item()) == 0.0
+    # padding between groups stays zero
+    pad = torch.ones_like(model.flat, dtype=torch.bool)
+    for k, (a, b) in {"means": (o[0], o[0] + 3 * n), "log_scales": (o[1], o[1] + 3 * n),
+                      "quats": (o[2], o[2] + 4 * n), "opacity_logit": (o[3], o[3] + n),
+                      "sh": (o[4], o[4] + 3 * K * n)}.items():
+        pad[a:b] = False
+    assert float(model.flat[pad].abs().max().item()) == 0.0

@@ -1,0 +1,165 @@
+"""GPU projection, binning/sort and compositing against the FP64 oracle.
+
+Tolerances: sort keys, values and tile ranges bit-exact given the same
+stage inputs; pixels within 1e-5 relative (normwise over the image, and per
+pixel against 1e-5 of the image's peak outside pixels the oracle flags as
+within 1e-5 of a threshold); projected quantities within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2603_08997_gb300 import gsr, raster
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+
+
+def _renderer(cams, n, sh_degree=0, tile=16, batch=256, cap=None, keys=True):
+    gpu_util.lib()
+    views = raster.Views(cams, tile)
+    st = raster.RasterSettings(tile=tile, batch=batch)
+    return raster.Renderer(n, sh_degree, views, st, pair_capacity=cap, keep_keys=keys)
+
+
+def _sorted_pairs(r):
+    P = int(r.pair_count.item())
+    keys = r.keys[:P].cpu().numpy().view(np.uint64)
+    vals = r.vals[:P].cpu().numpy().view(np.uint32)
+    ranges = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    return P, keys, vals, ranges
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("nviews", [1, 3])
+def test_bin_sort_bit_exact(tile, nviews):
+    sizes = [(97, 61), (64, 64), (130, 33)][:nviews]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(3000, w, h, seed=11 + v) for v, (w, h) in enumerate(sizes)]
+    r = _renderer(cams, 3000, tile=tile)
+    dev, orc = gpu_util.records(recs, cams, tile)
+    gpu_util.set_projected(r, dev)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    P, keys, vals, ranges = _sorted_pairs(r)
+    okeys, ovals, oranges, _ = oracle.bin_sort(orc, cams, tile)
+    assert P == len(okeys)
+    assert np.array_equal(keys, okeys)
+    assert np.array_equal(vals, ovals)
+    assert np.array_equal(ranges, oranges)
+
+
+def test_bin_sort_capacity_overflow_and_empty():
+    cams = [synth.camera_pinhole(50, 50, 32, 32, 64, 64)]
+    recs = [synth.projected_records(500, 64, 64, seed=2)]
+    dev, orc = gpu_util.records(recs, cams, 16)
+    need = int(sum(o["touched"].sum() for o in orc))
+    r = _renderer(cams, 500, cap=need - 1)
+    gpu_util.set_projected(r, dev)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == gsr.GS_ERR_CAPACITY
+    assert int(r.pair_count.item()) == need
+    assert int(r.ranges.abs().sum().item()) == 0
+    # all culled: no pairs, empty ranges, clean status
+    r2 = _renderer(cams, 500)
+    dev["touched"].zero_()
+    gpu_util.set_projected(r2, dev)
+    r2.bin_sort()
+    r2.render_fwd()
+    torch.cuda.synchronize()
+    assert int(r2.pair_count.item()) == 0 and int(r2.status.item()) == 0
+    assert float(r2.image.abs().max().item()) == 0.0
+
+
+def _compare_images(img, ref, margin, tol=1e-5):
+    img = np.asarray(img, np.float64)
+    ref = np.asarray(ref, np.float64)
+    mask = margin.astype(bool)[None].repeat(3, 0)
+    assert mask.mean() < 0.01
+    d = np.abs(img - ref)
+    d[mask] = 0.0
+    peak = np.abs(ref).max()
+    assert d.max() <= tol * peak, (d.max(), peak)
+    nd = np.linalg.norm(np.where(mask, 0.0, img - ref))
+    assert nd <= tol * np.linalg.norm(ref), nd / np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("tile,batch", [(16, 256), (8, 64), (32, 128), (16, 128)])
+def test_render_synthetic_records(tile, batch):
+    sizes = [(150, 97), (64, 40)]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(4000, w, h, seed=21 + v) for v, (w, h) in enumerate(sizes)]
+    r = _renderer(cams, 4000, tile=tile, batch=batch)
+    dev, orc = gpu_util.records(recs, cams, tile)
+    gpu_util.set_projected(r, dev)
+    r.bin_sort()
+    r.render_fwd()
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    rc = oracle.RasterConfig(tile=tile)
+    _, ovals, oranges, toff = oracle.bin_sort(orc, cams, tile)
+    for v, cam in enumerate(cams):
+        o = oracle.render(orc[v], cam, ovals, oranges, rc, int(toff[v]))
+        img = r.image_of(v).cpu().numpy()
+        _compare_images(img, o["image"], o["margin"])
+        off = r.views.pix_offsets[v]
+        w, h = sizes[v]
+        nl = r.n_last[off:off + w * h].view(h, w).cpu().numpy()
+        agree = (nl == o["n_last"]) | o["margin"].astype(bool)
+        assert agree.all()
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_render_end_to_end_c1(tile):
+    scene, cam, _ = synth.case_c1()
+    r = _renderer([cam], scene.n, tile=tile)
+    model = raster.GaussianModel.from_scene(scene)
+    r.forward(model.c_params())
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    o = oracle.forward(scene, cam, oracle.RasterConfig(tile=tile))
+    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])
+
+
+def test_projection_c2_like():
+    """Projection of an SH-degree-3 unit-ball scene seen by the C2 camera."""
+    scene, _, cam, _ = synth.case_c2(n=50_000)
+    r = _renderer([cam], scene.n, sh_degree=3)
+    model = raster.GaussianModel.from_scene(scene)
+    r.project(model.c_params())
+    torch.cuda.synchronize()
+    rec = r.records()[0].double().cpu().numpy()
+    rect = r.rect.view(-1, 4).cpu().numpy()
+    touched = r.touched.cpu().numpy()
+    o = oracle.project(scene, cam, oracle.RasterConfig())
+    vis = (o["touched"] > 0) & (touched > 0)
+    # culling agrees except within float rounding of a threshold
+    assert ((o["touched"] > 0) != (touched > 0)).sum() <= 5
+    np.testing.assert_allclose(rec[vis, 0:2], o["mean2d"][vis], rtol=1e-6, atol=1e-4)
+    np.testing.assert_allclose(rec[vis, 9], o["depth"][vis], rtol=1e-6)
+    np.testing.assert_allclose(rec[vis, 5], o["opacity"][vis], rtol=1e-5)
+    np.testing.assert_allclose(rec[vis, 6:9], o["rgb"][vis], rtol=1e-5, atol=1e-6)
+    U = rec[vis, 2:5]
+    Q = np.stack([U[:, 0] ** 2, U[:, 0] * U[:, 1], U[:, 1] ** 2 + U[:, 2] ** 2], 1)
+    Qo = o["conic"][vis]
+    err = np.linalg.norm(Q - Qo, axis=1) / np.linalg.norm(Qo, axis=1)
+    assert np.median(err) < 1e-6 and err.max() < 1e-3
+    # the GPU rectangle contains the oracle's
+    gr, orr = rect[vis], o["rect"][vis]
+    assert ((gr[:, 0] <= orr[:, 0]) & (gr[:, 1] <= orr[:, 1]) & (gr[:, 2] >= orr[:, 2]) & (gr[:, 3] >= orr[:, 3])).all()
+
+
+def test_render_end_to_end_c2_like():
+    scene, _, cam, _ = synth.case_c2(n=60_000)
+    r = _renderer([cam], scene.n, sh_degree=3)
+    model = raster.GaussianModel.from_scene(scene)
+    r.forward(model.c_params())
+    torch.cuda.synchronize()
+    o = oracle.forward(scene, cam, oracle.RasterConfig())
+    img = r.image_of(0).cpu().numpy()
+    rel = gpu_util.rel_err(img, o["image"])
+    assert rel < 1e-5, rel
