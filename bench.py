@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Post-densification refinement throughput with the SkipGS gate vs the
+always-backward loop, on the 3M-Gaussian synthetic workload (SH degree 3,
+200 ring views at 1297x840, views drawn uniformly, targets rendered from a
+ground-truth scene; the gate with W=500, beta=0.95, eps=1e-8, rho_lo=0.5).
+
+A step is one refinement iteration: view selection, projection, binning and
+sort, compositing, loss, gate decision, and - when the gate opens - the loss
+gradient, raster and projection adjoint and Adam, then the EMA update.  Each
+loop runs as one captured CUDA graph per iteration (the backward branch is an
+IF node set on the device).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsr|reference]
+
+Under torchrun every rank runs its own replica on its own GPU (the loop
+does not shard); value = all ranks' iterations / max wall time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "post-densif. iters/s fwd+gated bwd vs full bwd; bwd ms/view at 3M Gaussians"
+WORKLOAD = ("3M Gaussians SH3, 200 jittered-ring views 1297x840, post-densification refinement loop, "
+            "SkipGS gate W=500 beta=0.95 eps=1e-8 rho_lo=0.5, views uniform (seed 0), FP32 params + Adam")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
+    ap.add_argument("--n", type=int, default=3_000_000)
+    ap.add_argument("--views", type=int, default=200)
+    ap.add_argument("--width", type=int, default=1297)
+    ap.add_argument("--height", type=int, default=840)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--ref-seconds", type=float, default=150.0, help="budget of the reference arm")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.f = open(self.path, "w")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------- CPU oracle arm
+
+def oracle_sample_step(scene, cam, frac: float, seed: int = 0):
+    """One oracle refinement iteration on a bounded sample of the workload: the
+    crop of the view covering `frac` of its pixels (centred) with the Gaussians
+    whose projected centres fall in it (plus a 16-pixel border), against a
+    seeded target.  Returns (seconds, pixels of the crop)."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    rc = oracle.RasterConfig()
+    W, H = cam.width, cam.height
+    cw = max(16, int(round(W * math.sqrt(frac))))
+    ch = max(16, int(round(H * math.sqrt(frac))))
+    x0, y0 = (W - cw) // 2, (H - ch) // 2
+    crop = synth.Camera(cam.R, cam.t, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, cw, ch, cam.znear)
+    key = ("proj_full", id(cam))
+    if key not in scene.extra:
+        scene.extra[key] = oracle.project(scene, cam, rc)  # sample selection only, untimed
+    pr = scene.extra[key]
+    m = pr["mean2d"]
+    sel = np.nonzero((pr["touched"] > 0) & (m[:, 0] > x0 - 16) & (m[:, 0] < x0 + cw + 16) &
+                     (m[:, 1] > y0 - 16) & (m[:, 1] < y0 + ch + 16))[0]
+    sub = synth.Scene(scene.means[sel], scene.log_scales[sel], scene.quats[sel], scene.opacity_logit[sel],
+                      scene.sh[sel])
+    target = np.random.default_rng(seed).uniform(0, 1, (3, ch, cw))
+    from oracle.adam import AdamConfig, adam_step, lr_vector
+    cfg = AdamConfig()
+    p = sub.flat().astype(np.float64)
+    lr = lr_vector(sub.n, sub.sh.shape[1], cfg)
+    t0 = time.perf_counter()
+    f = oracle.forward(sub, crop, rc)
+    L, dL = oracle.loss_and_grad(f["image"], target)
+    g = oracle.backward(sub, crop, rc, f, dL)
+    gflat = np.concatenate([g["means"].ravel(), g["log_scales"].ravel(), g["quats"].ravel(),
+                            g["opacity_logit"].ravel(), g["sh"].ravel()])
+    adam_step(p, gflat, np.zeros_like(p), np.zeros_like(p), 0, lr, cfg)
+    return time.perf_counter() - t0, cw * ch
+
+
+def cpu_baseline(args, scene, cam, budget_s: float) -> dict:
+    """The FP64 oracle timed on this host's cores on bounded crops of one view,
+    scaled to iterations/s of the full view (the oracle's cost grows with the
+    crop's pixels and the Gaussians over them)."""
+    import oracle
+    oracle.core.build()
+    cores = oracle.num_threads()
+    dt, px = oracle_sample_step(scene, cam, 0.01)
+    full_px = cam.width * cam.height
+    frac = min(1.0, 0.01 * (budget_s / 3.0) / max(dt, 1e-3))
+    total, pix, runs = 0.0, 0, 0
+    while total < budget_s * 0.5 and runs < 3:
+        dt, px = oracle_sample_step(scene, cam, frac, seed=runs)
+        total += dt
+        pix += px
+        runs += 1
+    its = (pix / full_px) / total
+    return {"value": its, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{runs} oracle iteration(s) on a centred crop of {pix // runs} px of view 0 "
+                      f"({100.0 * pix / runs / full_px:.1f}% of 1297x840) with the Gaussians over it; "
+                      f"{total:.1f} s CPU wall time, scaled to the full view by the pixel fraction"}
+
+
+def run_reference(args) -> None:
+    import synth
+    K, W = args.steps, args.warmup
+    gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=max(K, 1),
+                                         width=args.width, height=args.height)
+    cam = cams[int(seq[0])]
+    import oracle
+    oracle.core.build()
+    cores = oracle.num_threads()
+    dt, _ = oracle_sample_step(start, cam, 0.002)
+    per_step = args.ref_seconds / (K + W)
+    frac = max(1e-4, min(1.0, 0.002 * per_step / max(dt, 1e-4)))
+    for w in range(W):
+        oracle_sample_step(start, cam, frac, seed=w)
+    total, pix = 0.0, 0
+    for k in range(K):
+        dt, px = oracle_sample_step(start, cam, frac, seed=100 + k)
+        total += dt
+        pix += px
+    value = (pix / (args.width * args.height)) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views": args.views,
+                       "width": args.width, "height": args.height},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle iteration on a centred crop covering "
+                                       f"{100 * frac:.3f}% of the view's pixels with the Gaussians over it, "
+                                       f"scaled to the full view by the pixel fraction"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import build, gsr, raster
+    from paper_2603_08997_gb300.refine import RefinementLoop
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    K, W = args.steps, args.warmup
+    seq_len = max(K, 5000)
+    gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=seq_len,
+                                         width=args.width, height=args.height)
+    dev = torch.device("cuda", local)
+    st = raster.RasterSettings()
+    cap = 24 * args.n
+    # targets: renders of the ground-truth scene (device-resident)
+    mgt = raster.GaussianModel.from_scene(gt, dev)
+    slot = raster.Views([cams[0]], st.tile, dev)
+    rgt = raster.Renderer(args.n, 3, slot, st, cap, dev)
+    targets = torch.empty((args.views, 3, args.height, args.width), dtype=torch.float32, device=dev)
+    for v, cam in enumerate(cams):
+        one = raster.Views([cam], st.tile, dev)
+        rgt.views = one
+        rgt.forward(mgt.c_params())
+        targets[v].copy_(rgt.image.view(3, args.height, args.width))
+    torch.cuda.synchronize()
+    del mgt, rgt
+    model = raster.GaussianModel.from_scene(start, dev)
+    init = model.flat.clone()
+
+    def timed_loop(gated: bool):
+        loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, pair_capacity=cap)
+        loop.reset(init)
+        loop.capture()
+        for _ in range(W):
+            loop.step_graph()
+        loop.reset(init)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clock = ClockSampler(local) if (gated and rank == 0) else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed_gated" if gated else "timed_full")
+        e0.record(loop.stream)
+        for _ in range(K):
+            loop.step_graph()
+        e1.record(loop.stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clocks = clock.stop() if clock else None
+        ms = e0.elapsed_time(e1)
+        gs = loop.gate.read(loop.stream)
+        status = int(loop.renderer.status.item())
+        final = float(np.mean(loop.evaluate()))
+        return loop, ms, wall, gs, status, final, clocks
+
+    full, ms_full, wall_full, gs_full, st_full, loss_full, _ = timed_loop(False)
+    kc_full = full.kernels_per_step
+    full.close()
+    gated, ms_gated, wall_gated, gs_gated, st_gated, loss_gated, clocks = timed_loop(True)
+    kc_gated = gated.kernels_per_step
+
+    # roofline of the dominant kernel (compositing forward), timed on the loop's stream
+    r = gated.renderer
+    s = gated.stream
+    reps = 20
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(s):
+        r.forward(gated.params, s)
+        torch.cuda.synchronize()
+        ev[0].record(s)
+        for _ in range(reps):
+            r.render_fwd(s)
+        ev[1].record(s)
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1]) / reps * 1e-3
+    evals = float(r.n_last.double().sum().item())
+    flops = 12.0 * evals
+    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12
+    roofline = {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": flops / t_fwd / 1e12,
+                "peak": peak_alu, "unit": "TFLOP/s", "frac": flops / t_fwd / 1e12 / peak_alu, "traffic": None,
+                "units_per_launch": evals, "flop_per_unit": 12, "launch_ms": t_fwd * 1e3,
+                "peak_note": "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"}
+
+    # end-to-end through the C ABI with host-resident targets
+    e2e = None
+    if not args.no_e2e:
+        host_targets = targets.cpu().pin_memory()
+        del targets
+        torch.cuda.empty_cache()
+        slot_target = torch.empty((1, 3, args.height, args.width), dtype=torch.float32, device=dev)
+        gated.close()
+        del gated
+        loop = RefinementLoop(model, cams, slot_target, seq, st, gated=True, pair_capacity=cap)
+        loop.target_offsets.zero_()  # every view's target is the slot the host fills each step
+        loop.reset(init)
+        loop.capture()
+        loss_host = torch.empty(K, dtype=torch.float32).pin_memory()
+        g_host = torch.empty(K, dtype=torch.uint8).pin_memory()
+        seq_np = np.asarray(seq)
+
+        def e2e_step(k):
+            v = int(seq_np[k % len(seq_np)])
+            with torch.cuda.stream(loop.stream):
+                slot_target[0].copy_(host_targets[v], non_blocking=True)
+            loop.step_graph()
+            with torch.cuda.stream(loop.stream):
+                loss_host[k:k + 1].copy_(loop.renderer.loss, non_blocking=True)
+                g_host[k:k + 1].copy_(loop.g, non_blocking=True)
+
+        for k in range(W):
+            e2e_step(k)
+        loop.reset(init)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        wall_e2e = time.perf_counter() - t0
+        e2e = {"value": K / wall_e2e, "unit": "iters/s",
+               "h2d_bytes_per_step": 3 * args.height * args.width * 4, "d2h_bytes_per_step": 4 + 1}
+        loop.close()
+
+    # aggregate over ranks: max time
+    t_gated = ms_gated * 1e-3
+    if dist:
+        t = torch.tensor([t_gated], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_gated = float(t.item())
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    b = gs_gated["b"]
+    it_full = K / (ms_full * 1e-3)
+    it_gated = K / t_gated
+    t_bwd = (ms_full - ms_gated) / max(K - b, 1)          # ms per backward (per view)
+    t_fwd_ms = ms_full / K - t_bwd
+    launches = kc_gated[0] * K + kc_gated[1] * b
+    line = {
+        "metric": METRIC, "value": it_gated * world, "unit": "iters/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_gated / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views": args.views, "width": args.width,
+                   "height": args.height, "iterations_timed": K, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (2.8 GB of parameters and Adam state, 2.6 GB of targets)"},
+        "full_bwd_iters_per_s": it_full * world, "gated_speedup": it_gated / it_full,
+        "bwd_ms_per_view": t_bwd, "fwd_ms_per_view": t_fwd_ms,
+        "backward_passes": b, "rho_cum": b / K, "rho_min": gs_gated["rho_min"],
+        "final_loss_gated": loss_gated, "final_loss_full": loss_full,
+        "final_loss_rel_diff": (loss_gated - loss_full) / loss_full,
+        "device_status": [st_full, st_gated],
+        "wall_s": {"full": wall_full, "gated": wall_gated},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+        "kernels_per_step": {"always": kc_gated[0], "backward_branch": kc_gated[1],
+                             "full_loop": kc_full[0] + kc_full[1]},
+        "roofline": roofline,
+    }
+    try:
+        line["cpu_baseline"] = cpu_baseline(args, start, cams[int(seq[0])], args.cpu_seconds)
+    except Exception as e:  # the baseline is a report, not the product
+        line["cpu_baseline"] = {"error": repr(e)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -276,7 +276,10 @@ size_t skipgs_gate_state_size(int32_t n_views);
 /* Initialise the state (Algorithm 1: EMA table empty, rho_min = rho_lo, b = 0). */
 gs_status skipgs_gate_init(const gs_gate_config *cfg /* host */, void *dev_state, cudaStream_t stream);
 
-/* Algorithm 1, per loss in order (reading: each one is its own iteration t):
+/* Algorithm 1, per loss in order (reading: each one is its own iteration t, and
+ * all losses of one call are compared with the EMA as it stood before the
+ * call - they come from the same parameters; skipgs_gate_update then applies
+ * their EMA updates in order):
  * deviation score s = L / (EMA + eps) or +inf without history (Eq. deviation),
  * skip test g = [s > 1] (Eq. gate); during warmup (t <= W) the test is recorded
  * for views with history and g is forced to 1; at t = W + 1 rho_min = rho_lo +
@@ -320,6 +323,10 @@ gs_status gs_graph_if_begin(cudaStream_t stream, cudaGraphConditionalHandle cond
 gs_status gs_graph_if_end(cudaStream_t stream, cudaStream_t body_stream);
 gs_status gs_graph_end(cudaStream_t stream, gs_graph *out /* host */);
 gs_status gs_graph_launch(gs_graph graph, cudaStream_t stream);
+/* Kernel nodes of the graph: out2[0] outside, out2[1] inside the IF bodies
+ * (host pointer).  One replay launches out2[0] kernels, plus out2[1] when the
+ * gate opens the branch. */
+gs_status gs_graph_kernel_counts(gs_graph graph, int64_t *out2 /* host */);
 gs_status gs_graph_destroy(gs_graph graph);
 
 /* Device-side view selection for graph replay: view_ids[k] =

@@ -16,7 +16,9 @@ Readings where the paper is silent or the algorithm listing and the text differ:
   (vi)  a non-finite loss: g = 0, the state is left untouched and the call
         reports an error;
   (vii) several views of one batched launch are decided one after another,
-        each as its own iteration t.
+        each as its own iteration t, all against the EMA as it stood before the
+        launch (their losses come from the same parameters); the EMA updates
+        of the launch follow, in order.  decide_batch / update_batch.
   rho_lo < 0 selects the ablation without budget control (Table 4): the skip
   test alone decides after warmup.
 """
@@ -91,6 +93,13 @@ class Gate:
         else:
             self.ema[v] = L
             self.hist[v] = True
+
+    def decide_batch(self, views, losses) -> list:
+        return [self.decide(int(v), float(L)) for v, L in zip(views, losses)]
+
+    def update_batch(self, views, losses) -> None:
+        for v, L in zip(views, losses):
+            self.update(int(v), float(L))
 
     def step(self, v: int, L: float) -> int:
         g = self.decide(v, L)

@@ -278,6 +278,10 @@ static void project_one(const double *mu, const double *log_s, const double *q, 
     const double hd = 0.5 * (g->cov[0] - g->cov[2]);
     const double lmax = mid + sqrt(hd * hd + g->cov[1] * g->cov[1]);
     g->radius = sqrt(2.0 * lmax * log(g->o / rc->alpha_min));
+    /* The rectangle may be any superset of the support (no pixel depends on
+     * it); a slight inflation keeps every pair whose alpha' lies near the
+     * cut-off in the tile lists, where the margin flags of orc_render see it. */
+    g->radius = g->radius * 1.001 + 0.01;
     double fx0 = ceil(g->mean2d[0] - g->radius - 0.5), fx1 = floor(g->mean2d[0] + g->radius - 0.5);
     double fy0 = ceil(g->mean2d[1] - g->radius - 0.5), fy1 = floor(g->mean2d[1] + g->radius - 0.5);
     if (fx0 < 0.0) fx0 = 0.0;

@@ -16,7 +16,8 @@
 // can be captured in a CUDA graph.  The radix sort is a reduce-then-scan LSD
 // sort: an upsweep histogram per block, one exclusive scan over the
 // digit-major (digit, block) counts, and a downsweep that ranks each tile of
-// 2048 keys with warp match/ballot and scatters them stably.
+// 2048 keys with warp match/ballot, reorders the tile by digit in shared
+// memory and writes each digit's run contiguously.
 #include "common.cuh"
 
 using namespace gsr;
@@ -29,8 +30,10 @@ constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int RS_MAX_BLOCKS = 1024;
+constexpr int RS_MAX_BLOCKS = 608;  // 4 x 152 SMs
 constexpr int SCAN_THREADS = 1024;
+static_assert(RS_THREADS == RADIX, "the downsweep gives each thread one digit");
+static_assert(RS_MAX_BLOCKS <= SCAN_THREADS, "count_top scans the block sums in one pass");
 
 __device__ __forceinline__ int64_t effective_count(const int64_t *d_count, int64_t cap) {
     if (!d_count) return cap;
@@ -60,26 +63,52 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t *__restr
     for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) counts[(int64_t)d * gridDim.x + blockIdx.x] = hist[d];
 }
 
-// In-place exclusive scan of n uint32 values by one block.
-__global__ void __launch_bounds__(SCAN_THREADS) rs_scan(uint32_t *a, int n) {
-    __shared__ uint32_t s[SCAN_THREADS];
-    const int per = (n + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int lo = threadIdx.x * per;
-    const int hi = min(n, lo + per);
-    uint32_t sum = 0;
-    for (int i = lo; i < hi; ++i) sum += a[i];
-    s[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-        const uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
-        __syncthreads();
-        s[threadIdx.x] += t;
-        __syncthreads();
+// Exclusive scan across a block of SCAN_THREADS threads; returns the
+// thread's exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sums, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
     }
-    uint32_t run = s[threadIdx.x] - sum;
-    for (int i = lo; i < hi; ++i) {
-        const uint32_t t = a[i];
-        a[i] = run;
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? warp_sums[warp - 1] : 0u;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + inc - x;
+}
+
+// In-place exclusive scan of the digit-major counts [RADIX][G] by one block:
+// thread t = 4 d + q owns the q-th quarter of digit d's row, so a block scan
+// over the 1024 partial sums in thread order is the digit-major order.
+__global__ void __launch_bounds__(SCAN_THREADS) rs_scan(uint32_t *a, int G) {
+    static_assert(SCAN_THREADS == 4 * RADIX, "four threads per digit");
+    __shared__ uint32_t warp_sums[32];
+    const int d = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const int per = (G + 3) / 4;
+    const int lo = min(G, q * per), hi = min(G, lo + per);
+    uint32_t *row = a + (int64_t)d * G;
+    uint32_t sum = 0;
+    for (int b = lo; b < hi; ++b) sum += row[b];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(sum, warp_sums, &total);
+    for (int b = lo; b < hi; ++b) {
+        const uint32_t t = row[b];
+        row[b] = run;
         run += t;
     }
 }
@@ -90,9 +119,13 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
                                                            uint32_t *__restrict__ vals_out, const int64_t *d_count,
                                                            int64_t cap, int shift, uint32_t mask,
                                                            const uint32_t *__restrict__ offsets) {
-    __shared__ uint32_t s_run[RADIX];
-    __shared__ uint32_t s_tot[RADIX];
+    __shared__ uint32_t s_run[RADIX];   // global start of this block's next run per digit
+    __shared__ uint32_t s_tot[RADIX];   // tile count per digit
+    __shared__ uint32_t s_loc[RADIX];   // tile-local start per digit
     __shared__ uint32_t s_wcnt[RS_WARPS][RADIX];
+    __shared__ uint32_t s_k[RS_TILE];
+    __shared__ uint32_t s_v[RS_TILE];
+    __shared__ uint32_t s_warp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) s_run[d] = offsets[(int64_t)d * gridDim.x + blockIdx.x];
@@ -100,16 +133,19 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     int64_t begin, end;
     block_range(count, gridDim.x, blockIdx.x, begin, end);
     for (int64_t base = begin; base < end; base += RS_TILE) {
+        const int n_tile = (int)min((int64_t)RS_TILE, end - base);
         for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&s_wcnt[0][0])[i] = 0u;
         __syncthreads();
+        // rank every item among the items of its digit in this tile (stable:
+        // warp-major, then round, then lane = item order)
         uint32_t k[RS_ITEMS], v[RS_ITEMS], lr[RS_ITEMS];
         int dg[RS_ITEMS];
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
-            const int64_t idx = base + (int64_t)warp * 32 * RS_ITEMS + r * 32 + lane;
-            const bool valid = idx < end;
-            k[r] = valid ? keys_in[idx] : 0u;
-            v[r] = valid ? vals_in[idx] : 0u;
+            const int li = warp * 32 * RS_ITEMS + r * 32 + lane;
+            const bool valid = li < n_tile;
+            k[r] = valid ? keys_in[base + li] : 0u;
+            v[r] = valid ? vals_in[base + li] : 0u;
             const int d = valid ? (int)((k[r] >> shift) & mask) : RADIX + lane;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const uint32_t rank = __popc(peers & lt_mask);
@@ -122,6 +158,8 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             dg[r] = d;
         }
         __syncthreads();
+        // per digit: exclusive prefix across warps and the tile total
+        uint32_t tot = 0;
         for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) {
             uint32_t run = 0;
 #pragma unroll
@@ -131,15 +169,30 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
                 run += c;
             }
             s_tot[d] = run;
+            tot = run;
         }
+        // tile-local digit starts (RS_THREADS == RADIX: thread d owns digit d)
+        uint32_t all;
+        const uint32_t loc = block_exclusive_scan(tot, s_warp, &all);
+        s_loc[threadIdx.x] = loc;
         __syncthreads();
+        // reorder the tile by digit in shared memory
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
             if (dg[r] < RADIX) {
-                const uint32_t pos = s_run[dg[r]] + s_wcnt[warp][dg[r]] + lr[r];
-                keys_out[pos] = k[r];
-                vals_out[pos] = v[r];
+                const uint32_t lp = s_loc[dg[r]] + s_wcnt[warp][dg[r]] + lr[r];
+                s_k[lp] = k[r];
+                s_v[lp] = v[r];
             }
+        }
+        __syncthreads();
+        // write out: consecutive items of one digit go to consecutive addresses
+        for (int i = threadIdx.x; i < n_tile; i += RS_THREADS) {
+            const uint32_t key = s_k[i];
+            const uint32_t d = (key >> shift) & mask;
+            const uint32_t pos = s_run[d] + (uint32_t)i - s_loc[d];
+            keys_out[pos] = key;
+            vals_out[pos] = s_v[i];
         }
         __syncthreads();
         for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) s_run[d] += s_tot[d];
@@ -166,7 +219,7 @@ int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int
         const uint32_t mask = (1u << nb) - 1u;
         uint32_t *ki = cur ? kb : ka, *vi = cur ? vb : va, *ko = cur ? ka : kb, *vo = cur ? va : vb;
         rs_upsweep<<<G, RS_THREADS, 0, stream>>>(ki, d_count, cap, shift, mask, counts);
-        rs_scan<<<1, SCAN_THREADS, 0, stream>>>(counts, RADIX * G);
+        rs_scan<<<1, SCAN_THREADS, 0, stream>>>(counts, G);
         rs_downsweep<<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts);
         cur ^= 1;
     }
@@ -204,28 +257,41 @@ __global__ void __launch_bounds__(RS_THREADS) count_reduce(const int32_t *__rest
     }
 }
 
-// Exclusive scan of the block sums (one block); writes the total pair count
-// and the count the pair sort will use (0 when over capacity).
-__global__ void count_top(unsigned long long *block_sums, int G, int64_t cap, int64_t *dev_pair_count,
-                          int64_t *sort_count, int32_t *dev_status) {
-    if (threadIdx.x != 0) return;
-    unsigned long long run = 0;
-    for (int b = 0; b < G; ++b) {
-        const unsigned long long t = block_sums[b];
-        block_sums[b] = run;
-        run += t;
+// Exclusive scan of the block sums (one block of SCAN_THREADS, G <= RS_MAX_BLOCKS);
+// writes the total pair count and the count the pair sort will use (0 when
+// over capacity).
+__global__ void __launch_bounds__(SCAN_THREADS) count_top(unsigned long long *block_sums, int G, int64_t cap,
+                                                          int64_t *dev_pair_count, int64_t *sort_count,
+                                                          int32_t *dev_status) {
+    __shared__ unsigned long long s[SCAN_THREADS];
+    const unsigned long long x = threadIdx.x < G ? block_sums[threadIdx.x] : 0ull;
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        const unsigned long long y = threadIdx.x >= off ? s[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        s[threadIdx.x] += y;
+        __syncthreads();
     }
-    *dev_pair_count = (int64_t)run;
-    if ((int64_t)run > cap) {
-        set_status(dev_status, GS_ERR_CAPACITY);
-        *sort_count = 0;
-    } else {
-        *sort_count = (int64_t)run;
+    if (threadIdx.x < G) block_sums[threadIdx.x] = s[threadIdx.x] - x;
+    if (threadIdx.x == SCAN_THREADS - 1) {
+        const unsigned long long run = s[threadIdx.x];
+        *dev_pair_count = (int64_t)run;
+        if ((int64_t)run > cap) {
+            set_status(dev_status, GS_ERR_CAPACITY);
+            *sort_count = 0;
+        } else {
+            *sort_count = (int64_t)run;
+        }
     }
 }
 
-// Scan phase fused with pair emission: every entry, in depth order, writes
-// one (tile id, Gaussian index) pair per tile of its rectangle, row-major.
+// Scan phase fused with pair emission.  Each block takes its range of
+// entries in depth order, RS_THREADS at a time: a block scan gives every
+// entry's first pair slot, then the block writes all pairs of those entries
+// cooperatively (thread i writes pair i, i + RS_THREADS, ...), finding the
+// owning entry by binary search over the scanned counts, so the writes are
+// contiguous.  Within an entry the tiles are row-major.
 __global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restrict__ touched,
                                                          const int4 *__restrict__ rect,
                                                          const uint32_t *__restrict__ order, int64_t total,
@@ -234,53 +300,75 @@ __global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restri
                                                          const int64_t *sort_count, uint32_t *__restrict__ pkeys,
                                                          uint32_t *__restrict__ pvals) {
     if (*sort_count == 0) return;  // nothing to emit, or over capacity
-    __shared__ unsigned long long s_scan[RS_THREADS];
+    __shared__ uint32_t s_incl[RS_THREADS];
+    __shared__ int s_x0[RS_THREADS], s_y0[RS_THREADS], s_w[RS_THREADS], s_base[RS_THREADS], s_tx[RS_THREADS];
+    __shared__ uint32_t s_gi[RS_THREADS];
+    __shared__ uint32_t s_warp[32];
     int64_t begin, end;
     block_range(total, gridDim.x, blockIdx.x, begin, end);
-    unsigned long long run = block_offsets[blockIdx.x];
-    for (int64_t base = begin; base < end; base += RS_THREADS) {
-        const int64_t m = base + threadIdx.x;
-        uint32_t e = 0;
-        unsigned long long c = 0;
+    uint64_t run = block_offsets[blockIdx.x];
+    for (int64_t b0 = begin; b0 < end; b0 += RS_THREADS) {
+        const int64_t m = b0 + threadIdx.x;
+        uint32_t c = 0;
         if (m < end) {
-            e = order[m];
-            c = (unsigned)touched[e];
+            const uint32_t e = order[m];
+            c = (uint32_t)touched[e];
+            if (c > 0) {
+                const int64_t v = (int64_t)e / n;
+                const int4 r = rect[e];
+                const gs_camera &cam = cams[v];
+                s_x0[threadIdx.x] = r.x;
+                s_y0[threadIdx.x] = r.y;
+                s_w[threadIdx.x] = r.z - r.x + 1;
+                s_tx[threadIdx.x] = (cam.width + tile - 1) / tile;
+                s_base[threadIdx.x] = cam.tile_offset;
+                s_gi[threadIdx.x] = (uint32_t)((int64_t)e - v * n);
+            }
         }
-        s_scan[threadIdx.x] = c;
+        uint32_t chunk_total;
+        const uint32_t excl = block_exclusive_scan(c, s_warp, &chunk_total);
+        s_incl[threadIdx.x] = excl + c;
         __syncthreads();
-        for (int off = 1; off < RS_THREADS; off <<= 1) {
-            const unsigned long long t = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0ull;
-            __syncthreads();
-            s_scan[threadIdx.x] += t;
-            __syncthreads();
+        for (uint32_t idx = threadIdx.x; idx < chunk_total; idx += RS_THREADS) {
+            // owner: first j with s_incl[j] > idx
+            int lo = 0, hi = RS_THREADS - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_incl[mid] > idx) hi = mid; else lo = mid + 1;
+            }
+            const uint32_t kk = idx - (lo > 0 ? s_incl[lo - 1] : 0u);
+            const int w = s_w[lo];
+            const int ty = s_y0[lo] + (int)(kk / (uint32_t)w), tx = s_x0[lo] + (int)(kk % (uint32_t)w);
+            pkeys[run + idx] = (uint32_t)(s_base[lo] + ty * s_tx[lo] + tx);
+            pvals[run + idx] = s_gi[lo];
         }
-        const unsigned long long incl = s_scan[threadIdx.x];
-        const unsigned long long tile_total = s_scan[RS_THREADS - 1];
-        if (c > 0) {
-            uint64_t off = run + incl - c;
-            const int64_t v = (int64_t)e / n;
-            const uint32_t gi = (uint32_t)((int64_t)e - v * n);
-            const gs_camera &cam = cams[v];
-            const int tiles_x = (cam.width + tile - 1) / tile;
-            const int4 r = rect[e];
-            for (int ty = r.y; ty <= r.w; ++ty)
-                for (int tx = r.x; tx <= r.z; ++tx) {
-                    pkeys[off] = (uint32_t)(cam.tile_offset + ty * tiles_x + tx);
-                    pvals[off] = gi;
-                    ++off;
-                }
-        }
-        run += tile_total;
+        run += chunk_total;
         __syncthreads();
     }
 }
 
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const int64_t *sort_count, uint2 *__restrict__ ranges) {
     const int64_t count = *sort_count;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-        if (i == count - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * c < count; c += stride) {
+        const int64_t i0 = 4 * c;
+        uint32_t k[6];
+        k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+        if (i0 + 4 <= count) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(keys + i0);
+            k[1] = q.x; k[2] = q.y; k[3] = q.z; k[4] = q.w;
+        } else {
+            for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < count ? keys[i0 + j] : 0xffffffffu;
+        }
+        k[5] = i0 + 4 < count ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = i0 + j;
+            if (i >= count) break;
+            const uint32_t t = k[1 + j];
+            if (k[j] != t || i == 0) ranges[t].x = (uint32_t)i;
+            if (k[2 + j] != t || i == count - 1) ranges[t].y = (uint32_t)(i + 1);
+        }
     }
 }
 
@@ -383,7 +471,8 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     // 2. pair offsets in depth order, fused pair emission
     const int G = rs_blocks(total);
     count_reduce<<<G, RS_THREADS, 0, stream>>>(proj->tiles_touched, order, total, w.block_sums);
-    count_top<<<1, 32, 0, stream>>>(w.block_sums, G, pair_capacity, dev_pair_count, w.sort_count, dev_status);
+    count_top<<<1, SCAN_THREADS, 0, stream>>>(w.block_sums, G, pair_capacity, dev_pair_count, w.sort_count,
+                                             dev_status);
     // The final pass must land in (pk[0], vals): emit into the buffer that an
     // even or odd number of passes maps there.
     const int tbits = bits_for(total_tiles);

@@ -11,9 +11,31 @@ using namespace gsr;
 struct gs_graph_s {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    int64_t kernels_main;  // kernel nodes outside conditional bodies
+    int64_t kernels_body;  // kernel nodes inside IF bodies
 };
 
 namespace {
+
+// IF bodies created by gs_graph_if_begin while a capture is open on this thread.
+thread_local cudaGraph_t t_bodies[8];
+thread_local int t_n_bodies = 0;
+
+int64_t count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    cudaGraphNode_t *nodes = new (std::nothrow) cudaGraphNode_t[n];
+    if (!nodes) return -1;
+    int64_t k = 0;
+    if (cudaGraphGetNodes(g, nodes, &n) == cudaSuccess) {
+        for (size_t i = 0; i < n; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+        }
+    }
+    delete[] nodes;
+    return k;
+}
 
 __global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t *iter, int n, int32_t *view_ids,
                                     const gs_camera *pose_src, gs_camera *slots) {
@@ -37,6 +59,7 @@ extern "C" {
 
 gs_status gs_graph_begin(cudaStream_t stream) {
     if (!stream) return GS_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+    t_n_bodies = 0;
     GS_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
     return GS_OK;
 }
@@ -69,6 +92,7 @@ gs_status gs_graph_if_begin(cudaStream_t stream, cudaGraphConditionalHandle cond
     GS_TRY(cudaGraphAddNode(&node, graph, deps, edata, ndeps, &params));
     GS_TRY(cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaGraph_t body = params.conditional.phGraph_out[0];
+    if (t_n_bodies < 8) t_bodies[t_n_bodies++] = body;
     GS_TRY(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     return GS_OK;
 }
@@ -89,13 +113,23 @@ gs_status gs_graph_end(cudaStream_t stream, gs_graph *out) {
         cudaGraphDestroy(graph);
         return GS_ERR_CUDA;
     }
-    gs_graph_s *g = new (std::nothrow) gs_graph_s{graph, exec};
+    int64_t kb = 0;
+    for (int i = 0; i < t_n_bodies; ++i) kb += count_kernel_nodes(t_bodies[i]);
+    t_n_bodies = 0;
+    gs_graph_s *g = new (std::nothrow) gs_graph_s{graph, exec, count_kernel_nodes(graph), kb};
     if (!g) {
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
         return GS_ERR_CUDA;
     }
     *out = g;
+    return GS_OK;
+}
+
+gs_status gs_graph_kernel_counts(gs_graph graph, int64_t *out2) {
+    if (!graph || !out2) return GS_ERR_INVALID_ARG;
+    out2[0] = graph->kernels_main;
+    out2[1] = graph->kernels_body;
     return GS_OK;
 }
 

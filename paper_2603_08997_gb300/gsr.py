@@ -96,6 +96,7 @@ _PROTOS = {
     "gs_graph_if_end": (C.c_int, [_S, _S]),
     "gs_graph_end": (C.c_int, [_S, C.POINTER(C.c_void_p)]),
     "gs_graph_launch": (C.c_int, [C.c_void_p, _S]),
+    "gs_graph_kernel_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "gs_graph_destroy": (C.c_int, [C.c_void_p]),
     "gs_select_views": (C.c_int, [_P, _I64, _P, _I32, _P, _P, _P, _S]),
 }

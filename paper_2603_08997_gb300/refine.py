@@ -100,6 +100,9 @@ class RefinementLoop:
             code = gsr.lib().gs_graph_end(hs, C.byref(g))
         gsr.check("gs_graph_end", code)
         self.graph = g
+        kc = (C.c_int64 * 2)()
+        gsr.call("gs_graph_kernel_counts", self.graph, kc)
+        self.kernels_per_step = (int(kc[0]), int(kc[1]))
 
     def step_graph(self) -> None:
         if self.graph is None:
@@ -120,6 +123,25 @@ class RefinementLoop:
             self.adam.v.zero_()
             self.adam.grad.zero_()
             self.adam.step_count.zero_()
+            self.iter.zero_()
+        self.gate.reset(self.stream)
+
+    def snapshot(self) -> dict:
+        """Parameters and optimizer state (device copies)."""
+        torch.cuda.synchronize()
+        return dict(flat=self.model.flat.clone(), m=self.adam.m.clone(), v=self.adam.v.clone(),
+                    step=self.adam.step_count.clone())
+
+    def restore(self, snap: dict) -> None:
+        """Continue from a snapshot: parameters and Adam state as saved, the gate
+        empty and the iteration counter at 0 (the start of a post-densification
+        phase)."""
+        with torch.cuda.stream(self.stream):
+            self.model.flat.copy_(snap["flat"])
+            self.adam.m.copy_(snap["m"])
+            self.adam.v.copy_(snap["v"])
+            self.adam.step_count.copy_(snap["step"])
+            self.adam.grad.zero_()
             self.iter.zero_()
         self.gate.reset(self.stream)
 

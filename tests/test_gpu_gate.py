@@ -27,9 +27,17 @@ def _run_gpu(cfg: GateConfig, views, losses, per_call=1):
     return g.cpu().numpy().astype(int), gate.read(), int(gate.status.item())
 
 
-def _run_oracle(cfg, views, losses):
+def _run_oracle(cfg, views, losses, per_call=1):
+    """Reading (vii) of the oracle gate: the losses of one launch are decided in
+    order, each its own t, against the EMA as it stood before the launch; the
+    EMA updates follow in order."""
     og = OGate(cfg)
-    gs = [og.step(int(v), float(np.float32(L))) for v, L in zip(views, losses)]
+    gs = []
+    for k in range(0, len(views), per_call):
+        items = [(int(v), float(np.float32(L))) for v, L in zip(views[k:k + per_call], losses[k:k + per_call])]
+        gs += [og.decide(v, L) for v, L in items]
+        for v, L in items:
+            og.update(v, L)
     return np.array(gs), og
 
 
@@ -44,7 +52,7 @@ def test_random_sequences_bit_exact(seed, per_call):
     # slowly decreasing losses with noise: the regime where the gate skips
     losses = (np.exp(rng.normal(0, 0.05, T)) * np.linspace(0.3, 0.2, T)).astype(np.float32)
     g_gpu, st, status = _run_gpu(cfg, views, losses, per_call)
-    g_orc, og = _run_oracle(cfg, views, losses)
+    g_orc, og = _run_oracle(cfg, views, losses, per_call)
     assert status == 0
     assert np.array_equal(g_gpu, g_orc)
     assert (st["t"], st["b"], st["n_w"], st["n_w1"]) == (og.t, og.b, og.n_w, og.n_w1)

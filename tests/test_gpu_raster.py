@@ -121,7 +121,9 @@ def test_render_end_to_end_c1(tile):
     r.forward(model.c_params())
     torch.cuda.synchronize()
     assert int(r.status.item()) == 0
-    o = oracle.forward(scene, cam, oracle.RasterConfig(tile=tile))
+    # end to end, the projection's float32 rounding moves alphas by up to ~1e-4
+    # relative for ill-conditioned footprints: flag pixels within that of a cut-off
+    o = oracle.forward(scene, cam, oracle.RasterConfig(tile=tile), margin_rel=1e-4)
     _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])
 
 
@@ -148,9 +150,15 @@ def test_projection_c2_like():
     Qo = o["conic"][vis]
     err = np.linalg.norm(Q - Qo, axis=1) / np.linalg.norm(Qo, axis=1)
     assert np.median(err) < 1e-6 and err.max() < 1e-3
-    # the GPU rectangle contains the oracle's
-    gr, orr = rect[vis], o["rect"][vis]
-    assert ((gr[:, 0] <= orr[:, 0]) & (gr[:, 1] <= orr[:, 1]) & (gr[:, 2] >= orr[:, 2]) & (gr[:, 3] >= orr[:, 3])).all()
+    # the GPU rectangle contains the exact support square (the oracle's radius
+    # before the oracle's own inflation, r -> 1.001 r + 0.01)
+    r_ex = (o["radius"][vis] - 0.01) / 1.001
+    m = o["mean2d"][vis]
+    ex = np.stack([np.maximum(np.ceil(m[:, 0] - r_ex - 0.5), 0) // 16, np.maximum(np.ceil(m[:, 1] - r_ex - 0.5), 0) // 16,
+                   np.minimum(np.floor(m[:, 0] + r_ex - 0.5), cam.width - 1) // 16,
+                   np.minimum(np.floor(m[:, 1] + r_ex - 0.5), cam.height - 1) // 16], 1)
+    gr = rect[vis]
+    assert ((gr[:, 0] <= ex[:, 0]) & (gr[:, 1] <= ex[:, 1]) & (gr[:, 2] >= ex[:, 2]) & (gr[:, 3] >= ex[:, 3])).all()
 
 
 def test_render_end_to_end_c2_like():
@@ -159,7 +167,5 @@ def test_render_end_to_end_c2_like():
     model = raster.GaussianModel.from_scene(scene)
     r.forward(model.c_params())
     torch.cuda.synchronize()
-    o = oracle.forward(scene, cam, oracle.RasterConfig())
-    img = r.image_of(0).cpu().numpy()
-    rel = gpu_util.rel_err(img, o["image"])
-    assert rel < 1e-5, rel
+    o = oracle.forward(scene, cam, oracle.RasterConfig(), margin_rel=1e-4)
+    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])

@@ -151,3 +151,20 @@ def test_exhaustive_tiny_orderings():
             assert gs[:2].all()
             for t in range(1, 7):
                 assert bs[t - 1] >= gate.rho_min * t - 1 - 1e-12
+
+
+def test_batch_reading_equals_sequential_for_distinct_views():
+    """Reading (vii): a launch's losses are decided against the EMA from before
+    the launch; with distinct views in each launch that is the sequential
+    algorithm exactly."""
+    rng = np.random.default_rng(5)
+    cfg = GateConfig(W=6, beta=0.9, eps=1e-8, rho_lo=0.5, n_views=8)
+    seq_gate, batch_gate = Gate(cfg), Gate(cfg)
+    for _ in range(60):
+        views = rng.permutation(8)[:4]
+        losses = rng.uniform(0.1, 1.0, 4)
+        g_seq = [seq_gate.step(int(v), float(L)) for v, L in zip(views, losses)]
+        g_bat = batch_gate.decide_batch(views, losses)
+        batch_gate.update_batch(views, losses)
+        assert g_seq == g_bat
+    assert seq_gate.state() == batch_gate.state()
