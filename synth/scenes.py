@@ -12,8 +12,12 @@ Workload recipes (all numpy ``default_rng(seed)``, float32 arrays):
   origin, 980x545, 60 degree horizontal field of view; target = render of a
   perturbed copy plus N(0,0.01) noise.
 * C3, refinement loop: ground truth = the C2 generator at N=3,000,000; start =
-  a perturbed copy (C2 perturbation x0.5); 200 cameras on a jittered ring at
-  1297x840; 5,000 iterations with views drawn uniformly with replacement.
+  a perturbed copy (C2 perturbation x0.2) that the caller first refines for
+  5,000 always-backward iterations (pre_sequence, a stand-in for the
+  densification phase, so the measured loop starts near its plateau as the
+  paper's post-densification phase does); 200 cameras on a jittered ring at
+  1297x840; 5,000 measured iterations with views drawn uniformly with
+  replacement.
 * C4: the C3 scene with 8 views per launch at resolutions drawn from
   {640x360, 980x545, 1297x840, 1600x1063}.
 * C5: N=6,000,000, four 1920x1080 views.
@@ -233,13 +237,18 @@ def case_c2(seed: int = 0, n: int = 200_000):
 
 
 def case_c3(seed: int = 0, n: int = 3_000_000, n_views: int = 200, n_iters: int = 5000,
-            width: int = 1297, height: int = 840):
+            width: int = 1297, height: int = 840, start_scale: float = 0.2):
     """Returns (ground-truth scene, start scene, cameras, view sequence)."""
     gt = scene_ball(n, seed, sh_degree=3, opacity_std=1.5)
-    start = perturb_scene(gt, seed + 1, 0.5)
+    start = perturb_scene(gt, seed + 1, start_scale)
     cams = ring_cameras(n_views, width, height, seed + 2)
     seq = view_sequence(n_iters, n_views, seed)
     return gt, start, cams, seq
+
+
+def pre_sequence(n_iters: int = 5000, n_views: int = 200, seed: int = 7) -> np.ndarray:
+    """View sequence of the refinement that precedes the measured loop."""
+    return view_sequence(n_iters, n_views, seed)
 
 
 C4_RESOLUTIONS = ((640, 360), (980, 545), (1297, 840), (1600, 1063))

@@ -146,3 +146,30 @@ def test_adam_against_oracle():
                       "sh": (o[4], o[4] + 3 * K * n)}.items():
         pad[a:b] = False
     assert float(model.flat[pad].abs().max().item()) == 0.0
+
+
+def test_autograd_function_matches_oracle():
+    """render() and photometric_loss() as torch.autograd.Functions: gradients of
+    the summed loss of two views against the oracle's."""
+    from paper_2603_08997_gb300 import autograd
+    gpu_util.lib()
+    scene, cam0 = synth.scene_tiny(60, seed=9, sh_degree=2)
+    cam1 = synth.camera_pinhole(28.0, 30.0, 20.0, 14.0, 40, 28)
+    views = raster.Views([cam0, cam1], 16)
+    r = raster.Renderer(scene.n, scene.sh_degree, views)
+    model = raster.GaussianModel.from_scene(scene)
+    rng = np.random.default_rng(1)
+    tg = [rng.uniform(0, 1, (3, c.height, c.width)) for c in (cam0, cam1)]
+    target = torch.from_numpy(np.concatenate([t.ravel() for t in tg]).astype(np.float32)).cuda()
+    flat = model.flat.clone().requires_grad_(True)
+    img = autograd.render(flat, model, r)
+    losses = autograd.photometric_loss(img, target, r)
+    losses.sum().backward()
+    torch.cuda.synchronize()
+    rc = oracle.RasterConfig()
+    og = None
+    for c, t in zip((cam0, cam1), tg):
+        f = oracle.forward(scene, c, rc)
+        L, dL = oracle.loss_and_grad(f["image"], t.astype(np.float32))
+        og = oracle.backward(scene, c, rc, f, dL, og)
+    _check_grads(gpu_util.gpu_grads(model, flat.grad), og)
