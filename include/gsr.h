@@ -182,6 +182,26 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
                       int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count,
                       int32_t *dev_status, cudaStream_t stream);
 
+/* gs_bin_sort without a caller-provided workspace, for callers that cannot
+ * allocate device memory: work issued while a CUDA graph is being captured
+ * (cudaMalloc cannot be captured), plugins whose host application owns all
+ * device memory, real-time loops that must not block on the allocator.  The
+ * paper has no counterpart; it is a deployment variant of gs_bin_sort.
+ * The scratch is a fixed array in the library's device memory (about 17 MB,
+ * on every GPU that loads the library, until the process exits), so the
+ * sizes are capped: n * n_views <= 262144 entries and pair_capacity <=
+ * 1048576 pairs; larger requests return GS_ERR_WORKSPACE and launch nothing.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array: calls that overlap on the GPU (different streams, or
+ * other threads) race and must be serialised by the caller.  Nothing in the
+ * array needs to start at zero: each call overwrites all scratch it reads.
+ * Other arguments, outputs and errors as gs_bin_sort. */
+gs_status gs_bin_sort_noalloc(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n,
+                              int64_t total_tiles, const gs_raster_config *cfg /* host */, uint64_t *keys,
+                              uint32_t *vals, int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count,
+                              int32_t *dev_status, cudaStream_t stream);
+
 /* --------------------------------------------------------------- forward */
 
 /* Eq. (blend) and Eq. (alpha): per tile, Gaussians staged `batch` at a time in

@@ -500,3 +500,51 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// gs_bin_sort_noalloc: gs_bin_sort with its scratch in a fixed device array.
+//
+// For callers that cannot allocate device memory: code that issues its work
+// while a CUDA graph is being captured (cudaMalloc cannot be captured),
+// plugins whose host application owns all device memory through its own
+// pool, and real-time loops that must not block on the allocator.  The
+// caller still owns and passes every input and output; only the scratch
+// comes from here.
+namespace {
+
+constexpr int64_t kNoAllocMaxEntries = (int64_t)1 << 18;  // n * n_views
+constexpr int64_t kNoAllocMaxPairs = (int64_t)1 << 20;    // pair_capacity
+
+// Size of the gs_bin_sort workspace at the limits above (same layout as
+// bin_ws_layout: each buffer rounded up to 256 bytes).
+constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNoAllocBytes = 4 * al256(4 * (size_t)kNoAllocMaxEntries) + 3 * al256(4 * (size_t)kNoAllocMaxPairs) +
+                                 al256(4 * (size_t)RADIX * RS_MAX_BLOCKS) + al256(8 * (size_t)RS_MAX_BLOCKS) + al256(8);
+
+// One copy per device that loads the library, held until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
+                                         int64_t total_tiles, const gs_raster_config *cfg, uint64_t *keys,
+                                         uint32_t *vals, int64_t pair_capacity, uint32_t *ranges,
+                                         int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
+    if (n < 0 || n_views <= 0 || pair_capacity < 0) return GS_ERR_INVALID_ARG;
+    if (n * n_views > kNoAllocMaxEntries || pair_capacity > kNoAllocMaxPairs) return GS_ERR_WORKSPACE;
+    int dev = 0;
+    GS_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
+    if (!g_noalloc_ptr[dev]) {
+        // Host code cannot use the array's name as a device address: look the
+        // address up once per device, with that device current.
+        void *p = nullptr;
+        GS_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    return gs_bin_sort(proj, cams, n_views, n, total_tiles, cfg, g_noalloc_ptr[dev], kNoAllocBytes, keys, vals,
+                       pair_capacity, ranges, dev_pair_count, dev_status, stream);
+}

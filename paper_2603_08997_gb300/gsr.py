@@ -76,6 +76,8 @@ _PROTOS = {
     "gs_bin_sort_workspace_size": (C.c_size_t, [_I64, _I32, _I64, _I64]),
     "gs_bin_sort": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, C.POINTER(gs_raster_config), _P, _SZ,
                               _P, _P, _I64, _P, _P, _P, _S]),
+    "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, C.POINTER(gs_raster_config),
+                                      _P, _P, _I64, _P, _P, _P, _S]),
     "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                 _P, gs_fwd_saved, _P, _S]),
     "gs_loss_workspace_size": (C.c_size_t, [C.POINTER(gs_camera), _I32]),
