@@ -262,6 +262,7 @@ gs_status gs_render_bwd(const gs_params *params /* host */, const gs_projected *
                         size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream);
 
 /* ----------------------------------------------------------------- Adam */
+/* (gs_adam_config and gs_adam_step below; gs_render_bwd_adam after them.) */
 
 /* Adam (Kingma & Ba, bias-corrected), the optimizer step of Algorithm 1.
  * lr[6]: means, log_scales, quats, opacity, SH DC, SH higher bands. */
@@ -278,6 +279,20 @@ typedef struct {
 gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t n, int32_t sh_degree,
                        const gs_adam_config *cfg /* host */, const int32_t *dev_do_step, int64_t *dev_step,
                        int32_t zero_grad, cudaStream_t stream);
+
+/* The backward pass and the optimizer step of Algorithm 1 in one call: the
+ * adjoint of gs_render_bwd, after which every parameter of the flat buffer
+ * (gs_param_layout; quats, m and v 16-byte aligned) takes one Adam step with
+ * the gradient just computed, without storing the gradient.  Equal to
+ * gs_render_bwd (accumulate = 0) followed by gs_adam_step; dev_do_step and
+ * dev_step as in gs_adam_step, view_gate as in gs_render_bwd. */
+gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                             const gs_projected *proj /* host */, const uint32_t *vals, const uint32_t *ranges,
+                             const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                             const gs_raster_config *cfg /* host */, gs_fwd_saved saved, const float *dL_dimage,
+                             const uint8_t *view_gate, const gs_adam_config *adam /* host */,
+                             const int32_t *dev_do_step, int64_t *dev_step, void *workspace, size_t workspace_bytes,
+                             int32_t *dev_status, cudaStream_t stream);
 
 /* ----------------------------------------------------------- SkipGS gate */
 

@@ -134,7 +134,7 @@ def sh_basis(deg: int, d) -> tuple:
 def project(scene, cam, rc: RasterConfig) -> dict:
     n, K = scene.n, scene.sh.shape[1]
     out = dict(mean2d=np.zeros((n, 2)), cov2d=np.zeros((n, 3)), conic=np.zeros((n, 3)),
-               depth=np.zeros(n), rgb=np.zeros((n, 3)), opacity=np.zeros(n), radius=np.zeros(n),
+               depth=np.zeros(n), rgb=np.zeros((n, 3)), opacity=np.zeros(n), radius=np.zeros((n, 2)),
                rect=np.zeros((n, 4), np.int32), touched=np.zeros(n, np.int32),
                flags=np.zeros(n, np.int32))
     cs, rs = camera_struct(cam), rc.struct()

@@ -181,7 +181,7 @@ typedef struct {
     double Y[16];
     double pre[3];        /* colour before the clamp at 0 */
     double rgb[3];
-    double radius;
+    double radius, radius_x, radius_y;
     int rect[4];          /* tile x0, y0, x1, y1 (inclusive) */
     int touched;
 } orc_gauss;
@@ -270,20 +270,22 @@ static void project_one(const double *mu, const double *log_s, const double *q, 
         g->rgb[ch] = g->pre[ch] > 0.0 ? g->pre[ch] : 0.0;
     }
     /* Reading R2: a pixel can only receive alpha' >= 1/255 if o >= 1/255, and
-     * only inside |dp| <= r with r^2 = 2 lambda_max ln(255 o), because
-     * dp^T Q dp >= |dp|^2 / lambda_max(Sigma2D).  The tile rectangle covers
-     * every pixel centre (i + 0.5) with |dp_x|, |dp_y| <= r. */
+     * only inside the ellipse dp^T Q dp <= c with c = 2 ln(255 o); its
+     * axis-aligned extents are sqrt(c Sigma2D_xx) and sqrt(c Sigma2D_yy) (the
+     * support function of an ellipse).  The tile rectangle covers every pixel
+     * centre (i + 0.5) inside those extents. */
     if (g->o < rc->alpha_min) { g->culled = 1; return; }
-    const double mid = 0.5 * (g->cov[0] + g->cov[2]);
-    const double hd = 0.5 * (g->cov[0] - g->cov[2]);
-    const double lmax = mid + sqrt(hd * hd + g->cov[1] * g->cov[1]);
-    g->radius = sqrt(2.0 * lmax * log(g->o / rc->alpha_min));
+    const double cth = 2.0 * log(g->o / rc->alpha_min);
+    g->radius_x = sqrt(cth * g->cov[0]);
+    g->radius_y = sqrt(cth * g->cov[2]);
     /* The rectangle may be any superset of the support (no pixel depends on
      * it); a slight inflation keeps every pair whose alpha' lies near the
      * cut-off in the tile lists, where the margin flags of orc_render see it. */
-    g->radius = g->radius * 1.001 + 0.01;
-    double fx0 = ceil(g->mean2d[0] - g->radius - 0.5), fx1 = floor(g->mean2d[0] + g->radius - 0.5);
-    double fy0 = ceil(g->mean2d[1] - g->radius - 0.5), fy1 = floor(g->mean2d[1] + g->radius - 0.5);
+    g->radius_x = g->radius_x * 1.001 + 0.01;
+    g->radius_y = g->radius_y * 1.001 + 0.01;
+    g->radius = g->radius_x > g->radius_y ? g->radius_x : g->radius_y;
+    double fx0 = ceil(g->mean2d[0] - g->radius_x - 0.5), fx1 = floor(g->mean2d[0] + g->radius_x - 0.5);
+    double fy0 = ceil(g->mean2d[1] - g->radius_y - 0.5), fy1 = floor(g->mean2d[1] + g->radius_y - 0.5);
     if (fx0 < 0.0) fx0 = 0.0;
     if (fy0 < 0.0) fy0 = 0.0;
     if (fx1 > cam->width - 1) fx1 = cam->width - 1;
@@ -296,7 +298,8 @@ static void project_one(const double *mu, const double *log_s, const double *q, 
 }
 
 /* Projection of n Gaussians for one camera.  Outputs (per Gaussian):
- * mean2d[2], cov2d[3], conic[3], depth, rgb[3], opacity, radius, rect[4],
+ * mean2d[2], cov2d[3], conic[3], depth, rgb[3], opacity, radius[2] (x and y
+ * extents of the support before clipping to the image), rect[4],
  * touched (0 = culled), flags (bit0/1: x/y frustum clamp of J active,
  * bits2-4: colour channel clamped at 0, bit5: culled). */
 void orc_project(int64_t n, int K, const double *means, const double *log_scales,
@@ -317,7 +320,8 @@ void orc_project(int64_t n, int K, const double *means, const double *log_scales
         }
         depth[i] = g.p[2];
         opacity[i] = g.o;
-        radius[i] = g.culled ? 0.0 : g.radius;
+        radius[2 * i] = g.culled ? 0.0 : g.radius_x;
+        radius[2 * i + 1] = g.culled ? 0.0 : g.radius_y;
         int fl = 0;
         if (g.clamp_x) fl |= 1;
         if (g.clamp_y) fl |= 2;

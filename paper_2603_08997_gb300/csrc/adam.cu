@@ -26,16 +26,10 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     if (do_step && *do_step == 0) return;
     __shared__ float s_lr[6];
     __shared__ float s_ibc2;
-    if (threadIdx.x == 0) {
-        const double t = (double)(*step + 1);
-        const double bc1 = 1.0 - pow((double)cfg.beta1, t);
-        const double bc2 = 1.0 - pow((double)cfg.beta2, t);
-        for (int k = 0; k < 6; ++k) s_lr[k] = (float)((double)cfg.lr[k] / bc1);
-        s_ibc2 = (float)(1.0 / sqrt(bc2));
-    }
+    if (threadIdx.x == 0) adam_scalars(cfg, *step, s_lr, &s_ibc2);
     __syncthreads();
     const float b1 = cfg.beta1, b2 = cfg.beta2, eps = cfg.eps;
-    const float ib1 = 1.f - b1, ib2 = 1.f - b2, ibc2 = s_ibc2;
+    const float ibc2 = s_ibc2;
     const int64_t nvec = G.total / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nvec; c += stride) {
@@ -46,12 +40,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
         float *pe = &pp.x, *me = &mm.x, *ve = &vv.x;
         const float *ge = &gg.x;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float lr = s_lr[group_of(4 * c + u, G)];
-            me[u] = b1 * me[u] + ib1 * ge[u];
-            ve[u] = b2 * ve[u] + ib2 * ge[u] * ge[u];
-            pe[u] -= lr * me[u] / (sqrtf(ve[u]) * ibc2 + eps);
-        }
+        for (int u = 0; u < 4; ++u) adam_update(pe[u], me[u], ve[u], ge[u], s_lr[group_of(4 * c + u, G)], b1, b2, ibc2, eps);
         reinterpret_cast<float4 *>(p)[c] = pp;
         reinterpret_cast<float4 *>(m)[c] = mm;
         reinterpret_cast<float4 *>(v)[c] = vv;
@@ -59,13 +48,11 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     }
     // scalar tail
     for (int64_t e = 4 * nvec + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < G.total; e += stride) {
-        const float lr = s_lr[group_of(e, G)];
-        const float ge = g[e];
-        const float me = b1 * m[e] + ib1 * ge;
-        const float ve = b2 * v[e] + ib2 * ge * ge;
+        float pe = p[e], me = m[e], ve = v[e];
+        adam_update(pe, me, ve, g[e], s_lr[group_of(e, G)], b1, b2, ibc2, eps);
+        p[e] = pe;
         m[e] = me;
         v[e] = ve;
-        p[e] -= lr * me / (sqrtf(ve) * ibc2 + eps);
         if (zero_grad) g[e] = 0.f;
     }
 }

@@ -34,6 +34,7 @@ constexpr int RS_MAX_BLOCKS = 608;  // 4 x 152 SMs
 constexpr int SCAN_THREADS = 1024;
 static_assert(RS_THREADS == RADIX, "the downsweep gives each thread one digit");
 static_assert(RS_MAX_BLOCKS <= SCAN_THREADS, "count_top scans the block sums in one pass");
+static_assert(RS_MAX_BLOCKS <= 4 * RS_THREADS, "rs_scan holds at most four counts per thread");
 
 __device__ __forceinline__ int64_t effective_count(const int64_t *d_count, int64_t cap) {
     if (!d_count) return cap;
@@ -92,25 +93,25 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
     return before + inc - x;
 }
 
-// In-place exclusive scan of the digit-major counts [RADIX][G] by one block:
-// thread t = 4 d + q owns the q-th quarter of digit d's row, so a block scan
-// over the 1024 partial sums in thread order is the digit-major order.
-__global__ void __launch_bounds__(SCAN_THREADS) rs_scan(uint32_t *a, int G) {
-    static_assert(SCAN_THREADS == 4 * RADIX, "four threads per digit");
+// Digit offsets, part 1: block d scans row d of the digit-major counts
+// [RADIX][G] (exclusive, in place) and writes the row total.  The downsweep
+// adds each digit's base (exclusive scan of the totals) itself.
+__global__ void __launch_bounds__(RS_THREADS) rs_scan(uint32_t *a, int G, uint32_t *totals) {
     __shared__ uint32_t warp_sums[32];
-    const int d = threadIdx.x >> 2, q = threadIdx.x & 3;
-    const int per = (G + 3) / 4;
-    const int lo = min(G, q * per), hi = min(G, lo + per);
-    uint32_t *row = a + (int64_t)d * G;
+    uint32_t *row = a + (int64_t)blockIdx.x * G;
+    const int per = (G + RS_THREADS - 1) / RS_THREADS;
+    const int lo = min(G, (int)threadIdx.x * per), hi = min(G, lo + per);
+    uint32_t v[4] = {0u, 0u, 0u, 0u};  // per <= 4 (G <= RS_MAX_BLOCKS <= 4 * RS_THREADS)
     uint32_t sum = 0;
-    for (int b = lo; b < hi; ++b) sum += row[b];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (lo + j < hi) { v[j] = row[lo + j]; sum += v[j]; }
     uint32_t total;
     uint32_t run = block_exclusive_scan(sum, warp_sums, &total);
-    for (int b = lo; b < hi; ++b) {
-        const uint32_t t = row[b];
-        row[b] = run;
-        run += t;
-    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (lo + j < hi) { row[lo + j] = run; run += v[j]; }
+    if (threadIdx.x == 0) totals[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__restrict__ keys_in,
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
                                                            uint32_t *__restrict__ keys_out,
                                                            uint32_t *__restrict__ vals_out, const int64_t *d_count,
                                                            int64_t cap, int shift, uint32_t mask,
-                                                           const uint32_t *__restrict__ offsets) {
+                                                           const uint32_t *__restrict__ offsets,
+                                                           const uint32_t *__restrict__ totals) {
     __shared__ uint32_t s_run[RADIX];   // global start of this block's next run per digit
     __shared__ uint32_t s_tot[RADIX];   // tile count per digit
     __shared__ uint32_t s_loc[RADIX];   // tile-local start per digit
@@ -128,7 +130,12 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     __shared__ uint32_t s_warp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) s_run[d] = offsets[(int64_t)d * gridDim.x + blockIdx.x];
+    {
+        // digit base = exclusive scan of the digit totals (thread d owns digit d)
+        uint32_t all;
+        const uint32_t dbase = block_exclusive_scan(totals[threadIdx.x], s_warp, &all);
+        s_run[threadIdx.x] = dbase + offsets[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+    }
     const int64_t count = effective_count(d_count, cap);
     int64_t begin, end;
     block_range(count, gridDim.x, blockIdx.x, begin, end);
@@ -218,9 +225,10 @@ int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int
         const int nb = bits - shift < RADIX_BITS ? bits - shift : RADIX_BITS;
         const uint32_t mask = (1u << nb) - 1u;
         uint32_t *ki = cur ? kb : ka, *vi = cur ? vb : va, *ko = cur ? ka : kb, *vo = cur ? va : vb;
+        uint32_t *totals = counts + (size_t)RADIX * RS_MAX_BLOCKS;
         rs_upsweep<<<G, RS_THREADS, 0, stream>>>(ki, d_count, cap, shift, mask, counts);
-        rs_scan<<<1, SCAN_THREADS, 0, stream>>>(counts, G);
-        rs_downsweep<<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts);
+        rs_scan<<<RADIX, RS_THREADS, 0, stream>>>(counts, G, totals);
+        rs_downsweep<<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts, totals);
         cur ^= 1;
     }
     return cur;
@@ -393,7 +401,7 @@ int bits_for(int64_t values) {  // bits needed to represent 0 .. values-1
 struct BinWorkspace {
     uint32_t *dk[2], *dv[2];        // depth keys / entry ids, ping-pong, [V*N]
     uint32_t *pk[2], *pv;           // pair tile keys ping-pong [cap], pair values scratch [cap]
-    uint32_t *counts;               // [RADIX * RS_MAX_BLOCKS]
+    uint32_t *counts;               // [RADIX * RS_MAX_BLOCKS] + [RADIX] digit totals
     unsigned long long *block_sums; // [RS_MAX_BLOCKS]
     int64_t *sort_count;            // [1]
 };
@@ -417,7 +425,7 @@ size_t bin_ws_layout(int64_t total, int64_t cap, BinWorkspace *w, char *base) {
         if (w) w->pk[i] = (uint32_t *)a;
     }
     char *pv = take(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
-    char *counts = take(sizeof(uint32_t) * RADIX * RS_MAX_BLOCKS);
+    char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1));
     char *bs = take(sizeof(unsigned long long) * RS_MAX_BLOCKS);
     char *sc = take(sizeof(int64_t));
     if (w) {
@@ -519,7 +527,7 @@ constexpr int64_t kNoAllocMaxPairs = (int64_t)1 << 20;    // pair_capacity
 // bin_ws_layout: each buffer rounded up to 256 bytes).
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kNoAllocBytes = 4 * al256(4 * (size_t)kNoAllocMaxEntries) + 3 * al256(4 * (size_t)kNoAllocMaxPairs) +
-                                 al256(4 * (size_t)RADIX * RS_MAX_BLOCKS) + al256(8 * (size_t)RS_MAX_BLOCKS) + al256(8);
+                                 al256(4 * (size_t)RADIX * (RS_MAX_BLOCKS + 1)) + al256(8 * (size_t)RS_MAX_BLOCKS) + al256(8);
 
 // One copy per device that loads the library, held until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

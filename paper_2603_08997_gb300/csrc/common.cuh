@@ -37,6 +37,25 @@ __host__ __device__ inline void param_offsets(int64_t n, int sh_degree, int64_t 
     o[5] = al(o[4] + 3 * K * n);
 }
 
+// One Adam update of a scalar (Kingma & Ba, bias-corrected): lr_t = lr / (1 -
+// beta1^t), ibc2 = 1 / sqrt(1 - beta2^t).  Shared by the standalone optimizer
+// kernel and the fused adjoint + optimizer kernel so both round alike.
+__device__ __forceinline__ void adam_update(float &p, float &m, float &v, float g, float lr_t, float b1, float b2,
+                                            float ibc2, float eps) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= lr_t * m / (sqrtf(v) * ibc2 + eps);
+}
+
+// Per-step Adam scalars from the executed-step counter (computed once per block).
+__device__ __forceinline__ void adam_scalars(const gs_adam_config &cfg, int64_t executed, float *lr_t, float *ibc2) {
+    const double t = (double)(executed + 1);
+    const double bc1 = 1.0 - pow((double)cfg.beta1, t);
+    const double bc2 = 1.0 - pow((double)cfg.beta2, t);
+    for (int k = 0; k < 6; ++k) lr_t[k] = (float)((double)cfg.lr[k] / bc1);
+    *ibc2 = (float)(1.0 / sqrt(bc2));
+}
+
 // First error wins.
 __device__ inline void set_status(int32_t *st, int32_t code) {
     if (st) atomicCAS(st, 0, code);

@@ -31,16 +31,17 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
     float r = 0.f;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
     if (!culled) {
-        // Conservative support radius: alpha' >= alpha_min needs
-        // dp^T Q dp <= 2 ln(o / alpha_min), and dp^T Q dp >= |dp|^2 / lambda_max.
-        const float mid = 0.5f * (g.s00 + g.s11);
-        const float hd = 0.5f * (g.s00 - g.s11);
-        const float lmax = mid + sqrtf(hd * hd + g.s01 * g.s01);
-        r = sqrtf(2.f * lmax * logf(g.o / cfg.alpha_min)) * 1.0001f + 1e-3f;
-        const float fx0 = fmaxf(ceilf(g.mean2d[0] - r - 0.5f), 0.f);
-        const float fx1 = fminf(floorf(g.mean2d[0] + r - 0.5f), (float)(c.width - 1));
-        const float fy0 = fmaxf(ceilf(g.mean2d[1] - r - 0.5f), 0.f);
-        const float fy1 = fminf(floorf(g.mean2d[1] + r - 0.5f), (float)(c.height - 1));
+        // Support of alpha' >= alpha_min: the ellipse dp^T Q dp <= 2 ln(o / alpha_min).
+        // Its axis-aligned extents are sqrt(2 ln(o/alpha_min) Sigma2D_xx) and
+        // sqrt(2 ln(o/alpha_min) Sigma2D_yy); inflated for float32 rounding.
+        const float c2 = 2.f * logf(g.o / cfg.alpha_min);
+        const float rx = sqrtf(c2 * g.s00) * 1.0001f + 1e-3f;
+        const float ry = sqrtf(c2 * g.s11) * 1.0001f + 1e-3f;
+        r = fmaxf(rx, ry);
+        const float fx0 = fmaxf(ceilf(g.mean2d[0] - rx - 0.5f), 0.f);
+        const float fx1 = fminf(floorf(g.mean2d[0] + rx - 0.5f), (float)(c.width - 1));
+        const float fy0 = fmaxf(ceilf(g.mean2d[1] - ry - 0.5f), 0.f);
+        const float fy1 = fminf(floorf(g.mean2d[1] + ry - 0.5f), (float)(c.height - 1));
         if (!(fx0 <= fx1) || !(fy0 <= fy1)) {
             culled = true;
         } else {

@@ -146,13 +146,13 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
                 if (ae.alpha >= amin) {
                     contrib = true;
                     const float om = __fsub_rn(1.f, ae.alpha);
-                    const float Tk = __fdiv_rn(T, om);
+                    const float inv = 1.f / om;
+                    const float Tk = T * inv;
                     const float wgt = ae.alpha * Tk;
                     const float c0 = sb.z, c1 = sb.w, c2 = s_c[j];
                     gv[6] = dC0 * wgt;
                     gv[7] = dC1 * wgt;
                     gv[8] = dC2 * wgt;
-                    const float inv = 1.f / om;
                     const float da = dC0 * (c0 * Tk - A0 * inv) + dC1 * (c1 * Tk - A1 * inv) + dC2 * (c2 * Tk - A2 * inv);
                     A0 += c0 * wgt;
                     A1 += c1 * wgt;
@@ -192,11 +192,40 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
     }
 }
 
-template <int DEG>
+// Optimizer fused into the projection adjoint: the parameters live in one flat
+// buffer (param_offsets) with Adam moments m, v in the same layout.
+struct AdamFuse {
+    float *p, *m, *v;
+    int64_t o[6];
+    gs_adam_config cfg;
+    const int32_t *do_step;
+    const int64_t *step;
+};
+
+__device__ __forceinline__ void adam_range(const AdamFuse &af, int64_t off, const float *g, int cnt, float lr_t,
+                                           float ibc2) {
+    for (int k = 0; k < cnt; ++k) {
+        float p = af.p[off + k], m = af.m[off + k], v = af.v[off + k];
+        adam_update(p, m, v, g[k], lr_t, af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+        af.p[off + k] = p;
+        af.m[off + k] = m;
+        af.v[off + k] = v;
+    }
+}
+
+template <int DEG, bool FUSED>
 __global__ void __launch_bounds__(128) proj_bwd_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
                                                        const uint8_t *__restrict__ view_gate, gs_raster_config cfg,
-                                                       const float4 *__restrict__ g2d, gs_grads gr, int accumulate) {
+                                                       const float4 *__restrict__ g2d, gs_grads gr, int accumulate,
+                                                       AdamFuse af) {
     constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ float s_lr[6];
+    __shared__ float s_ibc2;
+    if constexpr (FUSED) {
+        if (af.do_step && *af.do_step == 0) return;  // the same for every block
+        if (threadIdx.x == 0) adam_scalars(af.cfg, *af.step, s_lr, &s_ibc2);
+        __syncthreads();
+    }
     const int64_t n = prm.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -334,6 +363,17 @@ __global__ void __launch_bounds__(128) proj_bwd_kernel(gs_params prm, const gs_c
 #pragma unroll
         for (int a = 0; a < 4; ++a) dq[a] += (dqn[a] - g.qn[a] * qd) * g.qinv;
     }
+    if constexpr (FUSED) {
+        // every Gaussian takes the step (zero gradient where it was not seen)
+        const float ibc2 = s_ibc2;
+        adam_range(af, af.o[0] + 3 * i, dmu, 3, s_lr[0], ibc2);
+        adam_range(af, af.o[1] + 3 * i, dls, 3, s_lr[1], ibc2);
+        adam_range(af, af.o[2] + 4 * i, dq, 4, s_lr[2], ibc2);
+        adam_range(af, af.o[3] + i, &dlogit, 1, s_lr[3], ibc2);
+        adam_range(af, af.o[4] + (int64_t)3 * K * i, df, 3, s_lr[4], ibc2);
+        if (K > 1) adam_range(af, af.o[4] + (int64_t)3 * K * i + 3, df + 3, 3 * K - 3, s_lr[5], ibc2);
+        return;
+    }
     if (accumulate) {
         for (int a = 0; a < 3; ++a) { gr.means[3 * i + a] += dmu[a]; gr.log_scales[3 * i + a] += dls[a]; }
         for (int a = 0; a < 4; ++a) gr.quats[4 * i + a] += dq[a];
@@ -377,6 +417,45 @@ gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const 
     return GS_OK;
 }
 
+__global__ void adam_step_count_kernel(const int32_t *do_step, int64_t *step) {
+    if (!do_step || *do_step) *step += 1;
+}
+
+// The two adjoint passes shared by gs_render_bwd and gs_render_bwd_adam.
+template <bool FUSED>
+gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
+                          const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                          const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                          const uint8_t *view_gate, gs_grads grads, int32_t accumulate, const AdamFuse &af,
+                          void *workspace, cudaStream_t stream) {
+    const int64_t n = params->n;
+    float4 *g2d = reinterpret_cast<float4 *>(workspace);
+    GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
+    const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    gs_status st;
+    switch (cfg->tile) {
+        case 8: st = launch_bwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        case 16: st = launch_bwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        case 32: st = launch_bwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        default: return GS_ERR_INVALID_ARG;
+    }
+    if (st != GS_OK) return st;
+    const unsigned blocks = (unsigned)ceil_div(n, 128);
+    switch (params->sh_degree) {
+        case 0: proj_bwd_kernel<0, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
+        case 1: proj_bwd_kernel<1, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
+        case 2: proj_bwd_kernel<2, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
+        default: proj_bwd_kernel<3, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
+    }
+    GS_TRY_LAUNCH();
+    if constexpr (FUSED) {
+        adam_step_count_kernel<<<1, 1, 0, stream>>>(af.do_step, const_cast<int64_t *>(af.step));
+        GS_TRY_LAUNCH();
+    }
+    return GS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -405,27 +484,48 @@ gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const
     if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
     if (n == 0) return GS_OK;
-    float4 *g2d = reinterpret_cast<float4 *>(workspace);
-    GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
-    const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
-    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    gs_status st;
-    switch (cfg->tile) {
-        case 8: st = launch_bwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
-        case 16: st = launch_bwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
-        case 32: st = launch_bwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
-        default: return GS_ERR_INVALID_ARG;
-    }
-    if (st != GS_OK) return st;
-    const unsigned blocks = (unsigned)ceil_div(n, 128);
-    switch (params->sh_degree) {
-        case 0: proj_bwd_kernel<0><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
-        case 1: proj_bwd_kernel<1><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
-        case 2: proj_bwd_kernel<2><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
-        default: proj_bwd_kernel<3><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate); break;
-    }
-    GS_TRY_LAUNCH();
-    return GS_OK;
+    AdamFuse af{};
+    return render_bwd_impl<false>(params, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
+                                  view_gate, grads, accumulate, af, workspace, stream);
+}
+
+gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                             const gs_projected *proj, const uint32_t *vals, const uint32_t *ranges,
+                             const gs_camera *cams, int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg,
+                             gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate,
+                             const gs_adam_config *adam, const int32_t *dev_do_step, int64_t *dev_step,
+                             void *workspace, size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    if (!flat_params || !m || !v || !adam || !dev_step || n < 0 || n >= ((int64_t)1 << 31) || sh_degree < 0 ||
+        sh_degree > 3 || cfg == nullptr || cfg->sh_degree != sh_degree)
+        return GS_ERR_INVALID_ARG;
+    if (!proj || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0) return GS_ERR_INVALID_ARG;
+    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
+    if (((uintptr_t)flat_params | (uintptr_t)m | (uintptr_t)v | (uintptr_t)proj->rec) & 15) return GS_ERR_INVALID_ARG;
+    if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f && adam->eps >= 0.f))
+        return GS_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
+    if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
+    if (n == 0) return GS_OK;
+    AdamFuse af{};
+    af.p = flat_params;
+    af.m = m;
+    af.v = v;
+    param_offsets(n, sh_degree, af.o);
+    af.cfg = *adam;
+    af.do_step = dev_do_step;
+    af.step = dev_step;
+    gs_params prm;
+    prm.means = flat_params + af.o[0];
+    prm.log_scales = flat_params + af.o[1];
+    prm.quats = flat_params + af.o[2];
+    prm.opacity_logit = flat_params + af.o[3];
+    prm.sh = flat_params + af.o[4];
+    prm.n = n;
+    prm.sh_degree = sh_degree;
+    gs_grads none{};
+    return render_bwd_impl<true>(&prm, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
+                                 view_gate, none, 0, af, workspace, stream);
 }
 
 }  // extern "C"

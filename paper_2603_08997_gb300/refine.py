@@ -3,7 +3,9 @@
 One iteration: select the view of this iteration (device-side, from the
 pre-drawn view sequence) -> project -> bin/sort -> render -> loss (value) ->
 gate decision -> [loss gradient -> raster and projection adjoint -> Adam]
-only when g = 1 -> per-view EMA update.
+only when g = 1 -> per-view EMA update.  By default the projection adjoint
+and Adam run as one kernel (gs_render_bwd_adam); fused=False issues
+gs_render_bwd and gs_adam_step separately.
 
 `step_graph` replays the iteration as one CUDA graph: the bracketed branch is
 an IF conditional node that the gate kernel sets on the device, so no value
@@ -25,8 +27,10 @@ from .raster import AdamState, Gate, GaussianModel, RasterSettings, Renderer, Vi
 class RefinementLoop:
     def __init__(self, model: GaussianModel, train_cams: list, targets: torch.Tensor, view_seq,
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
-                 eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None):
+                 eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
+                 fused: bool = True):
         self.model = model
+        self.fused = bool(fused)
         self.s = settings or RasterSettings()
         self.gated = bool(gated)
         dev = model.flat.device
@@ -62,8 +66,12 @@ class RefinementLoop:
     def _back(self, s, predicated: bool):
         r = self.renderer
         r.loss_backward(self.targets, self.target_offsets, self.view_ids, stream=s)
-        r.backward(self.params, self.grads, view_gate=self.g if predicated else None, accumulate=False, stream=s)
-        self.adam.step(do_step=self.any if predicated else None, stream=s)
+        if self.fused:
+            r.backward_adam(self.model, self.adam, view_gate=self.g if predicated else None,
+                            do_step=self.any if predicated else None, stream=s)
+        else:
+            r.backward(self.params, self.grads, view_gate=self.g if predicated else None, accumulate=False, stream=s)
+            self.adam.step(do_step=self.any if predicated else None, stream=s)
 
     def _update(self, s):
         self.gate.update(self.view_ids, self.renderer.loss, stream=s)

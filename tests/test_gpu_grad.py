@@ -173,3 +173,30 @@ def test_autograd_function_matches_oracle():
         L, dL = oracle.loss_and_grad(f["image"], t.astype(np.float32))
         og = oracle.backward(scene, c, rc, f, dL, og)
     _check_grads(gpu_util.gpu_grads(model, flat.grad), og)
+
+
+@pytest.mark.parametrize("deg", [3, 0, 2])
+def test_fused_backward_adam_equals_separate_calls(deg):
+    """gs_render_bwd_adam = gs_render_bwd followed by gs_adam_step, over two steps."""
+    scene, cam = synth.scene_tiny(300, seed=2, sh_degree=deg)
+    target = torch.from_numpy(np.random.default_rng(3).uniform(0, 1, (3, cam.height, cam.width)).astype(np.float32))
+    target = target.cuda().view(-1)
+    out = []
+    for fused in (False, True):
+        r, model = _setup(scene, cam)
+        adam = raster.AdamState(model)
+        for _ in range(2):
+            r.forward(model.c_params())
+            r.compute_loss(target, with_grad=True)
+            if fused:
+                r.backward_adam(model, adam)
+            else:
+                r.backward(model.c_params(), model.c_grads(adam.grad))
+                adam.step()
+        torch.cuda.synchronize()
+        out.append((model.flat.clone(), adam.m.clone(), adam.v.clone(), int(adam.step_count.item())))
+    (p0, m0, v0, s0), (p1, m1, v1, s1) = out
+    assert s0 == s1 == 2
+    torch.testing.assert_close(p1, p0, rtol=1e-6, atol=1e-7)
+    torch.testing.assert_close(m1, m0, rtol=1e-5, atol=1e-10)
+    torch.testing.assert_close(v1, v0, rtol=1e-5, atol=1e-14)

@@ -150,13 +150,14 @@ def test_projection_c2_like():
     Qo = o["conic"][vis]
     err = np.linalg.norm(Q - Qo, axis=1) / np.linalg.norm(Qo, axis=1)
     assert np.median(err) < 1e-6 and err.max() < 1e-3
-    # the GPU rectangle contains the exact support square (the oracle's radius
+    # the GPU rectangle contains the exact support box (the oracle's extents
     # before the oracle's own inflation, r -> 1.001 r + 0.01)
     r_ex = (o["radius"][vis] - 0.01) / 1.001
     m = o["mean2d"][vis]
-    ex = np.stack([np.maximum(np.ceil(m[:, 0] - r_ex - 0.5), 0) // 16, np.maximum(np.ceil(m[:, 1] - r_ex - 0.5), 0) // 16,
-                   np.minimum(np.floor(m[:, 0] + r_ex - 0.5), cam.width - 1) // 16,
-                   np.minimum(np.floor(m[:, 1] + r_ex - 0.5), cam.height - 1) // 16], 1)
+    ex = np.stack([np.maximum(np.ceil(m[:, 0] - r_ex[:, 0] - 0.5), 0) // 16,
+                   np.maximum(np.ceil(m[:, 1] - r_ex[:, 1] - 0.5), 0) // 16,
+                   np.minimum(np.floor(m[:, 0] + r_ex[:, 0] - 0.5), cam.width - 1) // 16,
+                   np.minimum(np.floor(m[:, 1] + r_ex[:, 1] - 0.5), cam.height - 1) // 16], 1)
     gr = rect[vis]
     assert ((gr[:, 0] <= ex[:, 0]) & (gr[:, 1] <= ex[:, 1]) & (gr[:, 2] >= ex[:, 2]) & (gr[:, 3] >= ex[:, 3])).all()
 

@@ -64,7 +64,7 @@ def test_frustum_clamped_gaussian_fd():
     """A Gaussian outside 1.3x the field of view uses the clamped J (true derivative)."""
     cam = synth.camera_pinhole(32.0, 32.0, 16.0, 16.0, 32, 32)
     scene, _ = synth.scene_tiny(3, seed=2, sh_degree=0)
-    scene.means[0] = np.array([2.2, 0.1, 2.0], np.float32)     # x/z = 1.1 > 1.3 * 0.5
+    scene.means[0] = np.array([1.8, 0.1, 2.0], np.float32)     # x/z = 0.9 > 1.3 * 0.5
     scene.log_scales[0] = np.log(np.array([0.6, 0.3, 0.2], np.float32))
     scene.opacity_logit[0] = 3.0
     pr = oracle.project(scene, cam, RC)
