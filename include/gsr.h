@@ -39,8 +39,10 @@
  *     [3][height][width].  gs_camera_layout fills both offsets.
  *   - Projected Gaussians (gs_projected), per view and Gaussian, at index
  *     v * N + i: a 12-float record rec = (mean2d.x, mean2d.y, u00, u01, u11,
- *     opacity, r, g, b, depth, radius, 0), where U = [[u00, u01], [0, u11]] is
- *     the upper Cholesky factor of the conic Q = Sigma2D^-1 (Q = U^T U);
+ *     opacity, r, g, b, depth, rx, ry), where U = [[u00, u01], [0, u11]] is
+ *     the upper Cholesky factor of the conic Q = Sigma2D^-1 (Q = U^T U) and
+ *     (rx, ry) bound the support (alpha' >= alpha_min only where
+ *     |p.x - mean2d.x| <= rx and |p.y - mean2d.y| <= ry);
  *     rect = tile rectangle (x0, y0, x1, y1) inclusive; tiles_touched = its
  *     tile count (0 = culled).
  *   - Pixel centres are at (i + 0.5, j + 0.5); the principal point (cx, cy) is

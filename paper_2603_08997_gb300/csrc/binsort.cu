@@ -296,10 +296,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) count_top(unsigned long long *bl
 
 // Scan phase fused with pair emission.  Each block takes its range of
 // entries in depth order, RS_THREADS at a time: a block scan gives every
-// entry's first pair slot, then the block writes all pairs of those entries
-// cooperatively (thread i writes pair i, i + RS_THREADS, ...), finding the
-// owning entry by binary search over the scanned counts, so the writes are
-// contiguous.  Within an entry the tiles are row-major.
+// entry's first pair slot; each entry writes its own pairs (tiles of its
+// rectangle, row-major) into a shared staging buffer, which the block then
+// copies out contiguously.  A chunk with more pairs than the buffer holds
+// writes straight to global memory instead.
+constexpr int EMIT_STAGE = 4096;
+
 __global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restrict__ touched,
                                                          const int4 *__restrict__ rect,
                                                          const uint32_t *__restrict__ order, int64_t total,
@@ -308,47 +310,50 @@ __global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restri
                                                          const int64_t *sort_count, uint32_t *__restrict__ pkeys,
                                                          uint32_t *__restrict__ pvals) {
     if (*sort_count == 0) return;  // nothing to emit, or over capacity
-    __shared__ uint32_t s_incl[RS_THREADS];
-    __shared__ int s_x0[RS_THREADS], s_y0[RS_THREADS], s_w[RS_THREADS], s_base[RS_THREADS], s_tx[RS_THREADS];
-    __shared__ uint32_t s_gi[RS_THREADS];
+    __shared__ uint32_t s_k[EMIT_STAGE];
+    __shared__ uint32_t s_v[EMIT_STAGE];
     __shared__ uint32_t s_warp[32];
     int64_t begin, end;
     block_range(total, gridDim.x, blockIdx.x, begin, end);
     uint64_t run = block_offsets[blockIdx.x];
     for (int64_t b0 = begin; b0 < end; b0 += RS_THREADS) {
         const int64_t m = b0 + threadIdx.x;
-        uint32_t c = 0;
+        uint32_t c = 0, gi = 0;
+        int4 r = make_int4(0, 0, -1, -1);
+        int base = 0, tx_n = 0;
         if (m < end) {
             const uint32_t e = order[m];
             c = (uint32_t)touched[e];
             if (c > 0) {
                 const int64_t v = (int64_t)e / n;
-                const int4 r = rect[e];
+                r = rect[e];
                 const gs_camera &cam = cams[v];
-                s_x0[threadIdx.x] = r.x;
-                s_y0[threadIdx.x] = r.y;
-                s_w[threadIdx.x] = r.z - r.x + 1;
-                s_tx[threadIdx.x] = (cam.width + tile - 1) / tile;
-                s_base[threadIdx.x] = cam.tile_offset;
-                s_gi[threadIdx.x] = (uint32_t)((int64_t)e - v * n);
+                tx_n = (cam.width + tile - 1) / tile;
+                base = cam.tile_offset;
+                gi = (uint32_t)((int64_t)e - v * n);
             }
         }
         uint32_t chunk_total;
         const uint32_t excl = block_exclusive_scan(c, s_warp, &chunk_total);
-        s_incl[threadIdx.x] = excl + c;
-        __syncthreads();
-        for (uint32_t idx = threadIdx.x; idx < chunk_total; idx += RS_THREADS) {
-            // owner: first j with s_incl[j] > idx
-            int lo = 0, hi = RS_THREADS - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_incl[mid] > idx) hi = mid; else lo = mid + 1;
+        if (chunk_total <= EMIT_STAGE) {
+            uint32_t o = excl;
+            for (int ty = r.y; ty <= r.w; ++ty)
+                for (int tx = r.x; tx <= r.z; ++tx, ++o) {
+                    s_k[o] = (uint32_t)(base + ty * tx_n + tx);
+                    s_v[o] = gi;
+                }
+            __syncthreads();
+            for (uint32_t k = threadIdx.x; k < chunk_total; k += RS_THREADS) {
+                pkeys[run + k] = s_k[k];
+                pvals[run + k] = s_v[k];
             }
-            const uint32_t kk = idx - (lo > 0 ? s_incl[lo - 1] : 0u);
-            const int w = s_w[lo];
-            const int ty = s_y0[lo] + (int)(kk / (uint32_t)w), tx = s_x0[lo] + (int)(kk % (uint32_t)w);
-            pkeys[run + idx] = (uint32_t)(s_base[lo] + ty * s_tx[lo] + tx);
-            pvals[run + idx] = s_gi[lo];
+        } else {
+            uint64_t o = run + excl;
+            for (int ty = r.y; ty <= r.w; ++ty)
+                for (int tx = r.x; tx <= r.z; ++tx, ++o) {
+                    pkeys[o] = (uint32_t)(base + ty * tx_n + tx);
+                    pvals[o] = gi;
+                }
         }
         run += chunk_total;
         __syncthreads();

@@ -78,18 +78,41 @@ struct AlphaEval {
     bool clamped;
 };
 
+// 2^x on the special-function unit (PTX ex2.approx, relative error ~2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ AlphaEval eval_alpha(float4 a, float4 b, float px, float py, float alpha_max) {
+    constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -log2(e) / 2: exp(-q/2) = 2^(q * kNegHalfLog2e)
     AlphaEval r;
     r.dx = __fsub_rn(px, a.x);
     r.dy = __fsub_rn(py, a.y);
     r.z0 = __fmaf_rn(a.z, r.dx, __fmul_rn(a.w, r.dy));
     r.z1 = __fmul_rn(b.x, r.dy);
     const float q = __fmaf_rn(r.z0, r.z0, __fmul_rn(r.z1, r.z1));
-    r.G = __expf(__fmul_rn(-0.5f, q));
+    r.G = ex2_approx(__fmul_rn(kNegHalfLog2e, q));
     const float og = __fmul_rn(b.y, r.G);
     r.clamped = og > alpha_max;
     r.alpha = r.clamped ? alpha_max : og;
     return r;
+}
+
+// Pixel of thread t in a TILE x TILE tile: each warp covers an 8 x 4 block,
+// so a warp can skip a Gaussian whose support box misses its block.
+template <int TILE>
+__device__ __forceinline__ void tile_pixel(int t, int &lx, int &ly) {
+    const int w = t >> 5, lane = t & 31;
+    lx = (w % (TILE / 8)) * 8 + (lane & 7);
+    ly = (w / (TILE / 8)) * 4 + (lane >> 3);
+}
+
+// Does the support box [m - r, m + r] of a Gaussian reach any pixel centre of
+// the warp's 8 x 4 block whose first pixel centre is (wx, wy)?  Uniform per warp.
+__device__ __forceinline__ bool warp_overlaps(float4 a, float4 c, float wx, float wy) {
+    return fabsf(a.x - (wx + 3.5f)) <= c.z + 3.5f && fabsf(a.y - (wy + 1.5f)) <= c.w + 1.5f;
 }
 
 // Real spherical harmonics (Condon-Shortley phase) up to degree 3 at a unit

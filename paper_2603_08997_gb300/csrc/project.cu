@@ -28,16 +28,15 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
     ProjState g;
     project_state(mu, ls, q, prm.opacity_logit[i], c, cfg.lowpass, g);
     bool culled = g.culled || !(g.o >= cfg.alpha_min);
-    float r = 0.f;
+    float rx = 0.f, ry = 0.f;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
     if (!culled) {
         // Support of alpha' >= alpha_min: the ellipse dp^T Q dp <= 2 ln(o / alpha_min).
         // Its axis-aligned extents are sqrt(2 ln(o/alpha_min) Sigma2D_xx) and
         // sqrt(2 ln(o/alpha_min) Sigma2D_yy); inflated for float32 rounding.
         const float c2 = 2.f * logf(g.o / cfg.alpha_min);
-        const float rx = sqrtf(c2 * g.s00) * 1.0001f + 1e-3f;
-        const float ry = sqrtf(c2 * g.s11) * 1.0001f + 1e-3f;
-        r = fmaxf(rx, ry);
+        rx = sqrtf(c2 * g.s00) * 1.0001f + 1e-3f;
+        ry = sqrtf(c2 * g.s11) * 1.0001f + 1e-3f;
         const float fx0 = fmaxf(ceilf(g.mean2d[0] - rx - 0.5f), 0.f);
         const float fx1 = fminf(floorf(g.mean2d[0] + rx - 0.5f), (float)(c.width - 1));
         const float fy0 = fmaxf(ceilf(g.mean2d[1] - ry - 0.5f), 0.f);
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
     }
     out[0] = make_float4(g.mean2d[0], g.mean2d[1], u00, u01);
     out[1] = make_float4(u11, g.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
-    out[2] = make_float4(fmaxf(col[2], 0.f), g.p[2], r, 0.f);
+    out[2] = make_float4(fmaxf(col[2], 0.f), g.p[2], rx, ry);
     rect[e] = make_int4(x0, y0, x1, y1);
     touched[e] = (x1 - x0 + 1) * (y1 - y0 + 1);
 }

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
     constexpr int NT = TILE * TILE;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
-    __shared__ float s_c[BATCH];
+    __shared__ float4 s_c[BATCH];
     __shared__ uint32_t s_g[BATCH];
     __shared__ float s_acc[BATCH][9];
     __shared__ int s_max;
@@ -80,10 +80,12 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
     const int tiles_x = (cam.width + TILE - 1) / TILE;
     const int64_t lt = tile - cam.tile_offset;
     const int tx = (int)(lt % tiles_x), ty = (int)(lt / tiles_x);
-    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    int lx, ly;
+    tile_pixel<TILE>(threadIdx.x, lx, ly);
     const int x = tx * TILE + lx, y = ty * TILE + ly;
     const bool inside = x < cam.width && y < cam.height;
     const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const float wx = (float)(tx * TILE + (lx & ~7)) + 0.5f, wy = (float)(ty * TILE + (ly & ~3)) + 0.5f;
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[tile];
     const int64_t slot0 = (int64_t)(rg.x / BATCH) + tile;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
             const float4 *r = recv + (int64_t)g * 3;
             s_a[k] = r[0];
             s_b[k] = r[1];
-            s_c[k] = r[2].x;
+            s_c[k] = r[2];
             s_g[k] = g;
         }
         for (int k = threadIdx.x; k < BATCH * 9; k += NT) (&s_acc[0][0])[k] = 0.f;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
         }
         const int wj = __reduce_max_sync(FULL, jstart);
         for (int j = wj; j >= 0; --j) {
+            if (!warp_overlaps(s_a[j], s_c[j], wx, wy)) continue;  // no lane of the warp has this contributor
             float gv[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) gv[q] = 0.f;
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
                     const float inv = 1.f / om;
                     const float Tk = T * inv;
                     const float wgt = ae.alpha * Tk;
-                    const float c0 = sb.z, c1 = sb.w, c2 = s_c[j];
+                    const float c0 = sb.z, c1 = sb.w, c2 = s_c[j].x;
                     gv[6] = dC0 * wgt;
                     gv[7] = dC1 * wgt;
                     gv[8] = dC2 * wgt;
@@ -202,190 +205,230 @@ struct AdamFuse {
     const int64_t *step;
 };
 
-__device__ __forceinline__ void adam_range(const AdamFuse &af, int64_t off, const float *g, int cnt, float lr_t,
-                                           float ibc2) {
-    for (int k = 0; k < cnt; ++k) {
-        float p = af.p[off + k], m = af.m[off + k], v = af.v[off + k];
-        adam_update(p, m, v, g[k], lr_t, af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
-        af.p[off + k] = p;
-        af.m[off + k] = m;
-        af.v[off + k] = v;
+// Group strides (floats per Gaussian) and their offsets inside a staged block.
+template <int DEG>
+struct Groups {
+    static constexpr int K = (DEG + 1) * (DEG + 1);
+    static constexpr int TOT = 11 + 3 * K;
+    __host__ __device__ static constexpr int S(int g) { return g == 0 ? 3 : (g == 1 ? 3 : (g == 2 ? 4 : (g == 3 ? 1 : 3 * K))); }
+    __host__ __device__ static constexpr int off(int g, int nb) {
+        return g == 0 ? 0 : (g == 1 ? 3 * nb : (g == 2 ? 6 * nb : (g == 3 ? 10 * nb : 11 * nb)));
     }
-}
+};
 
-template <int DEG, bool FUSED>
-__global__ void __launch_bounds__(128) proj_bwd_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
-                                                       const uint8_t *__restrict__ view_gate, gs_raster_config cfg,
-                                                       const float4 *__restrict__ g2d, gs_grads gr, int accumulate,
-                                                       AdamFuse af) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
+constexpr int PB = 128;  // Gaussians (and threads) per projection-adjoint block
+
+template <int DEG>
+constexpr size_t proj_bwd_smem() { return sizeof(float) * 2 * Groups<DEG>::TOT * PB; }
+
+// Projection adjoint, staged through shared memory.  The block copies the
+// parameter slices of its PB Gaussians (contiguous in every group) into
+// shared memory with coalesced loads; each thread chains its Gaussian's 2D
+// gradients (all views) to parameter gradients, accumulated in its own
+// shared slots; the block then sweeps its slices again, coalesced, to store
+// the gradients (MODE 0 overwrite, 1 add) or to apply Adam (MODE 2) without
+// ever storing them.
+template <int DEG, int MODE>
+__global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
+                                                      const uint8_t *__restrict__ view_gate, gs_raster_config cfg,
+                                                      const float4 *__restrict__ g2d, gs_grads gr, AdamFuse af) {
+    using G = Groups<DEG>;
+    constexpr int K = G::K;
+    extern __shared__ float smem[];
+    float *s_par = smem;                  // [TOT * PB], group-major slices
+    float *s_grd = smem + G::TOT * PB;    // same layout
     __shared__ float s_lr[6];
     __shared__ float s_ibc2;
-    if constexpr (FUSED) {
+    if constexpr (MODE == 2) {
         if (af.do_step && *af.do_step == 0) return;  // the same for every block
         if (threadIdx.x == 0) adam_scalars(af.cfg, *af.step, s_lr, &s_ibc2);
-        __syncthreads();
     }
     const int64_t n = prm.n;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float mu[3] = {prm.means[3 * i], prm.means[3 * i + 1], prm.means[3 * i + 2]};
-    const float ls[3] = {prm.log_scales[3 * i], prm.log_scales[3 * i + 1], prm.log_scales[3 * i + 2]};
-    const float4 q4 = reinterpret_cast<const float4 *>(prm.quats)[i];
-    const float logit = prm.opacity_logit[i];
-    const float *f = prm.sh + i * (3 * K);
-    float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dlogit = 0.f;
-    float df[3 * K];
+    const int64_t i0 = (int64_t)blockIdx.x * PB;
+    const int nb = (int)min((int64_t)PB, n - i0);
+    const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
 #pragma unroll
-    for (int k = 0; k < 3 * K; ++k) df[k] = 0.f;
+    for (int g = 0; g < 5; ++g) {
+        const int cnt = G::S(g) * nb;
+        const float *sp = src[g] + (int64_t)G::S(g) * i0;
+        float *dp = s_par + G::off(g, PB);
+        for (int k = threadIdx.x; k < cnt; k += PB) dp[k] = sp[k];
+    }
+    for (int k = threadIdx.x; k < G::TOT * PB; k += PB) s_grd[k] = 0.f;
+    __syncthreads();
 
-    for (int v = 0; v < n_views; ++v) {
-        if (view_gate && !view_gate[v]) continue;
-        const float4 *gp = g2d + ((int64_t)v * n + i) * 3;
-        const float4 ga = gp[0], gb = gp[1];
-        const float gc = gp[2].x;
-        const float gd[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc};
-        bool nz = false;
+    const int t = threadIdx.x;
+    if (t < nb) {
+        const int64_t i = i0 + t;
+        const float *P0 = s_par + G::off(0, PB) + 3 * t;
+        const float *P1 = s_par + G::off(1, PB) + 3 * t;
+        const float *P2 = s_par + G::off(2, PB) + 4 * t;
+        const float logit = s_par[G::off(3, PB) + t];
+        const float *f = s_par + G::off(4, PB) + 3 * K * t;
+        float *D0 = s_grd + G::off(0, PB) + 3 * t;
+        float *D1 = s_grd + G::off(1, PB) + 3 * t;
+        float *D2 = s_grd + G::off(2, PB) + 4 * t;
+        float *D3 = s_grd + G::off(3, PB) + t;
+        float *DF = s_grd + G::off(4, PB) + 3 * K * t;
+        const float mu[3] = {P0[0], P0[1], P0[2]};
+        const float ls[3] = {P1[0], P1[1], P1[2]};
+        const float4 q4 = make_float4(P2[0], P2[1], P2[2], P2[3]);
+        for (int v = 0; v < n_views; ++v) {
+            if (view_gate && !view_gate[v]) continue;
+            const float4 *gp = g2d + ((int64_t)v * n + i) * 3;
+            const float4 ga = gp[0], gb = gp[1];
+            const float gc = gp[2].x;
+            const float gd[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc};
+            bool nz = false;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) nz |= gd[q] != 0.f;
-        if (!nz) continue;
-        const gs_camera &c = cams[v];
-        ProjState g;
-        project_state(mu, ls, q4, logit, c, cfg.lowpass, g);
-        if (g.culled) continue;
-        // opacity = sigmoid(logit)
-        dlogit += gd[5] * g.o * (1.f - g.o);
-        // colour = max(0, sum_k f_k Y_k(d) + 0.5), d = (mu - campos) / |mu - campos|
-        float cp[3];
-        cam_center(c, cp);
-        float dv[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
-        const float inv_n = 1.0f / sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-        const float d[3] = {dv[0] * inv_n, dv[1] * inv_n, dv[2] * inv_n};
-        float Y[16], dY[16][3];
-        sh_basis(DEG, d[0], d[1], d[2], Y);
-        sh_basis_grad(DEG, d[0], d[1], d[2], dY);
-        float ddir[3] = {0.f, 0.f, 0.f};
+            for (int q = 0; q < 9; ++q) nz |= gd[q] != 0.f;
+            if (!nz) continue;
+            const gs_camera &c = cams[v];
+            ProjState g;
+            project_state(mu, ls, q4, logit, c, cfg.lowpass, g);
+            if (g.culled) continue;
+            // opacity = sigmoid(logit)
+            D3[0] += gd[5] * g.o * (1.f - g.o);
+            // colour = max(0, sum_k f_k Y_k(d) + 0.5), d = (mu - campos) / |mu - campos|
+            float cp[3];
+            cam_center(c, cp);
+            const float dv[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
+            const float inv_n = 1.0f / sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            const float d[3] = {dv[0] * inv_n, dv[1] * inv_n, dv[2] * inv_n};
+            float Y[16], dY[16][3];
+            sh_basis(DEG, d[0], d[1], d[2], Y);
+            sh_basis_grad(DEG, d[0], d[1], d[2], dY);
+            float ddir[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float pre = 0.5f;
+            for (int ch = 0; ch < 3; ++ch) {
+                float pre = 0.5f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) pre += f[3 * k + ch] * Y[k];
-            if (!(pre > 0.f)) continue;
-            const float dc = gd[6 + ch];
+                for (int k = 0; k < K; ++k) pre += f[3 * k + ch] * Y[k];
+                if (!(pre > 0.f)) continue;
+                const float dc = gd[6 + ch];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                df[3 * k + ch] += dc * Y[k];
-                const float fk = f[3 * k + ch] * dc;
-                ddir[0] += fk * dY[k][0];
-                ddir[1] += fk * dY[k][1];
-                ddir[2] += fk * dY[k][2];
+                for (int k = 0; k < K; ++k) {
+                    DF[3 * k + ch] += dc * Y[k];
+                    const float fk = f[3 * k + ch] * dc;
+                    ddir[0] += fk * dY[k][0];
+                    ddir[1] += fk * dY[k][1];
+                    ddir[2] += fk * dY[k][2];
+                }
             }
-        }
-        const float dd = ddir[0] * d[0] + ddir[1] * d[1] + ddir[2] * d[2];
+            float dmu[3];
+            const float dd = ddir[0] * d[0] + ddir[1] * d[1] + ddir[2] * d[2];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - d[a] * dd) * inv_n;
-        // conic Q = Sigma2D^-1 -> dL/dSigma2D = -Q GQ Q (full symmetric matrices)
-        const float idet = 1.f / g.det;
-        const float Qa = g.s11 * idet, Qb = -g.s01 * idet, Qc = g.s00 * idet;
-        const float Ga = gd[2], Gb = 0.5f * gd[3], Gc = gd[4];
-        // tmp = GQ Q
-        const float t00 = Ga * Qa + Gb * Qb, t01 = Ga * Qb + Gb * Qc;
-        const float t10 = Gb * Qa + Gc * Qb, t11 = Gb * Qb + Gc * Qc;
-        const float S00 = -(Qa * t00 + Qb * t10), S01 = -(Qa * t01 + Qb * t11), S11 = -(Qb * t01 + Qc * t11);
-        // Sigma2D = M M^T + l I -> dL/dM = 2 S M
-        float dM[6];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            dM[k] = 2.f * (S00 * g.M[k] + S01 * g.M[3 + k]);
-            dM[3 + k] = 2.f * (S01 * g.M[k] + S11 * g.M[3 + k]);
-        }
-        // M = T R S: dT = dM (R S)^T, Gp = T^T dM, dR_jk = Gp_jk s_k, ds_k = sum_j Gp_jk R_jk
-        float dT[6];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                dT[3 * r + j] = dM[3 * r] * g.R[3 * j] * g.s[0] + dM[3 * r + 1] * g.R[3 * j + 1] * g.s[1] +
-                                dM[3 * r + 2] * g.R[3 * j + 2] * g.s[2];
-        float dR[9];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
+            for (int a = 0; a < 3; ++a) dmu[a] = (ddir[a] - d[a] * dd) * inv_n;
+            // conic Q = Sigma2D^-1 -> dL/dSigma2D = -Q GQ Q (full symmetric matrices)
+            const float idet = 1.f / g.det;
+            const float Qa = g.s11 * idet, Qb = -g.s01 * idet, Qc = g.s00 * idet;
+            const float Ga = gd[2], Gb = 0.5f * gd[3], Gc = gd[4];
+            const float t00 = Ga * Qa + Gb * Qb, t01 = Ga * Qb + Gb * Qc;
+            const float t10 = Gb * Qa + Gc * Qb, t11 = Gb * Qb + Gc * Qc;
+            const float S00 = -(Qa * t00 + Qb * t10), S01 = -(Qa * t01 + Qb * t11), S11 = -(Qb * t01 + Qc * t11);
+            // Sigma2D = M M^T + l I -> dL/dM = 2 S M
+            float dM[6];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float gp_ = g.T[j] * dM[k] + g.T[3 + j] * dM[3 + k];
-                dR[3 * j + k] = gp_ * g.s[k];
+                dM[k] = 2.f * (S00 * g.M[k] + S01 * g.M[3 + k]);
+                dM[3 + k] = 2.f * (S01 * g.M[k] + S11 * g.M[3 + k]);
             }
+            // M = T R S: dT = dM (R S)^T, Gp = T^T dM, dR_jk = Gp_jk s_k, ds_k = sum_j Gp_jk R_jk
+            float dT[6];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float ds = 0.f;
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) ds += (g.T[j] * dM[k] + g.T[3 + j] * dM[3 + k]) * g.R[3 * j + k];
-            dls[k] += ds * g.s[k];
+                for (int j = 0; j < 3; ++j)
+                    dT[3 * r + j] = dM[3 * r] * g.R[3 * j] * g.s[0] + dM[3 * r + 1] * g.R[3 * j + 1] * g.s[1] +
+                                    dM[3 * r + 2] * g.R[3 * j + 2] * g.s[2];
+            float dR[9];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) dR[3 * j + k] = (g.T[j] * dM[k] + g.T[3 + j] * dM[3 + k]) * g.s[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float ds = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) ds += (g.T[j] * dM[k] + g.T[3 + j] * dM[3 + k]) * g.R[3 * j + k];
+                D1[k] += ds * g.s[k];
+            }
+            // T = J W: dJ = dT W^T (only J00, J02, J11, J12 are non-zero)
+            const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
+            const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
+            const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
+            const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
+            const float z = g.p[2], iz = 1.f / z, iz2 = iz * iz;
+            float dp[3] = {0.f, 0.f, 0.f};
+            dp[2] += -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2;
+            if (g.clamp_x == 0) {
+                dp[0] += -dJ02 * c.fx * iz2;
+                dp[2] += dJ02 * 2.f * c.fx * g.txz * iz2;
+            } else {
+                dp[2] += dJ02 * c.fx * g.txz * iz2;
+            }
+            if (g.clamp_y == 0) {
+                dp[1] += -dJ12 * c.fy * iz2;
+                dp[2] += dJ12 * 2.f * c.fy * g.tyz * iz2;
+            } else {
+                dp[2] += dJ12 * c.fy * g.tyz * iz2;
+            }
+            // mean2D = (fx x/z + cx, fy y/z + cy)
+            dp[0] += gd[0] * c.fx * iz;
+            dp[1] += gd[1] * c.fy * iz;
+            dp[2] += -(gd[0] * c.fx * g.p[0] + gd[1] * c.fy * g.p[1]) * iz2;
+            // p = W mu + t
+#pragma unroll
+            for (int a = 0; a < 3; ++a) D0[a] += dmu[a] + c.R[a] * dp[0] + c.R[3 + a] * dp[1] + c.R[6 + a] * dp[2];
+            // R(qn): partial derivatives of the rotation matrix entries
+            const float w = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
+            float dqn[4];
+            dqn[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+            dqn[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - w * dR[5] + qz * dR[6] + w * dR[7] -
+                            2.f * qx * dR[8]);
+            dqn[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + w * dR[2] + qx * dR[3] + qz * dR[5] - w * dR[6] +
+                            qz * dR[7] - 2.f * qy * dR[8]);
+            dqn[3] = 2.f * (-2.f * qz * dR[0] - w * dR[1] + qx * dR[2] + w * dR[3] - 2.f * qz * dR[4] + qy * dR[5] +
+                            qx * dR[6] + qy * dR[7]);
+            const float qd = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) D2[a] += (dqn[a] - g.qn[a] * qd) * g.qinv;
         }
-        // T = J W: dJ = dT W^T (only J00, J02, J11, J12 are non-zero)
-        const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
-        const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
-        const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
-        const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
-        const float z = g.p[2], iz = 1.f / z, iz2 = iz * iz;
-        float dp[3] = {0.f, 0.f, 0.f};
-        dp[2] += -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2;
-        if (g.clamp_x == 0) {
-            dp[0] += -dJ02 * c.fx * iz2;
-            dp[2] += dJ02 * 2.f * c.fx * g.txz * iz2;
-        } else {
-            dp[2] += dJ02 * c.fx * g.txz * iz2;
-        }
-        if (g.clamp_y == 0) {
-            dp[1] += -dJ12 * c.fy * iz2;
-            dp[2] += dJ12 * 2.f * c.fy * g.tyz * iz2;
-        } else {
-            dp[2] += dJ12 * c.fy * g.tyz * iz2;
-        }
-        // mean2D = (fx x/z + cx, fy y/z + cy)
-        dp[0] += gd[0] * c.fx * iz;
-        dp[1] += gd[1] * c.fy * iz;
-        dp[2] += -(gd[0] * c.fx * g.p[0] + gd[1] * c.fy * g.p[1]) * iz2;
-        // p = W mu + t
-#pragma unroll
-        for (int a = 0; a < 3; ++a) dmu[a] += c.R[a] * dp[0] + c.R[3 + a] * dp[1] + c.R[6 + a] * dp[2];
-        // R(qn): partial derivatives of the rotation matrix entries
-        const float w = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
-        float dqn[4];
-        dqn[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
-        dqn[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - w * dR[5] + qz * dR[6] + w * dR[7] -
-                        2.f * qx * dR[8]);
-        dqn[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + w * dR[2] + qx * dR[3] + qz * dR[5] - w * dR[6] + qz * dR[7] -
-                        2.f * qy * dR[8]);
-        dqn[3] = 2.f * (-2.f * qz * dR[0] - w * dR[1] + qx * dR[2] + w * dR[3] - 2.f * qz * dR[4] + qy * dR[5] +
-                        qx * dR[6] + qy * dR[7]);
-        const float qd = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) dq[a] += (dqn[a] - g.qn[a] * qd) * g.qinv;
     }
-    if constexpr (FUSED) {
-        // every Gaussian takes the step (zero gradient where it was not seen)
+    __syncthreads();
+    // coalesced sweep over the block's slices
+    if constexpr (MODE == 2) {
         const float ibc2 = s_ibc2;
-        adam_range(af, af.o[0] + 3 * i, dmu, 3, s_lr[0], ibc2);
-        adam_range(af, af.o[1] + 3 * i, dls, 3, s_lr[1], ibc2);
-        adam_range(af, af.o[2] + 4 * i, dq, 4, s_lr[2], ibc2);
-        adam_range(af, af.o[3] + i, &dlogit, 1, s_lr[3], ibc2);
-        adam_range(af, af.o[4] + (int64_t)3 * K * i, df, 3, s_lr[4], ibc2);
-        if (K > 1) adam_range(af, af.o[4] + (int64_t)3 * K * i + 3, df + 3, 3 * K - 3, s_lr[5], ibc2);
-        return;
-    }
-    if (accumulate) {
-        for (int a = 0; a < 3; ++a) { gr.means[3 * i + a] += dmu[a]; gr.log_scales[3 * i + a] += dls[a]; }
-        for (int a = 0; a < 4; ++a) gr.quats[4 * i + a] += dq[a];
-        gr.opacity_logit[i] += dlogit;
+        float *pp[5];
+        for (int g = 0; g < 5; ++g) pp[g] = nullptr;
 #pragma unroll
-        for (int k = 0; k < 3 * K; ++k) gr.sh[i * 3 * K + k] += df[k];
+        for (int g = 0; g < 5; ++g) {
+            const int cnt = G::S(g) * nb;
+            const int64_t e0 = af.o[g] + (int64_t)G::S(g) * i0;
+            const float *sp = s_par + G::off(g, PB);
+            const float *sg = s_grd + G::off(g, PB);
+            for (int k = threadIdx.x; k < cnt; k += PB) {
+                const int lr = g < 4 ? g : ((k % (3 * K)) < 3 ? 4 : 5);
+                float p = sp[k], m = af.m[e0 + k], v = af.v[e0 + k];
+                adam_update(p, m, v, sg[k], s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+                af.p[e0 + k] = p;
+                af.m[e0 + k] = m;
+                af.v[e0 + k] = v;
+            }
+        }
+        (void)pp;
     } else {
-        for (int a = 0; a < 3; ++a) { gr.means[3 * i + a] = dmu[a]; gr.log_scales[3 * i + a] = dls[a]; }
-        reinterpret_cast<float4 *>(gr.quats)[i] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-        gr.opacity_logit[i] = dlogit;
+        float *dst[5] = {gr.means, gr.log_scales, gr.quats, gr.opacity_logit, gr.sh};
 #pragma unroll
-        for (int k = 0; k < 3 * K; ++k) gr.sh[i * 3 * K + k] = df[k];
+        for (int g = 0; g < 5; ++g) {
+            const int cnt = G::S(g) * nb;
+            float *dp = dst[g] + (int64_t)G::S(g) * i0;
+            const float *sg = s_grd + G::off(g, PB);
+            for (int k = threadIdx.x; k < cnt; k += PB) {
+                if constexpr (MODE == 1) dp[k] += sg[k];
+                else dp[k] = sg[k];
+            }
+        }
     }
 }
 
@@ -417,6 +460,32 @@ gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const 
     return GS_OK;
 }
 
+template <int DEG, int MODE>
+gs_status launch_proj_bwd_mode(unsigned blocks, cudaStream_t stream, const gs_params &prm, const gs_camera *cams,
+                               int n_views, const uint8_t *gate, const gs_raster_config &cfg, const float4 *g2d,
+                               const gs_grads &gr, const AdamFuse &af) {
+    constexpr size_t smem = proj_bwd_smem<DEG>();
+    static bool attr_set = false;  // raise the dynamic shared-memory limit once per instantiation
+    if (!attr_set) {
+        GS_TRY(cudaFuncSetAttribute(proj_bwd_kernel<DEG, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    proj_bwd_kernel<DEG, MODE><<<blocks, PB, smem, stream>>>(prm, cams, n_views, gate, cfg, g2d, gr, af);
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}
+
+template <int DEG>
+gs_status launch_proj_bwd(int mode, unsigned blocks, cudaStream_t stream, const gs_params &prm, const gs_camera *cams,
+                          int n_views, const uint8_t *gate, const gs_raster_config &cfg, const float4 *g2d,
+                          const gs_grads &gr, const AdamFuse &af) {
+    switch (mode) {
+        case 0: return launch_proj_bwd_mode<DEG, 0>(blocks, stream, prm, cams, n_views, gate, cfg, g2d, gr, af);
+        case 1: return launch_proj_bwd_mode<DEG, 1>(blocks, stream, prm, cams, n_views, gate, cfg, g2d, gr, af);
+        default: return launch_proj_bwd_mode<DEG, 2>(blocks, stream, prm, cams, n_views, gate, cfg, g2d, gr, af);
+    }
+}
+
 __global__ void adam_step_count_kernel(const int32_t *do_step, int64_t *step) {
     if (!do_step || *do_step) *step += 1;
 }
@@ -441,14 +510,15 @@ gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, con
         default: return GS_ERR_INVALID_ARG;
     }
     if (st != GS_OK) return st;
-    const unsigned blocks = (unsigned)ceil_div(n, 128);
+    const unsigned blocks = (unsigned)ceil_div(n, PB);
+    const int mode = FUSED ? 2 : (accumulate ? 1 : 0);
     switch (params->sh_degree) {
-        case 0: proj_bwd_kernel<0, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
-        case 1: proj_bwd_kernel<1, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
-        case 2: proj_bwd_kernel<2, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
-        default: proj_bwd_kernel<3, FUSED><<<blocks, 128, 0, stream>>>(*params, cams, n_views, view_gate, *cfg, g2d, grads, accumulate, af); break;
+        case 0: st = launch_proj_bwd<0>(mode, blocks, stream, *params, cams, n_views, view_gate, *cfg, g2d, grads, af); break;
+        case 1: st = launch_proj_bwd<1>(mode, blocks, stream, *params, cams, n_views, view_gate, *cfg, g2d, grads, af); break;
+        case 2: st = launch_proj_bwd<2>(mode, blocks, stream, *params, cams, n_views, view_gate, *cfg, g2d, grads, af); break;
+        default: st = launch_proj_bwd<3>(mode, blocks, stream, *params, cams, n_views, view_gate, *cfg, g2d, grads, af); break;
     }
-    GS_TRY_LAUNCH();
+    if (st != GS_OK) return st;
     if constexpr (FUSED) {
         adam_step_count_kernel<<<1, 1, 0, stream>>>(af.do_step, const_cast<int64_t *>(af.step));
         GS_TRY_LAUNCH();

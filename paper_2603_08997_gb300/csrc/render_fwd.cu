@@ -1,6 +1,7 @@
 // gs_render_fwd: Eq. (blend) / Eq. (alpha), front-to-back compositing.
 //
-// One CTA per tile, one thread per pixel.  The tile's depth-ordered list is
+// One CTA per tile, one thread per pixel, each warp an 8 x 4 pixel block that
+// skips Gaussians whose support box misses it.  The tile's depth-ordered list is
 // consumed `BATCH` Gaussians at a time: the CTA gathers the batch's packed
 // records into shared memory (one coalesced 48-byte record per Gaussian),
 // then every pixel walks the batch.  At the start of every batch each pixel
@@ -26,17 +27,19 @@ __global__ void __launch_bounds__(TILE *TILE) render_fwd_kernel(const float4 *__
     constexpr int NT = TILE * TILE;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
-    __shared__ float s_c[BATCH];
+    __shared__ float4 s_c[BATCH];
     const int64_t tile = blockIdx.x;
     const int v = view_of_tile(cams, n_views, tile);
     const gs_camera &cam = cams[v];
     const int tiles_x = (cam.width + TILE - 1) / TILE;
     const int64_t lt = tile - cam.tile_offset;
     const int tx = (int)(lt % tiles_x), ty = (int)(lt / tiles_x);
-    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    int lx, ly;
+    tile_pixel<TILE>(threadIdx.x, lx, ly);
     const int x = tx * TILE + lx, y = ty * TILE + ly;
     const bool inside = x < cam.width && y < cam.height;
     const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const float wx = (float)(tx * TILE + (lx & ~7)) + 0.5f, wy = (float)(ty * TILE + (ly & ~3)) + 0.5f;
     const uint2 rg = ranges[tile];
     const int64_t len = (int64_t)rg.y - rg.x;
     const int64_t nb = ceil_div(len, BATCH);
@@ -57,11 +60,12 @@ __global__ void __launch_bounds__(TILE *TILE) render_fwd_kernel(const float4 *__
             const float4 *r = recv + (int64_t)g * 3;
             s_a[k] = r[0];
             s_b[k] = r[1];
-            s_c[k] = r[2].x;
+            s_c[k] = r[2];
         }
         __syncthreads();
         if (!done) {
             for (int j = 0; j < cnt; ++j) {
+                if (!warp_overlaps(s_a[j], s_c[j], wx, wy)) continue;  // alpha' < alpha_min on all 32 pixels
                 const AlphaEval ae = eval_alpha(s_a[j], s_b[j], px, py, amax);
                 if (ae.alpha < amin) continue;
                 const float testT = __fmul_rn(T, __fsub_rn(1.f, ae.alpha));
@@ -73,7 +77,7 @@ __global__ void __launch_bounds__(TILE *TILE) render_fwd_kernel(const float4 *__
                 const float4 bb = s_b[j];
                 C0 += bb.z * w;
                 C1 += bb.w * w;
-                C2 += s_c[j] * w;
+                C2 += s_c[j].x * w;
                 T = testT;
                 last = (int32_t)(b * BATCH + j + 1);
             }

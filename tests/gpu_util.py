@@ -54,6 +54,10 @@ def records(rec: dict, cams: list, tile: int):
         R[v, :, 5] = r["opacity"]
         R[v, :, 6:9] = r["rgb"]
         R[v, :, 9] = r["depth"]
+        # support bound: alpha' >= 1/255 needs dp^T Q dp <= 2 ln 255 < 3.5^2, and
+        # the x (y) extent of that ellipse is at most 3.5 sigma1
+        R[v, :, 10] = 3.5 * r["sigma1"]
+        R[v, :, 11] = 3.5 * r["sigma1"]
         box = r["box"].astype(np.float64)
         x0 = np.maximum(np.ceil(box[:, 0] - 0.5), 0)
         x1 = np.minimum(np.floor(box[:, 1] - 0.5), cam.width - 1)
