@@ -33,7 +33,7 @@ constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int RS_MAX_BLOCKS = 608;  // 4 x 152 SMs
 constexpr int SCAN_THREADS = 1024;
 static_assert(RS_THREADS == RADIX, "the downsweep gives each thread one digit");
-static_assert(RS_MAX_BLOCKS <= SCAN_THREADS, "count_top scans the block sums in one pass");
+
 static_assert(RS_MAX_BLOCKS <= 4 * RS_THREADS, "rs_scan holds at most four counts per thread");
 
 __device__ __forceinline__ int64_t effective_count(const int64_t *d_count, int64_t cap) {
@@ -246,14 +246,13 @@ __global__ void depth_keys_kernel(const float *__restrict__ rec, const int32_t *
     vals[e] = (uint32_t)e;
 }
 
-// Scan of the tile counts in depth order, reduce phase: per-block sums.
+// Scan of the tile counts in depth order, reduce phase: one block per chunk of
+// RS_THREADS entries writes the chunk's pair count.
 __global__ void __launch_bounds__(RS_THREADS) count_reduce(const int32_t *__restrict__ touched,
                                                            const uint32_t *__restrict__ order, int64_t total,
-                                                           unsigned long long *__restrict__ block_sums) {
-    int64_t begin, end;
-    block_range(total, gridDim.x, blockIdx.x, begin, end);
-    unsigned long long s = 0;
-    for (int64_t m = begin + threadIdx.x; m < end; m += RS_THREADS) s += (unsigned)touched[order[m]];
+                                                           unsigned long long *__restrict__ chunk_sums) {
+    const int64_t m = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x;
+    unsigned long long s = m < total ? (unsigned)touched[order[m]] : 0u;
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     __shared__ unsigned long long ws[RS_WARPS];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -261,35 +260,40 @@ __global__ void __launch_bounds__(RS_THREADS) count_reduce(const int32_t *__rest
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int w = 0; w < RS_WARPS; ++w) t += ws[w];
-        block_sums[blockIdx.x] = t;
+        chunk_sums[blockIdx.x] = t;
     }
 }
 
-// Exclusive scan of the block sums (one block of SCAN_THREADS, G <= RS_MAX_BLOCKS);
-// writes the total pair count and the count the pair sort will use (0 when
-// over capacity).
-__global__ void __launch_bounds__(SCAN_THREADS) count_top(unsigned long long *block_sums, int G, int64_t cap,
+// Exclusive scan of the chunk sums by one block (SCAN_THREADS values per
+// round); writes the total pair count and the count the pair sort will use
+// (0 when over capacity).
+__global__ void __launch_bounds__(SCAN_THREADS) count_top(unsigned long long *chunk_sums, int64_t n_chunks, int64_t cap,
                                                           int64_t *dev_pair_count, int64_t *sort_count,
                                                           int32_t *dev_status) {
     __shared__ unsigned long long s[SCAN_THREADS];
-    const unsigned long long x = threadIdx.x < G ? block_sums[threadIdx.x] : 0ull;
-    s[threadIdx.x] = x;
-    __syncthreads();
-    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-        const unsigned long long y = threadIdx.x >= off ? s[threadIdx.x - off] : 0ull;
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < n_chunks; base += SCAN_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long x = i < n_chunks ? chunk_sums[i] : 0ull;
+        s[threadIdx.x] = x;
         __syncthreads();
-        s[threadIdx.x] += y;
+        for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+            const unsigned long long y = threadIdx.x >= off ? s[threadIdx.x - off] : 0ull;
+            __syncthreads();
+            s[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (i < n_chunks) chunk_sums[i] = carry + s[threadIdx.x] - x;
+        carry += s[SCAN_THREADS - 1];
         __syncthreads();
     }
-    if (threadIdx.x < G) block_sums[threadIdx.x] = s[threadIdx.x] - x;
-    if (threadIdx.x == SCAN_THREADS - 1) {
-        const unsigned long long run = s[threadIdx.x];
-        *dev_pair_count = (int64_t)run;
-        if ((int64_t)run > cap) {
+    if (threadIdx.x == 0) {
+        *dev_pair_count = (int64_t)carry;
+        if ((int64_t)carry > cap) {
             set_status(dev_status, GS_ERR_CAPACITY);
             *sort_count = 0;
         } else {
-            *sort_count = (int64_t)run;
+            *sort_count = (int64_t)carry;
         }
     }
 }
@@ -313,11 +317,10 @@ __global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restri
     __shared__ uint32_t s_k[EMIT_STAGE];
     __shared__ uint32_t s_v[EMIT_STAGE];
     __shared__ uint32_t s_warp[32];
-    int64_t begin, end;
-    block_range(total, gridDim.x, blockIdx.x, begin, end);
+    const int64_t end = total;
     uint64_t run = block_offsets[blockIdx.x];
-    for (int64_t b0 = begin; b0 < end; b0 += RS_THREADS) {
-        const int64_t m = b0 + threadIdx.x;
+    {
+        const int64_t m = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x;
         uint32_t c = 0, gi = 0;
         int4 r = make_int4(0, 0, -1, -1);
         int base = 0, tx_n = 0;
@@ -355,8 +358,6 @@ __global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restri
                     pvals[o] = gi;
                 }
         }
-        run += chunk_total;
-        __syncthreads();
     }
 }
 
@@ -407,7 +408,7 @@ struct BinWorkspace {
     uint32_t *dk[2], *dv[2];        // depth keys / entry ids, ping-pong, [V*N]
     uint32_t *pk[2], *pv;           // pair tile keys ping-pong [cap], pair values scratch [cap]
     uint32_t *counts;               // [RADIX * RS_MAX_BLOCKS] + [RADIX] digit totals
-    unsigned long long *block_sums; // [RS_MAX_BLOCKS]
+    unsigned long long *block_sums; // [ceil(total / RS_THREADS) + 1] chunk pair counts, then offsets
     int64_t *sort_count;            // [1]
 };
 
@@ -431,7 +432,7 @@ size_t bin_ws_layout(int64_t total, int64_t cap, BinWorkspace *w, char *base) {
     }
     char *pv = take(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
     char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1));
-    char *bs = take(sizeof(unsigned long long) * RS_MAX_BLOCKS);
+    char *bs = take(sizeof(unsigned long long) * (size_t)(ceil_div(total > 0 ? total : 1, RS_THREADS) + 1));
     char *sc = take(sizeof(int64_t));
     if (w) {
         w->pv = (uint32_t *)pv;
@@ -481,10 +482,10 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     const int dsel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream);
     GS_TRY_LAUNCH();
     const uint32_t *order = w.dv[dsel];
-    // 2. pair offsets in depth order, fused pair emission
-    const int G = rs_blocks(total);
-    count_reduce<<<G, RS_THREADS, 0, stream>>>(proj->tiles_touched, order, total, w.block_sums);
-    count_top<<<1, SCAN_THREADS, 0, stream>>>(w.block_sums, G, pair_capacity, dev_pair_count, w.sort_count,
+    // 2. pair offsets in depth order, fused pair emission (one block per chunk)
+    const int64_t n_chunks = ceil_div(total, RS_THREADS);
+    count_reduce<<<(unsigned)n_chunks, RS_THREADS, 0, stream>>>(proj->tiles_touched, order, total, w.block_sums);
+    count_top<<<1, SCAN_THREADS, 0, stream>>>(w.block_sums, n_chunks, pair_capacity, dev_pair_count, w.sort_count,
                                              dev_status);
     // The final pass must land in (pk[0], vals): emit into the buffer that an
     // even or odd number of passes maps there.
@@ -492,7 +493,7 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     const int passes = radix_passes(tbits);
     uint32_t *ek = (passes & 1) ? w.pk[1] : w.pk[0];
     uint32_t *ev = (passes & 1) ? w.pv : vals;
-    emit_pairs<<<G, RS_THREADS, 0, stream>>>(proj->tiles_touched, reinterpret_cast<const int4 *>(proj->rect), order,
+    emit_pairs<<<(unsigned)n_chunks, RS_THREADS, 0, stream>>>(proj->tiles_touched, reinterpret_cast<const int4 *>(proj->rect), order,
                                              total, n, cams, cfg->tile, w.block_sums, w.sort_count, ek, ev);
     GS_TRY_LAUNCH();
     // 3. stable sort of the pairs by tile id
@@ -532,7 +533,8 @@ constexpr int64_t kNoAllocMaxPairs = (int64_t)1 << 20;    // pair_capacity
 // bin_ws_layout: each buffer rounded up to 256 bytes).
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kNoAllocBytes = 4 * al256(4 * (size_t)kNoAllocMaxEntries) + 3 * al256(4 * (size_t)kNoAllocMaxPairs) +
-                                 al256(4 * (size_t)RADIX * (RS_MAX_BLOCKS + 1)) + al256(8 * (size_t)RS_MAX_BLOCKS) + al256(8);
+                                 al256(4 * (size_t)RADIX * (RS_MAX_BLOCKS + 1)) +
+                                 al256(8 * (size_t)(kNoAllocMaxEntries / RS_THREADS + 1)) + al256(8);
 
 // One copy per device that loads the library, held until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

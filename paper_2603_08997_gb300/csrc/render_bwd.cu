@@ -205,15 +205,22 @@ struct AdamFuse {
     const int64_t *step;
 };
 
-// Group strides (floats per Gaussian) and their offsets inside a staged block.
+// Group strides (floats per Gaussian) and the staged layout in shared memory:
+// per Gaussian each group is padded to an odd stride P(g), so the 32 threads
+// of a warp touching "their" element k hit 32 different banks.
 template <int DEG>
 struct Groups {
     static constexpr int K = (DEG + 1) * (DEG + 1);
-    static constexpr int TOT = 11 + 3 * K;
     __host__ __device__ static constexpr int S(int g) { return g == 0 ? 3 : (g == 1 ? 3 : (g == 2 ? 4 : (g == 3 ? 1 : 3 * K))); }
+    __host__ __device__ static constexpr int P(int g) { return S(g) | 1; }
+    static constexpr int TOT = P(0) + P(1) + P(2) + P(3) + P(4);  // padded floats per Gaussian
     __host__ __device__ static constexpr int off(int g, int nb) {
-        return g == 0 ? 0 : (g == 1 ? 3 * nb : (g == 2 ? 6 * nb : (g == 3 ? 10 * nb : 11 * nb)));
+        return g == 0 ? 0
+             : (g == 1 ? P(0) * nb
+             : (g == 2 ? (P(0) + P(1)) * nb : (g == 3 ? (P(0) + P(1) + P(2)) * nb : (P(0) + P(1) + P(2) + P(3)) * nb)));
     }
+    // linear index k of a group's contiguous global slice -> padded shared index
+    __host__ __device__ static constexpr int pad(int g, int k) { return (k / S(g)) * P(g) + k % S(g); }
 };
 
 constexpr int PB = 128;  // Gaussians (and threads) per projection-adjoint block
@@ -252,7 +259,7 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
         const int cnt = G::S(g) * nb;
         const float *sp = src[g] + (int64_t)G::S(g) * i0;
         float *dp = s_par + G::off(g, PB);
-        for (int k = threadIdx.x; k < cnt; k += PB) dp[k] = sp[k];
+        for (int k = threadIdx.x; k < cnt; k += PB) dp[G::pad(g, k)] = sp[k];
     }
     for (int k = threadIdx.x; k < G::TOT * PB; k += PB) s_grd[k] = 0.f;
     __syncthreads();
@@ -260,16 +267,16 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     const int t = threadIdx.x;
     if (t < nb) {
         const int64_t i = i0 + t;
-        const float *P0 = s_par + G::off(0, PB) + 3 * t;
-        const float *P1 = s_par + G::off(1, PB) + 3 * t;
-        const float *P2 = s_par + G::off(2, PB) + 4 * t;
-        const float logit = s_par[G::off(3, PB) + t];
-        const float *f = s_par + G::off(4, PB) + 3 * K * t;
-        float *D0 = s_grd + G::off(0, PB) + 3 * t;
-        float *D1 = s_grd + G::off(1, PB) + 3 * t;
-        float *D2 = s_grd + G::off(2, PB) + 4 * t;
-        float *D3 = s_grd + G::off(3, PB) + t;
-        float *DF = s_grd + G::off(4, PB) + 3 * K * t;
+        const float *P0 = s_par + G::off(0, PB) + G::P(0) * t;
+        const float *P1 = s_par + G::off(1, PB) + G::P(1) * t;
+        const float *P2 = s_par + G::off(2, PB) + G::P(2) * t;
+        const float logit = s_par[G::off(3, PB) + G::P(3) * t];
+        const float *f = s_par + G::off(4, PB) + G::P(4) * t;
+        float *D0 = s_grd + G::off(0, PB) + G::P(0) * t;
+        float *D1 = s_grd + G::off(1, PB) + G::P(1) * t;
+        float *D2 = s_grd + G::off(2, PB) + G::P(2) * t;
+        float *D3 = s_grd + G::off(3, PB) + G::P(3) * t;
+        float *DF = s_grd + G::off(4, PB) + G::P(4) * t;
         const float mu[3] = {P0[0], P0[1], P0[2]};
         const float ls[3] = {P1[0], P1[1], P1[2]};
         const float4 q4 = make_float4(P2[0], P2[1], P2[2], P2[3]);
@@ -409,8 +416,9 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
             const float *sg = s_grd + G::off(g, PB);
             for (int k = threadIdx.x; k < cnt; k += PB) {
                 const int lr = g < 4 ? g : ((k % (3 * K)) < 3 ? 4 : 5);
-                float p = sp[k], m = af.m[e0 + k], v = af.v[e0 + k];
-                adam_update(p, m, v, sg[k], s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+                const int ks = G::pad(g, k);
+                float p = sp[ks], m = af.m[e0 + k], v = af.v[e0 + k];
+                adam_update(p, m, v, sg[ks], s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
                 af.p[e0 + k] = p;
                 af.m[e0 + k] = m;
                 af.v[e0 + k] = v;
@@ -425,8 +433,8 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
             float *dp = dst[g] + (int64_t)G::S(g) * i0;
             const float *sg = s_grd + G::off(g, PB);
             for (int k = threadIdx.x; k < cnt; k += PB) {
-                if constexpr (MODE == 1) dp[k] += sg[k];
-                else dp[k] = sg[k];
+                if constexpr (MODE == 1) dp[k] += sg[G::pad(g, k)];
+                else dp[k] = sg[G::pad(g, k)];
             }
         }
     }
