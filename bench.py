@@ -284,20 +284,20 @@ def main():
         marks = sorted({m for m in (K - 3 * seg, K - 2 * seg, K - seg, K) if m > 0})
         ms, done, evals = 0.0, 0, []
         t0 = time.perf_counter()
-        torch.cuda.nvtx.range_push("timed_gated" if gated else "timed_full")
         for mark in marks:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("timed_gated" if gated else "timed_full")
             e0.record(loop.stream)
             for _ in range(mark - done):
                 loop.step_graph()
             e1.record(loop.stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             ms += e0.elapsed_time(e1)
             done = mark
             if mark >= K - 3 * seg:
                 evals.append(float(np.mean(loop.evaluate())))
-        torch.cuda.nvtx.range_pop()
         wall = time.perf_counter() - t0
         clocks = clock.stop() if clock else None
         gs = loop.gate.read(loop.stream)

@@ -16,7 +16,7 @@
 // can be captured in a CUDA graph.  The radix sort is a reduce-then-scan LSD
 // sort: an upsweep histogram per block, one exclusive scan over the
 // digit-major (digit, block) counts, and a downsweep that ranks each tile of
-// 2048 keys with warp match/ballot, reorders the tile by digit in shared
+// 2048 keys with warp ballots (one per digit bit), reorders the tile by digit in shared
 // memory and writes each digit's run contiguously.
 #include "common.cuh"
 
@@ -154,7 +154,13 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             k[r] = valid ? keys_in[base + li] : 0u;
             v[r] = valid ? vals_in[base + li] : 0u;
             const int d = valid ? (int)((k[r] >> shift) & mask) : RADIX + lane;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            // lanes with the same digit: intersect one ballot per digit bit
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int bit = 0; bit < RADIX_BITS; ++bit) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1);
+                peers &= ((d >> bit) & 1) ? bb : ~bb;
+            }
             const uint32_t rank = __popc(peers & lt_mask);
             uint32_t basec = 0;
             if (valid) basec = s_wcnt[warp][d];

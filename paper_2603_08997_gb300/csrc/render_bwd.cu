@@ -224,6 +224,7 @@ struct Groups {
 };
 
 constexpr int PB = 128;  // Gaussians (and threads) per projection-adjoint block
+constexpr int kStagedViews = 16;  // cameras copied to shared memory per block
 
 template <int DEG>
 constexpr size_t proj_bwd_smem() { return sizeof(float) * 2 * Groups<DEG>::TOT * PB; }
@@ -246,10 +247,12 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     float *s_grd = smem + G::TOT * PB;    // same layout
     __shared__ float s_lr[6];
     __shared__ float s_ibc2;
+    __shared__ gs_camera s_cams[kStagedViews];
     if constexpr (MODE == 2) {
         if (af.do_step && *af.do_step == 0) return;  // the same for every block
         if (threadIdx.x == 0) adam_scalars(af.cfg, *af.step, s_lr, &s_ibc2);
     }
+    if (threadIdx.x < n_views && threadIdx.x < kStagedViews) s_cams[threadIdx.x] = cams[threadIdx.x];
     const int64_t n = prm.n;
     const int64_t i0 = (int64_t)blockIdx.x * PB;
     const int nb = (int)min((int64_t)PB, n - i0);
@@ -257,9 +260,18 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
 #pragma unroll
     for (int g = 0; g < 5; ++g) {
         const int cnt = G::S(g) * nb;
-        const float *sp = src[g] + (int64_t)G::S(g) * i0;
+        const float *sp = src[g] + (int64_t)G::S(g) * i0;  // 16-byte aligned: i0 is a multiple of PB
         float *dp = s_par + G::off(g, PB);
-        for (int k = threadIdx.x; k < cnt; k += PB) dp[G::pad(g, k)] = sp[k];
+        const int cnt4 = cnt >> 2;
+#pragma unroll 4
+        for (int c = threadIdx.x; c < cnt4; c += PB) {
+            const float4 x = reinterpret_cast<const float4 *>(sp)[c];
+            dp[G::pad(g, 4 * c)] = x.x;
+            dp[G::pad(g, 4 * c + 1)] = x.y;
+            dp[G::pad(g, 4 * c + 2)] = x.z;
+            dp[G::pad(g, 4 * c + 3)] = x.w;
+        }
+        for (int k = 4 * cnt4 + threadIdx.x; k < cnt; k += PB) dp[G::pad(g, k)] = sp[k];
     }
     for (int k = threadIdx.x; k < G::TOT * PB; k += PB) s_grd[k] = 0.f;
     __syncthreads();
@@ -290,7 +302,7 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
 #pragma unroll
             for (int q = 0; q < 9; ++q) nz |= gd[q] != 0.f;
             if (!nz) continue;
-            const gs_camera &c = cams[v];
+            const gs_camera &c = v < kStagedViews ? s_cams[v] : cams[v];
             ProjState g;
             project_state(mu, ls, q4, logit, c, cfg.lowpass, g);
             if (g.culled) continue;
@@ -414,7 +426,29 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
             const int64_t e0 = af.o[g] + (int64_t)G::S(g) * i0;
             const float *sp = s_par + G::off(g, PB);
             const float *sg = s_grd + G::off(g, PB);
-            for (int k = threadIdx.x; k < cnt; k += PB) {
+            // float4 chunks (e0 is 16-byte aligned: group offsets are 64-float aligned, i0 a multiple of PB)
+            const int cnt4 = cnt >> 2;
+            float4 *P4 = reinterpret_cast<float4 *>(af.p + e0);
+            float4 *M4 = reinterpret_cast<float4 *>(af.m + e0);
+            float4 *V4 = reinterpret_cast<float4 *>(af.v + e0);
+#pragma unroll 2
+            for (int c = threadIdx.x; c < cnt4; c += PB) {
+                float4 m4 = M4[c], v4 = V4[c], p4;
+                float *pm = &m4.x, *pv = &v4.x, *pp4 = &p4.x;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = 4 * c + u;
+                    const int lr = g < 4 ? g : ((k % (3 * K)) < 3 ? 4 : 5);
+                    const int ks = G::pad(g, k);
+                    float p = sp[ks];
+                    adam_update(p, pm[u], pv[u], sg[ks], s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+                    pp4[u] = p;
+                }
+                P4[c] = p4;
+                M4[c] = m4;
+                V4[c] = v4;
+            }
+            for (int k = 4 * cnt4 + threadIdx.x; k < cnt; k += PB) {
                 const int lr = g < 4 ? g : ((k % (3 * K)) < 3 ? 4 : 5);
                 const int ks = G::pad(g, k);
                 float p = sp[ks], m = af.m[e0 + k], v = af.v[e0 + k];
