@@ -229,6 +229,70 @@ constexpr int kStagedViews = 16;  // cameras copied to shared memory per block
 template <int DEG>
 constexpr size_t proj_bwd_smem() { return sizeof(float) * 2 * Groups<DEG>::TOT * PB; }
 
+// Copy the float4 chunks [0, C4) of a global slice into the padded shared
+// layout; every load of the thread is issued before the first store.
+template <int DEG, int g, int C4>
+__device__ __forceinline__ void stage_full(const float *__restrict__ sp, float *dp) {
+    using G = Groups<DEG>;
+    constexpr int J = (C4 + PB - 1) / PB;
+    float4 x[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int c = threadIdx.x + j * PB;
+        if (c < C4) x[j] = reinterpret_cast<const float4 *>(sp)[c];
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int c = threadIdx.x + j * PB;
+        if (c < C4) {
+            dp[G::pad(g, 4 * c)] = x[j].x;
+            dp[G::pad(g, 4 * c + 1)] = x[j].y;
+            dp[G::pad(g, 4 * c + 2)] = x[j].z;
+            dp[G::pad(g, 4 * c + 3)] = x[j].w;
+        }
+    }
+}
+
+// Adam over the float4 chunks [0, C4) of a full block's slice of group g:
+// all m and v loads of the thread first, then the updates and stores.
+template <int DEG, int g, int C4>
+__device__ __forceinline__ void adam_full(float *__restrict__ P, float *__restrict__ M, float *__restrict__ V,
+                                          const float *sp, const float *sg, const float *lr_t, float ibc2,
+                                          const gs_adam_config &cfg) {
+    using G = Groups<DEG>;
+    constexpr int K3 = 3 * G::K;
+    constexpr int J = (C4 + PB - 1) / PB;
+    float4 m4[J], v4[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int c = threadIdx.x + j * PB;
+        if (c < C4) {
+            m4[j] = reinterpret_cast<const float4 *>(M)[c];
+            v4[j] = reinterpret_cast<const float4 *>(V)[c];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int c = threadIdx.x + j * PB;
+        if (c < C4) {
+            float4 p4;
+            float *pm = &m4[j].x, *pv = &v4[j].x, *pp = &p4.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = 4 * c + u;
+                const int lr = g < 4 ? g : ((k % K3) < 3 ? 4 : 5);
+                const int ks = G::pad(g, k);
+                float p = sp[ks];
+                adam_update(p, pm[u], pv[u], sg[ks], lr_t[lr], cfg.beta1, cfg.beta2, ibc2, cfg.eps);
+                pp[u] = p;
+            }
+            reinterpret_cast<float4 *>(P)[c] = p4;
+            reinterpret_cast<float4 *>(M)[c] = m4[j];
+            reinterpret_cast<float4 *>(V)[c] = v4[j];
+        }
+    }
+}
+
 // Projection adjoint, staged through shared memory.  The block copies the
 // parameter slices of its PB Gaussians (contiguous in every group) into
 // shared memory with coalesced loads; each thread chains its Gaussian's 2D
@@ -257,6 +321,13 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     const int64_t i0 = (int64_t)blockIdx.x * PB;
     const int nb = (int)min((int64_t)PB, n - i0);
     const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
+    if (nb == PB) {
+        stage_full<DEG, 0, 3 * PB / 4>(src[0] + 3 * i0, s_par + G::off(0, PB));
+        stage_full<DEG, 1, 3 * PB / 4>(src[1] + 3 * i0, s_par + G::off(1, PB));
+        stage_full<DEG, 2, PB>(src[2] + 4 * i0, s_par + G::off(2, PB));
+        stage_full<DEG, 3, PB / 4>(src[3] + i0, s_par + G::off(3, PB));
+        stage_full<DEG, 4, 3 * K * PB / 4>(src[4] + (int64_t)3 * K * i0, s_par + G::off(4, PB));
+    } else
 #pragma unroll
     for (int g = 0; g < 5; ++g) {
         const int cnt = G::S(g) * nb;
@@ -418,8 +489,20 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     // coalesced sweep over the block's slices
     if constexpr (MODE == 2) {
         const float ibc2 = s_ibc2;
-        float *pp[5];
-        for (int g = 0; g < 5; ++g) pp[g] = nullptr;
+        if (nb == PB) {
+            adam_full<DEG, 0, 3 * PB / 4>(af.p + af.o[0] + 3 * i0, af.m + af.o[0] + 3 * i0, af.v + af.o[0] + 3 * i0,
+                                         s_par + G::off(0, PB), s_grd + G::off(0, PB), s_lr, ibc2, af.cfg);
+            adam_full<DEG, 1, 3 * PB / 4>(af.p + af.o[1] + 3 * i0, af.m + af.o[1] + 3 * i0, af.v + af.o[1] + 3 * i0,
+                                         s_par + G::off(1, PB), s_grd + G::off(1, PB), s_lr, ibc2, af.cfg);
+            adam_full<DEG, 2, PB>(af.p + af.o[2] + 4 * i0, af.m + af.o[2] + 4 * i0, af.v + af.o[2] + 4 * i0,
+                                  s_par + G::off(2, PB), s_grd + G::off(2, PB), s_lr, ibc2, af.cfg);
+            adam_full<DEG, 3, PB / 4>(af.p + af.o[3] + i0, af.m + af.o[3] + i0, af.v + af.o[3] + i0,
+                                      s_par + G::off(3, PB), s_grd + G::off(3, PB), s_lr, ibc2, af.cfg);
+            const int64_t o4 = af.o[4] + (int64_t)3 * K * i0;
+            adam_full<DEG, 4, 3 * K * PB / 4>(af.p + o4, af.m + o4, af.v + o4, s_par + G::off(4, PB),
+                                              s_grd + G::off(4, PB), s_lr, ibc2, af.cfg);
+            return;
+        }
 #pragma unroll
         for (int g = 0; g < 5; ++g) {
             const int cnt = G::S(g) * nb;
@@ -458,7 +541,7 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
                 af.v[e0 + k] = v;
             }
         }
-        (void)pp;
+
     } else {
         float *dst[5] = {gr.means, gr.log_scales, gr.quats, gr.opacity_logit, gr.sh};
 #pragma unroll
