@@ -197,6 +197,95 @@ def run_reference(args) -> None:
 
 # ------------------------------------------------------------ GPU arm
 
+PEAK_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
+BACKWARD_STAGES = ("loss_bwd", "raster_bwd", "project_bwd", "adam")
+
+
+def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
+    """Time every entry point of one refinement iteration on the loop's stream
+    (CUDA events, `reps` launches each, state of the loop's last view)."""
+    import torch
+    r, s, adam = loop.renderer, loop.stream, loop.adam
+    params, grads = loop.params, loop.grads
+    snap = loop.snapshot()
+    fns = {
+        "project": lambda: r.project(params, s),
+        "bin_sort": lambda: r.bin_sort(s),
+        "render_fwd": lambda: r.render_fwd(s),
+        "loss": lambda: r.compute_loss(loop.targets, loop.target_offsets, loop.view_ids, stream=s),
+        "loss_bwd": lambda: r.loss_backward(loop.targets, loop.target_offsets, loop.view_ids, stream=s),
+        "raster_bwd": lambda: r.raster_bwd(stream=s),
+        "project_bwd": lambda: r.project_bwd(params, grads, stream=s),
+        "adam": lambda: adam.step(stream=s),
+    }
+    out = {}
+    with torch.cuda.stream(s):
+        for name, fn in fns.items():
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            out[name] = {"ms": e0.elapsed_time(e1) / reps}
+    loop.restore(snap)
+    tot = 0.0
+    for name, v in out.items():
+        v["weight"] = b_frac if name in BACKWARD_STAGES else 1.0
+        tot += v["weight"] * v["ms"]
+    for v in out.values():
+        v["share"] = v["weight"] * v["ms"] / tot
+    return out
+
+
+def roofline_of(stages: dict, loop, args) -> dict:
+    """Roofline of the stage with the largest share of the gated iteration.
+    Algorithmic work per launch (stated in the design doc): HBM stages count bytes
+    a launch must move; compositing stages count FLOPs per evaluated
+    (pixel, Gaussian) pair, with the evaluated pairs counted as sum(n_last)."""
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_note = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback 6.8 TB/s"
+    r = loop.renderer
+    N = r.n
+    E = N * r.views.n
+    P = int(r.pair_count.item())
+    px = r.views.total_pixels
+    evals = float(r.n_last.double().sum().item())
+    params = loop.model.flat.numel()
+    work = {
+        "project": ("hbm", N * (236 + 68), "bytes: 236 B parameters read + 68 B record, rectangle, count written per Gaussian"),
+        "bin_sort": ("hbm", 128 * E + 52 * P, "bytes: 128 B per (view, Gaussian) entry + 52 B per (Gaussian, tile) pair"),
+        "render_fwd": ("alu", 12.0 * evals, "FLOP: 12 per evaluated pair"),
+        "loss": ("hbm", 60 * px, "bytes: 60 B per pixel"),
+        "loss_bwd": ("hbm", 72 * px, "bytes: 72 B per pixel"),
+        "raster_bwd": ("alu", 40.0 * evals, "FLOP: 40 per evaluated pair"),
+        "project_bwd": ("hbm", N * (236 + 48 + 236), "bytes: 520 B per Gaussian"),
+        "adam": ("hbm", 28 * params, "bytes: 28 B per parameter (read p, g, m, v; write p, m, v)"),
+    }
+    name = max(stages, key=lambda k: stages[k]["share"])
+    bound, units, note = work[name]
+    t = stages[name]["ms"] * 1e-3
+    if bound == "hbm":
+        achieved, peak, unit, pk_note = units / t / 1e9, hbm, "GB/s", hbm_note
+    else:
+        achieved, peak, unit = units / t / 1e12, PEAK_ALU_TFLOPS, "TFLOP/s"
+        pk_note = "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": None, "work_per_launch": units, "work_def": note, "launch_ms": t * 1e3,
+            "share_of_gated_iteration": stages[name]["share"], "peak_note": pk_note,
+            "all_stages": {k: {"bound": w[0], "achieved": (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12),
+                               "frac": (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12) /
+                               (hbm if w[0] == "hbm" else PEAK_ALU_TFLOPS)} for k, w in work.items()}}
+
+
 def aggregate_time(t_local: float, dist, device) -> float:
     """Job time = the slowest rank's timed region (replicas, no data exchange)."""
     if dist is None:
@@ -311,28 +400,10 @@ def main():
     gated, ms_gated, wall_gated, gs_gated, st_gated, loss_gated, clocks = timed_loop(True)
     kc_gated = gated.kernels_per_step
 
-    # roofline of the dominant kernel (compositing forward), timed on the loop's stream
-    r = gated.renderer
-    s = gated.stream
-    reps = 20
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with torch.cuda.stream(s):
-        r.forward(gated.params, s)
-        torch.cuda.synchronize()
-        ev[0].record(s)
-        for _ in range(reps):
-            r.render_fwd(s)
-        ev[1].record(s)
-    torch.cuda.synchronize()
-    t_fwd = ev[0].elapsed_time(ev[1]) / reps * 1e-3
-    evals = float(r.n_last.double().sum().item())
-    flops = 12.0 * evals
-    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12
-    roofline = {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": flops / t_fwd / 1e12,
-                "peak": peak_alu, "unit": "TFLOP/s", "frac": flops / t_fwd / 1e12 / peak_alu, "traffic": None,
-                "units_per_launch": evals, "flop_per_unit": 12, "launch_ms": t_fwd * 1e3,
-                "peak_note": "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"}
-
+    # per-stage timing on the loop's stream (CUDA events, after the timed loops),
+    # weighted by how often each stage runs in the gated loop
+    stages = stage_times(gated, targets, b_frac=gs_gated["b"] / K)
+    roofline = roofline_of(stages, gated, args)
     # end-to-end through the C ABI with host-resident targets
     e2e = None
     if not args.no_e2e:
@@ -405,6 +476,8 @@ def main():
         "kernels_per_step": {"always": kc_gated[0], "backward_branch": kc_gated[1],
                              "full_loop": kc_full[0] + kc_full[1]},
         "roofline": roofline,
+        "stage_ms": {k: round(v["ms"], 4) for k, v in stages.items()},
+        "stage_share_gated": {k: round(v["share"], 4) for k, v in stages.items()},
     }
     try:
         line["cpu_baseline"] = cpu_baseline(args, start, cams[int(seq[0])], args.cpu_seconds)

@@ -263,6 +263,25 @@ gs_status gs_render_bwd(const gs_params *params /* host */, const gs_projected *
                         const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
                         size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream);
 
+/* The two passes of gs_render_bwd as separate calls (gs_render_bwd = the
+ * first followed by the second on the same g2d buffer):
+ * gs_raster_bwd - the raster adjoint: per view and Gaussian the gradients of
+ *   the loss with respect to (mean2D.x, mean2D.y, conic a, b, c, opacity, r, g,
+ *   b) into g2d [n_views][n][12] floats (3 padding; zeroed first; 16-byte
+ *   aligned; g2d_bytes >= gs_render_bwd_workspace_size(n, n_views)), where
+ *   the conic Q = [[a, b], [b, c]] is parameterised by its three entries;
+ * gs_project_bwd - the projection adjoint from g2d to the parameters, views
+ *   summed; grads overwritten (accumulate = 0) or added to.
+ * Parameter pointers must be 16-byte aligned (as inside gs_param_layout). */
+gs_status gs_raster_bwd(const gs_projected *proj /* host */, int64_t n, const uint32_t *vals, const uint32_t *ranges,
+                        const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                        const gs_raster_config *cfg /* host */, gs_fwd_saved saved, const float *dL_dimage,
+                        const uint8_t *view_gate, float *g2d, size_t g2d_bytes, int32_t *dev_status,
+                        cudaStream_t stream);
+gs_status gs_project_bwd(const gs_params *params /* host */, const gs_camera *cams, int32_t n_views,
+                         const gs_raster_config *cfg /* host */, const float *g2d, const uint8_t *view_gate,
+                         gs_grads grads, int32_t accumulate, int32_t *dev_status, cudaStream_t stream);
+
 /* ----------------------------------------------------------------- Adam */
 /* (gs_adam_config and gs_adam_step below; gs_render_bwd_adam after them.) */
 

@@ -615,28 +615,37 @@ __global__ void adam_step_count_kernel(const int32_t *do_step, int64_t *step) {
     if (!do_step || *do_step) *step += 1;
 }
 
-// The two adjoint passes shared by gs_render_bwd and gs_render_bwd_adam.
-template <bool FUSED>
-gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
-                          const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
-                          const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
-                          const uint8_t *view_gate, gs_grads grads, int32_t accumulate, const AdamFuse &af,
-                          void *workspace, cudaStream_t stream) {
-    const int64_t n = params->n;
-    float4 *g2d = reinterpret_cast<float4 *>(workspace);
+// The staged projection adjoint reads every parameter group with 16-byte loads.
+bool proj_params_aligned(const gs_params &p) {
+    return !(((uintptr_t)p.means | (uintptr_t)p.log_scales | (uintptr_t)p.quats | (uintptr_t)p.opacity_logit |
+              (uintptr_t)p.sh) & 15);
+}
+
+// Raster adjoint: zero the per-view 2D gradient buffer, then one CTA per tile.
+gs_status raster_bwd_impl(int64_t n, const gs_projected *proj, const uint32_t *vals, const uint32_t *ranges,
+                          const gs_camera *cams, int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg,
+                          gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate, float4 *g2d,
+                          cudaStream_t stream) {
     GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
     const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    gs_status st;
     switch (cfg->tile) {
-        case 8: st = launch_bwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
-        case 16: st = launch_bwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
-        case 32: st = launch_bwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d); break;
+        case 8: return launch_bwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 16: return launch_bwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 32: return launch_bwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
         default: return GS_ERR_INVALID_ARG;
     }
-    if (st != GS_OK) return st;
+}
+
+// Projection adjoint (MODE from `fused` / `accumulate`), then the step count when fused.
+template <bool FUSED>
+gs_status project_bwd_impl(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                           const gs_raster_config *cfg, const float4 *g2d, const uint8_t *view_gate, gs_grads grads,
+                           int32_t accumulate, const AdamFuse &af, cudaStream_t stream) {
+    const int64_t n = params->n;
     const unsigned blocks = (unsigned)ceil_div(n, PB);
     const int mode = FUSED ? 2 : (accumulate ? 1 : 0);
+    gs_status st;
     switch (params->sh_degree) {
         case 0: st = launch_proj_bwd<0>(mode, blocks, stream, *params, cams, n_views, view_gate, *cfg, g2d, grads, af); break;
         case 1: st = launch_proj_bwd<1>(mode, blocks, stream, *params, cams, n_views, view_gate, *cfg, g2d, grads, af); break;
@@ -649,6 +658,19 @@ gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, con
         GS_TRY_LAUNCH();
     }
     return GS_OK;
+}
+
+template <bool FUSED>
+gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
+                          const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                          const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                          const uint8_t *view_gate, gs_grads grads, int32_t accumulate, const AdamFuse &af,
+                          void *workspace, cudaStream_t stream) {
+    float4 *g2d = reinterpret_cast<float4 *>(workspace);
+    gs_status st = raster_bwd_impl(params->n, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
+                                   view_gate, g2d, stream);
+    if (st != GS_OK) return st;
+    return project_bwd_impl<FUSED>(params, cams, n_views, cfg, g2d, view_gate, grads, accumulate, af, stream);
 }
 
 }  // namespace
@@ -673,8 +695,7 @@ gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const
         return GS_ERR_INVALID_ARG;
     if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
     if (!grads.means || !grads.log_scales || !grads.quats || !grads.opacity_logit || !grads.sh) return GS_ERR_INVALID_ARG;
-    if (((uintptr_t)grads.quats & 15) || ((uintptr_t)params->quats & 15) || ((uintptr_t)proj->rec & 15))
-        return GS_ERR_INVALID_ARG;
+    if (!proj_params_aligned(*params) || ((uintptr_t)proj->rec & 15)) return GS_ERR_INVALID_ARG;
     const int64_t n = params->n;
     if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
@@ -682,6 +703,39 @@ gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const
     AdamFuse af{};
     return render_bwd_impl<false>(params, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
                                   view_gate, grads, accumulate, af, workspace, stream);
+}
+
+gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, const uint32_t *vals, const uint32_t *ranges,
+                        const gs_camera *cams, int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg,
+                        gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate, float *g2d,
+                        size_t g2d_bytes, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    if (!proj || !cfg || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0 || n < 0 ||
+        n >= ((int64_t)1 << 31))
+        return GS_ERR_INVALID_ARG;
+    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
+    if (!g2d || g2d_bytes < gs_render_bwd_workspace_size(n, n_views) || ((uintptr_t)g2d & 15)) return GS_ERR_WORKSPACE;
+    if (n == 0) return GS_OK;
+    return raster_bwd_impl(n, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage, view_gate,
+                           reinterpret_cast<float4 *>(g2d), stream);
+}
+
+gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg,
+                         const float *g2d, const uint8_t *view_gate, gs_grads grads, int32_t accumulate,
+                         int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    if (!params || !cams || !cfg || !g2d || n_views <= 0) return GS_ERR_INVALID_ARG;
+    if (params->n < 0 || params->n >= ((int64_t)1 << 31) || params->sh_degree < 0 || params->sh_degree > 3 ||
+        cfg->sh_degree != params->sh_degree)
+        return GS_ERR_INVALID_ARG;
+    if (!grads.means || !grads.log_scales || !grads.quats || !grads.opacity_logit || !grads.sh) return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)g2d & 15) return GS_ERR_INVALID_ARG;
+    if (params->n == 0) return GS_OK;
+    if (!proj_params_aligned(*params)) return GS_ERR_INVALID_ARG;
+    AdamFuse af{};
+    return project_bwd_impl<false>(params, cams, n_views, cfg, reinterpret_cast<const float4 *>(g2d), view_gate,
+                                   grads, accumulate, af, stream);
 }
 
 gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,

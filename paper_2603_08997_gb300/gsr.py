@@ -86,6 +86,10 @@ _PROTOS = {
     "gs_render_bwd_workspace_size": (C.c_size_t, [_I64, _I32]),
     "gs_render_bwd": (C.c_int, [C.POINTER(gs_params), C.POINTER(gs_projected), _P, _P, _P, _I32, _I64,
                                 C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, gs_grads, _I32, _P, _SZ, _P, _S]),
+    "gs_raster_bwd": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
+                                gs_fwd_saved, _P, _P, _P, _SZ, _P, _S]),
+    "gs_project_bwd": (C.c_int, [C.POINTER(gs_params), _P, _I32, C.POINTER(gs_raster_config), _P, _P, gs_grads, _I32,
+                                 _P, _S]),
     "gs_render_bwd_adam": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(gs_projected), _P, _P, _P, _I32, _I64,
                                      C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, C.POINTER(gs_adam_config), _P,
                                      _P, _P, _SZ, _P, _S]),

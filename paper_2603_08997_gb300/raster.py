@@ -215,6 +215,24 @@ class Renderer:
                  self.c_saved(), gsr.ptr(dl), gsr.ptr(view_gate), grads, int(bool(accumulate)),
                  gsr.ptr(self.bwd_ws), self.bwd_ws_bytes, gsr.ptr(self.status), gsr.stream_handle(stream))
 
+    def raster_bwd(self, dL_dimage: torch.Tensor | None = None, view_gate: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        """Raster adjoint only: per-view 2D gradients into self.bwd_ws ([V][N][12] floats)."""
+        proj = self.c_proj()
+        dl = self.dL_dimage if dL_dimage is None else dL_dimage
+        gsr.call("gs_raster_bwd", C.byref(proj), self.n, gsr.ptr(self.vals), gsr.ptr(self.ranges),
+                 gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg), self.c_saved(),
+                 gsr.ptr(dl), gsr.ptr(view_gate), gsr.ptr(self.bwd_ws), self.bwd_ws_bytes, gsr.ptr(self.status),
+                 gsr.stream_handle(stream))
+        return self.bwd_ws.view(torch.float32).view(self.views.n, self.n, 12)
+
+    def project_bwd(self, params: gsr.gs_params, grads: gsr.gs_grads, view_gate: torch.Tensor | None = None,
+                    accumulate: bool = False, stream=None) -> None:
+        """Projection adjoint from the 2D gradients that raster_bwd left in self.bwd_ws."""
+        gsr.call("gs_project_bwd", C.byref(params), gsr.ptr(self.views.dev), self.views.n, C.byref(self.cfg),
+                 gsr.ptr(self.bwd_ws), gsr.ptr(view_gate), grads, int(bool(accumulate)), gsr.ptr(self.status),
+                 gsr.stream_handle(stream))
+
     def backward_adam(self, model: "GaussianModel", adam: "AdamState", dL_dimage: torch.Tensor | None = None,
                       view_gate: torch.Tensor | None = None, do_step: torch.Tensor | None = None,
                       stream=None) -> None:

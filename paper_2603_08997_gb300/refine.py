@@ -3,9 +3,9 @@
 One iteration: select the view of this iteration (device-side, from the
 pre-drawn view sequence) -> project -> bin/sort -> render -> loss (value) ->
 gate decision -> [loss gradient -> raster and projection adjoint -> Adam]
-only when g = 1 -> per-view EMA update.  By default the projection adjoint
-and Adam run as one kernel (gs_render_bwd_adam); fused=False issues
-gs_render_bwd and gs_adam_step separately.
+only when g = 1 -> per-view EMA update.  The backward branch issues
+gs_render_bwd then gs_adam_step; fused=True uses gs_render_bwd_adam (the
+projection adjoint and Adam in one kernel) instead.
 
 `step_graph` replays the iteration as one CUDA graph: the bracketed branch is
 an IF conditional node that the gate kernel sets on the device, so no value
@@ -28,7 +28,7 @@ class RefinementLoop:
     def __init__(self, model: GaussianModel, train_cams: list, targets: torch.Tensor, view_seq,
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
-                 fused: bool = True):
+                 fused: bool = False):
         self.model = model
         self.fused = bool(fused)
         self.s = settings or RasterSettings()
