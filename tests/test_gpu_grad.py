@@ -241,4 +241,5 @@ def test_split_backward_equals_render_bwd():
     r.raster_bwd(dL_dimage=dl)
     r.project_bwd(model.c_params(), model.c_grads(g2))
     torch.cuda.synchronize()
-    torch.testing.assert_close(g2, g1, rtol=1e-5, atol=1e-9)
+    # equal up to the order of the float atomics in the raster adjoint
+    assert gpu_util.rel_err(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-6
