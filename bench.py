@@ -217,6 +217,7 @@ def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
         "raster_bwd": lambda: r.raster_bwd(stream=s),
         "project_bwd": lambda: r.project_bwd(params, grads, stream=s),
         "adam": lambda: adam.step(stream=s),
+        "project_bwd_adam": lambda: r.backward_adam(loop.model, adam, stream=s),  # fused alternative
     }
     out = {}
     with torch.cuda.stream(s):
@@ -231,9 +232,12 @@ def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
             torch.cuda.synchronize()
             out[name] = {"ms": e0.elapsed_time(e1) / reps}
     loop.restore(snap)
+    # the fused call includes its raster adjoint: its own cost is the difference
+    out["project_bwd_adam"]["ms"] = max(out["project_bwd_adam"]["ms"] - out["raster_bwd"]["ms"], 0.0)
     tot = 0.0
     for name, v in out.items():
-        v["weight"] = b_frac if name in BACKWARD_STAGES else 1.0
+        v["weight"] = (0.0 if name == "project_bwd_adam" else b_frac) if name in BACKWARD_STAGES + ("project_bwd_adam",) \
+            else 1.0
         tot += v["weight"] * v["ms"]
     for v in out.values():
         v["share"] = v["weight"] * v["ms"] / tot
@@ -269,6 +273,7 @@ def roofline_of(stages: dict, loop, args) -> dict:
         "raster_bwd": ("alu", 40.0 * evals, "FLOP: 40 per evaluated pair"),
         "project_bwd": ("hbm", N * (236 + 48 + 236), "bytes: 520 B per Gaussian"),
         "adam": ("hbm", 28 * params, "bytes: 28 B per parameter (read p, g, m, v; write p, m, v)"),
+        "project_bwd_adam": ("hbm", N * (48 + 236) + 24 * params, "bytes: 284 B per Gaussian + 24 B per parameter"),
     }
     name = max(stages, key=lambda k: stages[k]["share"])
     bound, units, note = work[name]

@@ -37,6 +37,19 @@ __host__ __device__ inline void param_offsets(int64_t n, int sh_degree, int64_t 
     o[5] = al(o[4] + 3 * K * n);
 }
 
+// sqrt and reciprocal on the special-function unit (PTX sqrt.approx /
+// rcp.approx, relative error ~2^-22): the optimizer step needs no more.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One Adam update of a scalar (Kingma & Ba, bias-corrected): lr_t = lr / (1 -
 // beta1^t), ibc2 = 1 / sqrt(1 - beta2^t).  Shared by the standalone optimizer
 // kernel and the fused adjoint + optimizer kernel so both round alike.
@@ -44,7 +57,7 @@ __device__ __forceinline__ void adam_update(float &p, float &m, float &v, float 
                                             float ibc2, float eps) {
     m = b1 * m + (1.f - b1) * g;
     v = b2 * v + (1.f - b2) * g * g;
-    p -= lr_t * m / (sqrtf(v) * ibc2 + eps);
+    p -= lr_t * m * rcp_approx(sqrt_approx(v) * ibc2 + eps);
 }
 
 // Per-step Adam scalars from the executed-step counter (computed once per block).
@@ -100,19 +113,23 @@ __device__ __forceinline__ AlphaEval eval_alpha(float4 a, float4 b, float px, fl
     return r;
 }
 
-// Pixel of thread t in a TILE x TILE tile: each warp covers an 8 x 4 block,
-// so a warp can skip a Gaussian whose support box misses its block.
-template <int TILE>
-__device__ __forceinline__ void tile_pixel(int t, int &lx, int &ly) {
+// Pixels of thread t in a TILE x TILE tile when each thread owns PPT pixels:
+// each warp covers an 8 x (4 PPT) block (pixel k of a thread is 4k rows below
+// its first), so a warp can skip a Gaussian whose support box misses its block.
+// Pixel k of thread t has the in-tile slot t + k * (TILE * TILE / PPT).
+template <int TILE, int PPT>
+__device__ __forceinline__ void tile_pixel(int t, int k, int &lx, int &ly) {
     const int w = t >> 5, lane = t & 31;
     lx = (w % (TILE / 8)) * 8 + (lane & 7);
-    ly = (w / (TILE / 8)) * 4 + (lane >> 3);
+    ly = (w / (TILE / 8)) * (4 * PPT) + (lane >> 3) + 4 * k;
 }
 
 // Does the support box [m - r, m + r] of a Gaussian reach any pixel centre of
-// the warp's 8 x 4 block whose first pixel centre is (wx, wy)?  Uniform per warp.
+// the warp's 8 x H block whose first pixel centre is (wx, wy)?  Uniform per warp.
+template <int H>
 __device__ __forceinline__ bool warp_overlaps(float4 a, float4 c, float wx, float wy) {
-    return fabsf(a.x - (wx + 3.5f)) <= c.z + 3.5f && fabsf(a.y - (wy + 1.5f)) <= c.w + 1.5f;
+    constexpr float hy = 0.5f * (H - 1);
+    return fabsf(a.x - (wx + 3.5f)) <= c.z + 3.5f && fabsf(a.y - (wy + hy)) <= c.w + hy;
 }
 
 // Real spherical harmonics (Condon-Shortley phase) up to degree 3 at a unit

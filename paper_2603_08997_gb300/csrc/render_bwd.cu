@@ -1,6 +1,6 @@
 // gs_render_bwd: analytic adjoint of gs_render_fwd and gs_project.
 //
-// Raster adjoint (one CTA per tile, one thread per pixel).  With
+// Raster adjoint (one CTA per tile, PPT = 1 or 2 pixels per thread).  With
 // A_k = sum_{j>k} c_j a_j T_j + T_end bg (the colour behind contributor k),
 // Eq. (blend) gives dC/dc_k = a_k T_k and dC/da_k = c_k T_k - A_k / (1 - a_k).
 // Batches are visited last to first and each pixel walks back from its last
@@ -10,8 +10,8 @@
 // spans more than one batch.  The alphas come from the same bit-exact
 // evaluation as the forward pass, so the contributor set is identical.
 //
-// Per pair the 9 gradients (mean2D 2, conic 3, opacity 1, colour 3) are
-// reduced across the warp with a halving shuffle tree (12 shuffles for 9
+// Per Gaussian the 9 gradients (mean2D 2, conic 3, opacity 1, colour 3) of a
+// thread's pixels are summed, then reduced across the warp with a halving shuffle tree (12 shuffles for 9
 // values), summed per Gaussian in shared memory, and added once per
 // (Gaussian, tile) to a per-view buffer with float4 vector atomics.
 //
@@ -60,13 +60,14 @@ __device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane, int
     return d;
 }
 
-template <int TILE, int BATCH>
-__global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
+template <int TILE, int BATCH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     const float4 *__restrict__ rec, int64_t n, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
     const gs_camera *__restrict__ cams, int n_views, gs_raster_config cfg, const float *__restrict__ T_final,
     const int32_t *__restrict__ n_last, const float *__restrict__ ckpt, int64_t ckpt_slots,
     const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d) {
     constexpr int NT = TILE * TILE;
+    constexpr int NTH = TILE * TILE / PPT;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
     __shared__ float4 s_c[BATCH];
@@ -80,98 +81,123 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
     const int tiles_x = (cam.width + TILE - 1) / TILE;
     const int64_t lt = tile - cam.tile_offset;
     const int tx = (int)(lt % tiles_x), ty = (int)(lt / tiles_x);
-    int lx, ly;
-    tile_pixel<TILE>(threadIdx.x, lx, ly);
-    const int x = tx * TILE + lx, y = ty * TILE + ly;
-    const bool inside = x < cam.width && y < cam.height;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    const float wx = (float)(tx * TILE + (lx & ~7)) + 0.5f, wy = (float)(ty * TILE + (ly & ~3)) + 0.5f;
+    int lx0, ly0;
+    tile_pixel<TILE, PPT>(threadIdx.x & ~31, 0, lx0, ly0);  // first pixel of the warp's block
+    const float wx = (float)(tx * TILE + lx0) + 0.5f, wy = (float)(ty * TILE + ly0) + 0.5f;
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[tile];
     const int64_t slot0 = (int64_t)(rg.x / BATCH) + tile;
     const float4 *recv = rec + (int64_t)v * n * 3;
     const float amax = cfg.alpha_max, amin = cfg.alpha_min;
 
-    int my_last = 0;
-    float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, T_end = 0.f;
-    if (inside) {
-        const int64_t hw = (int64_t)cam.width * cam.height;
-        const int64_t pix = (int64_t)y * cam.width + x;
-        my_last = n_last[cam.pix_offset + pix];
-        T_end = T_final[cam.pix_offset + pix];
-        const float *g = dL_dimage + 3 * cam.pix_offset;
-        dC0 = g[pix];
-        dC1 = g[hw + pix];
-        dC2 = g[2 * hw + pix];
+    int lp[PPT], my_last[PPT];
+    float px[PPT], py[PPT], dC0[PPT], dC1[PPT], dC2[PPT], T_end[PPT];
+    int local_max = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        int lx, ly;
+        tile_pixel<TILE, PPT>(threadIdx.x, k, lx, ly);
+        lp[k] = ly * TILE + lx;
+        const int x = tx * TILE + lx, y = ty * TILE + ly;
+        px[k] = (float)x + 0.5f;
+        py[k] = (float)y + 0.5f;
+        my_last[k] = 0;
+        dC0[k] = dC1[k] = dC2[k] = T_end[k] = 0.f;
+        if (x < cam.width && y < cam.height) {
+            const int64_t hw = (int64_t)cam.width * cam.height;
+            const int64_t pix = (int64_t)y * cam.width + x;
+            my_last[k] = n_last[cam.pix_offset + pix];
+            T_end[k] = T_final[cam.pix_offset + pix];
+            const float *g = dL_dimage + 3 * cam.pix_offset;
+            dC0[k] = g[pix];
+            dC1[k] = g[hw + pix];
+            dC2[k] = g[2 * hw + pix];
+        }
+        local_max = max(local_max, my_last[k]);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    if (my_last > 0) atomicMax(&s_max, my_last);
+    if (local_max > 0) atomicMax(&s_max, local_max);
     __syncthreads();
     const int max_last = s_max;
-    float A0 = T_end * cfg.bg[0], A1 = T_end * cfg.bg[1], A2 = T_end * cfg.bg[2];
+    float A0[PPT], A1[PPT], A2[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        A0[k] = T_end[k] * cfg.bg[0];
+        A1[k] = T_end[k] * cfg.bg[1];
+        A2[k] = T_end[k] * cfg.bg[2];
+    }
 
     for (int b = (max_last + BATCH - 1) / BATCH - 1; b >= 0; --b) {
         __syncthreads();
         const int64_t b0 = (int64_t)rg.x + (int64_t)b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const uint32_t g = vals[b0 + k];
+        for (int kk = threadIdx.x; kk < cnt; kk += NTH) {
+            const uint32_t g = vals[b0 + kk];
             const float4 *r = recv + (int64_t)g * 3;
-            s_a[k] = r[0];
-            s_b[k] = r[1];
-            s_c[k] = r[2];
-            s_g[k] = g;
+            s_a[kk] = r[0];
+            s_b[kk] = r[1];
+            s_c[kk] = r[2];
+            s_g[kk] = g;
         }
-        for (int k = threadIdx.x; k < BATCH * 9; k += NT) (&s_acc[0][0])[k] = 0.f;
+        for (int kk = threadIdx.x; kk < BATCH * 9; kk += NTH) (&s_acc[0][0])[kk] = 0.f;
         __syncthreads();
         const int lo = b * BATCH;
-        int jstart = -1;
-        float T = 0.f;
-        if (my_last > lo + cnt) {
-            jstart = cnt - 1;
-            const int64_t slot = slot0 + b + 1;
-            T = slot < ckpt_slots ? ckpt[slot * NT + threadIdx.x] : 0.f;
-        } else if (my_last > lo) {
-            jstart = my_last - 1 - lo;
-            T = T_end;
+        int jstart[PPT];
+        float T[PPT];
+        int jmax = -1;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            jstart[k] = -1;
+            T[k] = 0.f;
+            if (my_last[k] > lo + cnt) {
+                jstart[k] = cnt - 1;
+                const int64_t slot = slot0 + b + 1;
+                T[k] = slot < ckpt_slots ? ckpt[slot * NT + lp[k]] : 0.f;
+            } else if (my_last[k] > lo) {
+                jstart[k] = my_last[k] - 1 - lo;
+                T[k] = T_end[k];
+            }
+            jmax = max(jmax, jstart[k]);
         }
-        const int wj = __reduce_max_sync(FULL, jstart);
+        const int wj = __reduce_max_sync(FULL, jmax);
         for (int j = wj; j >= 0; --j) {
-            if (!warp_overlaps(s_a[j], s_c[j], wx, wy)) continue;  // no lane of the warp has this contributor
+            const float4 sa = s_a[j], sc = s_c[j];
+            if (!warp_overlaps<4 * PPT>(sa, sc, wx, wy)) continue;  // no lane of the warp has this contributor
+            const float4 sb = s_b[j];
             float gv[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) gv[q] = 0.f;
             bool contrib = false;
-            if (j <= jstart) {
-                const float4 sa = s_a[j], sb = s_b[j];
-                const AlphaEval ae = eval_alpha(sa, sb, px, py, amax);
-                if (ae.alpha >= amin) {
-                    contrib = true;
-                    const float om = __fsub_rn(1.f, ae.alpha);
-                    const float inv = 1.f / om;
-                    const float Tk = T * inv;
-                    const float wgt = ae.alpha * Tk;
-                    const float c0 = sb.z, c1 = sb.w, c2 = s_c[j].x;
-                    gv[6] = dC0 * wgt;
-                    gv[7] = dC1 * wgt;
-                    gv[8] = dC2 * wgt;
-                    const float da = dC0 * (c0 * Tk - A0 * inv) + dC1 * (c1 * Tk - A1 * inv) + dC2 * (c2 * Tk - A2 * inv);
-                    A0 += c0 * wgt;
-                    A1 += c1 * wgt;
-                    A2 += c2 * wgt;
-                    T = Tk;
-                    if (!ae.clamped) {
-                        gv[5] = da * ae.G;                   // dL/d opacity
-                        const float dG = da * sb.y;          // dL/dG
-                        const float gG = dG * ae.G;
-                        gv[0] = gG * sa.z * ae.z0;                       // dL/d mean2D.x = G dG (Q dp)_x
-                        gv[1] = gG * (sa.w * ae.z0 + sb.x * ae.z1);     // dL/d mean2D.y
-                        const float dq = -0.5f * gG;                     // dL/d(dp^T Q dp)
-                        gv[2] = dq * ae.dx * ae.dx;
-                        gv[3] = 2.f * dq * ae.dx * ae.dy;
-                        gv[4] = dq * ae.dy * ae.dy;
-                    }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (j > jstart[k]) continue;
+                const AlphaEval ae = eval_alpha(sa, sb, px[k], py[k], amax);
+                if (ae.alpha < amin) continue;
+                contrib = true;
+                const float om = __fsub_rn(1.f, ae.alpha);
+                const float inv = 1.f / om;
+                const float Tk = T[k] * inv;
+                const float wgt = ae.alpha * Tk;
+                const float c0 = sb.z, c1 = sb.w, c2 = sc.x;
+                gv[6] += dC0[k] * wgt;
+                gv[7] += dC1[k] * wgt;
+                gv[8] += dC2[k] * wgt;
+                const float da = dC0[k] * (c0 * Tk - A0[k] * inv) + dC1[k] * (c1 * Tk - A1[k] * inv) +
+                                 dC2[k] * (c2 * Tk - A2[k] * inv);
+                A0[k] += c0 * wgt;
+                A1[k] += c1 * wgt;
+                A2[k] += c2 * wgt;
+                T[k] = Tk;
+                if (!ae.clamped) {
+                    gv[5] += da * ae.G;                      // dL/d opacity
+                    const float gG = da * sb.y * ae.G;       // G dL/dG
+                    gv[0] += gG * sa.z * ae.z0;              // dL/d mean2D.x = G dG (Q dp)_x
+                    gv[1] += gG * (sa.w * ae.z0 + sb.x * ae.z1);  // dL/d mean2D.y
+                    const float dq = -0.5f * gG;             // dL/d(dp^T Q dp)
+                    gv[2] += dq * ae.dx * ae.dx;
+                    gv[3] += 2.f * dq * ae.dx * ae.dy;
+                    gv[4] += dq * ae.dy * ae.dy;
                 }
             }
             if (__any_sync(FULL, contrib)) {
@@ -181,13 +207,13 @@ __global__ void __launch_bounds__(TILE *TILE) render_bwd_kernel(
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const float *a = s_acc[k];
+        for (int kk = threadIdx.x; kk < cnt; kk += NTH) {
+            const float *a = s_acc[kk];
             bool nz = false;
 #pragma unroll
             for (int q = 0; q < 9; ++q) nz |= a[q] != 0.f;
             if (!nz) continue;
-            float4 *dst = g2d + ((int64_t)v * n + s_g[k]) * 3;
+            float4 *dst = g2d + ((int64_t)v * n + s_g[kk]) * 3;
             atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
             atomicAdd(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
             atomicAdd(&dst[2].x, a[8]);
@@ -557,32 +583,39 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     }
 }
 
-template <int TILE>
+template <int TILE, int PPT>
 gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
                      const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
                      const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate, float4 *g2d) {
     const dim3 grid((unsigned)total_tiles);
+    constexpr int NTH = TILE * TILE / PPT;
     switch (batch) {
         case 64:
-            render_bwd_kernel<TILE, 64><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
-                                                                         s.T_final, s.n_last, s.ckpt, s.ckpt_slots, dL,
-                                                                         gate, g2d);
+            render_bwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
+                                                                      s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d);
             break;
         case 128:
-            render_bwd_kernel<TILE, 128><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
-                                                                          s.T_final, s.n_last, s.ckpt, s.ckpt_slots,
-                                                                          dL, gate, g2d);
+            render_bwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
+                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d);
             break;
         case 256:
-            render_bwd_kernel<TILE, 256><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
-                                                                          s.T_final, s.n_last, s.ckpt, s.ckpt_slots,
-                                                                          dL, gate, g2d);
+            render_bwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
+                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d);
             break;
         default:
             return GS_ERR_UNSUPPORTED;
     }
     GS_TRY_LAUNCH();
     return GS_OK;
+}
+
+template <int TILE>
+gs_status launch_bwd_ppt(int ppt, int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
+                         const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                         const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate,
+                         float4 *g2d) {
+    if (ppt == 2) return launch_bwd<TILE, 2>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
+    return launch_bwd<TILE, 1>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
 }
 
 template <int DEG, int MODE>
@@ -629,10 +662,11 @@ gs_status raster_bwd_impl(int64_t n, const gs_projected *proj, const uint32_t *v
     GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
     const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2) return GS_ERR_INVALID_ARG;
     switch (cfg->tile) {
-        case 8: return launch_bwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
-        case 16: return launch_bwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
-        case 32: return launch_bwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 8: return launch_bwd_ppt<8>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 16: return launch_bwd_ppt<16>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 32: return launch_bwd_ppt<32>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
         default: return GS_ERR_INVALID_ARG;
     }
 }

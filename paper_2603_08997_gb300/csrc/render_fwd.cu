@@ -1,13 +1,14 @@
 // gs_render_fwd: Eq. (blend) / Eq. (alpha), front-to-back compositing.
 //
-// One CTA per tile, one thread per pixel, each warp an 8 x 4 pixel block that
-// skips Gaussians whose support box misses it.  The tile's depth-ordered list is
+// One CTA per tile, PPT pixels per thread (1 or 2), each warp an 8 x 4 PPT
+// pixel block that skips Gaussians whose support box misses it.  The tile's
+// depth-ordered list is
 // consumed `BATCH` Gaussians at a time: the CTA gathers the batch's packed
 // records into shared memory (one coalesced 48-byte record per Gaussian),
 // then every pixel walks the batch.  At the start of every batch each pixel
 // stores its transmittance into the checkpoint slot
-//   slot(tile, b) = floor(range_start / BATCH) + tile + b,
-// which the backward pass uses to rebuild T without dividing across batches.
+//   slot(tile, b) = floor(range_start / BATCH) + tile + b
+// (TILE * TILE floats, row-major over the tile's pixels), which the backward pass uses to rebuild T without dividing across batches.
 // The CTA stops as soon as every pixel has hit the transmittance floor.
 #include "common.cuh"
 
@@ -15,16 +16,17 @@ using namespace gsr;
 
 namespace {
 
-template <int TILE, int BATCH>
-__global__ void __launch_bounds__(TILE *TILE) render_fwd_kernel(const float4 *__restrict__ rec, int64_t n,
-                                                                 const uint32_t *__restrict__ vals,
-                                                                 const uint2 *__restrict__ ranges,
-                                                                 const gs_camera *__restrict__ cams, int n_views,
-                                                                 gs_raster_config cfg, float *__restrict__ image,
-                                                                 float *__restrict__ T_final,
-                                                                 int32_t *__restrict__ n_last,
-                                                                 float *__restrict__ ckpt, int64_t ckpt_slots) {
-    constexpr int NT = TILE * TILE;
+template <int TILE, int BATCH, int PPT>
+__global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const float4 *__restrict__ rec, int64_t n,
+                                                                       const uint32_t *__restrict__ vals,
+                                                                       const uint2 *__restrict__ ranges,
+                                                                       const gs_camera *__restrict__ cams, int n_views,
+                                                                       gs_raster_config cfg, float *__restrict__ image,
+                                                                       float *__restrict__ T_final,
+                                                                       int32_t *__restrict__ n_last,
+                                                                       float *__restrict__ ckpt, int64_t ckpt_slots) {
+    constexpr int NT = TILE * TILE;        // pixels per tile (checkpoint slot size)
+    constexpr int NTH = TILE * TILE / PPT; // threads
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
     __shared__ float4 s_c[BATCH];
@@ -34,12 +36,23 @@ __global__ void __launch_bounds__(TILE *TILE) render_fwd_kernel(const float4 *__
     const int tiles_x = (cam.width + TILE - 1) / TILE;
     const int64_t lt = tile - cam.tile_offset;
     const int tx = (int)(lt % tiles_x), ty = (int)(lt / tiles_x);
-    int lx, ly;
-    tile_pixel<TILE>(threadIdx.x, lx, ly);
-    const int x = tx * TILE + lx, y = ty * TILE + ly;
-    const bool inside = x < cam.width && y < cam.height;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    const float wx = (float)(tx * TILE + (lx & ~7)) + 0.5f, wy = (float)(ty * TILE + (ly & ~3)) + 0.5f;
+    int x[PPT], y[PPT], lp[PPT];
+    bool inside[PPT];
+    float px[PPT], py[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        int lx, ly;
+        tile_pixel<TILE, PPT>(threadIdx.x, k, lx, ly);
+        lp[k] = ly * TILE + lx;  // checkpoint slot layout is row-major in the tile
+        x[k] = tx * TILE + lx;
+        y[k] = ty * TILE + ly;
+        inside[k] = x[k] < cam.width && y[k] < cam.height;
+        px[k] = (float)x[k] + 0.5f;
+        py[k] = (float)y[k] + 0.5f;
+    }
+    int lx0, ly0;
+    tile_pixel<TILE, PPT>(threadIdx.x & ~31, 0, lx0, ly0);  // first pixel of the warp's block
+    const float wx = (float)(tx * TILE + lx0) + 0.5f, wy = (float)(ty * TILE + ly0) + 0.5f;
     const uint2 rg = ranges[tile];
     const int64_t len = (int64_t)rg.y - rg.x;
     const int64_t nb = ceil_div(len, BATCH);
@@ -47,79 +60,107 @@ __global__ void __launch_bounds__(TILE *TILE) render_fwd_kernel(const float4 *__
     const float4 *recv = rec + (int64_t)v * n * 3;
     const float amax = cfg.alpha_max, amin = cfg.alpha_min, tmin = cfg.t_min;
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int32_t last = 0;
-    bool done = !inside;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    int32_t last[PPT];
+    bool done[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; done[k] = !inside[k];
+    }
     for (int64_t b = 0; b < nb; ++b) {
-        if (__syncthreads_count(!done) == 0) break;
-        if (inside && slot0 + b < ckpt_slots) ckpt[(slot0 + b) * NT + threadIdx.x] = T;
+        bool all_done = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) all_done &= done[k];
+        if (__syncthreads_count(!all_done) == 0) break;
+        if (slot0 + b < ckpt_slots) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (inside[k]) ckpt[(slot0 + b) * NT + lp[k]] = T[k];
+        }
         const int64_t b0 = (int64_t)rg.x + b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const uint32_t g = vals[b0 + k];
+        for (int kk = threadIdx.x; kk < cnt; kk += NTH) {
+            const uint32_t g = vals[b0 + kk];
             const float4 *r = recv + (int64_t)g * 3;
-            s_a[k] = r[0];
-            s_b[k] = r[1];
-            s_c[k] = r[2];
+            s_a[kk] = r[0];
+            s_b[kk] = r[1];
+            s_c[kk] = r[2];
         }
         __syncthreads();
-        if (!done) {
+        if (!all_done) {
             for (int j = 0; j < cnt; ++j) {
-                if (!warp_overlaps(s_a[j], s_c[j], wx, wy)) continue;  // alpha' < alpha_min on all 32 pixels
-                const AlphaEval ae = eval_alpha(s_a[j], s_b[j], px, py, amax);
-                if (ae.alpha < amin) continue;
-                const float testT = __fmul_rn(T, __fsub_rn(1.f, ae.alpha));
-                if (testT < tmin) {
-                    done = true;
-                    break;
+                const float4 sa = s_a[j], sc = s_c[j];
+                if (!warp_overlaps<4 * PPT>(sa, sc, wx, wy)) continue;  // alpha' < alpha_min on the warp's block
+                const float4 sb = s_b[j];
+                bool alive = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (done[k]) continue;
+                    alive = true;
+                    const AlphaEval ae = eval_alpha(sa, sb, px[k], py[k], amax);
+                    if (ae.alpha < amin) continue;
+                    const float testT = __fmul_rn(T[k], __fsub_rn(1.f, ae.alpha));
+                    if (testT < tmin) {
+                        done[k] = true;
+                        continue;
+                    }
+                    const float w = ae.alpha * T[k];
+                    C0[k] += sb.z * w;
+                    C1[k] += sb.w * w;
+                    C2[k] += sc.x * w;
+                    T[k] = testT;
+                    last[k] = (int32_t)(b * BATCH + j + 1);
                 }
-                const float w = ae.alpha * T;
-                const float4 bb = s_b[j];
-                C0 += bb.z * w;
-                C1 += bb.w * w;
-                C2 += s_c[j].x * w;
-                T = testT;
-                last = (int32_t)(b * BATCH + j + 1);
+                if (!alive) break;
             }
         }
     }
-    if (inside) {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!inside[k]) continue;
         const int64_t hw = (int64_t)cam.width * cam.height;
-        const int64_t pix = (int64_t)y * cam.width + x;
+        const int64_t pix = (int64_t)y[k] * cam.width + x[k];
         float *img = image + 3 * cam.pix_offset;
-        img[pix] = C0 + T * cfg.bg[0];
-        img[hw + pix] = C1 + T * cfg.bg[1];
-        img[2 * hw + pix] = C2 + T * cfg.bg[2];
-        T_final[cam.pix_offset + pix] = T;
-        n_last[cam.pix_offset + pix] = last;
+        img[pix] = C0[k] + T[k] * cfg.bg[0];
+        img[hw + pix] = C1[k] + T[k] * cfg.bg[1];
+        img[2 * hw + pix] = C2[k] + T[k] * cfg.bg[2];
+        T_final[cam.pix_offset + pix] = T[k];
+        n_last[cam.pix_offset + pix] = last[k];
     }
 }
 
-template <int TILE>
+template <int TILE, int PPT>
 gs_status launch_fwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
                      const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
                      const gs_raster_config &cfg, float *image, gs_fwd_saved s) {
     const dim3 grid((unsigned)total_tiles);
+    constexpr int NTH = TILE * TILE / PPT;
     switch (batch) {
         case 64:
-            render_fwd_kernel<TILE, 64><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                         s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
+            render_fwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
+                                                                      s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
             break;
         case 128:
-            render_fwd_kernel<TILE, 128><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
-                                                                          image, s.T_final, s.n_last, s.ckpt,
-                                                                          s.ckpt_slots);
+            render_fwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
+                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
             break;
         case 256:
-            render_fwd_kernel<TILE, 256><<<grid, TILE * TILE, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg,
-                                                                          image, s.T_final, s.n_last, s.ckpt,
-                                                                          s.ckpt_slots);
+            render_fwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
+                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
             break;
         default:
             return GS_ERR_UNSUPPORTED;
     }
     GS_TRY_LAUNCH();
     return GS_OK;
+}
+
+template <int TILE>
+gs_status launch_fwd_ppt(int ppt, int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
+                         const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                         const gs_raster_config &cfg, float *image, gs_fwd_saved s) {
+    if (ppt == 2) return launch_fwd<TILE, 2>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
+    return launch_fwd<TILE, 1>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
 }
 
 }  // namespace
@@ -137,10 +178,11 @@ extern "C" gs_status gs_render_fwd(const gs_projected *proj, int64_t n, const ui
     if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2) return GS_ERR_INVALID_ARG;
     switch (cfg->tile) {
-        case 8: return launch_fwd<8>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
-        case 16: return launch_fwd<16>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
-        case 32: return launch_fwd<32>(cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
+        case 8: return launch_fwd_ppt<8>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
+        case 16: return launch_fwd_ppt<16>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
+        case 32: return launch_fwd_ppt<32>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
         default: return GS_ERR_INVALID_ARG;
     }
 }

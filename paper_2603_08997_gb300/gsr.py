@@ -31,7 +31,8 @@ class gs_camera(C.Structure):
 
 class gs_raster_config(C.Structure):
     _fields_ = [("lowpass", C.c_float), ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float),
-                ("bg", C.c_float * 3), ("tile", C.c_int32), ("batch", C.c_int32), ("sh_degree", C.c_int32)]
+                ("bg", C.c_float * 3), ("tile", C.c_int32), ("batch", C.c_int32), ("sh_degree", C.c_int32),
+                ("pixels_per_thread", C.c_int32)]
 
 
 class gs_params(C.Structure):

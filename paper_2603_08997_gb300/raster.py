@@ -28,6 +28,7 @@ class RasterSettings:
     t_min: float = 1e-4
     bg: tuple = (0.0, 0.0, 0.0)
     lambda_ssim: float = 0.2
+    pixels_per_thread: int = 2
 
     def struct(self, sh_degree: int) -> gsr.gs_raster_config:
         c = gsr.gs_raster_config()
@@ -35,6 +36,7 @@ class RasterSettings:
         for i in range(3):
             c.bg[i] = float(self.bg[i])
         c.tile, c.batch, c.sh_degree = int(self.tile), int(self.batch), int(sh_degree)
+        c.pixels_per_thread = int(self.pixels_per_thread)
         return c
 
 

@@ -17,10 +17,11 @@ pytestmark = pytest.mark.gpu
 GROUPS = ("means", "log_scales", "quats", "opacity_logit", "sh")
 
 
-def _setup(scene, cam, tile=16, batch=256):
+def _setup(scene, cam, tile=16, batch=256, ppt=2):
     gpu_util.lib()
     views = raster.Views([cam], tile)
-    r = raster.Renderer(scene.n, scene.sh_degree, views, raster.RasterSettings(tile=tile, batch=batch))
+    r = raster.Renderer(scene.n, scene.sh_degree, views,
+                        raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt))
     model = raster.GaussianModel.from_scene(scene)
     return r, model
 
@@ -70,10 +71,10 @@ def test_backward_linear_functional_tiny(seed, deg):
     _check_grads(gpu_util.gpu_grads(model, adam.grad), og)
 
 
-@pytest.mark.parametrize("tile,batch", [(16, 256), (8, 64), (32, 128)])
-def test_backward_full_loss_c1(tile, batch):
+@pytest.mark.parametrize("tile,batch,ppt", [(16, 256, 2), (8, 64, 2), (32, 128, 2), (16, 128, 1)])
+def test_backward_full_loss_c1(tile, batch, ppt):
     scene, cam, target = synth.case_c1()
-    r, model = _setup(scene, cam, tile, batch)
+    r, model = _setup(scene, cam, tile, batch, ppt)
     adam = raster.AdamState(model)
     r.forward(model.c_params())
     r.compute_loss(torch.from_numpy(target.ravel()).cuda(), with_grad=True)
@@ -202,8 +203,8 @@ def test_fused_backward_adam_equals_separate_calls(deg):
     torch.testing.assert_close(v1, v0, rtol=1e-5, atol=1e-14)
 
 
-@pytest.mark.parametrize("tile", [16, 8])
-def test_raster_bwd_g2d_against_oracle(tile):
+@pytest.mark.parametrize("tile,ppt", [(16, 2), (8, 2), (32, 2), (16, 1)])
+def test_raster_bwd_g2d_against_oracle(tile, ppt):
     """gs_raster_bwd alone, on synthetic records both sides share: the per-view
     per-Gaussian gradients wrt (mean2D, conic a b c, opacity, colour)."""
     sizes = [(150, 97), (64, 40)]
@@ -211,7 +212,7 @@ def test_raster_bwd_g2d_against_oracle(tile):
     recs = [synth.projected_records(3000, w, h, seed=31 + v) for v, (w, h) in enumerate(sizes)]
     gpu_util.lib()
     views = raster.Views(cams, tile)
-    r = raster.Renderer(3000, 0, views, raster.RasterSettings(tile=tile))
+    r = raster.Renderer(3000, 0, views, raster.RasterSettings(tile=tile, pixels_per_thread=ppt))
     dev, orc = gpu_util.records(recs, cams, tile)
     gpu_util.set_projected(r, dev)
     r.bin_sort()
@@ -243,3 +244,23 @@ def test_split_backward_equals_render_bwd():
     torch.cuda.synchronize()
     # equal up to the order of the float atomics in the raster adjoint
     assert gpu_util.rel_err(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-6
+
+
+def test_backward_mixed_pixels_per_thread():
+    """The checkpoint layout is independent of the thread mapping: a forward
+    pass with 2 pixels per thread feeds a backward pass with 1 and the other
+    way round, with the same gradients up to float atomic order."""
+    scene, cam = synth.scene_tiny(300, seed=8, sh_degree=2)
+    dl = torch.from_numpy(synth.dl_dimage(cam.width, cam.height, 3).ravel()).cuda()
+    res = []
+    for f_ppt, b_ppt in ((1, 1), (2, 1), (1, 2), (2, 2)):
+        r, model = _setup(scene, cam, tile=8, batch=64, ppt=f_ppt)
+        g = torch.zeros_like(model.flat)
+        r.forward(model.c_params())
+        r.cfg.pixels_per_thread = b_ppt
+        r.backward(model.c_params(), model.c_grads(g), dL_dimage=dl)
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        res.append(g.cpu().numpy())
+    for g in res[1:]:
+        assert gpu_util.rel_err(g, res[0]) < 1e-6

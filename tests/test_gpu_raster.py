@@ -17,10 +17,10 @@ from tests import gpu_util
 pytestmark = pytest.mark.gpu
 
 
-def _renderer(cams, n, sh_degree=0, tile=16, batch=256, cap=None, keys=True):
+def _renderer(cams, n, sh_degree=0, tile=16, batch=256, cap=None, keys=True, ppt=2):
     gpu_util.lib()
     views = raster.Views(cams, tile)
-    st = raster.RasterSettings(tile=tile, batch=batch)
+    st = raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt)
     return raster.Renderer(n, sh_degree, views, st, pair_capacity=cap, keep_keys=keys)
 
 
@@ -88,12 +88,13 @@ def _compare_images(img, ref, margin, tol=1e-5):
     assert nd <= tol * np.linalg.norm(ref), nd / np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("tile,batch", [(16, 256), (8, 64), (32, 128), (16, 128)])
-def test_render_synthetic_records(tile, batch):
+@pytest.mark.parametrize("tile,batch,ppt", [(16, 256, 2), (8, 64, 2), (32, 128, 2), (16, 128, 1), (8, 256, 1),
+                                            (32, 64, 1)])
+def test_render_synthetic_records(tile, batch, ppt):
     sizes = [(150, 97), (64, 40)]
     cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
     recs = [synth.projected_records(4000, w, h, seed=21 + v) for v, (w, h) in enumerate(sizes)]
-    r = _renderer(cams, 4000, tile=tile, batch=batch)
+    r = _renderer(cams, 4000, tile=tile, batch=batch, ppt=ppt)
     dev, orc = gpu_util.records(recs, cams, tile)
     gpu_util.set_projected(r, dev)
     r.bin_sort()
@@ -113,10 +114,10 @@ def test_render_synthetic_records(tile, batch):
         assert agree.all()
 
 
-@pytest.mark.parametrize("tile", [8, 16, 32])
-def test_render_end_to_end_c1(tile):
+@pytest.mark.parametrize("tile,ppt", [(8, 2), (16, 2), (32, 2), (16, 1)])
+def test_render_end_to_end_c1(tile, ppt):
     scene, cam, _ = synth.case_c1()
-    r = _renderer([cam], scene.n, tile=tile)
+    r = _renderer([cam], scene.n, tile=tile, ppt=ppt)
     model = raster.GaussianModel.from_scene(scene)
     r.forward(model.c_params())
     torch.cuda.synchronize()
@@ -170,3 +171,26 @@ def test_render_end_to_end_c2_like():
     torch.cuda.synchronize()
     o = oracle.forward(scene, cam, oracle.RasterConfig(), margin_rel=1e-4)
     _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_pixels_per_thread_is_bit_invariant(tile):
+    """The per-pixel arithmetic does not depend on how pixels map to threads:
+    images, final transmittance, last-contributor counts and checkpoints are
+    bit-identical for 1 and 2 pixels per thread."""
+    sizes = [(150, 97), (41, 70)]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(4000, w, h, seed=41 + v) for v, (w, h) in enumerate(sizes)]
+    dev, _ = gpu_util.records(recs, cams, tile)
+    out = []
+    for ppt in (1, 2):
+        r = _renderer(cams, 4000, tile=tile, batch=64, ppt=ppt)
+        gpu_util.set_projected(r, dev)
+        r.ckpt.fill_(-1.0)
+        r.bin_sort()
+        r.render_fwd()
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        out.append([t.clone().cpu() for t in (r.image, r.T_final, r.n_last, r.ckpt)])
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
