@@ -169,8 +169,8 @@ gs_status gs_project(const gs_params *params /* host */, const gs_camera *cams, 
 
 /* ------------------------------------------------------ binning and sort */
 
-/* Scratch bytes gs_bin_sort needs for n Gaussians x n_views views and
- * pair_capacity pairs. */
+/* Scratch bytes gs_bin_sort needs for n Gaussians x n_views views over
+ * total_tiles tiles (pair_capacity does not change it). */
 size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capacity, int64_t total_tiles);
 
 /* Tile binning + depth order ("depth-sorted Gaussians overlapping a pixel",
@@ -178,10 +178,16 @@ size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capac
  * (global tile id, float32 bits of depth, Gaussian index) - the stable sort
  * of the 64-bit keys (tile << 32 | depth bits) in emission order.  Writes
  * vals[pair] = Gaussian index, ranges[tile] = [start, end) (empty = [0,0)),
- * *dev_pair_count, and - if keys is not NULL - the 64-bit keys.  More pairs
- * than pair_capacity: GS_ERR_CAPACITY in dev_status, ranges left empty
- * (only the tile geometry of cams is read). */
-gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n, int64_t total_tiles, const gs_raster_config *cfg /* host */,
+ * *dev_pair_count, and - if keys is not NULL - the 64-bit keys.
+ * max_view_tiles: the largest tile count of one view (0 = total_tiles); at
+ * most 49152, else GS_ERR_UNSUPPORTED; a view with more tiles than given
+ * sets GS_ERR_INVALID_ARG in dev_status and emits no pairs.  Rectangles are
+ * clipped to the view's tile grid; entries with tiles_touched <= 0 emit
+ * nothing.  More pairs than pair_capacity: GS_ERR_CAPACITY in dev_status,
+ * the full count in *dev_pair_count, ranges left empty, vals untouched.
+ * Only the tile geometry of cams is read. */
+gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n,
+                      int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg /* host */,
                       void *workspace, size_t workspace_bytes, uint64_t *keys, uint32_t *vals,
                       int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count,
                       int32_t *dev_status, cudaStream_t stream);
@@ -191,10 +197,11 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
  * (cudaMalloc cannot be captured), plugins whose host application owns all
  * device memory, real-time loops that must not block on the allocator.  The
  * paper has no counterpart; it is a deployment variant of gs_bin_sort.
- * The scratch is a fixed array in the library's device memory (about 17 MB,
- * on every GPU that loads the library, until the process exits), so the
- * sizes are capped: n * n_views <= 262144 entries and pair_capacity <=
- * 1048576 pairs; larger requests return GS_ERR_WORKSPACE and launch nothing.
+ * The scratch is a fixed 16 MB array in the library's device memory (on
+ * every GPU that loads the library, until the process exits), so the sizes
+ * are capped: n * n_views <= 262144 entries and
+ * gs_bin_sort_workspace_size(...) <= 16 MB; larger requests return
+ * GS_ERR_WORKSPACE and launch nothing.
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.  Every call
  * shares the one array: calls that overlap on the GPU (different streams, or
@@ -202,9 +209,9 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
  * array needs to start at zero: each call overwrites all scratch it reads.
  * Other arguments, outputs and errors as gs_bin_sort. */
 gs_status gs_bin_sort_noalloc(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n,
-                              int64_t total_tiles, const gs_raster_config *cfg /* host */, uint64_t *keys,
-                              uint32_t *vals, int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count,
-                              int32_t *dev_status, cudaStream_t stream);
+                              int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg /* host */,
+                              uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *ranges,
+                              int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream);
 
 /* --------------------------------------------------------------- forward */
 

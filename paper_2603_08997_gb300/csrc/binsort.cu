@@ -4,16 +4,16 @@
 // The required order is the stable sort of the 64-bit keys
 // (global tile id << 32 | float32 depth bits) in emission order (Gaussian
 // index ascending, tiles row-major).  It is produced in two stages that give
-// the same permutation with far less traffic than sorting 64-bit pair keys:
+// the same permutation without materialising or sorting any pair key:
 //   1. sort the V*N (view, Gaussian) entries by depth bits (stable, so equal
-//      depths keep ascending index);
-//   2. emit each entry's pairs in that order and stably sort the pairs by
-//      tile id alone (ceil(log2(tiles)) bits, 8 per pass).
+//      depths keep ascending index), then stably by view;
+//   2. place every pair by a counting sort over tiles that walks the entries
+//      in that order (see bin_count .. bin_scatter below).
 // A stable sort by tile of a depth-ordered list is ordered by
 // (tile, depth, index), i.e. exactly the 64-bit key order.
 //
-// Every kernel reads the pair count from device memory, so the whole call
-// can be captured in a CUDA graph.  The radix sort is a reduce-then-scan LSD
+// Every kernel reads the counts it needs from device memory, so the whole
+// call can be captured in a CUDA graph.  The radix sort is a reduce-then-scan LSD
 // sort: an upsweep histogram per block, one exclusive scan over the
 // digit-major (digit, block) counts, and a downsweep that ranks each tile of
 // 2048 keys with warp ballots (one per digit bit), reorders the tile by digit in shared
@@ -252,155 +252,307 @@ __global__ void depth_keys_kernel(const float *__restrict__ rec, const int32_t *
     vals[e] = (uint32_t)e;
 }
 
-// Scan of the tile counts in depth order, reduce phase: one block per chunk of
-// RS_THREADS entries writes the chunk's pair count.
-__global__ void __launch_bounds__(RS_THREADS) count_reduce(const int32_t *__restrict__ touched,
-                                                           const uint32_t *__restrict__ order, int64_t total,
-                                                           unsigned long long *__restrict__ chunk_sums) {
-    const int64_t m = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x;
-    unsigned long long s = m < total ? (unsigned)touched[order[m]] : 0u;
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    __shared__ unsigned long long ws[RS_WARPS];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+// entry -> view key, for the stable pass that groups the depth order by view
+__global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t total, int64_t n,
+                                 uint32_t *__restrict__ keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) keys[i] = (uint32_t)(order[i] / n);
+}
+
+// ----------------------------------------------------------------------------
+// Stage 2: counting sort of the pairs by tile, in depth order.
+//
+// The depth-ordered entries of view v are cut into chunks of C entries.  For
+// chunk c of view v and tile t of that view, let cnt(c, t) be the number of
+// the chunk's entries whose rectangle covers t.  The pair of entry e at tile t
+// then lands at
+//   start(t) + sum_{c' < c} cnt(c', t) + #(earlier entries of chunk c covering t),
+// with start(t) the exclusive scan of the tile totals over global tile ids.
+// That is the position of the pair in the stable sort by tile of the
+// depth-ordered pair list, so no pair key is ever materialised or sorted.
+//   bin_count:   one block per chunk: per-tile counts in shared memory, written
+//                as the chunk's row of the count matrix (chunk-major per view)
+//                and added into the per-group sums (BIN_GROUP chunks a group);
+//   bin_groups:  per tile, exclusive scan over its groups and the tile total;
+//   bin_starts:  exclusive scan of the tile totals (one block), pair count and
+//                capacity check;
+//   bin_offsets: per (group, tile), the count matrix becomes the chunks' first
+//                slots, and group 0 writes the tile's range;
+//   bin_scatter: one warp per chunk walks its entries in depth order and
+//                writes each pair at its tile's running slot (shared memory).
+constexpr int BIN_GROUP = 64;
+constexpr int COUNT_THREADS = 256;
+
+struct BinGeom {
+    int64_t n;       // entries per view
+    int64_t chunk;   // entries per chunk
+    int64_t n_c;     // chunks per view
+    int64_t n_g;     // groups per view
+    int64_t tiles;   // total tiles over all views
+    int tile;        // pixels per tile side
+    int max_vt;      // tiles per view the shared-memory tables hold
+};
+
+// Entries per chunk: about 1500 chunks per view (ten resident per SM), in
+// multiples of 256, at least 256.
+int64_t bin_chunk(int64_t n) {
+    int64_t c = ceil_div(n, (int64_t)1520);
+    c = ceil_div(c, (int64_t)256) * 256;
+    return c < 256 ? 256 : c;
+}
+
+struct ViewTiles {
+    int64_t off;  // first global tile id
+    int tx, ty;   // tile grid
+};
+
+__device__ __forceinline__ ViewTiles view_tiles(const gs_camera &cam, int tile) {
+    ViewTiles vt;
+    vt.off = cam.tile_offset;
+    vt.tx = (cam.width + tile - 1) / tile;
+    vt.ty = (cam.height + tile - 1) / tile;
+    return vt;
+}
+
+// Does the view's tile table fit the shared-memory tables and the global
+// tile range?  (Tile offsets that disagree with total_tiles would not.)
+__device__ __forceinline__ bool view_fits(const ViewTiles &vt, int64_t tiles, int max_vt) {
+    const int64_t T = (int64_t)vt.tx * vt.ty;
+    return vt.tx > 0 && vt.ty > 0 && T <= max_vt && vt.off >= 0 && vt.off + T <= tiles;
+}
+
+// The rectangle of entry e clipped to the view's tile grid; false if it
+// emits no pair (culled or empty).
+__device__ __forceinline__ bool entry_rect(const int4 *__restrict__ rect, const int32_t *__restrict__ touched,
+                                           uint32_t e, const ViewTiles &vt, int4 &r) {
+    if (touched[e] <= 0) return false;
+    r = rect[e];
+    r.x = max(r.x, 0);
+    r.y = max(r.y, 0);
+    r.z = min(r.z, vt.tx - 1);
+    r.w = min(r.w, vt.ty - 1);
+    return r.x <= r.z && r.y <= r.w;
+}
+
+__global__ void __launch_bounds__(COUNT_THREADS) bin_count(const int4 *__restrict__ rect,
+                                                           const int32_t *__restrict__ touched,
+                                                           const uint32_t *__restrict__ order,
+                                                           const gs_camera *__restrict__ cams, BinGeom g,
+                                                           uint32_t *__restrict__ M, uint32_t *__restrict__ G1,
+                                                           int32_t *dev_status) {
+    extern __shared__ uint32_t s_h[];
+    const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
+    const ViewTiles vt = view_tiles(cams[v], g.tile);
+    if (!view_fits(vt, g.tiles, g.max_vt)) {
+        if (threadIdx.x == 0) set_status(dev_status, GS_ERR_INVALID_ARG);
+        return;
+    }
+    const int T = vt.tx * vt.ty;
+    for (int t = threadIdx.x; t < T; t += COUNT_THREADS) s_h[t] = 0u;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < RS_WARPS; ++w) t += ws[w];
-        chunk_sums[blockIdx.x] = t;
+    const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += COUNT_THREADS) {
+        int4 r;
+        if (!entry_rect(rect, touched, order[i], vt, r)) continue;
+        for (int ty = r.y; ty <= r.w; ++ty)
+            for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&s_h[ty * vt.tx + tx], 1u);
+    }
+    __syncthreads();
+    uint32_t *row = M + g.n_c * vt.off + c * T;
+    uint32_t *grp = G1 + (c / BIN_GROUP) * g.tiles + vt.off;
+    for (int t = threadIdx.x; t < T; t += COUNT_THREADS) {
+        const uint32_t h = s_h[t];
+        row[t] = h;
+        if (h) atomicAdd(&grp[t], h);
     }
 }
 
-// Exclusive scan of the chunk sums by one block (SCAN_THREADS values per
-// round); writes the total pair count and the count the pair sort will use
-// (0 when over capacity).
-__global__ void __launch_bounds__(SCAN_THREADS) count_top(unsigned long long *chunk_sums, int64_t n_chunks, int64_t cap,
-                                                          int64_t *dev_pair_count, int64_t *sort_count,
-                                                          int32_t *dev_status) {
+// Per global tile: exclusive scan of its group sums (in place) and its total.
+__global__ void bin_groups(BinGeom g, uint32_t *__restrict__ G1, uint32_t *__restrict__ tile_total) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= g.tiles) return;
+    uint32_t run = 0;
+    for (int64_t k = 0; k < g.n_g; ++k) {
+        const uint32_t x = G1[k * g.tiles + gt];
+        G1[k * g.tiles + gt] = run;
+        run += x;
+    }
+    tile_total[gt] = run;
+}
+
+// Exclusive scan of the tile totals by one block: each thread sums a
+// contiguous run of tiles, the block scans the run sums, each thread writes
+// its run's starts.  Writes the pair count; over capacity (or past 32-bit
+// slots) sets GS_ERR_CAPACITY and a sort count of 0, which stops the later
+// stages and leaves the ranges empty.
+__global__ void __launch_bounds__(SCAN_THREADS) bin_starts(BinGeom g, const uint32_t *__restrict__ tile_total,
+                                                           uint32_t *__restrict__ tile_start, int64_t cap,
+                                                           int64_t *dev_pair_count, int64_t *sort_count,
+                                                           int32_t *dev_status) {
     __shared__ unsigned long long s[SCAN_THREADS];
-    unsigned long long carry = 0;
-    for (int64_t base = 0; base < n_chunks; base += SCAN_THREADS) {
-        const int64_t i = base + threadIdx.x;
-        const unsigned long long x = i < n_chunks ? chunk_sums[i] : 0ull;
-        s[threadIdx.x] = x;
+    const int64_t per = ceil_div(g.tiles, (int64_t)SCAN_THREADS);
+    const int64_t lo = min(g.tiles, (int64_t)threadIdx.x * per), hi = min(g.tiles, lo + per);
+    unsigned long long sum = 0;
+    for (int64_t t = lo; t < hi; ++t) sum += tile_total[t];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        const unsigned long long y = threadIdx.x >= off ? s[threadIdx.x - off] : 0ull;
         __syncthreads();
-        for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-            const unsigned long long y = threadIdx.x >= off ? s[threadIdx.x - off] : 0ull;
-            __syncthreads();
-            s[threadIdx.x] += y;
-            __syncthreads();
+        s[threadIdx.x] += y;
+        __syncthreads();
+    }
+    const unsigned long long P = s[SCAN_THREADS - 1];
+    const bool ok = (int64_t)P <= cap && P < 0xffffffffull;
+    unsigned long long run = s[threadIdx.x] - sum;
+    if (ok) {
+        for (int64_t t = lo; t < hi; ++t) {
+            tile_start[t] = (uint32_t)run;
+            run += tile_total[t];
         }
-        if (i < n_chunks) chunk_sums[i] = carry + s[threadIdx.x] - x;
-        carry += s[SCAN_THREADS - 1];
-        __syncthreads();
     }
     if (threadIdx.x == 0) {
-        *dev_pair_count = (int64_t)carry;
-        if ((int64_t)carry > cap) {
-            set_status(dev_status, GS_ERR_CAPACITY);
-            *sort_count = 0;
-        } else {
-            *sort_count = (int64_t)carry;
-        }
+        *dev_pair_count = (int64_t)P;
+        *sort_count = ok ? (int64_t)P : 0;
+        if (!ok) set_status(dev_status, GS_ERR_CAPACITY);
     }
 }
 
-// Scan phase fused with pair emission.  Each block takes its range of
-// entries in depth order, RS_THREADS at a time: a block scan gives every
-// entry's first pair slot; each entry writes its own pairs (tiles of its
-// rectangle, row-major) into a shared staging buffer, which the block then
-// copies out contiguously.  A chunk with more pairs than the buffer holds
-// writes straight to global memory instead.
-constexpr int EMIT_STAGE = 4096;
-
-__global__ void __launch_bounds__(RS_THREADS) emit_pairs(const int32_t *__restrict__ touched,
-                                                         const int4 *__restrict__ rect,
-                                                         const uint32_t *__restrict__ order, int64_t total,
-                                                         int64_t n, const gs_camera *__restrict__ cams, int tile,
-                                                         const unsigned long long *__restrict__ block_offsets,
-                                                         const int64_t *sort_count, uint32_t *__restrict__ pkeys,
-                                                         uint32_t *__restrict__ pvals) {
-    if (*sort_count == 0) return;  // nothing to emit, or over capacity
-    __shared__ uint32_t s_k[EMIT_STAGE];
-    __shared__ uint32_t s_v[EMIT_STAGE];
-    __shared__ uint32_t s_warp[32];
-    const int64_t end = total;
-    uint64_t run = block_offsets[blockIdx.x];
-    {
-        const int64_t m = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x;
-        uint32_t c = 0, gi = 0;
-        int4 r = make_int4(0, 0, -1, -1);
-        int base = 0, tx_n = 0;
-        if (m < end) {
-            const uint32_t e = order[m];
-            c = (uint32_t)touched[e];
-            if (c > 0) {
-                const int64_t v = (int64_t)e / n;
-                r = rect[e];
-                const gs_camera &cam = cams[v];
-                tx_n = (cam.width + tile - 1) / tile;
-                base = cam.tile_offset;
-                gi = (uint32_t)((int64_t)e - v * n);
-            }
-        }
-        uint32_t chunk_total;
-        const uint32_t excl = block_exclusive_scan(c, s_warp, &chunk_total);
-        if (chunk_total <= EMIT_STAGE) {
-            uint32_t o = excl;
-            for (int ty = r.y; ty <= r.w; ++ty)
-                for (int tx = r.x; tx <= r.z; ++tx, ++o) {
-                    s_k[o] = (uint32_t)(base + ty * tx_n + tx);
-                    s_v[o] = gi;
-                }
-            __syncthreads();
-            for (uint32_t k = threadIdx.x; k < chunk_total; k += RS_THREADS) {
-                pkeys[run + k] = s_k[k];
-                pvals[run + k] = s_v[k];
-            }
-        } else {
-            uint64_t o = run + excl;
-            for (int ty = r.y; ty <= r.w; ++ty)
-                for (int tx = r.x; tx <= r.z; ++tx, ++o) {
-                    pkeys[o] = (uint32_t)(base + ty * tx_n + tx);
-                    pvals[o] = gi;
-                }
-        }
-    }
-}
-
-__global__ void ranges_kernel(const uint32_t *__restrict__ keys, const int64_t *sort_count, uint2 *__restrict__ ranges) {
-    const int64_t count = *sort_count;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * c < count; c += stride) {
-        const int64_t i0 = 4 * c;
-        uint32_t k[6];
-        k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
-        if (i0 + 4 <= count) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(keys + i0);
-            k[1] = q.x; k[2] = q.y; k[3] = q.z; k[4] = q.w;
-        } else {
-            for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < count ? keys[i0 + j] : 0xffffffffu;
-        }
-        k[5] = i0 + 4 < count ? keys[i0 + 4] : 0xffffffffu;
+// Per (group, global tile): rewrite the group's counts cnt(c, t) as the
+// chunks' first slots; group 0 also writes the tile's range.  The group's
+// counts are read in runs of 16 before any is written back.
+__global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n_views,
+                            const uint32_t *__restrict__ G1, const uint32_t *__restrict__ tile_start,
+                            const uint32_t *__restrict__ tile_total, const int64_t *sort_count,
+                            uint32_t *__restrict__ M, uint2 *__restrict__ ranges) {
+    if (*sort_count == 0) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_g * g.tiles) return;
+    const int64_t k = i / g.tiles, gt = i % g.tiles;
+    const int v = view_of_tile(cams, n_views, gt);
+    const ViewTiles vt = view_tiles(cams[v], g.tile);
+    if (!view_fits(vt, g.tiles, g.max_vt)) return;
+    const int T = vt.tx * vt.ty;
+    const int64_t t = gt - vt.off;
+    if (t < 0 || t >= T) return;
+    uint32_t run = tile_start[gt] + G1[k * g.tiles + gt];
+    const int64_t c0 = k * BIN_GROUP, c1 = min(g.n_c, c0 + BIN_GROUP);
+    uint32_t *col = M + g.n_c * vt.off + t;
+    constexpr int R = 16;
+    for (int64_t cb = c0; cb < c1; cb += R) {
+        uint32_t x[R];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t i = i0 + j;
-            if (i >= count) break;
-            const uint32_t t = k[1 + j];
-            if (k[j] != t || i == 0) ranges[t].x = (uint32_t)i;
-            if (k[2 + j] != t || i == count - 1) ranges[t].y = (uint32_t)(i + 1);
+        for (int j = 0; j < R; ++j) x[j] = cb + j < c1 ? col[(cb + j) * T] : 0u;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (cb + j < c1) col[(cb + j) * T] = run;
+            run += x[j];
+        }
+    }
+    if (k == 0) {
+        const uint32_t tot = tile_total[gt];
+        ranges[gt] = tot ? make_uint2(tile_start[gt], tile_start[gt] + tot) : make_uint2(0u, 0u);
+    }
+}
+
+// One warp per chunk.  The chunk's first slot per tile goes to shared memory
+// (s_off).  The warp takes its entries 32 at a time; their pairs, in order
+// (entry, then tile row-major), are written tile by tile into a staging list
+// in windows of SCATTER_STAGE pairs, and each window is placed 32 pairs per
+// step: lanes holding the same tile find each other (match.any), rank among
+// themselves by lane (= list order), and the lowest of them advances the
+// tile's running slot.
+constexpr int SCATTER_STAGE = 512;
+
+__global__ void __launch_bounds__(32) bin_scatter(const int4 *__restrict__ rect, const int32_t *__restrict__ touched,
+                                                  const uint32_t *__restrict__ order,
+                                                  const gs_camera *__restrict__ cams, BinGeom g,
+                                                  const uint32_t *__restrict__ M, const int64_t *sort_count,
+                                                  uint32_t *__restrict__ vals) {
+    extern __shared__ uint32_t s_off[];
+    __shared__ int s_t[SCATTER_STAGE];
+    __shared__ uint32_t s_g[SCATTER_STAGE];
+    if (*sort_count == 0) return;
+    const int lane = threadIdx.x;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
+    const ViewTiles vt = view_tiles(cams[v], g.tile);
+    if (!view_fits(vt, g.tiles, g.max_vt)) return;
+    const int T = vt.tx * vt.ty;
+    const uint32_t *row = M + g.n_c * vt.off + c * T;
+    for (int t = lane; t < T; t += 32) s_off[t] = row[t];
+    __syncwarp();
+    const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t i = base + lane;
+        int4 r = make_int4(0, 0, -1, -1);
+        uint32_t gi = 0;
+        bool any = false;
+        if (i < e1) {
+            const uint32_t e = order[i];
+            any = entry_rect(rect, touched, e, vt, r);
+            gi = (uint32_t)((int64_t)e - v * g.n);
+        }
+        const int w = r.z - r.x + 1;
+        const int area = any ? w * (r.w - r.y + 1) : 0;
+        // exclusive prefix of the areas over the warp
+        int inc = area;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        const int pre = inc - area;
+        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        for (int w0 = 0; w0 < tot; w0 += SCATTER_STAGE) {
+            // stage this lane's pairs that fall in [w0, w0 + SCATTER_STAGE)
+            const int k0 = max(pre, w0) - pre, k1 = min(pre + area, w0 + SCATTER_STAGE) - pre;
+            if (k0 < k1) {
+                int dy = k0 / w, dx = k0 - dy * w;
+                int t = (r.y + dy) * vt.tx + r.x + dx;
+                for (int k = k0; k < k1; ++k) {
+                    s_t[pre + k - w0] = t;
+                    s_g[pre + k - w0] = gi;
+                    if (++dx == w) {
+                        dx = 0;
+                        t += vt.tx - (w - 1);
+                    } else {
+                        ++t;
+                    }
+                }
+            }
+            __syncwarp();
+            const int cnt = min(SCATTER_STAGE, tot - w0);
+            for (int m0 = 0; m0 < cnt; m0 += 32) {
+                const int m = m0 + lane;
+                const bool valid = m < cnt;
+                const int t = valid ? s_t[m] : -1 - lane;  // invalid lanes match nobody
+                const uint32_t peers = __match_any_sync(0xffffffffu, t);
+                uint32_t slot = 0;
+                if (valid) slot = s_off[t];
+                __syncwarp();
+                if (valid) {
+                    if ((peers & lt_mask) == 0) s_off[t] = slot + __popc(peers);
+                    vals[slot + __popc(peers & lt_mask)] = s_g[m];
+                }
+                __syncwarp();
+            }
         }
     }
 }
 
-__global__ void keys64_kernel(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals,
+// 64-bit keys of the sorted pairs (for checking the order): one block per tile.
+__global__ void keys64_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                               const int64_t *sort_count, const gs_camera *__restrict__ cams, int n_views, int64_t n,
                               const float *__restrict__ rec, uint64_t *__restrict__ keys) {
-    const int64_t count = *sort_count;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = tkeys[i];
-        const int v = view_of_tile(cams, n_views, t);
+    if (*sort_count == 0) return;
+    const int64_t gt = blockIdx.x;
+    const uint2 rg = ranges[gt];
+    if (rg.y <= rg.x) return;
+    const int v = view_of_tile(cams, n_views, gt);
+    for (uint32_t i = rg.x + threadIdx.x; i < rg.y; i += blockDim.x) {
         const int64_t e = (int64_t)v * n + vals[i];
-        keys[i] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(rec[e * kRecFloats + 9]);
+        keys[i] = ((uint64_t)gt << 32) | (uint64_t)__float_as_uint(rec[e * kRecFloats + 9]);
     }
 }
 
@@ -410,17 +562,33 @@ int bits_for(int64_t values) {  // bits needed to represent 0 .. values-1
     return b < 1 ? 1 : b;
 }
 
+BinGeom bin_geom(int64_t n, int64_t total_tiles, int tile, int max_vt) {
+    BinGeom g;
+    g.n = n;
+    g.chunk = bin_chunk(n);
+    g.n_c = ceil_div(n > 0 ? n : 1, g.chunk);
+    g.n_g = ceil_div(g.n_c, (int64_t)BIN_GROUP);
+    g.tiles = total_tiles;
+    g.tile = tile;
+    g.max_vt = max_vt;
+    return g;
+}
+
 struct BinWorkspace {
-    uint32_t *dk[2], *dv[2];        // depth keys / entry ids, ping-pong, [V*N]
-    uint32_t *pk[2], *pv;           // pair tile keys ping-pong [cap], pair values scratch [cap]
-    uint32_t *counts;               // [RADIX * RS_MAX_BLOCKS] + [RADIX] digit totals
-    unsigned long long *block_sums; // [ceil(total / RS_THREADS) + 1] chunk pair counts, then offsets
-    int64_t *sort_count;            // [1]
+    uint32_t *dk[2], *dv[2];   // depth (then view) keys / entry ids, ping-pong, [V*N]
+    uint32_t *counts;          // [RADIX * RS_MAX_BLOCKS] + [RADIX] digit totals
+    uint32_t *M;               // [n_c * total_tiles] chunk x tile counts, then first slots
+    uint32_t *G1;              // [n_g * total_tiles] group sums, then group offsets
+    uint32_t *tile_total;      // [total_tiles]
+    uint32_t *tile_start;      // [total_tiles]
+    int64_t *sort_count;       // [1]
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t bin_ws_layout(int64_t total, int64_t cap, BinWorkspace *w, char *base) {
+size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspace *w, char *base) {
+    const int64_t total = n * n_views;
+    const BinGeom g = bin_geom(n, total_tiles, 16, 0);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char *p = base ? base + off : nullptr;
@@ -432,21 +600,39 @@ size_t bin_ws_layout(int64_t total, int64_t cap, BinWorkspace *w, char *base) {
         char *b = take(sizeof(uint32_t) * (size_t)(total > 0 ? total : 1));
         if (w) { w->dk[i] = (uint32_t *)a; w->dv[i] = (uint32_t *)b; }
     }
-    for (int i = 0; i < 2; ++i) {
-        char *a = take(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
-        if (w) w->pk[i] = (uint32_t *)a;
-    }
-    char *pv = take(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
     char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1));
-    char *bs = take(sizeof(unsigned long long) * (size_t)(ceil_div(total > 0 ? total : 1, RS_THREADS) + 1));
+    char *M = take(sizeof(uint32_t) * (size_t)(g.n_c * total_tiles));
+    char *G1 = take(sizeof(uint32_t) * (size_t)(g.n_g * total_tiles));
+    char *tt = take(sizeof(uint32_t) * (size_t)total_tiles);
+    char *ts = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *sc = take(sizeof(int64_t));
     if (w) {
-        w->pv = (uint32_t *)pv;
         w->counts = (uint32_t *)counts;
-        w->block_sums = (unsigned long long *)bs;
+        w->M = (uint32_t *)M;
+        w->G1 = (uint32_t *)G1;
+        w->tile_total = (uint32_t *)tt;
+        w->tile_start = (uint32_t *)ts;
         w->sort_count = (int64_t *)sc;
     }
     return off;
+}
+
+// Tables of up to this many tiles per view fit the shared memory of the
+// counting and scatter kernels (192 KB).
+constexpr int kMaxViewTiles = 49152;
+
+// Raise the dynamic shared-memory limit of the table kernels to the largest
+// table, once per device (before any stream capture, on the first call).
+gs_status bin_smem_attributes() {
+    static bool done[64] = {};
+    int dev = 0;
+    GS_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
+    const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
+    GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return GS_OK;
 }
 
 }  // namespace
@@ -454,66 +640,72 @@ size_t bin_ws_layout(int64_t total, int64_t cap, BinWorkspace *w, char *base) {
 extern "C" {
 
 size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capacity, int64_t total_tiles) {
-    (void)total_tiles;
-    if (n < 0 || n_views <= 0 || pair_capacity < 0) return 0;
-    return bin_ws_layout(n * n_views, pair_capacity, nullptr, nullptr);
+    if (n < 0 || n_views <= 0 || pair_capacity < 0 || total_tiles <= 0) return 0;
+    return bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr);
 }
 
 gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
-                      int64_t total_tiles, const gs_raster_config *cfg, void *workspace, size_t workspace_bytes,
-                      uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *ranges,
-                      int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
+                      int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg, void *workspace,
+                      size_t workspace_bytes, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
+                      uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
     if (!proj || !cams || !cfg || n_views <= 0 || n < 0 || total_tiles <= 0 || !vals || !ranges || !dev_pair_count)
         return GS_ERR_INVALID_ARG;
     if (cfg->tile != 8 && cfg->tile != 16 && cfg->tile != 32) return GS_ERR_INVALID_ARG;
     if (pair_capacity < 0 || pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_INVALID_ARG;
     if (total_tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
+    const int64_t mvt = max_view_tiles > 0 ? max_view_tiles : total_tiles;
+    if (mvt > total_tiles || mvt > kMaxViewTiles) return GS_ERR_UNSUPPORTED;
     const int64_t total = n * n_views;
     if (total >= ((int64_t)1 << 32) - 1) return GS_ERR_INVALID_ARG;
     if (total > 0 && (!proj->rec || !proj->rect || !proj->tiles_touched)) return GS_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < bin_ws_layout(total, pair_capacity, nullptr, nullptr)) return GS_ERR_WORKSPACE;
+    if (!workspace || workspace_bytes < bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr))
+        return GS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 255) return GS_ERR_WORKSPACE;
     BinWorkspace w;
-    bin_ws_layout(total, pair_capacity, &w, (char *)workspace);
+    bin_ws_layout(n, n_views, total_tiles, &w, (char *)workspace);
 
     GS_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, stream));
     if (total == 0) {
         GS_TRY(cudaMemsetAsync(dev_pair_count, 0, sizeof(int64_t), stream));
         return GS_OK;
     }
-    // 1. depth order of all (view, Gaussian) entries
+    const BinGeom g = bin_geom(n, total_tiles, cfg->tile, (int)mvt);
+    // 1. depth order of all (view, Gaussian) entries, then grouped by view
     depth_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(proj->rec, proj->tiles_touched, total,
                                                                          w.dk[0], w.dv[0]);
     GS_TRY_LAUNCH();
-    const int dsel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream);
+    int sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream);
     GS_TRY_LAUNCH();
-    const uint32_t *order = w.dv[dsel];
-    // 2. pair offsets in depth order, fused pair emission (one block per chunk)
-    const int64_t n_chunks = ceil_div(total, RS_THREADS);
-    count_reduce<<<(unsigned)n_chunks, RS_THREADS, 0, stream>>>(proj->tiles_touched, order, total, w.block_sums);
-    count_top<<<1, SCAN_THREADS, 0, stream>>>(w.block_sums, n_chunks, pair_capacity, dev_pair_count, w.sort_count,
-                                             dev_status);
-    // The final pass must land in (pk[0], vals): emit into the buffer that an
-    // even or odd number of passes maps there.
-    const int tbits = bits_for(total_tiles);
-    const int passes = radix_passes(tbits);
-    uint32_t *ek = (passes & 1) ? w.pk[1] : w.pk[0];
-    uint32_t *ev = (passes & 1) ? w.pv : vals;
-    emit_pairs<<<(unsigned)n_chunks, RS_THREADS, 0, stream>>>(proj->tiles_touched, reinterpret_cast<const int4 *>(proj->rect), order,
-                                             total, n, cams, cfg->tile, w.block_sums, w.sort_count, ek, ev);
+    if (n_views > 1) {
+        view_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(w.dv[sel], total, n, w.dk[sel]);
+        GS_TRY_LAUNCH();
+        sel ^= radix_sort(w.dk[sel], w.dv[sel], w.dk[sel ^ 1], w.dv[sel ^ 1], nullptr, total, bits_for(n_views),
+                          w.counts, stream);
+        GS_TRY_LAUNCH();
+    }
+    const uint32_t *order = w.dv[sel];
+    const int4 *rect = reinterpret_cast<const int4 *>(proj->rect);
+    // 2. counting sort of the pairs by tile, in depth order
+    const size_t smem = sizeof(uint32_t) * (size_t)mvt;
+    GS_TRY(bin_smem_attributes());
+    GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
+    const unsigned n_chunks = (unsigned)(g.n_c * n_views);
+    bin_count<<<n_chunks, COUNT_THREADS, smem, stream>>>(rect, proj->tiles_touched, order, cams, g, w.M, w.G1,
+                                                        dev_status);
     GS_TRY_LAUNCH();
-    // 3. stable sort of the pairs by tile id
-    const int psel = (passes & 1) ? radix_sort(w.pk[1], w.pv, w.pk[0], vals, w.sort_count, pair_capacity, tbits,
-                                               w.counts, stream)
-                                  : radix_sort(w.pk[0], vals, w.pk[1], w.pv, w.sort_count, pair_capacity, tbits,
-                                               w.counts, stream);
+    bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
     GS_TRY_LAUNCH();
-    (void)psel;  // by construction the result is in (pk[0], vals)
-    // 4. per-tile ranges and, on request, the 64-bit keys
-    ranges_kernel<<<4 * 152, 256, 0, stream>>>(w.pk[0], w.sort_count, reinterpret_cast<uint2 *>(ranges));
+    bin_starts<<<1, SCAN_THREADS, 0, stream>>>(g, w.tile_total, w.tile_start, pair_capacity, dev_pair_count,
+                                               w.sort_count, dev_status);
+    GS_TRY_LAUNCH();
+    bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
+        g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
+    GS_TRY_LAUNCH();
+    bin_scatter<<<n_chunks, 32, smem, stream>>>(rect, proj->tiles_touched, order, cams, g, w.M, w.sort_count, vals);
     GS_TRY_LAUNCH();
     if (keys) {
-        keys64_kernel<<<4 * 152, 256, 0, stream>>>(w.pk[0], vals, w.sort_count, cams, n_views, n, proj->rec, keys);
+        keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,
+                                                                 w.sort_count, cams, n_views, n, proj->rec, keys);
         GS_TRY_LAUNCH();
     }
     return GS_OK;
@@ -533,14 +725,7 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
 namespace {
 
 constexpr int64_t kNoAllocMaxEntries = (int64_t)1 << 18;  // n * n_views
-constexpr int64_t kNoAllocMaxPairs = (int64_t)1 << 20;    // pair_capacity
-
-// Size of the gs_bin_sort workspace at the limits above (same layout as
-// bin_ws_layout: each buffer rounded up to 256 bytes).
-constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t kNoAllocBytes = 4 * al256(4 * (size_t)kNoAllocMaxEntries) + 3 * al256(4 * (size_t)kNoAllocMaxPairs) +
-                                 al256(4 * (size_t)RADIX * (RS_MAX_BLOCKS + 1)) +
-                                 al256(8 * (size_t)(kNoAllocMaxEntries / RS_THREADS + 1)) + al256(8);
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;        // the whole scratch
 
 // One copy per device that loads the library, held until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -551,11 +736,13 @@ void *g_noalloc_ptr[kMaxDevices] = {};
 }  // namespace
 
 extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
-                                         int64_t total_tiles, const gs_raster_config *cfg, uint64_t *keys,
-                                         uint32_t *vals, int64_t pair_capacity, uint32_t *ranges,
+                                         int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg,
+                                         uint64_t *keys, uint32_t *vals, int64_t pair_capacity, uint32_t *ranges,
                                          int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
-    if (n < 0 || n_views <= 0 || pair_capacity < 0) return GS_ERR_INVALID_ARG;
-    if (n * n_views > kNoAllocMaxEntries || pair_capacity > kNoAllocMaxPairs) return GS_ERR_WORKSPACE;
+    if (n < 0 || n_views <= 0 || pair_capacity < 0 || total_tiles <= 0) return GS_ERR_INVALID_ARG;
+    if (n * n_views > kNoAllocMaxEntries) return GS_ERR_WORKSPACE;
+    if (total_tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
+    if (bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr) > kNoAllocBytes) return GS_ERR_WORKSPACE;
     int dev = 0;
     GS_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
@@ -566,6 +753,6 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, const gs_came
         GS_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         g_noalloc_ptr[dev] = p;
     }
-    return gs_bin_sort(proj, cams, n_views, n, total_tiles, cfg, g_noalloc_ptr[dev], kNoAllocBytes, keys, vals,
-                       pair_capacity, ranges, dev_pair_count, dev_status, stream);
+    return gs_bin_sort(proj, cams, n_views, n, total_tiles, max_view_tiles, cfg, g_noalloc_ptr[dev], kNoAllocBytes,
+                       keys, vals, pair_capacity, ranges, dev_pair_count, dev_status, stream);
 }

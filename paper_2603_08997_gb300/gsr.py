@@ -75,9 +75,9 @@ _PROTOS = {
     "gs_ckpt_slots": (C.c_int64, [_I64, _I64, _I32]),
     "gs_project": (C.c_int, [C.POINTER(gs_params), _P, _I32, C.POINTER(gs_raster_config), gs_projected, _P, _S]),
     "gs_bin_sort_workspace_size": (C.c_size_t, [_I64, _I32, _I64, _I64]),
-    "gs_bin_sort": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, C.POINTER(gs_raster_config), _P, _SZ,
+    "gs_bin_sort": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config), _P, _SZ,
                               _P, _P, _I64, _P, _P, _P, _S]),
-    "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, C.POINTER(gs_raster_config),
+    "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config),
                                       _P, _P, _I64, _P, _P, _P, _S]),
     "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                 _P, gs_fwd_saved, _P, _S]),

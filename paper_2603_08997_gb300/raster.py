@@ -114,6 +114,7 @@ class Views:
         raw = bytes(C.string_at(C.addressof(self.host), C.sizeof(self.host)))
         self.dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
         self.sizes = [(int(c.width), int(c.height)) for c in cams]
+        self.max_view_tiles = max(-(-w // tile) * -(-h // tile) for w, h in self.sizes)
         self.pix_offsets = [int(self.host[v].pix_offset) for v in range(self.n)]
 
     def image_view(self, flat: torch.Tensor, v: int) -> torch.Tensor:
@@ -178,7 +179,7 @@ class Renderer:
     def bin_sort(self, stream=None) -> None:
         proj = self.c_proj()
         gsr.call("gs_bin_sort", C.byref(proj), gsr.ptr(self.views.dev), self.views.n, self.n,
-                 self.views.total_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws), self.bin_ws_bytes,
+                 self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws), self.bin_ws_bytes,
                  gsr.ptr(self.keys), gsr.ptr(self.vals), self.cap, gsr.ptr(self.ranges), gsr.ptr(self.pair_count),
                  gsr.ptr(self.status), gsr.stream_handle(stream))
 

@@ -73,6 +73,6 @@ def test_workspace_too_small_is_refused(lib):
     rc = gsr.gs_raster_config()
     rc.tile, rc.batch = 16, 256
     need = lib.gs_bin_sort_workspace_size(100, 1, 1000, 4)
-    code = lib.gs_bin_sort(C.byref(proj), C.c_void_p(256), 1, 100, 4, C.byref(rc), C.c_void_p(256), need - 1,
+    code = lib.gs_bin_sort(C.byref(proj), C.c_void_p(256), 1, 100, 4, 4, C.byref(rc), C.c_void_p(256), need - 1,
                            None, C.c_void_p(256), 1000, C.c_void_p(256), C.c_void_p(256), None, None)
     assert code == gsr.GS_ERR_WORKSPACE

@@ -39,7 +39,7 @@ def _noalloc(r):
     proj = r.c_proj()
     r.status.zero_()
     code = L.gs_bin_sort_noalloc(C.byref(proj), gsr.ptr(r.views.dev), r.views.n, r.n, r.views.total_tiles,
-                                 C.byref(r.cfg), gsr.ptr(r.keys), gsr.ptr(r.vals), r.cap, gsr.ptr(r.ranges),
+                                 r.views.max_view_tiles, C.byref(r.cfg), gsr.ptr(r.keys), gsr.ptr(r.vals), r.cap, gsr.ptr(r.ranges),
                                  gsr.ptr(r.pair_count), gsr.ptr(r.status), gsr.stream_handle())
     assert code == gsr.GS_OK, gsr.status_string(code)
     return _sorted(r)
@@ -72,12 +72,15 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     proj = r.c_proj()
     r.ranges.fill_(7)
     code = L.gs_bin_sort_noalloc(C.byref(proj), gsr.ptr(r.views.dev), r.views.n, (1 << 18) + 1, r.views.total_tiles,
-                                 C.byref(r.cfg), None, gsr.ptr(r.vals), 1024, gsr.ptr(r.ranges),
+                                 r.views.max_view_tiles, C.byref(r.cfg), None, gsr.ptr(r.vals), 1024, gsr.ptr(r.ranges),
                                  gsr.ptr(r.pair_count), gsr.ptr(r.status), gsr.stream_handle())
     assert code == gsr.GS_ERR_WORKSPACE
-    code = L.gs_bin_sort_noalloc(C.byref(proj), gsr.ptr(r.views.dev), r.views.n, r.n, r.views.total_tiles,
-                                 C.byref(r.cfg), None, gsr.ptr(r.vals), (1 << 20) + 1, gsr.ptr(r.ranges),
-                                 gsr.ptr(r.pair_count), gsr.ptr(r.status), gsr.stream_handle())
+    # a tile count whose count matrix would not fit the array (checked on the
+    # host from the sizes alone, before anything reads the cameras)
+    assert L.gs_bin_sort_workspace_size(r.n, r.views.n, 1024, 1 << 22) > 16 << 20
+    code = L.gs_bin_sort_noalloc(C.byref(proj), gsr.ptr(r.views.dev), r.views.n, r.n, 1 << 22,
+                                 r.views.max_view_tiles, C.byref(r.cfg), None, gsr.ptr(r.vals), 1024,
+                                 gsr.ptr(r.ranges), gsr.ptr(r.pair_count), gsr.ptr(r.status), gsr.stream_handle())
     assert code == gsr.GS_ERR_WORKSPACE
     torch.cuda.synchronize()
     assert int(r.ranges.min().item()) == 7  # nothing was launched
