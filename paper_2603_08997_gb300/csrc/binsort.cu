@@ -270,6 +270,7 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 // with start(t) the exclusive scan of the tile totals over global tile ids.
 // That is the position of the pair in the stable sort by tile of the
 // depth-ordered pair list, so no pair key is ever materialised or sorted.
+//   bin_rects:   the clipped rectangles in depth order (one gather);
 //   bin_count:   one block per chunk: per-tile counts in shared memory, written
 //                as the chunk's row of the count matrix (chunk-major per view)
 //                and added into the per-group sums (BIN_GROUP chunks a group);
@@ -278,10 +279,16 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 //                capacity check;
 //   bin_offsets: per (group, tile), the count matrix becomes the chunks' first
 //                slots, and group 0 writes the tile's range;
-//   bin_scatter: one warp per chunk walks its entries in depth order and
-//                writes each pair at its tile's running slot (shared memory).
-constexpr int BIN_GROUP = 64;
-constexpr int COUNT_THREADS = 256;
+//   bin_scatter: one block per chunk places the chunk's pairs (below).
+// There are only about two chunks per SM, so the pair writes of all chunks in
+// flight together cover a few tens of MB: partly written 32-byte sectors are
+// completed in L2 instead of being read back from DRAM.
+constexpr int BIN_GROUP = 16;
+constexpr int COUNT_THREADS = 1024;
+constexpr int SCATTER_THREADS = 256;
+constexpr int SCATTER_OWNERS = SCATTER_THREADS / 32;  // one owner warp per tile class t % 8
+constexpr int SCATTER_STAGE = 4096;                   // staged pairs per window
+static_assert(SCATTER_OWNERS == 8, "the owner counts are packed as 8 x 16 bits");
 
 struct BinGeom {
     int64_t n;       // entries per view
@@ -293,12 +300,12 @@ struct BinGeom {
     int max_vt;      // tiles per view the shared-memory tables hold
 };
 
-// Entries per chunk: about 1500 chunks per view (ten resident per SM), in
-// multiples of 256, at least 256.
+// Entries per chunk: about two chunks per SM for one view, at least 1024, in
+// multiples of 256.
 int64_t bin_chunk(int64_t n) {
-    int64_t c = ceil_div(n, (int64_t)1520);
+    int64_t c = ceil_div(n, (int64_t)304);
     c = ceil_div(c, (int64_t)256) * 256;
-    return c < 256 ? 256 : c;
+    return c < 1024 ? 1024 : c;
 }
 
 struct ViewTiles {
@@ -321,22 +328,27 @@ __device__ __forceinline__ bool view_fits(const ViewTiles &vt, int64_t tiles, in
     return vt.tx > 0 && vt.ty > 0 && T <= max_vt && vt.off >= 0 && vt.off + T <= tiles;
 }
 
-// The rectangle of entry e clipped to the view's tile grid; false if it
-// emits no pair (culled or empty).
-__device__ __forceinline__ bool entry_rect(const int4 *__restrict__ rect, const int32_t *__restrict__ touched,
-                                           uint32_t e, const ViewTiles &vt, int4 &r) {
-    if (touched[e] <= 0) return false;
-    r = rect[e];
-    r.x = max(r.x, 0);
-    r.y = max(r.y, 0);
-    r.z = min(r.z, vt.tx - 1);
-    r.w = min(r.w, vt.ty - 1);
-    return r.x <= r.z && r.y <= r.w;
+// Rectangle of an entry clipped to its view's tile grid, packed as
+// (x0, y0, width, height) in 16 bits each; width 0 = no pair (culled/empty).
+__global__ void bin_rects(const int4 *__restrict__ rect, const int32_t *__restrict__ touched,
+                          const uint32_t *__restrict__ order, const gs_camera *__restrict__ cams, BinGeom g,
+                          int64_t total, ushort4 *__restrict__ srect) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const uint32_t e = order[i];
+    const ViewTiles vt = view_tiles(cams[i / g.n], g.tile);
+    ushort4 o = make_ushort4(0, 0, 0, 0);
+    if (touched[e] > 0 && view_fits(vt, g.tiles, g.max_vt)) {
+        const int4 r = rect[e];
+        const int x0 = max(r.x, 0), y0 = max(r.y, 0), x1 = min(r.z, vt.tx - 1), y1 = min(r.w, vt.ty - 1);
+        if (x0 <= x1 && y0 <= y1)
+            o = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)(x1 - x0 + 1),
+                             (unsigned short)(y1 - y0 + 1));
+    }
+    srect[i] = o;
 }
 
-__global__ void __launch_bounds__(COUNT_THREADS) bin_count(const int4 *__restrict__ rect,
-                                                           const int32_t *__restrict__ touched,
-                                                           const uint32_t *__restrict__ order,
+__global__ void __launch_bounds__(COUNT_THREADS) bin_count(const ushort4 *__restrict__ srect,
                                                            const gs_camera *__restrict__ cams, BinGeom g,
                                                            uint32_t *__restrict__ M, uint32_t *__restrict__ G1,
                                                            int32_t *dev_status) {
@@ -352,10 +364,11 @@ __global__ void __launch_bounds__(COUNT_THREADS) bin_count(const int4 *__restric
     __syncthreads();
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
     for (int64_t i = e0 + threadIdx.x; i < e1; i += COUNT_THREADS) {
-        int4 r;
-        if (!entry_rect(rect, touched, order[i], vt, r)) continue;
-        for (int ty = r.y; ty <= r.w; ++ty)
-            for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&s_h[ty * vt.tx + tx], 1u);
+        const ushort4 r = srect[i];
+        for (int dy = 0; dy < r.w; ++dy) {
+            uint32_t *rowp = s_h + (r.y + dy) * vt.tx + r.x;
+            for (int dx = 0; dx < r.z; ++dx) atomicAdd(rowp + dx, 1u);
+        }
     }
     __syncthreads();
     uint32_t *row = M + g.n_c * vt.off + c * T;
@@ -420,7 +433,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) bin_starts(BinGeom g, const uint
 
 // Per (group, global tile): rewrite the group's counts cnt(c, t) as the
 // chunks' first slots; group 0 also writes the tile's range.  The group's
-// counts are read in runs of 16 before any is written back.
+// counts are read before any is written back.
 __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n_views,
                             const uint32_t *__restrict__ G1, const uint32_t *__restrict__ tile_start,
                             const uint32_t *__restrict__ tile_total, const int64_t *sort_count,
@@ -438,16 +451,13 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
     uint32_t run = tile_start[gt] + G1[k * g.tiles + gt];
     const int64_t c0 = k * BIN_GROUP, c1 = min(g.n_c, c0 + BIN_GROUP);
     uint32_t *col = M + g.n_c * vt.off + t;
-    constexpr int R = 16;
-    for (int64_t cb = c0; cb < c1; cb += R) {
-        uint32_t x[R];
+    uint32_t x[BIN_GROUP];
 #pragma unroll
-        for (int j = 0; j < R; ++j) x[j] = cb + j < c1 ? col[(cb + j) * T] : 0u;
+    for (int j = 0; j < BIN_GROUP; ++j) x[j] = c0 + j < c1 ? col[(c0 + j) * T] : 0u;
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            if (cb + j < c1) col[(cb + j) * T] = run;
-            run += x[j];
-        }
+    for (int j = 0; j < BIN_GROUP; ++j) {
+        if (c0 + j < c1) col[(c0 + j) * T] = run;
+        run += x[j];
     }
     if (k == 0) {
         const uint32_t tot = tile_total[gt];
@@ -455,78 +465,137 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
     }
 }
 
-// One warp per chunk.  The chunk's first slot per tile goes to shared memory
-// (s_off).  The warp takes its entries 32 at a time; their pairs, in order
-// (entry, then tile row-major), are written tile by tile into a staging list
-// in windows of SCATTER_STAGE pairs, and each window is placed 32 pairs per
+// Exclusive block scan of two packed 64-bit vectors (lane-wise sums of 16-bit
+// fields that never carry); returns the block totals in tot_lo / tot_hi.
+__device__ __forceinline__ void block_scan_u64x2(unsigned long long &lo, unsigned long long &hi,
+                                                 unsigned long long *s_w /* [2][SCATTER_OWNERS + 1] */,
+                                                 unsigned long long &tot_lo, unsigned long long &tot_hi) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long a = lo, b = hi;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long ya = __shfl_up_sync(0xffffffffu, a, off);
+        const unsigned long long yb = __shfl_up_sync(0xffffffffu, b, off);
+        if (lane >= off) { a += ya; b += yb; }
+    }
+    if (lane == 31) { s_w[warp] = a; s_w[SCATTER_OWNERS + 1 + warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ra = 0, rb = 0;
+        for (int w = 0; w < SCATTER_OWNERS; ++w) {
+            const unsigned long long xa = s_w[w], xb = s_w[SCATTER_OWNERS + 1 + w];
+            s_w[w] = ra; s_w[SCATTER_OWNERS + 1 + w] = rb;
+            ra += xa; rb += xb;
+        }
+        s_w[SCATTER_OWNERS] = ra;
+        s_w[2 * SCATTER_OWNERS + 1] = rb;
+    }
+    __syncthreads();
+    lo = s_w[warp] + a - lo;
+    hi = s_w[SCATTER_OWNERS + 1 + warp] + b - hi;
+    tot_lo = s_w[SCATTER_OWNERS];
+    tot_hi = s_w[2 * SCATTER_OWNERS + 1];
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned field16(unsigned long long lo, unsigned long long hi, int o) {
+    return (unsigned)(((o < 4 ? lo : hi) >> (16 * (o & 3))) & 0xffffu);
+}
+
+// One block per chunk.  The chunk's first slot per tile goes to shared memory
+// (s_off).  Tiles are split into SCATTER_OWNERS classes (t % 8), each placed
+// by one warp, so no two warps touch the same slot.  The block takes its
+// entries 256 at a time (one per thread); their pairs, in order (entry, then
+// tile row-major), go in windows of SCATTER_STAGE pairs into a staging list
+// partitioned stably by owner class (packed per-thread class counts, one
+// block scan).  Each owner warp then walks its part in order, 32 pairs per
 // step: lanes holding the same tile find each other (match.any), rank among
 // themselves by lane (= list order), and the lowest of them advances the
 // tile's running slot.
-constexpr int SCATTER_STAGE = 512;
-
-__global__ void __launch_bounds__(32) bin_scatter(const int4 *__restrict__ rect, const int32_t *__restrict__ touched,
-                                                  const uint32_t *__restrict__ order,
-                                                  const gs_camera *__restrict__ cams, BinGeom g,
-                                                  const uint32_t *__restrict__ M, const int64_t *sort_count,
-                                                  uint32_t *__restrict__ vals) {
-    extern __shared__ uint32_t s_off[];
-    __shared__ int s_t[SCATTER_STAGE];
-    __shared__ uint32_t s_g[SCATTER_STAGE];
+__global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
+                                                               const uint32_t *__restrict__ order,
+                                                               const gs_camera *__restrict__ cams, BinGeom g,
+                                                               const uint32_t *__restrict__ M,
+                                                               const int64_t *sort_count,
+                                                               uint32_t *__restrict__ vals) {
+    extern __shared__ uint32_t s_dyn[];
+    uint32_t *s_g = s_dyn;                                                // [SCATTER_STAGE]
+    unsigned short *s_t = reinterpret_cast<unsigned short *>(s_dyn + SCATTER_STAGE);  // [SCATTER_STAGE]
+    uint32_t *s_off = s_dyn + SCATTER_STAGE + SCATTER_STAGE / 2;          // [max_vt]
+    __shared__ unsigned long long s_w[2 * (SCATTER_OWNERS + 1)];
+    __shared__ uint32_t s_a[SCATTER_OWNERS + 1];
     if (*sort_count == 0) return;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
     const ViewTiles vt = view_tiles(cams[v], g.tile);
     if (!view_fits(vt, g.tiles, g.max_vt)) return;
     const int T = vt.tx * vt.ty;
     const uint32_t *row = M + g.n_c * vt.off + c * T;
-    for (int t = lane; t < T; t += 32) s_off[t] = row[t];
-    __syncwarp();
+    for (int t = threadIdx.x; t < T; t += SCATTER_THREADS) s_off[t] = row[t];
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
-    for (int64_t base = e0; base < e1; base += 32) {
-        const int64_t i = base + lane;
-        int4 r = make_int4(0, 0, -1, -1);
+    for (int64_t base = e0; base < e1; base += SCATTER_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        ushort4 r = make_ushort4(0, 0, 0, 0);
         uint32_t gi = 0;
-        bool any = false;
         if (i < e1) {
-            const uint32_t e = order[i];
-            any = entry_rect(rect, touched, e, vt, r);
-            gi = (uint32_t)((int64_t)e - v * g.n);
+            r = srect[i];
+            gi = (uint32_t)((int64_t)order[i] - v * g.n);
         }
-        const int w = r.z - r.x + 1;
-        const int area = any ? w * (r.w - r.y + 1) : 0;
-        // exclusive prefix of the areas over the warp
-        int inc = area;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, off);
-            if (lane >= off) inc += y;
-        }
-        const int pre = inc - area;
-        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        const int w = r.z, area = (int)r.z * r.w;
+        // exclusive prefix of the areas over the block
+        unsigned long long pa = (unsigned long long)area, zero = 0, tot_a, tot_z;
+        block_scan_u64x2(pa, zero, s_w, tot_a, tot_z);
+        const int pre = (int)pa, tot = (int)tot_a;
         for (int w0 = 0; w0 < tot; w0 += SCATTER_STAGE) {
-            // stage this lane's pairs that fall in [w0, w0 + SCATTER_STAGE)
             const int k0 = max(pre, w0) - pre, k1 = min(pre + area, w0 + SCATTER_STAGE) - pre;
+            int dy0 = 0, dx0 = 0, t0 = 0;
             if (k0 < k1) {
-                int dy = k0 / w, dx = k0 - dy * w;
-                int t = (r.y + dy) * vt.tx + r.x + dx;
+                dy0 = k0 / w;
+                dx0 = k0 - dy0 * w;
+                t0 = (r.y + dy0) * vt.tx + r.x + dx0;
+            }
+            // pass 1: this thread's pair count per owner class
+            unsigned long long clo = 0, chi = 0;
+            {
+                int dx = dx0, t = t0;
                 for (int k = k0; k < k1; ++k) {
-                    s_t[pre + k - w0] = t;
-                    s_g[pre + k - w0] = gi;
-                    if (++dx == w) {
-                        dx = 0;
-                        t += vt.tx - (w - 1);
-                    } else {
-                        ++t;
-                    }
+                    const int o = t & (SCATTER_OWNERS - 1);
+                    if (o < 4) clo += 1ull << (16 * o); else chi += 1ull << (16 * (o - 4));
+                    if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
                 }
             }
-            __syncwarp();
-            const int cnt = min(SCATTER_STAGE, tot - w0);
-            for (int m0 = 0; m0 < cnt; m0 += 32) {
+            unsigned long long plo = clo, phi = chi, tlo, thi;
+            block_scan_u64x2(plo, phi, s_w, tlo, thi);
+            if (threadIdx.x == 0) {
+                uint32_t run = 0;
+                for (int o = 0; o < SCATTER_OWNERS; ++o) {
+                    s_a[o] = run;
+                    run += field16(tlo, thi, o);
+                }
+                s_a[SCATTER_OWNERS] = run;
+            }
+            __syncthreads();
+            // pass 2: stage the pairs, stably partitioned by owner class
+            {
+                unsigned long long rlo = plo, rhi = phi;  // running slots within each class
+                int dx = dx0, t = t0;
+                for (int k = k0; k < k1; ++k) {
+                    const int o = t & (SCATTER_OWNERS - 1);
+                    const uint32_t pos = s_a[o] + field16(rlo, rhi, o);
+                    if (o < 4) rlo += 1ull << (16 * o); else rhi += 1ull << (16 * (o - 4));
+                    s_t[pos] = (unsigned short)t;
+                    s_g[pos] = gi;
+                    if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
+                }
+            }
+            __syncthreads();
+            // walk: warp `warp` places the pairs of owner class `warp`, in order
+            const int m_lo = (int)s_a[warp], m_hi = (int)s_a[warp + 1];
+            for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
                 const int m = m0 + lane;
-                const bool valid = m < cnt;
-                const int t = valid ? s_t[m] : -1 - lane;  // invalid lanes match nobody
+                const bool valid = m < m_hi;
+                const int t = valid ? (int)s_t[m] : -1 - lane;  // invalid lanes match nobody
                 const uint32_t peers = __match_any_sync(0xffffffffu, t);
                 uint32_t slot = 0;
                 if (valid) slot = s_off[t];
@@ -537,6 +606,7 @@ __global__ void __launch_bounds__(32) bin_scatter(const int4 *__restrict__ rect,
                 }
                 __syncwarp();
             }
+            __syncthreads();
         }
     }
 }
@@ -581,6 +651,7 @@ struct BinWorkspace {
     uint32_t *G1;              // [n_g * total_tiles] group sums, then group offsets
     uint32_t *tile_total;      // [total_tiles]
     uint32_t *tile_start;      // [total_tiles]
+    ushort4 *srect;            // [V*N] clipped rectangles in depth order
     int64_t *sort_count;       // [1]
 };
 
@@ -605,6 +676,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
     char *G1 = take(sizeof(uint32_t) * (size_t)(g.n_g * total_tiles));
     char *tt = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *ts = take(sizeof(uint32_t) * (size_t)total_tiles);
+    char *sr = take(sizeof(ushort4) * (size_t)(total > 0 ? total : 1));
     char *sc = take(sizeof(int64_t));
     if (w) {
         w->counts = (uint32_t *)counts;
@@ -612,6 +684,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
         w->G1 = (uint32_t *)G1;
         w->tile_total = (uint32_t *)tt;
         w->tile_start = (uint32_t *)ts;
+        w->srect = (ushort4 *)sr;
         w->sort_count = (int64_t *)sc;
     }
     return off;
@@ -620,6 +693,9 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
 // Tables of up to this many tiles per view fit the shared memory of the
 // counting and scatter kernels (192 KB).
 constexpr int kMaxViewTiles = 49152;
+
+// Shared memory of bin_scatter ahead of its tile table: the staged pairs.
+constexpr size_t scatter_stage_bytes() { return sizeof(uint32_t) * (SCATTER_STAGE + SCATTER_STAGE / 2); }
 
 // Raise the dynamic shared-memory limit of the table kernels to the largest
 // table, once per device (before any stream capture, on the first call).
@@ -630,7 +706,8 @@ gs_status bin_smem_attributes() {
     if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes + (int)scatter_stage_bytes()));
     if (dev >= 0 && dev < 64) done[dev] = true;
     return GS_OK;
 }
@@ -688,10 +765,12 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     // 2. counting sort of the pairs by tile, in depth order
     const size_t smem = sizeof(uint32_t) * (size_t)mvt;
     GS_TRY(bin_smem_attributes());
+    bin_rects<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(rect, proj->tiles_touched, order, cams, g, total,
+                                                                 w.srect);
+    GS_TRY_LAUNCH();
     GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
     const unsigned n_chunks = (unsigned)(g.n_c * n_views);
-    bin_count<<<n_chunks, COUNT_THREADS, smem, stream>>>(rect, proj->tiles_touched, order, cams, g, w.M, w.G1,
-                                                        dev_status);
+    bin_count<<<n_chunks, COUNT_THREADS, smem, stream>>>(w.srect, cams, g, w.M, w.G1, dev_status);
     GS_TRY_LAUNCH();
     bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
     GS_TRY_LAUNCH();
@@ -701,7 +780,8 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
         g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
-    bin_scatter<<<n_chunks, 32, smem, stream>>>(rect, proj->tiles_touched, order, cams, g, w.M, w.sort_count, vals);
+    bin_scatter<<<n_chunks, SCATTER_THREADS, smem + scatter_stage_bytes(), stream>>>(w.srect, order, cams, g, w.M,
+                                                                                      w.sort_count, vals);
     GS_TRY_LAUNCH();
     if (keys) {
         keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,
