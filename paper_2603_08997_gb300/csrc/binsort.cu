@@ -505,13 +505,14 @@ __device__ __forceinline__ unsigned field16(unsigned long long lo, unsigned long
 // One block per chunk.  The chunk's first slot per tile goes to shared memory
 // (s_off).  Tiles are split into SCATTER_OWNERS classes (t % 8), each placed
 // by one warp, so no two warps touch the same slot.  The block takes its
-// entries 256 at a time (one per thread); their pairs, in order (entry, then
-// tile row-major), go in windows of SCATTER_STAGE pairs into a staging list
-// partitioned stably by owner class (packed per-thread class counts, one
-// block scan).  Each owner warp then walks its part in order, 32 pairs per
-// step: lanes holding the same tile find each other (match.any), rank among
-// themselves by lane (= list order), and the lowest of them advances the
-// tile's running slot.
+// entries 256 at a time; their pairs, in order (entry, then tile row-major),
+// are cut into windows of at most SCATTER_STAGE pairs and each thread expands
+// an equal contiguous run of a window's pairs (so one large rectangle does not
+// stall the block).  The window is staged in shared memory partitioned stably
+// by owner class (packed per-thread class counts, one block scan); each owner
+// warp then walks its part in order, 32 pairs per step: lanes holding the same
+// tile find each other (match.any), rank among themselves by lane (= list
+// order), and the lowest of them advances the tile's running slot.
 __global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                                const uint32_t *__restrict__ order,
                                                                const gs_camera *__restrict__ cams, BinGeom g,
@@ -524,6 +525,9 @@ __global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__
     uint32_t *s_off = s_dyn + SCATTER_STAGE + SCATTER_STAGE / 2;          // [max_vt]
     __shared__ unsigned long long s_w[2 * (SCATTER_OWNERS + 1)];
     __shared__ uint32_t s_a[SCATTER_OWNERS + 1];
+    __shared__ ushort4 s_er[SCATTER_THREADS];        // the round's entries: rectangle
+    __shared__ uint32_t s_eg[SCATTER_THREADS];       // Gaussian index
+    __shared__ int s_pre[SCATTER_THREADS + 1];       // first pair of each entry in the round
     if (*sort_count == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -542,24 +546,43 @@ __global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__
             r = srect[i];
             gi = (uint32_t)((int64_t)order[i] - v * g.n);
         }
-        const int w = r.z, area = (int)r.z * r.w;
+        s_er[threadIdx.x] = r;
+        s_eg[threadIdx.x] = gi;
         // exclusive prefix of the areas over the block
-        unsigned long long pa = (unsigned long long)area, zero = 0, tot_a, tot_z;
+        unsigned long long pa = (unsigned long long)((int)r.z * r.w), zero = 0, tot_a, tot_z;
         block_scan_u64x2(pa, zero, s_w, tot_a, tot_z);
-        const int pre = (int)pa, tot = (int)tot_a;
+        s_pre[threadIdx.x] = (int)pa;
+        if (threadIdx.x == 0) s_pre[SCATTER_THREADS] = (int)tot_a;
+        __syncthreads();
+        const int tot = (int)tot_a;
         for (int w0 = 0; w0 < tot; w0 += SCATTER_STAGE) {
-            const int k0 = max(pre, w0) - pre, k1 = min(pre + area, w0 + SCATTER_STAGE) - pre;
-            int dy0 = 0, dx0 = 0, t0 = 0;
-            if (k0 < k1) {
-                dy0 = k0 / w;
-                dx0 = k0 - dy0 * w;
-                t0 = (r.y + dy0) * vt.tx + r.x + dx0;
+            const int cnt = min(SCATTER_STAGE, tot - w0);
+            const int q = (cnt + SCATTER_THREADS - 1) / SCATTER_THREADS;
+            const int p0 = w0 + min(cnt, (int)threadIdx.x * q), p1 = w0 + min(cnt, ((int)threadIdx.x + 1) * q);
+            // the entry holding pair p0: last j with s_pre[j] <= p0 (largest such j skips empty entries)
+            int j = 0;
+            if (p0 < p1) {
+                int lo = 0, hi = SCATTER_THREADS - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
+                }
+                j = lo;
             }
             // pass 1: this thread's pair count per owner class
             unsigned long long clo = 0, chi = 0;
             {
-                int dx = dx0, t = t0;
-                for (int k = k0; k < k1; ++k) {
+                int jj = j, dx = 0, t = 0, w = 1, nxt = 0;
+                for (int p = p0; p < p1; ++p) {
+                    if (p == p0 || p == nxt) {
+                        while (s_pre[jj + 1] <= p) ++jj;
+                        const ushort4 er = s_er[jj];
+                        w = er.z;
+                        const int k = p - s_pre[jj], dy = k / w;
+                        dx = k - dy * w;
+                        t = (er.y + dy) * vt.tx + er.x + dx;
+                        nxt = s_pre[jj + 1];
+                    }
                     const int o = t & (SCATTER_OWNERS - 1);
                     if (o < 4) clo += 1ull << (16 * o); else chi += 1ull << (16 * (o - 4));
                     if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
@@ -579,13 +602,24 @@ __global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__
             // pass 2: stage the pairs, stably partitioned by owner class
             {
                 unsigned long long rlo = plo, rhi = phi;  // running slots within each class
-                int dx = dx0, t = t0;
-                for (int k = k0; k < k1; ++k) {
+                int jj = j, dx = 0, t = 0, w = 1, nxt = 0;
+                uint32_t eg = 0;
+                for (int p = p0; p < p1; ++p) {
+                    if (p == p0 || p == nxt) {
+                        while (s_pre[jj + 1] <= p) ++jj;
+                        const ushort4 er = s_er[jj];
+                        w = er.z;
+                        const int k = p - s_pre[jj], dy = k / w;
+                        dx = k - dy * w;
+                        t = (er.y + dy) * vt.tx + er.x + dx;
+                        nxt = s_pre[jj + 1];
+                        eg = s_eg[jj];
+                    }
                     const int o = t & (SCATTER_OWNERS - 1);
                     const uint32_t pos = s_a[o] + field16(rlo, rhi, o);
                     if (o < 4) rlo += 1ull << (16 * o); else rhi += 1ull << (16 * (o - 4));
                     s_t[pos] = (unsigned short)t;
-                    s_g[pos] = gi;
+                    s_g[pos] = eg;
                     if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
                 }
             }
