@@ -180,7 +180,7 @@ size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capac
  * vals[pair] = Gaussian index, ranges[tile] = [start, end) (empty = [0,0)),
  * *dev_pair_count, and - if keys is not NULL - the 64-bit keys.
  * max_view_tiles: the largest tile count of one view (0 = total_tiles); at
- * most 49152, else GS_ERR_UNSUPPORTED; a view with more tiles than given
+ * most 20480, else GS_ERR_UNSUPPORTED; a view with more tiles than given
  * sets GS_ERR_INVALID_ARG in dev_status and emits no pairs.  Rectangles are
  * clipped to the view's tile grid; entries with tiles_touched <= 0 emit
  * nothing.  More pairs than pair_capacity: GS_ERR_CAPACITY in dev_status,

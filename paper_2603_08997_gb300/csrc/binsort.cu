@@ -285,10 +285,6 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 // completed in L2 instead of being read back from DRAM.
 constexpr int BIN_GROUP = 16;
 constexpr int COUNT_THREADS = 1024;
-constexpr int SCATTER_THREADS = 256;
-constexpr int SCATTER_OWNERS = SCATTER_THREADS / 32;  // one owner warp per tile class t % 8
-constexpr int SCATTER_STAGE = 4096;                   // staged pairs per window
-static_assert(SCATTER_OWNERS == 8, "the owner counts are packed as 8 x 16 bits");
 
 struct BinGeom {
     int64_t n;       // entries per view
@@ -465,114 +461,109 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
     }
 }
 
-// Exclusive block scan of two packed 64-bit vectors (lane-wise sums of 16-bit
-// fields that never carry); returns the block totals in tot_lo / tot_hi.
-__device__ __forceinline__ void block_scan_u64x2(unsigned long long &lo, unsigned long long &hi,
-                                                 unsigned long long *s_w /* [2][SCATTER_OWNERS + 1] */,
-                                                 unsigned long long &tot_lo, unsigned long long &tot_hi) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long a = lo, b = hi;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long ya = __shfl_up_sync(0xffffffffu, a, off);
-        const unsigned long long yb = __shfl_up_sync(0xffffffffu, b, off);
-        if (lane >= off) { a += ya; b += yb; }
+// Exclusive scan, in place, of the first n words of s (one block, each
+// thread a contiguous run).
+__device__ __forceinline__ void block_scan_table(uint32_t *s, int n, uint32_t *warp_sums) {
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    uint32_t sum = 0;
+    for (int t = lo; t < hi; ++t) sum += s[t];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(sum, warp_sums, &total);
+    for (int t = lo; t < hi; ++t) {
+        const uint32_t x = s[t];
+        s[t] = run;
+        run += x;
     }
-    if (lane == 31) { s_w[warp] = a; s_w[SCATTER_OWNERS + 1 + warp] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long ra = 0, rb = 0;
-        for (int w = 0; w < SCATTER_OWNERS; ++w) {
-            const unsigned long long xa = s_w[w], xb = s_w[SCATTER_OWNERS + 1 + w];
-            s_w[w] = ra; s_w[SCATTER_OWNERS + 1 + w] = rb;
-            ra += xa; rb += xb;
-        }
-        s_w[SCATTER_OWNERS] = ra;
-        s_w[2 * SCATTER_OWNERS + 1] = rb;
-    }
-    __syncthreads();
-    lo = s_w[warp] + a - lo;
-    hi = s_w[SCATTER_OWNERS + 1 + warp] + b - hi;
-    tot_lo = s_w[SCATTER_OWNERS];
-    tot_hi = s_w[2 * SCATTER_OWNERS + 1];
     __syncthreads();
 }
 
-__device__ __forceinline__ unsigned field16(unsigned long long lo, unsigned long long hi, int o) {
-    return (unsigned)(((o < 4 ? lo : hi) >> (16 * (o & 3))) & 0xffffu);
+// One block per chunk.  The chunk's first slot per tile is held in shared
+// memory (s_off).  The block takes its entries SC_ROUND at a time; their
+// pairs, in order (entry, then tile row-major), are cut into windows of at
+// most SC_STAGE pairs, each thread expanding an equal contiguous run of a
+// window (so one large rectangle does not stall the block).  A window is
+// counting-sorted by tile in shared memory (count, scan, place; the places
+// inside a tile's segment come from shared atomics, in no particular order),
+// then every staged pair takes as its rank the number of pairs of its tile in
+// the window from earlier entries - segments are a few pairs long - and goes
+// to s_off[tile] + rank.  Pairs of one tile sit together in the staging list,
+// so consecutive threads write consecutive slots.
+constexpr int SC_THREADS = 512;
+constexpr int SC_ROUND = 1024;  // entries per round
+constexpr int SC_STAGE = 8192;  // pairs per window
+
+// Shared memory of bin_scatter besides its two tile tables.
+constexpr size_t scatter_stage_bytes() {
+    return sizeof(uint32_t) * SC_STAGE + sizeof(ushort4) * SC_ROUND + sizeof(uint32_t) * SC_ROUND +
+           sizeof(int) * (SC_ROUND + 1);
 }
 
-// One block per chunk.  The chunk's first slot per tile goes to shared memory
-// (s_off).  Tiles are split into SCATTER_OWNERS classes (t % 8), each placed
-// by one warp, so no two warps touch the same slot.  The block takes its
-// entries 256 at a time; their pairs, in order (entry, then tile row-major),
-// are cut into windows of at most SCATTER_STAGE pairs and each thread expands
-// an equal contiguous run of a window's pairs (so one large rectangle does not
-// stall the block).  The window is staged in shared memory partitioned stably
-// by owner class (packed per-thread class counts, one block scan); each owner
-// warp then walks its part in order, 32 pairs per step: lanes holding the same
-// tile find each other (match.any), rank among themselves by lane (= list
-// order), and the lowest of them advances the tile's running slot.
-__global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
-                                                               const uint32_t *__restrict__ order,
-                                                               const gs_camera *__restrict__ cams, BinGeom g,
-                                                               const uint32_t *__restrict__ M,
-                                                               const int64_t *sort_count,
-                                                               uint32_t *__restrict__ vals) {
+__global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
+                                                          const uint32_t *__restrict__ order,
+                                                          const gs_camera *__restrict__ cams, BinGeom g,
+                                                          const uint32_t *__restrict__ M,
+                                                          const int64_t *sort_count, uint32_t *__restrict__ vals) {
     extern __shared__ uint32_t s_dyn[];
-    uint32_t *s_g = s_dyn;                                                // [SCATTER_STAGE]
-    unsigned short *s_t = reinterpret_cast<unsigned short *>(s_dyn + SCATTER_STAGE);  // [SCATTER_STAGE]
-    uint32_t *s_off = s_dyn + SCATTER_STAGE + SCATTER_STAGE / 2;          // [max_vt]
-    __shared__ unsigned long long s_w[2 * (SCATTER_OWNERS + 1)];
-    __shared__ uint32_t s_a[SCATTER_OWNERS + 1];
-    __shared__ ushort4 s_er[SCATTER_THREADS];        // the round's entries: rectangle
-    __shared__ uint32_t s_eg[SCATTER_THREADS];       // Gaussian index
-    __shared__ int s_pre[SCATTER_THREADS + 1];       // first pair of each entry in the round
+    ushort4 *s_er = reinterpret_cast<ushort4 *>(s_dyn);             // [SC_ROUND] the round's rectangles
+    uint32_t *s_stage = s_dyn + 2 * SC_ROUND;                         // [SC_STAGE] (tile << 16 | entry)
+    uint32_t *s_eg = s_stage + SC_STAGE;                              // [SC_ROUND] Gaussian index
+    int *s_pre = reinterpret_cast<int *>(s_eg + SC_ROUND);            // [SC_ROUND + 1] first pair of each entry
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_pre + SC_ROUND + 1);  // [max_vt] running slot per tile
+    uint32_t *s_x = s_off + g.max_vt;                                 // [max_vt] window counts / segment ends
+    __shared__ uint32_t s_warp[32];
     if (*sort_count == 0) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
     const ViewTiles vt = view_tiles(cams[v], g.tile);
     if (!view_fits(vt, g.tiles, g.max_vt)) return;
     const int T = vt.tx * vt.ty;
     const uint32_t *row = M + g.n_c * vt.off + c * T;
-    for (int t = threadIdx.x; t < T; t += SCATTER_THREADS) s_off[t] = row[t];
+    for (int t = threadIdx.x; t < T; t += SC_THREADS) {
+        s_off[t] = row[t];
+        s_x[t] = 0u;
+    }
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
-    for (int64_t base = e0; base < e1; base += SCATTER_THREADS) {
-        const int64_t i = base + threadIdx.x;
-        ushort4 r = make_ushort4(0, 0, 0, 0);
-        uint32_t gi = 0;
-        if (i < e1) {
-            r = srect[i];
-            gi = (uint32_t)((int64_t)order[i] - v * g.n);
+    for (int64_t base = e0; base < e1; base += SC_ROUND) {
+        // the round's entries, two per thread
+        int a2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jl = 2 * threadIdx.x + h;
+            const int64_t i = base + jl;
+            ushort4 r = make_ushort4(0, 0, 0, 0);
+            uint32_t gi = 0;
+            if (i < e1) {
+                r = srect[i];
+                gi = (uint32_t)((int64_t)order[i] - v * g.n);
+            }
+            s_er[jl] = r;
+            s_eg[jl] = gi;
+            a2[h] = (int)r.z * r.w;
         }
-        s_er[threadIdx.x] = r;
-        s_eg[threadIdx.x] = gi;
-        // exclusive prefix of the areas over the block
-        unsigned long long pa = (unsigned long long)((int)r.z * r.w), zero = 0, tot_a, tot_z;
-        block_scan_u64x2(pa, zero, s_w, tot_a, tot_z);
-        s_pre[threadIdx.x] = (int)pa;
-        if (threadIdx.x == 0) s_pre[SCATTER_THREADS] = (int)tot_a;
+        uint32_t tot_u;
+        const int pre = (int)block_exclusive_scan((uint32_t)(a2[0] + a2[1]), s_warp, &tot_u);
+        s_pre[2 * threadIdx.x] = pre;
+        s_pre[2 * threadIdx.x + 1] = pre + a2[0];
+        if (threadIdx.x == 0) s_pre[SC_ROUND] = (int)tot_u;
         __syncthreads();
-        const int tot = (int)tot_a;
-        for (int w0 = 0; w0 < tot; w0 += SCATTER_STAGE) {
-            const int cnt = min(SCATTER_STAGE, tot - w0);
-            const int q = (cnt + SCATTER_THREADS - 1) / SCATTER_THREADS;
+        const int tot = (int)tot_u;
+        for (int w0 = 0; w0 < tot; w0 += SC_STAGE) {
+            const int cnt = min(SC_STAGE, tot - w0);
+            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
             const int p0 = w0 + min(cnt, (int)threadIdx.x * q), p1 = w0 + min(cnt, ((int)threadIdx.x + 1) * q);
-            // the entry holding pair p0: last j with s_pre[j] <= p0 (largest such j skips empty entries)
-            int j = 0;
+            // the entry holding pair p0: the last j with s_pre[j] <= p0 (so empty entries are skipped)
+            int j0 = 0;
             if (p0 < p1) {
-                int lo = 0, hi = SCATTER_THREADS - 1;
+                int lo = 0, hi = SC_ROUND - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
                 }
-                j = lo;
+                j0 = lo;
             }
-            // pass 1: this thread's pair count per owner class
-            unsigned long long clo = 0, chi = 0;
+            // pass A: pairs per tile
             {
-                int jj = j, dx = 0, t = 0, w = 1, nxt = 0;
+                int jj = j0, dx = 0, t = 0, w = 1, nxt = 0;
                 for (int p = p0; p < p1; ++p) {
                     if (p == p0 || p == nxt) {
                         while (s_pre[jj + 1] <= p) ++jj;
@@ -583,27 +574,15 @@ __global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__
                         t = (er.y + dy) * vt.tx + er.x + dx;
                         nxt = s_pre[jj + 1];
                     }
-                    const int o = t & (SCATTER_OWNERS - 1);
-                    if (o < 4) clo += 1ull << (16 * o); else chi += 1ull << (16 * (o - 4));
+                    atomicAdd(&s_x[t], 1u);
                     if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
                 }
             }
-            unsigned long long plo = clo, phi = chi, tlo, thi;
-            block_scan_u64x2(plo, phi, s_w, tlo, thi);
-            if (threadIdx.x == 0) {
-                uint32_t run = 0;
-                for (int o = 0; o < SCATTER_OWNERS; ++o) {
-                    s_a[o] = run;
-                    run += field16(tlo, thi, o);
-                }
-                s_a[SCATTER_OWNERS] = run;
-            }
             __syncthreads();
-            // pass 2: stage the pairs, stably partitioned by owner class
+            block_scan_table(s_x, T, s_warp);  // s_x[t] = first staging slot of tile t
+            // pass B: stage (tile, entry); afterwards s_x[t] = end of tile t's segment
             {
-                unsigned long long rlo = plo, rhi = phi;  // running slots within each class
-                int jj = j, dx = 0, t = 0, w = 1, nxt = 0;
-                uint32_t eg = 0;
+                int jj = j0, dx = 0, t = 0, w = 1, nxt = 0;
                 for (int p = p0; p < p1; ++p) {
                     if (p == p0 || p == nxt) {
                         while (s_pre[jj + 1] <= p) ++jj;
@@ -613,33 +592,28 @@ __global__ void __launch_bounds__(SCATTER_THREADS) bin_scatter(const ushort4 *__
                         dx = k - dy * w;
                         t = (er.y + dy) * vt.tx + er.x + dx;
                         nxt = s_pre[jj + 1];
-                        eg = s_eg[jj];
                     }
-                    const int o = t & (SCATTER_OWNERS - 1);
-                    const uint32_t pos = s_a[o] + field16(rlo, rhi, o);
-                    if (o < 4) rlo += 1ull << (16 * o); else rhi += 1ull << (16 * (o - 4));
-                    s_t[pos] = (unsigned short)t;
-                    s_g[pos] = eg;
+                    const uint32_t pos = atomicAdd(&s_x[t], 1u);
+                    s_stage[pos] = ((uint32_t)t << 16) | (uint32_t)jj;
                     if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
                 }
             }
             __syncthreads();
-            // walk: warp `warp` places the pairs of owner class `warp`, in order
-            const int m_lo = (int)s_a[warp], m_hi = (int)s_a[warp + 1];
-            for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
-                const int m = m0 + lane;
-                const bool valid = m < m_hi;
-                const int t = valid ? (int)s_t[m] : -1 - lane;  // invalid lanes match nobody
-                const uint32_t peers = __match_any_sync(0xffffffffu, t);
-                uint32_t slot = 0;
-                if (valid) slot = s_off[t];
-                __syncwarp();
-                if (valid) {
-                    if ((peers & lt_mask) == 0) s_off[t] = slot + __popc(peers);
-                    vals[slot + __popc(peers & lt_mask)] = s_g[m];
-                }
-                __syncwarp();
+            // place: rank = pairs of the same tile from earlier entries of the window
+            for (int p = threadIdx.x; p < cnt; p += SC_THREADS) {
+                const uint32_t e = s_stage[p];
+                const int t = (int)(e >> 16);
+                const uint32_t j = e & 0xffffu;
+                const int lo = t > 0 ? (int)s_x[t - 1] : 0, hi = (int)s_x[t];
+                uint32_t rank = 0;
+                for (int qq = lo; qq < hi; ++qq) rank += (s_stage[qq] & 0xffffu) < j;
+                vals[s_off[t] + rank] = s_eg[j];
             }
+            __syncthreads();
+            // advance the running slots, then clear the counts for the next window
+            for (int t = threadIdx.x; t < T; t += SC_THREADS) s_off[t] += s_x[t] - (t > 0 ? s_x[t - 1] : 0u);
+            __syncthreads();
+            for (int t = threadIdx.x; t < T; t += SC_THREADS) s_x[t] = 0u;
             __syncthreads();
         }
     }
@@ -725,11 +699,8 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
 }
 
 // Tables of up to this many tiles per view fit the shared memory of the
-// counting and scatter kernels (192 KB).
-constexpr int kMaxViewTiles = 49152;
-
-// Shared memory of bin_scatter ahead of its tile table: the staged pairs.
-constexpr size_t scatter_stage_bytes() { return sizeof(uint32_t) * (SCATTER_STAGE + SCATTER_STAGE / 2); }
+// counting and scatter kernels (the scatter holds two 4-byte tables).
+constexpr int kMaxViewTiles = 20480;
 
 // Raise the dynamic shared-memory limit of the table kernels to the largest
 // table, once per device (before any stream capture, on the first call).
@@ -741,7 +712,7 @@ gs_status bin_smem_attributes() {
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     GS_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes + (int)scatter_stage_bytes()));
+                                2 * bytes + (int)scatter_stage_bytes()));
     if (dev >= 0 && dev < 64) done[dev] = true;
     return GS_OK;
 }
@@ -814,8 +785,8 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
         g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
-    bin_scatter<<<n_chunks, SCATTER_THREADS, smem + scatter_stage_bytes(), stream>>>(w.srect, order, cams, g, w.M,
-                                                                                      w.sort_count, vals);
+    bin_scatter<<<n_chunks, SC_THREADS, 2 * smem + scatter_stage_bytes(), stream>>>(w.srect, order, cams, g, w.M,
+                                                                                     w.sort_count, vals);
     GS_TRY_LAUNCH();
     if (keys) {
         keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,
