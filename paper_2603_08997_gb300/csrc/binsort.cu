@@ -479,38 +479,78 @@ __device__ __forceinline__ void block_scan_table(uint32_t *s, int n, uint32_t *w
 }
 
 // One block per chunk.  The chunk's first slot per tile is held in shared
-// memory (s_off).  The block takes its entries SC_ROUND at a time; their
-// pairs, in order (entry, then tile row-major), are cut into windows of at
-// most SC_STAGE pairs, each thread expanding an equal contiguous run of a
-// window (so one large rectangle does not stall the block).  A window is
-// counting-sorted by tile in shared memory (count, scan, place; the places
-// inside a tile's segment come from shared atomics, in no particular order),
-// then every staged pair takes as its rank the number of pairs of its tile in
-// the window from earlier entries - segments are a few pairs long - and goes
-// to s_off[tile] + rank.  Pairs of one tile sit together in the staging list,
-// so consecutive threads write consecutive slots.
+// memory (s_off).  The block takes its entries WIN at a time (a window, WIN =
+// the bits of one tile's entry mask); the window's pairs, in order (entry,
+// then tile row-major), are expanded with each thread taking an equal
+// contiguous run, so one large rectangle does not stall the block.
+//   pass A: every pair sets bit j (its entry within the window) in its tile's
+//           mask (shared atomicOr, order-free);
+//   pass B: a pair's rank among the window's pairs of its tile is the number
+//           of mask bits below j; it goes to s_off[tile] + rank.  The pair
+//           with the highest bit then advances s_off[tile] by the mask's
+//           population and clears the mask.
+// Pass B runs in sub-windows of SC_THREADS * SC_Q pairs; a tile's last pair is
+// never in an earlier sub-window than its other pairs, so each sub-window's
+// advances can follow it directly.
 constexpr int SC_THREADS = 512;
-constexpr int SC_ROUND = 1024;  // entries per round
-constexpr int SC_STAGE = 8192;  // pairs per window
+constexpr int SC_Q = 4;  // pairs per thread per sub-window
 
-// Shared memory of bin_scatter besides its two tile tables.
-constexpr size_t scatter_stage_bytes() {
-    return sizeof(uint32_t) * SC_STAGE + sizeof(ushort4) * SC_ROUND + sizeof(uint32_t) * SC_ROUND +
-           sizeof(int) * (SC_ROUND + 1);
-}
+template <typename W, int NW>
+struct ScatterMask {
+    static constexpr int WB = 8 * (int)sizeof(W);
+    static constexpr int WIN = WB * NW;  // entries per window
+    static constexpr size_t bytes_per_tile = sizeof(W) * NW + sizeof(uint32_t);
+};
 
+// Walks the pairs [p0, p1) of a window in list order.
+struct PairWalk {
+    int jj, dx, t, w, nxt;
+    __device__ __forceinline__ void start(int p0, const int *s_pre, const ushort4 *s_er, int win, int tx) {
+        int lo = 0, hi = win - 1;  // the last j with s_pre[j] <= p0 (so empty entries are skipped)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
+        }
+        jj = lo;
+        const ushort4 er = s_er[jj];
+        w = er.z;
+        const int k = p0 - s_pre[jj], dy = k / w;
+        dx = k - dy * w;
+        t = (er.y + dy) * tx + er.x + dx;
+        nxt = s_pre[jj + 1];
+    }
+    // step from pair p to pair p + 1 (p + 1 < end of the window)
+    __device__ __forceinline__ void next(int p, const int *s_pre, const ushort4 *s_er, int tx) {
+        if (p + 1 == nxt) {
+            do { ++jj; } while (s_pre[jj + 1] <= p + 1);
+            const ushort4 er = s_er[jj];
+            w = er.z;
+            dx = 0;
+            t = er.y * tx + er.x;
+            nxt = s_pre[jj + 1];
+        } else if (++dx == w) {
+            dx = 0;
+            t += tx - (w - 1);
+        } else {
+            ++t;
+        }
+    }
+};
+
+template <typename W, int NW>
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                           const uint32_t *__restrict__ order,
                                                           const gs_camera *__restrict__ cams, BinGeom g,
                                                           const uint32_t *__restrict__ M,
                                                           const int64_t *sort_count, uint32_t *__restrict__ vals) {
-    extern __shared__ uint32_t s_dyn[];
-    ushort4 *s_er = reinterpret_cast<ushort4 *>(s_dyn);             // [SC_ROUND] the round's rectangles
-    uint32_t *s_stage = s_dyn + 2 * SC_ROUND;                         // [SC_STAGE] (tile << 16 | entry)
-    uint32_t *s_eg = s_stage + SC_STAGE;                              // [SC_ROUND] Gaussian index
-    int *s_pre = reinterpret_cast<int *>(s_eg + SC_ROUND);            // [SC_ROUND + 1] first pair of each entry
-    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_pre + SC_ROUND + 1);  // [max_vt] running slot per tile
-    uint32_t *s_x = s_off + g.max_vt;                                 // [max_vt] window counts / segment ends
+    using SM = ScatterMask<W, NW>;
+    constexpr int WB = SM::WB, WIN = SM::WIN;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    W *s_mask = reinterpret_cast<W *>(s_raw);                                     // [max_vt][NW]
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_mask + (size_t)g.max_vt * NW);  // [max_vt]
+    __shared__ ushort4 s_er[WIN];    // the window's rectangles
+    __shared__ uint32_t s_eg[WIN];   // Gaussian indices
+    __shared__ int s_pre[WIN + 1];   // first pair of each entry
     __shared__ uint32_t s_warp[32];
     if (*sort_count == 0) return;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
@@ -520,103 +560,103 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     const uint32_t *row = M + g.n_c * vt.off + c * T;
     for (int t = threadIdx.x; t < T; t += SC_THREADS) {
         s_off[t] = row[t];
-        s_x[t] = 0u;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_mask[t * NW + k] = 0;
     }
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
-    for (int64_t base = e0; base < e1; base += SC_ROUND) {
-        // the round's entries, two per thread
-        int a2[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int jl = 2 * threadIdx.x + h;
-            const int64_t i = base + jl;
+    for (int64_t base = e0; base < e1; base += WIN) {
+        int area = 0;
+        if (threadIdx.x < WIN) {
+            const int64_t i = base + threadIdx.x;
             ushort4 r = make_ushort4(0, 0, 0, 0);
             uint32_t gi = 0;
             if (i < e1) {
                 r = srect[i];
                 gi = (uint32_t)((int64_t)order[i] - v * g.n);
             }
-            s_er[jl] = r;
-            s_eg[jl] = gi;
-            a2[h] = (int)r.z * r.w;
+            s_er[threadIdx.x] = r;
+            s_eg[threadIdx.x] = gi;
+            area = (int)r.z * r.w;
         }
         uint32_t tot_u;
-        const int pre = (int)block_exclusive_scan((uint32_t)(a2[0] + a2[1]), s_warp, &tot_u);
-        s_pre[2 * threadIdx.x] = pre;
-        s_pre[2 * threadIdx.x + 1] = pre + a2[0];
-        if (threadIdx.x == 0) s_pre[SC_ROUND] = (int)tot_u;
+        const int pre = (int)block_exclusive_scan((uint32_t)area, s_warp, &tot_u);
+        if (threadIdx.x < WIN) s_pre[threadIdx.x] = pre;
+        if (threadIdx.x == 0) s_pre[WIN] = (int)tot_u;
         __syncthreads();
         const int tot = (int)tot_u;
-        for (int w0 = 0; w0 < tot; w0 += SC_STAGE) {
-            const int cnt = min(SC_STAGE, tot - w0);
+        // pass A: entry masks per tile
+        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
+            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
             const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
-            const int p0 = w0 + min(cnt, (int)threadIdx.x * q), p1 = w0 + min(cnt, ((int)threadIdx.x + 1) * q);
-            // the entry holding pair p0: the last j with s_pre[j] <= p0 (so empty entries are skipped)
-            int j0 = 0;
+            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
             if (p0 < p1) {
-                int lo = 0, hi = SC_ROUND - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
+                PairWalk it;
+                it.start(p0, s_pre, s_er, WIN, vt.tx);
+                for (int p = p0;; ++p) {
+                    atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
+                    if (p + 1 >= p1) break;
+                    it.next(p, s_pre, s_er, vt.tx);
                 }
-                j0 = lo;
             }
-            // pass A: pairs per tile
-            {
-                int jj = j0, dx = 0, t = 0, w = 1, nxt = 0;
-                for (int p = p0; p < p1; ++p) {
-                    if (p == p0 || p == nxt) {
-                        while (s_pre[jj + 1] <= p) ++jj;
-                        const ushort4 er = s_er[jj];
-                        w = er.z;
-                        const int k = p - s_pre[jj], dy = k / w;
-                        dx = k - dy * w;
-                        t = (er.y + dy) * vt.tx + er.x + dx;
-                        nxt = s_pre[jj + 1];
+        }
+        __syncthreads();
+        // pass B: place, then advance the tiles whose last pair is in this sub-window
+        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
+            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
+            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
+            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
+            int last_t[SC_Q];
+            uint32_t last_n[SC_Q];
+#pragma unroll
+            for (int k = 0; k < SC_Q; ++k) last_t[k] = -1;
+            if (p0 < p1) {
+                PairWalk it;
+                it.start(p0, s_pre, s_er, WIN, vt.tx);
+#pragma unroll
+                for (int k = 0; k < SC_Q; ++k) {
+                    const int p = p0 + k;
+                    if (p >= p1) break;
+                    if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
+                    const int jw = it.jj / WB, jb = it.jj % WB;
+                    uint32_t below = 0, all = 0;
+                    bool higher = false;
+#pragma unroll
+                    for (int wd = 0; wd < NW; ++wd) {
+                        const W m = s_mask[it.t * NW + wd];
+                        const uint32_t pc = (uint32_t)__popcll((unsigned long long)m);
+                        all += pc;
+                        if (wd < jw) below += pc;
+                        if (wd == jw) {
+                            below += (uint32_t)__popcll((unsigned long long)(m & (((W)1 << jb) - 1)));
+                            higher |= (jb + 1 < WB) && (m >> (jb + 1)) != 0;
+                        }
+                        if (wd > jw) higher |= m != 0;
                     }
-                    atomicAdd(&s_x[t], 1u);
-                    if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
-                }
-            }
-            __syncthreads();
-            block_scan_table(s_x, T, s_warp);  // s_x[t] = first staging slot of tile t
-            // pass B: stage (tile, entry); afterwards s_x[t] = end of tile t's segment
-            {
-                int jj = j0, dx = 0, t = 0, w = 1, nxt = 0;
-                for (int p = p0; p < p1; ++p) {
-                    if (p == p0 || p == nxt) {
-                        while (s_pre[jj + 1] <= p) ++jj;
-                        const ushort4 er = s_er[jj];
-                        w = er.z;
-                        const int k = p - s_pre[jj], dy = k / w;
-                        dx = k - dy * w;
-                        t = (er.y + dy) * vt.tx + er.x + dx;
-                        nxt = s_pre[jj + 1];
+                    vals[s_off[it.t] + below] = s_eg[it.jj];
+                    if (!higher) {
+                        last_t[k] = it.t;
+                        last_n[k] = all;
                     }
-                    const uint32_t pos = atomicAdd(&s_x[t], 1u);
-                    s_stage[pos] = ((uint32_t)t << 16) | (uint32_t)jj;
-                    if (++dx == w) { dx = 0; t += vt.tx - (w - 1); } else { ++t; }
                 }
             }
             __syncthreads();
-            // place: rank = pairs of the same tile from earlier entries of the window
-            for (int p = threadIdx.x; p < cnt; p += SC_THREADS) {
-                const uint32_t e = s_stage[p];
-                const int t = (int)(e >> 16);
-                const uint32_t j = e & 0xffffu;
-                const int lo = t > 0 ? (int)s_x[t - 1] : 0, hi = (int)s_x[t];
-                uint32_t rank = 0;
-                for (int qq = lo; qq < hi; ++qq) rank += (s_stage[qq] & 0xffffu) < j;
-                vals[s_off[t] + rank] = s_eg[j];
+#pragma unroll
+            for (int k = 0; k < SC_Q; ++k) {
+                if (last_t[k] >= 0) {
+                    s_off[last_t[k]] += last_n[k];
+#pragma unroll
+                    for (int wd = 0; wd < NW; ++wd) s_mask[last_t[k] * NW + wd] = 0;
+                }
             }
-            __syncthreads();
-            // advance the running slots, then clear the counts for the next window
-            for (int t = threadIdx.x; t < T; t += SC_THREADS) s_off[t] += s_x[t] - (t > 0 ? s_x[t - 1] : 0u);
-            __syncthreads();
-            for (int t = threadIdx.x; t < T; t += SC_THREADS) s_x[t] = 0u;
             __syncthreads();
         }
     }
+}
+
+// Window width for a tile table: 128 entries (two 64-bit masks per tile) where
+// it fits two blocks per SM, else 32 (one 32-bit mask).
+bool scatter_wide(int64_t max_vt) {
+    return (size_t)max_vt * ScatterMask<unsigned long long, 2>::bytes_per_tile <= (size_t)96 * 1024;
 }
 
 // 64-bit keys of the sorted pairs (for checking the order): one block per tile.
@@ -711,8 +751,10 @@ gs_status bin_smem_attributes() {
     if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                2 * bytes + (int)scatter_stage_bytes()));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<unsigned long long, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(96 * 1024)));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(ScatterMask<uint32_t, 1>::bytes_per_tile * kMaxViewTiles)));
     if (dev >= 0 && dev < 64) done[dev] = true;
     return GS_OK;
 }
@@ -785,8 +827,12 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
         g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
-    bin_scatter<<<n_chunks, SC_THREADS, 2 * smem + scatter_stage_bytes(), stream>>>(w.srect, order, cams, g, w.M,
-                                                                                     w.sort_count, vals);
+    if (scatter_wide(mvt))
+        bin_scatter<unsigned long long, 2><<<n_chunks, SC_THREADS, ScatterMask<unsigned long long, 2>::bytes_per_tile * mvt,
+                                             stream>>>(w.srect, order, cams, g, w.M, w.sort_count, vals);
+    else
+        bin_scatter<uint32_t, 1><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 1>::bytes_per_tile * mvt, stream>>>(
+            w.srect, order, cams, g, w.M, w.sort_count, vals);
     GS_TRY_LAUNCH();
     if (keys) {
         keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,

@@ -52,6 +52,26 @@ def test_bin_sort_bit_exact(tile, nviews):
     assert np.array_equal(ranges, oranges)
 
 
+@pytest.mark.parametrize("sizes,tile,n", [([(700, 560)], 8, 20000), ([(300, 200), (90, 300)], 16, 30000)])
+def test_bin_sort_bit_exact_large(sizes, tile, n):
+    """Larger tile grids (the 32-entry window path past about 4900 tiles per
+    view) and dense scenes (many entries of one window on one tile)."""
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(n, w, h, seed=5 + v) for v, (w, h) in enumerate(sizes)]
+    r = _renderer(cams, n, tile=tile, cap=64 * n)
+    dev, orc = gpu_util.records(recs, cams, tile)
+    gpu_util.set_projected(r, dev)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    P, keys, vals, ranges = _sorted_pairs(r)
+    okeys, ovals, oranges, _ = oracle.bin_sort(orc, cams, tile)
+    assert P == len(okeys)
+    assert np.array_equal(keys, okeys)
+    assert np.array_equal(vals, ovals)
+    assert np.array_equal(ranges, oranges)
+
+
 def test_bin_sort_capacity_overflow_and_empty():
     cams = [synth.camera_pinhole(50, 50, 32, 32, 64, 64)]
     recs = [synth.projected_records(500, 64, 64, seed=2)]
