@@ -537,7 +537,7 @@ struct PairWalk {
     }
 };
 
-template <typename W, int NW>
+template <typename W, int NW>  // W: 32-bit mask words
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                           const uint32_t *__restrict__ order,
                                                           const gs_camera *__restrict__ cams, BinGeom g,
@@ -584,7 +584,9 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
         if (threadIdx.x == 0) s_pre[WIN] = (int)tot_u;
         __syncthreads();
         const int tot = (int)tot_u;
-        // pass A: entry masks per tile
+        // pass A: entry masks per tile (the walk's start in the first
+        // sub-window is kept for pass B)
+        PairWalk first;
         for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
             const int cnt = min(SC_THREADS * SC_Q, tot - sw);
             const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
@@ -592,6 +594,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             if (p0 < p1) {
                 PairWalk it;
                 it.start(p0, s_pre, s_er, WIN, vt.tx);
+                if (sw == 0) first = it;
                 for (int p = p0;; ++p) {
                     atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
                     if (p + 1 >= p1) break;
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             for (int k = 0; k < SC_Q; ++k) last_t[k] = -1;
             if (p0 < p1) {
                 PairWalk it;
-                it.start(p0, s_pre, s_er, WIN, vt.tx);
+                if (sw == 0) it = first; else it.start(p0, s_pre, s_er, WIN, vt.tx);
 #pragma unroll
                 for (int k = 0; k < SC_Q; ++k) {
                     const int p = p0 + k;
@@ -623,11 +626,11 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
 #pragma unroll
                     for (int wd = 0; wd < NW; ++wd) {
                         const W m = s_mask[it.t * NW + wd];
-                        const uint32_t pc = (uint32_t)__popcll((unsigned long long)m);
+                        const uint32_t pc = (uint32_t)__popc((uint32_t)m);
                         all += pc;
                         if (wd < jw) below += pc;
                         if (wd == jw) {
-                            below += (uint32_t)__popcll((unsigned long long)(m & (((W)1 << jb) - 1)));
+                            below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
                             higher |= (jb + 1 < WB) && (m >> (jb + 1)) != 0;
                         }
                         if (wd > jw) higher |= m != 0;
@@ -653,10 +656,11 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     }
 }
 
-// Window width for a tile table: 128 entries (two 64-bit masks per tile) where
-// it fits two blocks per SM, else 32 (one 32-bit mask).
+// Window width for a tile table: 128 entries (four 32-bit masks per tile)
+// where it fits two blocks per SM, else 32 (one mask).  The masks are 32-bit
+// words because shared-memory atomicOr is native at that width.
 bool scatter_wide(int64_t max_vt) {
-    return (size_t)max_vt * ScatterMask<unsigned long long, 2>::bytes_per_tile <= (size_t)96 * 1024;
+    return (size_t)max_vt * ScatterMask<uint32_t, 4>::bytes_per_tile <= (size_t)96 * 1024;
 }
 
 // 64-bit keys of the sorted pairs (for checking the order): one block per tile.
@@ -751,7 +755,7 @@ gs_status bin_smem_attributes() {
     if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter<unsigned long long, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(96 * 1024)));
     GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(ScatterMask<uint32_t, 1>::bytes_per_tile * kMaxViewTiles)));
@@ -828,8 +832,8 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
         g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
     if (scatter_wide(mvt))
-        bin_scatter<unsigned long long, 2><<<n_chunks, SC_THREADS, ScatterMask<unsigned long long, 2>::bytes_per_tile * mvt,
-                                             stream>>>(w.srect, order, cams, g, w.M, w.sort_count, vals);
+        bin_scatter<uint32_t, 4><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 4>::bytes_per_tile * mvt, stream>>>(
+            w.srect, order, cams, g, w.M, w.sort_count, vals);
     else
         bin_scatter<uint32_t, 1><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 1>::bytes_per_tile * mvt, stream>>>(
             w.srect, order, cams, g, w.M, w.sort_count, vals);
