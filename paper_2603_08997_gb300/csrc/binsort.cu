@@ -296,10 +296,10 @@ struct BinGeom {
     int max_vt;      // tiles per view the shared-memory tables hold
 };
 
-// Entries per chunk: about two chunks per SM for one view, at least 1024, in
+// Entries per chunk: about four chunks per SM for one view, at least 1024, in
 // multiples of 256.
 int64_t bin_chunk(int64_t n) {
-    int64_t c = ceil_div(n, (int64_t)304);
+    int64_t c = ceil_div(n, (int64_t)608);
     c = ceil_div(c, (int64_t)256) * 256;
     return c < 1024 ? 1024 : c;
 }
@@ -478,46 +478,7 @@ __device__ __forceinline__ void block_scan_table(uint32_t *s, int n, uint32_t *w
     __syncthreads();
 }
 
-// Row bands for the scatter: per view, SC_BANDS contiguous ranges of tile
-// rows holding about equal numbers of pairs (from the tile totals), so the
-// band warps of bin_scatter get about equal work.  bands[v][0..SC_BANDS].
-constexpr int SC_BANDS = 8;
-
-__global__ void bin_bands(const gs_camera *__restrict__ cams, BinGeom g, const uint32_t *__restrict__ tile_total,
-                          int *__restrict__ bands) {
-    __shared__ uint32_t s_row[1024];
-    const int v = blockIdx.x;
-    const ViewTiles vt = view_tiles(cams[v], g.tile);
-    int *out = bands + v * (SC_BANDS + 1);
-    if (!view_fits(vt, g.tiles, g.max_vt)) {
-        if (threadIdx.x <= SC_BANDS) out[threadIdx.x] = 0;
-        return;
-    }
-    const int rows = vt.ty;
-    // rows are grouped into at most 1024 strips of `per` rows for the quantiles
-    const int per = (rows + 1023) / 1024, strips = (rows + per - 1) / per;
-    for (int s = threadIdx.x; s < strips; s += blockDim.x) {
-        uint32_t sum = 0;
-        for (int r = s * per; r < min(rows, (s + 1) * per); ++r)
-            for (int x = 0; x < vt.tx; ++x) sum += tile_total[vt.off + (int64_t)r * vt.tx + x];
-        s_row[s] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long total = 0;
-        for (int s = 0; s < strips; ++s) total += s_row[s];
-        out[0] = 0;
-        int b = 1;
-        unsigned long long run = 0;
-        for (int s = 0; s < strips && b < SC_BANDS; ++s) {
-            run += s_row[s];
-            // close band b-1 after the strip where the running total passes b/SC_BANDS
-            while (b < SC_BANDS && run * SC_BANDS >= total * (unsigned long long)b && total > 0) out[b++] = min(rows, (s + 1) * per);
-        }
-        for (; b < SC_BANDS; ++b) out[b] = total > 0 ? rows : (int)((int64_t)rows * b / SC_BANDS);
-        out[SC_BANDS] = rows;
-    }
-}
+constexpr int SC_BANDS = 8;  // row bands (and warps) per scatter block
 
 // Exact floor(k / w) for k, w < 2^16 with m = ceil(2^32 / w): the
 // multiply-high method of Granlund and Montgomery (1994).  w = 1 (where m
@@ -525,7 +486,7 @@ __global__ void bin_bands(const gs_camera *__restrict__ cams, BinGeom g, const u
 __device__ __forceinline__ uint32_t div_magic(uint32_t w) { return w == 1u ? 0u : 0xffffffffu / w + 1u; }
 __device__ __forceinline__ uint32_t div_by(uint32_t k, uint32_t m) { return m ? __umulhi(k, m) : k; }
 
-// One block per chunk, one warp per row band.  The chunk's first slot per
+// One block per chunk, one warp per band of tile rows (equal row counts).  The chunk's first slot per
 // tile is held in shared memory (s_off); warp b owns the tiles of band b, so
 // no two warps touch the same slot.  Each warp takes the chunk's entries 32 at
 // a time, keeps those whose rectangle reaches its band (ballot + compaction
@@ -536,14 +497,13 @@ __device__ __forceinline__ uint32_t div_by(uint32_t k, uint32_t m) { return m ? 
 constexpr int SC_THREADS = 32 * SC_BANDS;
 
 struct BandEntry {
-    int x0, ya, w, n;  // first tile column, first row in the band, width, pairs in the band
-    uint32_t m, g;     // division magic for w, Gaussian index
+    unsigned short x0, ya, w, n;  // first tile column, first row in the band, width, pairs in the band
+    uint32_t m, g;                // division magic for w, Gaussian index
 };
 
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                           const uint32_t *__restrict__ order,
                                                           const gs_camera *__restrict__ cams, BinGeom g,
-                                                          const int *__restrict__ bands,
                                                           const uint32_t *__restrict__ M,
                                                           const int64_t *sort_count, uint32_t *__restrict__ vals) {
     extern __shared__ uint32_t s_off[];  // [max_vt]
@@ -557,7 +517,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     const uint32_t *row = M + g.n_c * vt.off + c * T;
     for (int t = threadIdx.x; t < T; t += SC_THREADS) s_off[t] = row[t];
     __syncthreads();
-    const int r_lo = bands[v * (SC_BANDS + 1) + warp], r_hi = bands[v * (SC_BANDS + 1) + warp + 1];
+    const int r_lo = vt.ty * warp / SC_BANDS, r_hi = vt.ty * (warp + 1) / SC_BANDS;
     if (r_lo >= r_hi) return;  // an empty band (only this warp leaves; no block barrier follows)
     BandEntry *list = s_list[warp];
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
@@ -565,27 +525,29 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
         const int64_t i = base + lane;
         BandEntry be;
         be.n = 0;
+        int nb = 0;
         if (i < e1) {
             const ushort4 r = srect[i];
             const int ya = max((int)r.y, r_lo), yb = min((int)r.y + (int)r.w, r_hi);
             if (r.z > 0 && ya < yb) {
+                nb = (int)r.z * (yb - ya);
                 be.x0 = r.x;
-                be.ya = ya;
+                be.ya = (unsigned short)ya;
                 be.w = r.z;
-                be.n = (int)r.z * (yb - ya);
+                be.n = (unsigned short)((int)r.z * (yb - ya));
                 be.m = div_magic(r.z);
                 be.g = (uint32_t)((int64_t)order[i] - v * g.n);
             }
         }
-        const uint32_t keep = __ballot_sync(0xffffffffu, be.n > 0);
-        if (be.n > 0) list[__popc(keep & ((1u << lane) - 1u))] = be;
+        const uint32_t keep = __ballot_sync(0xffffffffu, nb > 0);
+        if (nb > 0) list[__popc(keep & ((1u << lane) - 1u))] = be;
         __syncwarp();
         const int cnt = __popc(keep);
         for (int j = 0; j < cnt; ++j) {
             const BandEntry e = list[j];
-            for (int k = lane; k < e.n; k += 32) {
+            for (int k = lane; k < (int)e.n; k += 32) {
                 const int dy = (int)div_by((uint32_t)k, e.m);
-                const int t = (e.ya + dy) * vt.tx + e.x0 + (k - dy * e.w);
+                const int t = ((int)e.ya + dy) * vt.tx + (int)e.x0 + (k - dy * (int)e.w);
                 const uint32_t pos = s_off[t];
                 s_off[t] = pos + 1;
                 vals[pos] = e.g;
@@ -636,7 +598,6 @@ struct BinWorkspace {
     uint32_t *tile_total;      // [total_tiles]
     uint32_t *tile_start;      // [total_tiles]
     ushort4 *srect;            // [V*N] clipped rectangles in depth order
-    int *bands;                // [V][SC_BANDS + 1] band row boundaries
     int64_t *sort_count;       // [1]
 };
 
@@ -662,7 +623,6 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
     char *tt = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *ts = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *sr = take(sizeof(ushort4) * (size_t)(total > 0 ? total : 1));
-    char *bd = take(sizeof(int) * (SC_BANDS + 1) * (size_t)n_views);
     char *sc = take(sizeof(int64_t));
     if (w) {
         w->counts = (uint32_t *)counts;
@@ -671,7 +631,6 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
         w->tile_total = (uint32_t *)tt;
         w->tile_start = (uint32_t *)ts;
         w->srect = (ushort4 *)sr;
-        w->bands = (int *)bd;
         w->sort_count = (int64_t *)sc;
     }
     return off;
@@ -757,15 +716,13 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     GS_TRY_LAUNCH();
     bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
     GS_TRY_LAUNCH();
-    bin_bands<<<(unsigned)n_views, 256, 0, stream>>>(cams, g, w.tile_total, w.bands);
-    GS_TRY_LAUNCH();
     bin_starts<<<1, SCAN_THREADS, 0, stream>>>(g, w.tile_total, w.tile_start, pair_capacity, dev_pair_count,
                                                w.sort_count, dev_status);
     GS_TRY_LAUNCH();
     bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
         g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
-    bin_scatter<<<n_chunks, SC_THREADS, smem, stream>>>(w.srect, order, cams, g, w.bands, w.M, w.sort_count, vals);
+    bin_scatter<<<n_chunks, SC_THREADS, smem, stream>>>(w.srect, order, cams, g, w.M, w.sort_count, vals);
     GS_TRY_LAUNCH();
     if (keys) {
         keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,
