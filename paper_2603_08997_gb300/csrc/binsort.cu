@@ -296,10 +296,10 @@ struct BinGeom {
     int max_vt;      // tiles per view the shared-memory tables hold
 };
 
-// Entries per chunk: about four chunks per SM for one view, at least 1024, in
+// Entries per chunk: about two chunks per SM for one view, at least 1024, in
 // multiples of 256.
 int64_t bin_chunk(int64_t n) {
-    int64_t c = ceil_div(n, (int64_t)608);
+    int64_t c = ceil_div(n, (int64_t)304);
     c = ceil_div(c, (int64_t)256) * 256;
     return c < 1024 ? 1024 : c;
 }
@@ -478,83 +478,189 @@ __device__ __forceinline__ void block_scan_table(uint32_t *s, int n, uint32_t *w
     __syncthreads();
 }
 
-constexpr int SC_BANDS = 8;  // row bands (and warps) per scatter block
+// One block per chunk.  The chunk's first slot per tile is held in shared
+// memory (s_off).  The block takes its entries WIN at a time (a window, WIN =
+// the bits of one tile's entry mask); the window's pairs, in order (entry,
+// then tile row-major), are expanded with each thread taking an equal
+// contiguous run, so one large rectangle does not stall the block.
+//   pass A: every pair sets bit j (its entry within the window) in its tile's
+//           mask (shared atomicOr, order-free);
+//   pass B: a pair's rank among the window's pairs of its tile is the number
+//           of mask bits below j; it goes to s_off[tile] + rank.  The pair
+//           with the highest bit then advances s_off[tile] by the mask's
+//           population and clears the mask.
+// Pass B runs in sub-windows of SC_THREADS * SC_Q pairs; a tile's last pair is
+// never in an earlier sub-window than its other pairs, so each sub-window's
+// advances can follow it directly.
+constexpr int SC_THREADS = 512;
+constexpr int SC_Q = 4;  // pairs per thread per sub-window
 
-// Exact floor(k / w) for k, w < 2^16 with m = ceil(2^32 / w): the
-// multiply-high method of Granlund and Montgomery (1994).  w = 1 (where m
-// would be 2^32) is marked by m = 0.
-__device__ __forceinline__ uint32_t div_magic(uint32_t w) { return w == 1u ? 0u : 0xffffffffu / w + 1u; }
-__device__ __forceinline__ uint32_t div_by(uint32_t k, uint32_t m) { return m ? __umulhi(k, m) : k; }
-
-// One block per chunk, one warp per band of tile rows (equal row counts).  The chunk's first slot per
-// tile is held in shared memory (s_off); warp b owns the tiles of band b, so
-// no two warps touch the same slot.  Each warp takes the chunk's entries 32 at
-// a time, keeps those whose rectangle reaches its band (ballot + compaction
-// into a per-warp list), and then, entry by entry in depth order, spreads the
-// entry's tiles in the band over the lanes: each lane writes one pair at its
-// tile's running slot and advances it.  An entry covers a tile at most once,
-// so the lanes of one step never share a slot; __syncwarp orders the steps.
-constexpr int SC_THREADS = 32 * SC_BANDS;
-
-struct BandEntry {
-    unsigned short x0, ya, w, n;  // first tile column, first row in the band, width, pairs in the band
-    uint32_t m, g;                // division magic for w, Gaussian index
+template <typename W, int NW>
+struct ScatterMask {
+    static constexpr int WB = 8 * (int)sizeof(W);
+    static constexpr int WIN = WB * NW;  // entries per window
+    static constexpr size_t bytes_per_tile = sizeof(W) * NW + sizeof(uint32_t);
 };
 
+// Walks the pairs [p0, p1) of a window in list order.
+struct PairWalk {
+    int jj, dx, t, w, nxt;
+    __device__ __forceinline__ void start(int p0, const int *s_pre, const ushort4 *s_er, int win, int tx) {
+        int lo = 0, hi = win - 1;  // the last j with s_pre[j] <= p0 (so empty entries are skipped)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
+        }
+        jj = lo;
+        const ushort4 er = s_er[jj];
+        w = er.z;
+        const int k = p0 - s_pre[jj], dy = k / w;
+        dx = k - dy * w;
+        t = (er.y + dy) * tx + er.x + dx;
+        nxt = s_pre[jj + 1];
+    }
+    // step from pair p to pair p + 1 (p + 1 < end of the window)
+    __device__ __forceinline__ void next(int p, const int *s_pre, const ushort4 *s_er, int tx) {
+        if (p + 1 == nxt) {
+            do { ++jj; } while (s_pre[jj + 1] <= p + 1);
+            const ushort4 er = s_er[jj];
+            w = er.z;
+            dx = 0;
+            t = er.y * tx + er.x;
+            nxt = s_pre[jj + 1];
+        } else if (++dx == w) {
+            dx = 0;
+            t += tx - (w - 1);
+        } else {
+            ++t;
+        }
+    }
+};
+
+template <typename W, int NW>  // W: 32-bit mask words
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                           const uint32_t *__restrict__ order,
                                                           const gs_camera *__restrict__ cams, BinGeom g,
                                                           const uint32_t *__restrict__ M,
                                                           const int64_t *sort_count, uint32_t *__restrict__ vals) {
-    extern __shared__ uint32_t s_off[];  // [max_vt]
-    __shared__ BandEntry s_list[SC_BANDS][32];
+    using SM = ScatterMask<W, NW>;
+    constexpr int WB = SM::WB, WIN = SM::WIN;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    W *s_mask = reinterpret_cast<W *>(s_raw);                                     // [max_vt][NW]
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_mask + (size_t)g.max_vt * NW);  // [max_vt]
+    __shared__ ushort4 s_er[WIN];    // the window's rectangles
+    __shared__ uint32_t s_eg[WIN];   // Gaussian indices
+    __shared__ int s_pre[WIN + 1];   // first pair of each entry
+    __shared__ uint32_t s_warp[32];
     if (*sort_count == 0) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
     const ViewTiles vt = view_tiles(cams[v], g.tile);
     if (!view_fits(vt, g.tiles, g.max_vt)) return;
     const int T = vt.tx * vt.ty;
     const uint32_t *row = M + g.n_c * vt.off + c * T;
-    for (int t = threadIdx.x; t < T; t += SC_THREADS) s_off[t] = row[t];
-    __syncthreads();
-    const int r_lo = vt.ty * warp / SC_BANDS, r_hi = vt.ty * (warp + 1) / SC_BANDS;
-    if (r_lo >= r_hi) return;  // an empty band (only this warp leaves; no block barrier follows)
-    BandEntry *list = s_list[warp];
+    for (int t = threadIdx.x; t < T; t += SC_THREADS) {
+        s_off[t] = row[t];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s_mask[t * NW + k] = 0;
+    }
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
-    for (int64_t base = e0; base < e1; base += 32) {
-        const int64_t i = base + lane;
-        BandEntry be;
-        be.n = 0;
-        int nb = 0;
-        if (i < e1) {
-            const ushort4 r = srect[i];
-            const int ya = max((int)r.y, r_lo), yb = min((int)r.y + (int)r.w, r_hi);
-            if (r.z > 0 && ya < yb) {
-                nb = (int)r.z * (yb - ya);
-                be.x0 = r.x;
-                be.ya = (unsigned short)ya;
-                be.w = r.z;
-                be.n = (unsigned short)((int)r.z * (yb - ya));
-                be.m = div_magic(r.z);
-                be.g = (uint32_t)((int64_t)order[i] - v * g.n);
+    for (int64_t base = e0; base < e1; base += WIN) {
+        int area = 0;
+        if (threadIdx.x < WIN) {
+            const int64_t i = base + threadIdx.x;
+            ushort4 r = make_ushort4(0, 0, 0, 0);
+            uint32_t gi = 0;
+            if (i < e1) {
+                r = srect[i];
+                gi = (uint32_t)((int64_t)order[i] - v * g.n);
+            }
+            s_er[threadIdx.x] = r;
+            s_eg[threadIdx.x] = gi;
+            area = (int)r.z * r.w;
+        }
+        uint32_t tot_u;
+        const int pre = (int)block_exclusive_scan((uint32_t)area, s_warp, &tot_u);
+        if (threadIdx.x < WIN) s_pre[threadIdx.x] = pre;
+        if (threadIdx.x == 0) s_pre[WIN] = (int)tot_u;
+        __syncthreads();
+        const int tot = (int)tot_u;
+        // pass A: entry masks per tile (the walk's start in the first
+        // sub-window is kept for pass B)
+        PairWalk first;
+        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
+            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
+            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
+            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
+            if (p0 < p1) {
+                PairWalk it;
+                it.start(p0, s_pre, s_er, WIN, vt.tx);
+                if (sw == 0) first = it;
+                for (int p = p0;; ++p) {
+                    atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
+                    if (p + 1 >= p1) break;
+                    it.next(p, s_pre, s_er, vt.tx);
+                }
             }
         }
-        const uint32_t keep = __ballot_sync(0xffffffffu, nb > 0);
-        if (nb > 0) list[__popc(keep & ((1u << lane) - 1u))] = be;
-        __syncwarp();
-        const int cnt = __popc(keep);
-        for (int j = 0; j < cnt; ++j) {
-            const BandEntry e = list[j];
-            for (int k = lane; k < (int)e.n; k += 32) {
-                const int dy = (int)div_by((uint32_t)k, e.m);
-                const int t = ((int)e.ya + dy) * vt.tx + (int)e.x0 + (k - dy * (int)e.w);
-                const uint32_t pos = s_off[t];
-                s_off[t] = pos + 1;
-                vals[pos] = e.g;
+        __syncthreads();
+        // pass B: place, then advance the tiles whose last pair is in this sub-window
+        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
+            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
+            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
+            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
+            int last_t[SC_Q];
+            uint32_t last_n[SC_Q];
+#pragma unroll
+            for (int k = 0; k < SC_Q; ++k) last_t[k] = -1;
+            if (p0 < p1) {
+                PairWalk it;
+                if (sw == 0) it = first; else it.start(p0, s_pre, s_er, WIN, vt.tx);
+#pragma unroll
+                for (int k = 0; k < SC_Q; ++k) {
+                    const int p = p0 + k;
+                    if (p >= p1) break;
+                    if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
+                    const int jw = it.jj / WB, jb = it.jj % WB;
+                    uint32_t below = 0, all = 0;
+                    bool higher = false;
+#pragma unroll
+                    for (int wd = 0; wd < NW; ++wd) {
+                        const W m = s_mask[it.t * NW + wd];
+                        const uint32_t pc = (uint32_t)__popc((uint32_t)m);
+                        all += pc;
+                        if (wd < jw) below += pc;
+                        if (wd == jw) {
+                            below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
+                            higher |= (jb + 1 < WB) && (m >> (jb + 1)) != 0;
+                        }
+                        if (wd > jw) higher |= m != 0;
+                    }
+                    vals[s_off[it.t] + below] = s_eg[it.jj];
+                    if (!higher) {
+                        last_t[k] = it.t;
+                        last_n[k] = all;
+                    }
+                }
             }
-            __syncwarp();
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < SC_Q; ++k) {
+                if (last_t[k] >= 0) {
+                    s_off[last_t[k]] += last_n[k];
+#pragma unroll
+                    for (int wd = 0; wd < NW; ++wd) s_mask[last_t[k] * NW + wd] = 0;
+                }
+            }
+            __syncthreads();
         }
     }
+}
+
+// Window width for a tile table: 128 entries (four 32-bit masks per tile)
+// where it fits two blocks per SM, else 32 (one mask).  The masks are 32-bit
+// words because shared-memory atomicOr is native at that width.
+bool scatter_wide(int64_t max_vt) {
+    return (size_t)max_vt * ScatterMask<uint32_t, 4>::bytes_per_tile <= (size_t)96 * 1024;
 }
 
 // 64-bit keys of the sorted pairs (for checking the order): one block per tile.
@@ -649,7 +755,10 @@ gs_status bin_smem_attributes() {
     if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(96 * 1024)));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(ScatterMask<uint32_t, 1>::bytes_per_tile * kMaxViewTiles)));
     if (dev >= 0 && dev < 64) done[dev] = true;
     return GS_OK;
 }
@@ -722,7 +831,12 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
         g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
-    bin_scatter<<<n_chunks, SC_THREADS, smem, stream>>>(w.srect, order, cams, g, w.M, w.sort_count, vals);
+    if (scatter_wide(mvt))
+        bin_scatter<uint32_t, 4><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 4>::bytes_per_tile * mvt, stream>>>(
+            w.srect, order, cams, g, w.M, w.sort_count, vals);
+    else
+        bin_scatter<uint32_t, 1><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 1>::bytes_per_tile * mvt, stream>>>(
+            w.srect, order, cams, g, w.M, w.sort_count, vals);
     GS_TRY_LAUNCH();
     if (keys) {
         keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,

@@ -54,8 +54,9 @@ def test_bin_sort_bit_exact(tile, nviews):
 
 @pytest.mark.parametrize("sizes,tile,n", [([(700, 560)], 8, 20000), ([(300, 200), (90, 300)], 16, 30000)])
 def test_bin_sort_bit_exact_large(sizes, tile, n):
-    """Larger tile grids (6160 tiles in one view) and dense scenes (many
-    entries of one chunk on one tile, several row bands per Gaussian)."""
+    """Larger tile grids (the 32-entry window path past about 4900 tiles per
+    view) and dense scenes (many entries of one window on one tile, more than
+    one window word)."""
     cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
     recs = [synth.projected_records(n, w, h, seed=5 + v) for v, (w, h) in enumerate(sizes)]
     r = _renderer(cams, n, tile=tile, cap=64 * n)
