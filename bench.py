@@ -263,10 +263,16 @@ def roofline_of(stages: dict, loop, args) -> dict:
     P = int(r.pair_count.item())
     px = r.views.total_pixels
     evals = float(r.n_last.double().sum().item())
+    T = r.views.total_tiles
+    chunk = max(1024, -(-(-(-N // 304)) // 256) * 256)  # entries per chunk of the tile counting sort
+    n_c = -(-N // chunk) * r.views.n
     params = loop.model.flat.numel()
     work = {
         "project": ("hbm", N * (236 + 68), "bytes: 236 B parameters read + 68 B record, rectangle, count written per Gaussian"),
-        "bin_sort": ("hbm", 128 * E + 52 * P, "bytes: 128 B per (view, Gaussian) entry + 52 B per (Gaussian, tile) pair"),
+        "bin_sort": ("hbm", 148 * E + 4 * P + 16 * n_c * T + 8 * T,
+                     "bytes: 148 B per (view, Gaussian) entry (depth keys 16, four radix passes 80, clipped "
+                     "rectangles 32, counting 8, placement 12) + 4 B per (Gaussian, tile) pair + 16 B per "
+                     "(chunk, tile) count-matrix cell + 8 B per tile range"),
         "render_fwd": ("alu", 12.0 * evals, "FLOP: 12 per evaluated pair"),
         "loss": ("hbm", 60 * px, "bytes: 60 B per pixel"),
         "loss_bwd": ("hbm", 72 * px, "bytes: 72 B per pixel"),

@@ -28,7 +28,8 @@ class RasterSettings:
     t_min: float = 1e-4
     bg: tuple = (0.0, 0.0, 0.0)
     lambda_ssim: float = 0.2
-    pixels_per_thread: int = 2
+    pixels_per_thread: int = 2      # raster adjoint
+    pixels_per_thread_fwd: int = 1  # forward compositing
 
     def struct(self, sh_degree: int) -> gsr.gs_raster_config:
         c = gsr.gs_raster_config()
@@ -131,6 +132,8 @@ class Renderer:
         self.s = settings or RasterSettings()
         self.n, self.sh_degree, self.views = int(n), int(sh_degree), views
         self.cfg = self.s.struct(sh_degree)
+        self.cfg_fwd = self.s.struct(sh_degree)
+        self.cfg_fwd.pixels_per_thread = int(self.s.pixels_per_thread_fwd)
         V, T, P = views.n, views.total_tiles, views.total_pixels
         if pair_capacity is None:
             pair_capacity = max(1 << 16, 16 * n * V)
@@ -186,7 +189,7 @@ class Renderer:
     def render_fwd(self, stream=None) -> None:
         proj = self.c_proj()
         gsr.call("gs_render_fwd", C.byref(proj), self.n, gsr.ptr(self.vals), gsr.ptr(self.ranges),
-                 gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg),
+                 gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg_fwd),
                  gsr.ptr(self.image), self.c_saved(), gsr.ptr(self.status), gsr.stream_handle(stream))
 
     def forward(self, params: gsr.gs_params, stream=None) -> torch.Tensor:

@@ -21,7 +21,8 @@ def _setup(scene, cam, tile=16, batch=256, ppt=2):
     gpu_util.lib()
     views = raster.Views([cam], tile)
     r = raster.Renderer(scene.n, scene.sh_degree, views,
-                        raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt))
+                        raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt,
+                                              pixels_per_thread_fwd=ppt))
     model = raster.GaussianModel.from_scene(scene)
     return r, model
 
@@ -212,7 +213,7 @@ def test_raster_bwd_g2d_against_oracle(tile, ppt):
     recs = [synth.projected_records(3000, w, h, seed=31 + v) for v, (w, h) in enumerate(sizes)]
     gpu_util.lib()
     views = raster.Views(cams, tile)
-    r = raster.Renderer(3000, 0, views, raster.RasterSettings(tile=tile, pixels_per_thread=ppt))
+    r = raster.Renderer(3000, 0, views, raster.RasterSettings(tile=tile, pixels_per_thread=ppt, pixels_per_thread_fwd=ppt))
     dev, orc = gpu_util.records(recs, cams, tile)
     gpu_util.set_projected(r, dev)
     r.bin_sort()

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 def _renderer(cams, n, sh_degree=0, tile=16, batch=256, cap=None, keys=True, ppt=2):
     gpu_util.lib()
     views = raster.Views(cams, tile)
-    st = raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt)
+    st = raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt, pixels_per_thread_fwd=ppt)
     return raster.Renderer(n, sh_degree, views, st, pair_capacity=cap, keep_keys=keys)
 
 
