@@ -50,7 +50,39 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--ref-seconds", type=float, default=150.0, help="budget of the reference arm")
     ap.add_argument("--pre", type=int, default=5000, help="always-backward iterations before the measured loop")
+    ap.add_argument("--stages-once", action="store_true",
+                    help="run two eager iterations of every stage on one view of the workload and exit "
+                         "(a small, fixed launch sequence for hardware-counter captures)")
     return ap.parse_args()
+
+
+def stages_once(args) -> None:
+    """Two eager forward + backward iterations of every stage on view 0 of the
+    workload's scene (perturbed start, ground-truth target), for counters."""
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import build, raster
+
+    build.build()
+    gt, start, cams, _ = synth.case_c3(n=args.n, n_views=4, n_iters=10, width=args.width, height=args.height)
+    views = raster.Views([cams[0]], 16)
+    r = raster.Renderer(args.n, 3, views, raster.RasterSettings(), pair_capacity=24 * args.n)
+    r.forward(raster.GaussianModel.from_scene(gt).c_params())
+    torch.cuda.synchronize()
+    target = r.image.clone()
+    m = raster.GaussianModel.from_scene(start)
+    adam = raster.AdamState(m)
+    p, gr = m.c_params(), m.c_grads(adam.grad)
+    for _ in range(2):
+        r.forward(p)
+        r.compute_loss(target)
+        r.loss_backward(target)
+        r.raster_bwd()
+        r.project_bwd(p, gr)
+        adam.step()
+    torch.cuda.synchronize()
+    print(json.dumps({"stages_once": True, "status": int(r.status.item()), "pairs": int(r.pair_count.item())}))
 
 
 # ---------------------------------------------------------------- clocks
@@ -283,6 +315,7 @@ def roofline_of(stages: dict, loop, args) -> dict:
     }
     name = max(stages, key=lambda k: stages[k]["share"])
     bound, units, note = work[name]
+    traffic, traffic_note = stage_traffic(name)
     t = stages[name]["ms"] * 1e-3
     if bound == "hbm":
         achieved, peak, unit, pk_note = units / t / 1e9, hbm, "GB/s", hbm_note
@@ -290,11 +323,37 @@ def roofline_of(stages: dict, loop, args) -> dict:
         achieved, peak, unit = units / t / 1e12, PEAK_ALU_TFLOPS, "TFLOP/s"
         pk_note = "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": None, "work_per_launch": units, "work_def": note, "launch_ms": t * 1e3,
+            "traffic": traffic, "traffic_note": traffic_note, "work_per_launch": units, "work_def": note, "launch_ms": t * 1e3,
             "share_of_gated_iteration": stages[name]["share"], "peak_note": pk_note,
             "all_stages": {k: {"bound": w[0], "achieved": (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12),
                                "frac": (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12) /
                                (hbm if w[0] == "hbm" else PEAK_ALU_TFLOPS)} for k, w in work.items()}}
+
+
+def sources_sha256() -> str:
+    """Digest of the CUDA sources (any kernel change invalidates stored counters)."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2603_08997_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def stage_traffic(stage: str):
+    """DRAM bytes per launch of a stage from the committed ncu summary, or
+    None when the kernels changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "stage_traffic_3M.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None, "no stored capture"
+    if rec.get("sources_sha256") != sources_sha256():
+        return None, "kernels changed since the stored capture"
+    b = rec.get("per_launch_bytes", {}).get(stage)
+    return (float(b) if b is not None else None), "profiles/stage_traffic_3M.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
 
 
 def aggregate_time(t_local: float, dist, device) -> float:
@@ -320,6 +379,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.stages_once:
+        stages_once(args)
         return
 
     import numpy as np
