@@ -162,8 +162,10 @@ int64_t gs_ckpt_slots(int64_t pair_capacity, int64_t total_tiles, int32_t batch)
  * opacity = sigmoid(logit), colour = max(0, sum_k f_k Y_k(d) + 0.5) for the
  * direction d from the camera centre (real SH, Condon-Shortley phase), and
  * the conservative tile rectangle of the region where alpha' >= alpha_min
- * can hold: |p - mean2D| <= r with r^2 = 2 lambda_max(Sigma2D) ln(opacity /
- * alpha_min), inflated for float32 rounding. */
+ * can hold: the bounding box of the ellipse dp^T Q dp <= c with
+ * c = 2 ln(opacity / alpha_min), i.e. half-extents r_x = sqrt(c Sigma2D_xx),
+ * r_y = sqrt(c Sigma2D_yy), inflated by x1.0001 + 0.001 px for float32
+ * rounding (stored in the record's last two floats). */
 gs_status gs_project(const gs_params *params /* host */, const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg /* host */, gs_projected out,
                      int32_t *dev_status, cudaStream_t stream);
 
