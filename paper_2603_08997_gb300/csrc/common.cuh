@@ -132,6 +132,25 @@ __device__ __forceinline__ bool warp_overlaps(float4 a, float4 c, float wx, floa
     return fabsf(a.x - (wx + 3.5f)) <= c.z + 3.5f && fabsf(a.y - (wy + hy)) <= c.w + hy;
 }
 
+// Overlap masks of one staged batch of records: for every warp w of the CTA,
+// bit (j % 32) of word j / 32 of row w is set when record j's support box
+// reaches w's pixel block (the warp_overlaps test).  Called by whole warps for
+// batch slots kk = threadIdx.x, threadIdx.x + NTH, ... < BATCH; a (a.x, a.y =
+// mean2D) and c (c.z, c.w = support half-extents) are the slot's record, valid
+// false past the batch's end.  One ballot per target warp and 32 slots.
+template <int TILE, int PPT, int NW, int NWORD>
+__device__ __forceinline__ void overlap_masks(uint32_t (*s_ov)[NWORD], int kk, bool valid, float4 a, float4 c,
+                                              int tile_x0, int tile_y0) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        int lx0, ly0;
+        tile_pixel<TILE, PPT>(w * 32, 0, lx0, ly0);
+        const float wx = (float)(tile_x0 + lx0) + 0.5f, wy = (float)(tile_y0 + ly0) + 0.5f;
+        const uint32_t m = __ballot_sync(0xffffffffu, valid && warp_overlaps<4 * PPT>(a, c, wx, wy));
+        if ((threadIdx.x & 31) == 0) s_ov[w][kk >> 5] = m;
+    }
+}
+
 // Real spherical harmonics (Condon-Shortley phase) up to degree 3 at a unit
 // direction (x, y, z), basis order k = l*l + l + m.  Constants are the
 // normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0)

@@ -1,6 +1,8 @@
 // gs_render_bwd: analytic adjoint of gs_render_fwd and gs_project.
 //
-// Raster adjoint (one CTA per tile, PPT = 1 or 2 pixels per thread).  With
+// Raster adjoint (one CTA per tile, PPT = 1 or 2 pixels per thread; each
+// warp walks only the staged records whose support box reaches its pixel
+// block, marked per batch with one ballot per warp and 32 records).  With
 // A_k = sum_{j>k} c_j a_j T_j + T_end bg (the colour behind contributor k),
 // Eq. (blend) gives dC/dc_k = a_k T_k and dC/da_k = c_k T_k - A_k / (1 - a_k).
 // Batches are visited last to first and each pixel walks back from its last
@@ -68,10 +70,12 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d) {
     constexpr int NT = TILE * TILE;
     constexpr int NTH = TILE * TILE / PPT;
+    constexpr int NW = NTH / 32, NWORD = BATCH / 32;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
     __shared__ float4 s_c[BATCH];
     __shared__ uint32_t s_g[BATCH];
+    __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     __shared__ float s_acc[BATCH][9];
     __shared__ int s_max;
     const int64_t tile = blockIdx.x;
@@ -81,10 +85,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     const int tiles_x = (cam.width + TILE - 1) / TILE;
     const int64_t lt = tile - cam.tile_offset;
     const int tx = (int)(lt % tiles_x), ty = (int)(lt / tiles_x);
-    int lx0, ly0;
-    tile_pixel<TILE, PPT>(threadIdx.x & ~31, 0, lx0, ly0);  // first pixel of the warp's block
-    const float wx = (float)(tx * TILE + lx0) + 0.5f, wy = (float)(ty * TILE + ly0) + 0.5f;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint2 rg = ranges[tile];
     const int64_t slot0 = (int64_t)(rg.x / BATCH) + tile;
     const float4 *recv = rec + (int64_t)v * n * 3;
@@ -132,13 +133,20 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
         __syncthreads();
         const int64_t b0 = (int64_t)rg.x + (int64_t)b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
-        for (int kk = threadIdx.x; kk < cnt; kk += NTH) {
-            const uint32_t g = vals[b0 + kk];
-            const float4 *r = recv + (int64_t)g * 3;
-            s_a[kk] = r[0];
-            s_b[kk] = r[1];
-            s_c[kk] = r[2];
-            s_g[kk] = g;
+        for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
+            const bool valid = kk < cnt;
+            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+            if (valid) {
+                const uint32_t g = vals[b0 + kk];
+                const float4 *r = recv + (int64_t)g * 3;
+                ra = r[0];
+                rc = r[2];
+                s_a[kk] = ra;
+                s_b[kk] = r[1];
+                s_c[kk] = rc;
+                s_g[kk] = g;
+            }
+            overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rc, tx * TILE, ty * TILE);
         }
         for (int kk = threadIdx.x; kk < BATCH * 9; kk += NTH) (&s_acc[0][0])[kk] = 0.f;
         __syncthreads();
@@ -161,10 +169,15 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
             jmax = max(jmax, jstart[k]);
         }
         const int wj = __reduce_max_sync(FULL, jmax);
-        for (int j = wj; j >= 0; --j) {
-            const float4 sa = s_a[j], sc = s_c[j];
-            if (!warp_overlaps<4 * PPT>(sa, sc, wx, wy)) continue;  // no lane of the warp has this contributor
-            const float4 sb = s_b[j];
+        // the warp's marked records at or below wj, last to first
+        for (int wd = wj >> 5; wj >= 0 && wd >= 0; --wd) {
+          uint32_t m = s_ov[warp][wd];
+          if (wd == (wj >> 5)) m &= (2u << (wj & 31)) - 1u;
+          while (m) {
+            const int bit = 31 - __clz(m);
+            m &= ~(1u << bit);
+            const int j = wd * 32 + bit;
+            const float4 sa = s_a[j], sb = s_b[j], sc = s_c[j];
             float gv[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) gv[q] = 0.f;
@@ -205,6 +218,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                 const float tot = warp_reduce9(gv, lane, idx);
                 if (idx >= 0 && tot != 0.f) atomicAdd(&s_acc[j][idx], tot);
             }
+          }
         }
         __syncthreads();
         for (int kk = threadIdx.x; kk < cnt; kk += NTH) {

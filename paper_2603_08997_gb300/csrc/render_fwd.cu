@@ -1,11 +1,12 @@
 // gs_render_fwd: Eq. (blend) / Eq. (alpha), front-to-back compositing.
 //
 // One CTA per tile, PPT pixels per thread (1 or 2), each warp an 8 x 4 PPT
-// pixel block that skips Gaussians whose support box misses it.  The tile's
-// depth-ordered list is
+// pixel block.  The tile's depth-ordered list is
 // consumed `BATCH` Gaussians at a time: the CTA gathers the batch's packed
-// records into shared memory (one coalesced 48-byte record per Gaussian),
-// then every pixel walks the batch.  At the start of every batch each pixel
+// records into shared memory (one coalesced 48-byte record per Gaussian) and
+// marks, per warp, the records whose support box reaches the warp's pixel
+// block (one ballot per warp and 32 records); every warp then walks only its
+// marked records, in order.  At the start of every batch each pixel
 // stores its transmittance into the checkpoint slot
 //   slot(tile, b) = floor(range_start / BATCH) + tile + b
 // (TILE * TILE floats, row-major over the tile's pixels), which the backward pass uses to rebuild T without dividing across batches.
@@ -27,9 +28,11 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
                                                                        float *__restrict__ ckpt, int64_t ckpt_slots) {
     constexpr int NT = TILE * TILE;        // pixels per tile (checkpoint slot size)
     constexpr int NTH = TILE * TILE / PPT; // threads
+    constexpr int NW = NTH / 32, NWORD = BATCH / 32;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
     __shared__ float4 s_c[BATCH];
+    __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     const int64_t tile = blockIdx.x;
     const int v = view_of_tile(cams, n_views, tile);
     const gs_camera &cam = cams[v];
@@ -50,9 +53,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
         px[k] = (float)x[k] + 0.5f;
         py[k] = (float)y[k] + 0.5f;
     }
-    int lx0, ly0;
-    tile_pixel<TILE, PPT>(threadIdx.x & ~31, 0, lx0, ly0);  // first pixel of the warp's block
-    const float wx = (float)(tx * TILE + lx0) + 0.5f, wy = (float)(ty * TILE + ly0) + 0.5f;
+    const int warp = threadIdx.x >> 5;
     const uint2 rg = ranges[tile];
     const int64_t len = (int64_t)rg.y - rg.x;
     const int64_t nb = ceil_div(len, BATCH);
@@ -79,39 +80,51 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
         }
         const int64_t b0 = (int64_t)rg.x + b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
-        for (int kk = threadIdx.x; kk < cnt; kk += NTH) {
-            const uint32_t g = vals[b0 + kk];
-            const float4 *r = recv + (int64_t)g * 3;
-            s_a[kk] = r[0];
-            s_b[kk] = r[1];
-            s_c[kk] = r[2];
+        for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
+            const bool valid = kk < cnt;
+            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+            if (valid) {
+                const uint32_t g = vals[b0 + kk];
+                const float4 *r = recv + (int64_t)g * 3;
+                ra = r[0];
+                rc = r[2];
+                s_a[kk] = ra;
+                s_b[kk] = r[1];
+                s_c[kk] = rc;
+            }
+            overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rc, tx * TILE, ty * TILE);
         }
         __syncthreads();
         if (!all_done) {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 sa = s_a[j], sc = s_c[j];
-                if (!warp_overlaps<4 * PPT>(sa, sc, wx, wy)) continue;  // alpha' < alpha_min on the warp's block
-                const float4 sb = s_b[j];
-                bool alive = false;
+            bool alive = true;
+            for (int wd = 0; wd < NWORD && alive; ++wd) {
+                // only records whose support box reaches the warp's block can have alpha' >= alpha_min there
+                uint32_t m = s_ov[warp][wd];
+                while (m) {
+                    const int j = wd * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    const float4 sa = s_a[j], sb = s_b[j], sc = s_c[j];
+                    alive = false;
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    if (done[k]) continue;
-                    alive = true;
-                    const AlphaEval ae = eval_alpha(sa, sb, px[k], py[k], amax);
-                    if (ae.alpha < amin) continue;
-                    const float testT = __fmul_rn(T[k], __fsub_rn(1.f, ae.alpha));
-                    if (testT < tmin) {
-                        done[k] = true;
-                        continue;
+                    for (int k = 0; k < PPT; ++k) {
+                        if (done[k]) continue;
+                        alive = true;
+                        const AlphaEval ae = eval_alpha(sa, sb, px[k], py[k], amax);
+                        if (ae.alpha < amin) continue;
+                        const float testT = __fmul_rn(T[k], __fsub_rn(1.f, ae.alpha));
+                        if (testT < tmin) {
+                            done[k] = true;
+                            continue;
+                        }
+                        const float w = ae.alpha * T[k];
+                        C0[k] += sb.z * w;
+                        C1[k] += sb.w * w;
+                        C2[k] += sc.x * w;
+                        T[k] = testT;
+                        last[k] = (int32_t)(b * BATCH + j + 1);
                     }
-                    const float w = ae.alpha * T[k];
-                    C0[k] += sb.z * w;
-                    C1[k] += sb.w * w;
-                    C2[k] += sc.x * w;
-                    T[k] = testT;
-                    last[k] = (int32_t)(b * BATCH + j + 1);
+                    if (!alive) break;
                 }
-                if (!alive) break;
             }
         }
     }
