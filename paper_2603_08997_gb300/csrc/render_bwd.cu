@@ -27,6 +27,9 @@ using namespace gsr;
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+// Up to this many contributing lanes of a warp add their 9 gradients to shared
+// memory directly instead of reducing over the warp first.
+constexpr int kDirectLanes = 1;
 
 // Reduces v[0..9) over the warp.  On return the even lane L with valid index
 // `idx` holds the warp total of v[idx]; other lanes get idx = -1.
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                 if (ae.alpha < amin) continue;
                 contrib = true;
                 const float om = __fsub_rn(1.f, ae.alpha);
-                const float inv = 1.f / om;
+                const float inv = rcp_approx(om);  // 1 - alpha >= 0.01
                 const float Tk = T[k] * inv;
                 const float wgt = ae.alpha * Tk;
                 const float c0 = sb.z, c1 = sb.w, c2 = sc.x;
@@ -213,10 +216,15 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                     gv[4] += dq * ae.dy * ae.dy;
                 }
             }
-            if (__any_sync(FULL, contrib)) {
+            const uint32_t cm = __ballot_sync(FULL, contrib);
+            if (__popc(cm) > kDirectLanes) {  // many lanes: reduce over the warp first
                 int idx;
                 const float tot = warp_reduce9(gv, lane, idx);
                 if (idx >= 0 && tot != 0.f) atomicAdd(&s_acc[j][idx], tot);
+            } else if (contrib) {  // a few lanes: their values go straight to shared memory
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    if (gv[q] != 0.f) atomicAdd(&s_acc[j][q], gv[q]);
             }
           }
         }
