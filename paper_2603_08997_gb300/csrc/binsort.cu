@@ -344,33 +344,56 @@ __global__ void bin_rects(const int4 *__restrict__ rect, const int32_t *__restri
     srect[i] = o;
 }
 
+// Pair counts of one chunk per tile by a 2D difference array: each entry adds
+// +1 / -1 / -1 / +1 at the four corners of its rectangle on a (tx + 1) x
+// (ty + 1) grid, and prefix sums along rows, then columns, give every tile the
+// number of the chunk's rectangles covering it (four shared atomics per entry
+// instead of one per pair, and no divergence on large rectangles).
 __global__ void __launch_bounds__(COUNT_THREADS) bin_count(const ushort4 *__restrict__ srect,
                                                            const gs_camera *__restrict__ cams, BinGeom g,
                                                            uint32_t *__restrict__ M, uint32_t *__restrict__ G1,
                                                            int32_t *dev_status) {
-    extern __shared__ uint32_t s_h[];
+    extern __shared__ int s_d[];  // [(tx + 1) * (ty + 1)] <= 2 max_vt + 2
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
     const ViewTiles vt = view_tiles(cams[v], g.tile);
     if (!view_fits(vt, g.tiles, g.max_vt)) {
         if (threadIdx.x == 0) set_status(dev_status, GS_ERR_INVALID_ARG);
         return;
     }
-    const int T = vt.tx * vt.ty;
-    for (int t = threadIdx.x; t < T; t += COUNT_THREADS) s_h[t] = 0u;
+    const int T = vt.tx * vt.ty, W = vt.tx + 1, D = W * (vt.ty + 1);
+    for (int t = threadIdx.x; t < D; t += COUNT_THREADS) s_d[t] = 0;
     __syncthreads();
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
     for (int64_t i = e0 + threadIdx.x; i < e1; i += COUNT_THREADS) {
         const ushort4 r = srect[i];
-        for (int dy = 0; dy < r.w; ++dy) {
-            uint32_t *rowp = s_h + (r.y + dy) * vt.tx + r.x;
-            for (int dx = 0; dx < r.z; ++dx) atomicAdd(rowp + dx, 1u);
+        if (r.z == 0) continue;
+        const int x0 = r.x, y0 = r.y, x1 = x0 + r.z, y1 = y0 + r.w;
+        atomicAdd(&s_d[y0 * W + x0], 1);
+        atomicSub(&s_d[y0 * W + x1], 1);
+        atomicSub(&s_d[y1 * W + x0], 1);
+        atomicAdd(&s_d[y1 * W + x1], 1);
+    }
+    __syncthreads();
+    for (int y = threadIdx.x; y < vt.ty; y += COUNT_THREADS) {  // along rows
+        int run = 0;
+        for (int x = 0; x < vt.tx; ++x) {
+            run += s_d[y * W + x];
+            s_d[y * W + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < vt.tx; x += COUNT_THREADS) {  // along columns
+        int run = 0;
+        for (int y = 0; y < vt.ty; ++y) {
+            run += s_d[y * W + x];
+            s_d[y * W + x] = run;
         }
     }
     __syncthreads();
     uint32_t *row = M + g.n_c * vt.off + c * T;
     uint32_t *grp = G1 + (c / BIN_GROUP) * g.tiles + vt.off;
     for (int t = threadIdx.x; t < T; t += COUNT_THREADS) {
-        const uint32_t h = s_h[t];
+        const uint32_t h = (uint32_t)s_d[(t / vt.tx) * W + (t % vt.tx)];
         row[t] = h;
         if (h) atomicAdd(&grp[t], h);
     }
@@ -754,7 +777,7 @@ gs_status bin_smem_attributes() {
     GS_TRY(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
-    GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bytes + 8));
     GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(96 * 1024)));
     GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -821,7 +844,7 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     GS_TRY_LAUNCH();
     GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
     const unsigned n_chunks = (unsigned)(g.n_c * n_views);
-    bin_count<<<n_chunks, COUNT_THREADS, smem, stream>>>(w.srect, cams, g, w.M, w.G1, dev_status);
+    bin_count<<<n_chunks, COUNT_THREADS, 2 * smem + 8, stream>>>(w.srect, cams, g, w.M, w.G1, dev_status);
     GS_TRY_LAUNCH();
     bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
     GS_TRY_LAUNCH();
