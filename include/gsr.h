@@ -135,6 +135,9 @@ typedef struct {
     int32_t *n_last;
     float *ckpt;
     int64_t ckpt_slots;
+    const uint32_t *tile_order;  /* [total_tiles] visiting order of the tiles (gs_tile_order), or NULL for
+                                    ascending tile id; a permutation of 0..total_tiles-1; results do not
+                                    depend on it */
 } gs_fwd_saved;
 
 /* --------------------------------------------------------------- layout */
@@ -216,6 +219,15 @@ gs_status gs_bin_sort_noalloc(const gs_projected *proj /* host */, const gs_came
                               int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream);
 
 /* --------------------------------------------------------------- forward */
+
+/* Visiting order of the tiles for the compositing kernels, longest list
+ * first: tiles grouped by list length (ranges from gs_bin_sort) on a
+ * logarithmic scale, eight groups per doubling, longest group first; the
+ * order within a group is unspecified.  Writes tile_order[total_tiles], a
+ * permutation of 0..total_tiles-1, for gs_fwd_saved.tile_order.  The paper
+ * has no counterpart: it is a scheduling choice (one CTA per tile, launched
+ * in this order) that changes no result. */
+gs_status gs_tile_order(const uint32_t *ranges, int64_t total_tiles, uint32_t *tile_order, cudaStream_t stream);
 
 /* Eq. (blend) and Eq. (alpha): per tile, Gaussians staged `batch` at a time in
  * shared memory; per pixel front to back alpha' = min(alpha_max, o exp(-1/2

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     const float4 *__restrict__ rec, int64_t n, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
     const gs_camera *__restrict__ cams, int n_views, gs_raster_config cfg, const float *__restrict__ T_final,
     const int32_t *__restrict__ n_last, const float *__restrict__ ckpt, int64_t ckpt_slots,
-    const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d) {
+    const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d,
+    const uint32_t *__restrict__ tile_order) {
     constexpr int NT = TILE * TILE;
     constexpr int NTH = TILE * TILE / PPT;
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     __shared__ float s_acc[BATCH][9];
     __shared__ int s_max;
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const int v = view_of_tile(cams, n_views, tile);
     if (view_gate && !view_gate[v]) return;
     const gs_camera &cam = cams[v];
@@ -614,15 +615,15 @@ gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const 
     switch (batch) {
         case 64:
             render_bwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                      s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d);
+                                                                      s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order);
             break;
         case 128:
             render_bwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d);
+                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order);
             break;
         case 256:
             render_bwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d);
+                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order);
             break;
         default:
             return GS_ERR_UNSUPPORTED;

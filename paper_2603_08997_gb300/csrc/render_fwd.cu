@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
                                                                        gs_raster_config cfg, float *__restrict__ image,
                                                                        float *__restrict__ T_final,
                                                                        int32_t *__restrict__ n_last,
-                                                                       float *__restrict__ ckpt, int64_t ckpt_slots) {
+                                                                       float *__restrict__ ckpt, int64_t ckpt_slots,
+                                                                       const uint32_t *__restrict__ tile_order) {
     constexpr int NT = TILE * TILE;        // pixels per tile (checkpoint slot size)
     constexpr int NTH = TILE * TILE / PPT; // threads
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
     __shared__ float4 s_b[BATCH];
     __shared__ float4 s_c[BATCH];
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const int v = view_of_tile(cams, n_views, tile);
     const gs_camera &cam = cams[v];
     const int tiles_x = (cam.width + TILE - 1) / TILE;
@@ -151,15 +152,15 @@ gs_status launch_fwd(int batch, int64_t total_tiles, cudaStream_t stream, const 
     switch (batch) {
         case 64:
             render_fwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                      s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
+                                                                      s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order);
             break;
         case 128:
             render_fwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
+                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order);
             break;
         case 256:
             render_fwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots);
+                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order);
             break;
         default:
             return GS_ERR_UNSUPPORTED;

@@ -50,7 +50,8 @@ class gs_projected(C.Structure):
 
 
 class gs_fwd_saved(C.Structure):
-    _fields_ = [("T_final", C.c_void_p), ("n_last", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_slots", C.c_int64)]
+    _fields_ = [("T_final", C.c_void_p), ("n_last", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_slots", C.c_int64),
+                ("tile_order", C.c_void_p)]
 
 
 class gs_adam_config(C.Structure):
@@ -79,6 +80,7 @@ _PROTOS = {
                               _P, _P, _I64, _P, _P, _P, _S]),
     "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config),
                                       _P, _P, _I64, _P, _P, _P, _S]),
+    "gs_tile_order": (C.c_int, [_P, _I64, _P, _S]),
     "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                 _P, gs_fwd_saved, _P, _S]),
     "gs_loss_workspace_size": (C.c_size_t, [C.POINTER(gs_camera), _I32]),

@@ -30,6 +30,7 @@ class RasterSettings:
     lambda_ssim: float = 0.2
     pixels_per_thread: int = 2      # raster adjoint
     pixels_per_thread_fwd: int = 1  # forward compositing
+    longest_tiles_first: bool = True  # launch tiles by descending list length (gs_tile_order)
 
     def struct(self, sh_degree: int) -> gsr.gs_raster_config:
         c = gsr.gs_raster_config()
@@ -145,6 +146,7 @@ class Renderer:
         self.vals = torch.empty(max(self.cap, 1), dtype=torch.int32, device=dev)
         self.keys = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev) if keep_keys else None
         self.ranges = torch.empty(2 * T, dtype=torch.int32, device=dev)
+        self.tile_order = torch.empty(T, dtype=torch.int32, device=dev) if self.s.longest_tiles_first else None
         self.pair_count = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.image = torch.empty(3 * P, dtype=torch.float32, device=dev)
@@ -172,6 +174,7 @@ class Renderer:
         s = gsr.gs_fwd_saved()
         s.T_final, s.n_last, s.ckpt, s.ckpt_slots = (self.T_final.data_ptr(), self.n_last.data_ptr(),
                                                      self.ckpt.data_ptr(), self.ckpt_slots)
+        s.tile_order = self.tile_order.data_ptr() if self.tile_order is not None else None
         return s
 
     # --- pipeline steps (each one C-ABI call)
@@ -185,6 +188,9 @@ class Renderer:
                  self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws), self.bin_ws_bytes,
                  gsr.ptr(self.keys), gsr.ptr(self.vals), self.cap, gsr.ptr(self.ranges), gsr.ptr(self.pair_count),
                  gsr.ptr(self.status), gsr.stream_handle(stream))
+        if self.tile_order is not None:
+            gsr.call("gs_tile_order", gsr.ptr(self.ranges), self.views.total_tiles, gsr.ptr(self.tile_order),
+                     gsr.stream_handle(stream))
 
     def render_fwd(self, stream=None) -> None:
         proj = self.c_proj()

@@ -215,3 +215,36 @@ def test_pixels_per_thread_is_bit_invariant(tile):
         out.append([t.clone().cpu() for t in (r.image, r.T_final, r.n_last, r.ckpt)])
     for a, b in zip(*out):
         assert torch.equal(a, b)
+
+
+def test_tile_order_is_a_permutation_by_work_and_changes_nothing():
+    """gs_tile_order: a permutation of the tiles, list lengths non-increasing
+    across the logarithmic groups; rendering in that order gives the same
+    image, final transmittance, last-contributor counts and checkpoints."""
+    sizes = [(150, 97), (64, 40)]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(4000, w, h, seed=61 + v) for v, (w, h) in enumerate(sizes)]
+    dev, _ = gpu_util.records(recs, cams, 8)
+    out = []
+    for ordered in (False, True):
+        gpu_util.lib()
+        views = raster.Views(cams, 8)
+        st = raster.RasterSettings(tile=8, batch=64, longest_tiles_first=ordered)
+        r = raster.Renderer(4000, 0, views, st)
+        gpu_util.set_projected(r, dev)
+        r.ckpt.fill_(-1.0)
+        r.bin_sort()
+        r.render_fwd()
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        out.append([t.clone().cpu() for t in (r.image, r.T_final, r.n_last, r.ckpt)])
+        if ordered:
+            order = r.tile_order.cpu().numpy().astype(np.int64)
+            T = r.views.total_tiles
+            assert np.array_equal(np.sort(order), np.arange(T))
+            rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+            length = (rg[:, 1] - rg[:, 0])[order]
+            group = np.floor(8 * np.log2(length + 1.0) + 1e-9)
+            assert np.all(np.diff(group) <= 0)
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
