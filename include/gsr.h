@@ -221,9 +221,10 @@ gs_status gs_bin_sort_noalloc(const gs_projected *proj /* host */, const gs_came
 /* --------------------------------------------------------------- forward */
 
 /* Visiting order of the tiles for the compositing kernels, longest list
- * first: tiles grouped by list length (ranges from gs_bin_sort) on a
- * logarithmic scale, eight groups per doubling, longest group first; the
- * order within a group is unspecified.  Writes tile_order[total_tiles], a
+ * first: tiles grouped by x = list length + 1 (ranges from gs_bin_sort) into
+ * 8 (bit length of x - 1) + (the three bits of x after its leading one),
+ * eight groups per doubling, longest group first; the order within a group
+ * is unspecified.  Writes tile_order[total_tiles], a
  * permutation of 0..total_tiles-1, for gs_fwd_saved.tile_order.  The paper
  * has no counterpart: it is a scheduling choice (one CTA per tile, launched
  * in this order) that changes no result. */

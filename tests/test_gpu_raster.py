@@ -244,7 +244,11 @@ def test_tile_order_is_a_permutation_by_work_and_changes_nothing():
             assert np.array_equal(np.sort(order), np.arange(T))
             rg = r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
             length = (rg[:, 1] - rg[:, 0])[order]
-            group = np.floor(8 * np.log2(length + 1.0) + 1e-9)
+            # group: 8 x (bit length of len + 1, minus one) + the three bits after its leading one
+            x = length + 1
+            e = np.floor(np.log2(x)).astype(np.int64)
+            frac = np.where(e >= 3, (x >> np.maximum(e - 3, 0)) & 7, (x << np.maximum(3 - e, 0)) & 7)
+            group = 8 * e + frac
             assert np.all(np.diff(group) <= 0)
     for a, b in zip(*out):
         assert torch.equal(a, b)
