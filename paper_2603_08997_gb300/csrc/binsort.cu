@@ -504,21 +504,19 @@ __device__ __forceinline__ void block_scan_table(uint32_t *s, int n, uint32_t *w
 // One block per chunk.  The chunk's first slot per tile is held in shared
 // memory (s_off).  The block takes its entries WIN at a time (a window, WIN =
 // the bits of one tile's entry mask); the window's pairs, in order (entry,
-// then tile row-major), are handled SC_STAGE at a time (a stage): every entry
-// marks the stage position of its first pair and a block max-scan gives each
-// position its entry, so thread i takes pairs i, i + SC_THREADS, ... without
-// searching and without diverging on entry boundaries.
+// then tile row-major), are expanded with each thread taking an equal
+// contiguous run, so one large rectangle does not stall the block.
 //   pass A: every pair sets bit j (its entry within the window) in its tile's
 //           mask (shared atomicOr, order-free);
 //   pass B: a pair's rank among the window's pairs of its tile is the number
 //           of mask bits below j; it goes to s_off[tile] + rank.  The pair
 //           with the highest bit then advances s_off[tile] by the mask's
 //           population and clears the mask.
-// A tile's last pair is never in an earlier stage than its other pairs, so
-// each stage's advances can follow it directly.
+// Pass B runs in sub-windows of SC_THREADS * SC_Q pairs; a tile's last pair is
+// never in an earlier sub-window than its other pairs, so each sub-window's
+// advances can follow it directly.
 constexpr int SC_THREADS = 512;
-constexpr int SC_STAGE = 2048;                  // pairs per stage
-constexpr int SC_Q = SC_STAGE / SC_THREADS;     // pairs per thread per stage
+constexpr int SC_Q = 4;  // pairs per thread per sub-window
 
 template <typename W, int NW>
 struct ScatterMask {
@@ -527,41 +525,40 @@ struct ScatterMask {
     static constexpr size_t bytes_per_tile = sizeof(W) * NW + sizeof(uint32_t);
 };
 
-// Inclusive max-scan of s[0, SC_STAGE) in place (values are entry indices).
-__device__ __forceinline__ void block_max_scan_stage(int *s, int *s_wmax) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int v[SC_Q];
-    int run = 0;
-#pragma unroll
-    for (int q = 0; q < SC_Q; ++q) {
-        v[q] = max(run, s[threadIdx.x * SC_Q + q]);
-        run = v[q];
-    }
-    int inc = run;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc = max(inc, y);
-    }
-    if (lane == 31) s_wmax[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < SC_THREADS / 32 ? s_wmax[lane] : 0;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w = max(w, y);
+// Walks the pairs [p0, p1) of a window in list order.
+struct PairWalk {
+    int jj, dx, t, w, nxt;
+    __device__ __forceinline__ void start(int p0, const int *s_pre, const ushort4 *s_er, int win, int tx) {
+        int lo = 0, hi = win - 1;  // the last j with s_pre[j] <= p0 (so empty entries are skipped)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
         }
-        if (lane < SC_THREADS / 32) s_wmax[lane] = w;
+        jj = lo;
+        const ushort4 er = s_er[jj];
+        w = er.z;
+        const int k = p0 - s_pre[jj], dy = k / w;
+        dx = k - dy * w;
+        t = (er.y + dy) * tx + er.x + dx;
+        nxt = s_pre[jj + 1];
     }
-    __syncthreads();
-    int before = warp > 0 ? s_wmax[warp - 1] : 0;
-    const int y = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane > 0) before = max(before, y);
-#pragma unroll
-    for (int q = 0; q < SC_Q; ++q) s[threadIdx.x * SC_Q + q] = max(before, v[q]);
-    __syncthreads();
-}
+    // step from pair p to pair p + 1 (p + 1 < end of the window)
+    __device__ __forceinline__ void next(int p, const int *s_pre, const ushort4 *s_er, int tx) {
+        if (p + 1 == nxt) {
+            do { ++jj; } while (s_pre[jj + 1] <= p + 1);
+            const ushort4 er = s_er[jj];
+            w = er.z;
+            dx = 0;
+            t = er.y * tx + er.x;
+            nxt = s_pre[jj + 1];
+        } else if (++dx == w) {
+            dx = 0;
+            t += tx - (w - 1);
+        } else {
+            ++t;
+        }
+    }
+};
 
 template <typename W, int NW>  // W: 32-bit mask words
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
@@ -574,14 +571,10 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     extern __shared__ __align__(16) unsigned char s_raw[];
     W *s_mask = reinterpret_cast<W *>(s_raw);                                     // [max_vt][NW]
     uint32_t *s_off = reinterpret_cast<uint32_t *>(s_mask + (size_t)g.max_vt * NW);  // [max_vt]
-    __shared__ ushort4 s_er[WIN];             // the window's rectangles
-    __shared__ uint32_t s_eg[WIN];            // Gaussian indices
-    __shared__ uint32_t s_em[WIN];            // division magic of the rectangle widths
-    __shared__ int s_pre[WIN + 1];            // first pair of each entry
-    __shared__ int s_pe[SC_STAGE];            // stage position -> entry
-    __shared__ uint32_t s_tj[SC_STAGE];       // stage position -> (tile << 8 | entry)
+    __shared__ ushort4 s_er[WIN];    // the window's rectangles
+    __shared__ uint32_t s_eg[WIN];   // Gaussian indices
+    __shared__ int s_pre[WIN + 1];   // first pair of each entry
     __shared__ uint32_t s_warp[32];
-    __shared__ int s_wmax[32];
     if (*sort_count == 0) return;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
     const ViewTiles vt = view_tiles(cams[v], g.tile);
@@ -593,27 +586,6 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
 #pragma unroll
         for (int k = 0; k < NW; ++k) s_mask[t * NW + k] = 0;
     }
-    // (tile, entry) of the stage's pairs [sw, sw + SC_STAGE) into s_tj
-    auto stage = [&](int sw, int cnt) {
-        for (int q = threadIdx.x; q < SC_STAGE; q += SC_THREADS) s_pe[q] = 0;
-        __syncthreads();
-        if (threadIdx.x < WIN) {
-            const int j = threadIdx.x, lo = s_pre[j], hi = s_pre[j + 1];
-            if (lo < hi && hi > sw && lo < sw + cnt) s_pe[max(lo, sw) - sw] = j;
-        }
-        __syncthreads();
-        block_max_scan_stage(s_pe, s_wmax);
-        for (int q = threadIdx.x; q < cnt; q += SC_THREADS) {
-            const int j = s_pe[q];
-            const ushort4 er = s_er[j];
-            const uint32_t k = (uint32_t)(sw + q - s_pre[j]);
-            const uint32_t m = s_em[j];
-            const int dy = (int)(m ? __umulhi(k, m) : k);
-            const int t = ((int)er.y + dy) * vt.tx + (int)er.x + ((int)k - dy * (int)er.z);
-            s_tj[q] = ((uint32_t)t << 8) | (uint32_t)j;
-        }
-        __syncthreads();
-    };
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
     for (int64_t base = e0; base < e1; base += WIN) {
         int area = 0;
@@ -627,7 +599,6 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             }
             s_er[threadIdx.x] = r;
             s_eg[threadIdx.x] = gi;
-            s_em[threadIdx.x] = r.z > 1 ? 0xffffffffu / r.z + 1u : 0u;  // ceil(2^32 / w); w = 1 marked 0
             area = (int)r.z * r.w;
         }
         uint32_t tot_u;
@@ -636,59 +607,71 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
         if (threadIdx.x == 0) s_pre[WIN] = (int)tot_u;
         __syncthreads();
         const int tot = (int)tot_u;
-        const bool one_stage = tot <= SC_STAGE;
-        // pass A: entry masks per tile
-        for (int sw = 0; sw < tot; sw += SC_STAGE) {
-            const int cnt = min(SC_STAGE, tot - sw);
-            stage(sw, cnt);
-            for (int q = threadIdx.x; q < cnt; q += SC_THREADS) {
-                const uint32_t tj = s_tj[q];
-                const int j = (int)(tj & 0xffu);
-                atomicOr(&s_mask[(tj >> 8) * NW + j / WB], (W)1 << (j % WB));
+        // pass A: entry masks per tile (the walk's start in the first
+        // sub-window is kept for pass B)
+        PairWalk first;
+        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
+            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
+            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
+            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
+            if (p0 < p1) {
+                PairWalk it;
+                it.start(p0, s_pre, s_er, WIN, vt.tx);
+                if (sw == 0) first = it;
+                for (int p = p0;; ++p) {
+                    atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
+                    if (p + 1 >= p1) break;
+                    it.next(p, s_pre, s_er, vt.tx);
+                }
             }
         }
         __syncthreads();
-        // pass B: place, then advance the tiles whose last pair is in this stage
-        for (int sw = 0; sw < tot; sw += SC_STAGE) {
-            const int cnt = min(SC_STAGE, tot - sw);
-            if (!one_stage) stage(sw, cnt);
+        // pass B: place, then advance the tiles whose last pair is in this sub-window
+        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
+            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
+            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
+            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
             int last_t[SC_Q];
             uint32_t last_n[SC_Q];
 #pragma unroll
-            for (int r = 0; r < SC_Q; ++r) {
-                last_t[r] = -1;
-                const int q = threadIdx.x + r * SC_THREADS;
-                if (q >= cnt) continue;
-                const uint32_t tj = s_tj[q];
-                const int t = (int)(tj >> 8), j = (int)(tj & 0xffu);
-                const int jw = j / WB, jb = j % WB;
-                uint32_t below = 0, all = 0;
-                bool higher = false;
+            for (int k = 0; k < SC_Q; ++k) last_t[k] = -1;
+            if (p0 < p1) {
+                PairWalk it;
+                if (sw == 0) it = first; else it.start(p0, s_pre, s_er, WIN, vt.tx);
 #pragma unroll
-                for (int wd = 0; wd < NW; ++wd) {
-                    const W m = s_mask[t * NW + wd];
-                    const uint32_t pc = (uint32_t)__popc((uint32_t)m);
-                    all += pc;
-                    if (wd < jw) below += pc;
-                    if (wd == jw) {
-                        below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
-                        higher |= (jb + 1 < WB) && (m >> (jb + 1)) != 0;
+                for (int k = 0; k < SC_Q; ++k) {
+                    const int p = p0 + k;
+                    if (p >= p1) break;
+                    if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
+                    const int jw = it.jj / WB, jb = it.jj % WB;
+                    uint32_t below = 0, all = 0;
+                    bool higher = false;
+#pragma unroll
+                    for (int wd = 0; wd < NW; ++wd) {
+                        const W m = s_mask[it.t * NW + wd];
+                        const uint32_t pc = (uint32_t)__popc((uint32_t)m);
+                        all += pc;
+                        if (wd < jw) below += pc;
+                        if (wd == jw) {
+                            below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
+                            higher |= (jb + 1 < WB) && (m >> (jb + 1)) != 0;
+                        }
+                        if (wd > jw) higher |= m != 0;
                     }
-                    if (wd > jw) higher |= m != 0;
-                }
-                vals[s_off[t] + below] = s_eg[j];
-                if (!higher) {
-                    last_t[r] = t;
-                    last_n[r] = all;
+                    vals[s_off[it.t] + below] = s_eg[it.jj];
+                    if (!higher) {
+                        last_t[k] = it.t;
+                        last_n[k] = all;
+                    }
                 }
             }
             __syncthreads();
 #pragma unroll
-            for (int r = 0; r < SC_Q; ++r) {
-                if (last_t[r] >= 0) {
-                    s_off[last_t[r]] += last_n[r];
+            for (int k = 0; k < SC_Q; ++k) {
+                if (last_t[k] >= 0) {
+                    s_off[last_t[k]] += last_n[k];
 #pragma unroll
-                    for (int wd = 0; wd < NW; ++wd) s_mask[last_t[r] * NW + wd] = 0;
+                    for (int wd = 0; wd < NW; ++wd) s_mask[last_t[k] * NW + wd] = 0;
                 }
             }
             __syncthreads();
