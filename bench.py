@@ -487,7 +487,8 @@ def main():
         gated.close()
         del gated
         loop = RefinementLoop(model, cams, slot_target, seq, st, gated=True, pair_capacity=cap)
-        loop.target_offsets.zero_()  # every view's target is the slot the host fills each step
+        # every view's target is the slot the host fills each step
+        loop.target_offsets = torch.zeros(len(cams), dtype=torch.int64, device=dev)
         loop.restore(init)
         loop.capture()
         loss_host = torch.empty(K, dtype=torch.float32).pin_memory()

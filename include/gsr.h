@@ -249,7 +249,11 @@ size_t gs_loss_workspace_size(const gs_camera *cams_host, int32_t n_views);
 /* Eq. (loss): L_v = (1 - lambda) mean|C - C_hat| + lambda (1 - mean SSIM) per
  * view (11x11 Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2, zero
  * padding, 'same' size, means over 3HW).  cams_host: the views' cameras in
- * host memory (only width, height and pix_offset are read).  image: as
+ * host memory (only width, height and pix_offset are read); cams_dev (device
+ * memory, nullable): when given, view v's actual width and height are read
+ * from cams_dev[v] on the device - at most cams_host[v]'s, which then give
+ * the launch size and the slot's capacity (views chosen on the device, e.g.
+ * by gs_select_views inside a captured step).  image: as
  * written by gs_render_fwd; target: same layout, or - when target_offsets is
  * given - view slot v's target starts at target + target_offsets[view_ids[v]]
  * (floats; view_ids in device memory).  Writes
@@ -257,15 +261,15 @@ size_t gs_loss_workspace_size(const gs_camera *cams_host, int32_t n_views);
  * derivatives in the workspace for gs_loss_backward.  If dL_dimage is not NULL
  * the gradient is written too (as gs_loss_backward would). */
 gs_status gs_loss(const float *image, const float *target, const int64_t *target_offsets,
-                  const gs_camera *cams_host, const int32_t *view_ids, int32_t n_views, float lambda_ssim,
-                  void *workspace, size_t workspace_bytes, float *loss_per_view, float *dL_dimage,
-                  cudaStream_t stream);
+                  const gs_camera *cams_host, const gs_camera *cams_dev, const int32_t *view_ids, int32_t n_views,
+                  float lambda_ssim, void *workspace, size_t workspace_bytes, float *loss_per_view,
+                  float *dL_dimage, cudaStream_t stream);
 
 /* dL/dimage from the state gs_loss left in the workspace (same arguments). */
 gs_status gs_loss_backward(const float *image, const float *target, const int64_t *target_offsets,
-                           const gs_camera *cams_host, const int32_t *view_ids, int32_t n_views,
-                           float lambda_ssim, void *workspace, size_t workspace_bytes, float *dL_dimage,
-                           cudaStream_t stream);
+                           const gs_camera *cams_host, const gs_camera *cams_dev, const int32_t *view_ids,
+                           int32_t n_views, float lambda_ssim, void *workspace, size_t workspace_bytes,
+                           float *dL_dimage, cudaStream_t stream);
 
 /* -------------------------------------------------------------- backward */
 
@@ -411,9 +415,10 @@ gs_status gs_graph_destroy(gs_graph graph);
 
 /* Device-side view selection for graph replay: view_ids[k] =
  * seq[(*iter * n + k) mod seq_len] for k < n, then *iter += 1 (int64, device).
- * If pose_src and slots are given, slots[k].R and slots[k].t are set to the
- * pose of pose_src[view_ids[k]] (intrinsics, size and offsets of the slot are
- * kept), so a captured step renders the selected views. */
+ * If pose_src and slots are given, slot k takes the pose, intrinsics, size and
+ * near plane of pose_src[view_ids[k]] and keeps its own tile_offset and
+ * pix_offset, so a captured step renders the selected views; a view larger
+ * than the slot's capacity is the caller's error. */
 gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
                           const gs_camera *pose_src, gs_camera *slots, cudaStream_t stream);
 

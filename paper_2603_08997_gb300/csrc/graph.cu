@@ -45,9 +45,18 @@ __global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t
         const int64_t idx = (it * n + k) % seq_len;
         const int32_t vid = seq[idx];
         view_ids[k] = vid;
-        if (pose_src && slots) {
-            for (int a = 0; a < 9; ++a) slots[k].R[a] = pose_src[vid].R[a];
-            for (int a = 0; a < 3; ++a) slots[k].t[a] = pose_src[vid].t[a];
+        if (pose_src && slots) {  // the pose, intrinsics and size; the slot keeps its tile and pixel offsets
+            const gs_camera &src = pose_src[vid];
+            gs_camera &dst = slots[k];
+            for (int a = 0; a < 9; ++a) dst.R[a] = src.R[a];
+            for (int a = 0; a < 3; ++a) dst.t[a] = src.t[a];
+            dst.fx = src.fx;
+            dst.fy = src.fy;
+            dst.cx = src.cx;
+            dst.cy = src.cy;
+            dst.width = src.width;
+            dst.height = src.height;
+            dst.znear = src.znear;
         }
     }
     *iter = it + 1;

@@ -49,18 +49,33 @@ __device__ __forceinline__ const float *target_base(const float *target, const i
     return target + 3 * pix_offset;
 }
 
+// The view's size: from the device camera when given (a slot whose camera is
+// chosen on the device, at most the launch's capacity), else the launch's.
+__device__ __forceinline__ void view_size(const gs_camera *cam_dev, int &W, int &H) {
+    if (cam_dev) {
+        W = min(W, cam_dev->width);
+        H = min(H, cam_dev->height);
+    }
+}
+
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__ img, const float *__restrict__ target,
                                                        const int64_t *__restrict__ target_offsets,
                                                        const int32_t *__restrict__ view_ids, int v,
-                                                       int64_t pix_offset, int W, int H, Win win,
+                                                       int64_t pix_offset, int W, int H,
+                                                       const gs_camera *__restrict__ cam_dev, Win win,
                                                        float *__restrict__ dmaps, double2 *__restrict__ partials) {
     __shared__ float sx[LH][LW];
     __shared__ float sy[LH][LW];
     __shared__ float hs[5][LH][LTW];
     __shared__ double red[2][8];
+    view_size(cam_dev, W, H);
     const float *tgt = target_base(target, target_offsets, view_ids, v, pix_offset);
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int bx0 = blockIdx.x * LTW, by0 = blockIdx.y * LTH;
+    if (bx0 >= W || by0 >= H) {  // past the device camera's size
+        if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(0.0, 0.0);
+        return;
+    }
     const int64_t hw = (int64_t)W * H;
     const int ccx = min(bx0 + LTW / 2, W - 1), ccy = min(by0 + LTH / 2, H - 1);
     float ssim_acc = 0.f, l1_acc = 0.f;
@@ -140,9 +155,11 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__
     }
 }
 
-// Per view: fixed-order sum of the block partials -> loss.
-__global__ void loss_reduce_kernel(const double2 *__restrict__ partials, int nblocks, double n, float lambda,
-                                   float *__restrict__ loss_out) {
+// Per view: fixed-order sum of the block partials -> loss (n = 3 W H, from
+// the device camera when given).
+__global__ void loss_reduce_kernel(const double2 *__restrict__ partials, int nblocks, double n,
+                                   const gs_camera *__restrict__ cam_dev, float lambda, float *__restrict__ loss_out) {
+    if (cam_dev) n = 3.0 * (double)cam_dev->width * (double)cam_dev->height;
     __shared__ double s0[256], s1[256];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nblocks; i += 256) {
@@ -169,13 +186,16 @@ __global__ void loss_reduce_kernel(const double2 *__restrict__ partials, int nbl
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__ img, const float *__restrict__ target,
                                                        const int64_t *__restrict__ target_offsets,
                                                        const int32_t *__restrict__ view_ids, int v,
-                                                       int64_t pix_offset, int W, int H, float lambda, Win win,
+                                                       int64_t pix_offset, int W, int H,
+                                                       const gs_camera *__restrict__ cam_dev, float lambda, Win win,
                                                        const float *__restrict__ dmaps, float *__restrict__ grad) {
     __shared__ float sp[3][LH][LW];
     __shared__ float hs[3][LH][LTW];
+    view_size(cam_dev, W, H);
     const float *tgt = target_base(target, target_offsets, view_ids, v, pix_offset);
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int bx0 = blockIdx.x * LTW, by0 = blockIdx.y * LTH;
+    if (bx0 >= W || by0 >= H) return;
     const int64_t hw = (int64_t)W * H;
     const float inv_n = 1.f / (3.f * (float)hw);
     for (int ch = 0; ch < 3; ++ch) {
@@ -269,8 +289,9 @@ size_t gs_loss_workspace_size(const gs_camera *cams_host, int32_t n_views) {
 }
 
 gs_status gs_loss(const float *image, const float *target, const int64_t *target_offsets, const gs_camera *cams_host,
-                  const int32_t *view_ids, int32_t n_views, float lambda_ssim, void *workspace,
-                  size_t workspace_bytes, float *loss_per_view, float *dL_dimage, cudaStream_t stream) {
+                  const gs_camera *cams_dev, const int32_t *view_ids, int32_t n_views, float lambda_ssim,
+                  void *workspace, size_t workspace_bytes, float *loss_per_view, float *dL_dimage,
+                  cudaStream_t stream) {
     LossLayout L;
     gs_status st = check_loss_args(image, target, cams_host, n_views, workspace, workspace_bytes, L);
     if (st != GS_OK) return st;
@@ -284,23 +305,26 @@ gs_status gs_loss(const float *image, const float *target, const int64_t *target
         const gs_camera &c = cams_host[v];
         const dim3 grid((unsigned)ceil_div(c.width, LTW), (unsigned)ceil_div(c.height, LTH));
         ssim_fwd_kernel<<<grid, dim3(32, 8), 0, stream>>>(image + 3 * c.pix_offset, target, target_offsets, view_ids, v,
-                                                          c.pix_offset, c.width, c.height, win,
+                                                          c.pix_offset, c.width, c.height,
+                                                          cams_dev ? cams_dev + v : nullptr, win,
                                                           dmaps + 9 * c.pix_offset, partials + boff);
         GS_TRY_LAUNCH();
         loss_reduce_kernel<<<1, 256, 0, stream>>>(partials + boff, (int)(grid.x * grid.y),
-                                                  3.0 * (double)c.width * c.height, lambda_ssim, loss_per_view + v);
+                                                  3.0 * (double)c.width * c.height, cams_dev ? cams_dev + v : nullptr,
+                                                  lambda_ssim, loss_per_view + v);
         GS_TRY_LAUNCH();
         boff += (int64_t)grid.x * grid.y;
     }
     if (dL_dimage)
-        return gs_loss_backward(image, target, target_offsets, cams_host, view_ids, n_views, lambda_ssim, workspace,
-                                workspace_bytes, dL_dimage, stream);
+        return gs_loss_backward(image, target, target_offsets, cams_host, cams_dev, view_ids, n_views, lambda_ssim,
+                                workspace, workspace_bytes, dL_dimage, stream);
     return GS_OK;
 }
 
 gs_status gs_loss_backward(const float *image, const float *target, const int64_t *target_offsets,
-                           const gs_camera *cams_host, const int32_t *view_ids, int32_t n_views, float lambda_ssim,
-                           void *workspace, size_t workspace_bytes, float *dL_dimage, cudaStream_t stream) {
+                           const gs_camera *cams_host, const gs_camera *cams_dev, const int32_t *view_ids,
+                           int32_t n_views, float lambda_ssim, void *workspace, size_t workspace_bytes,
+                           float *dL_dimage, cudaStream_t stream) {
     LossLayout L;
     gs_status st = check_loss_args(image, target, cams_host, n_views, workspace, workspace_bytes, L);
     if (st != GS_OK) return st;
@@ -312,7 +336,8 @@ gs_status gs_loss_backward(const float *image, const float *target, const int64_
         const gs_camera &c = cams_host[v];
         const dim3 grid((unsigned)ceil_div(c.width, LTW), (unsigned)ceil_div(c.height, LTH));
         ssim_bwd_kernel<<<grid, dim3(32, 8), 0, stream>>>(image + 3 * c.pix_offset, target, target_offsets, view_ids, v,
-                                                          c.pix_offset, c.width, c.height, lambda_ssim, win,
+                                                          c.pix_offset, c.width, c.height,
+                                                          cams_dev ? cams_dev + v : nullptr, lambda_ssim, win,
                                                           dmaps + 9 * c.pix_offset, dL_dimage + 3 * c.pix_offset);
         GS_TRY_LAUNCH();
     }

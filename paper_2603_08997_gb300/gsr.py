@@ -84,8 +84,8 @@ _PROTOS = {
     "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                 _P, gs_fwd_saved, _P, _S]),
     "gs_loss_workspace_size": (C.c_size_t, [C.POINTER(gs_camera), _I32]),
-    "gs_loss": (C.c_int, [_P, _P, _P, C.POINTER(gs_camera), _P, _I32, _F32, _P, _SZ, _P, _P, _S]),
-    "gs_loss_backward": (C.c_int, [_P, _P, _P, C.POINTER(gs_camera), _P, _I32, _F32, _P, _SZ, _P, _S]),
+    "gs_loss": (C.c_int, [_P, _P, _P, C.POINTER(gs_camera), _P, _P, _I32, _F32, _P, _SZ, _P, _P, _S]),
+    "gs_loss_backward": (C.c_int, [_P, _P, _P, C.POINTER(gs_camera), _P, _P, _I32, _F32, _P, _SZ, _P, _S]),
     "gs_render_bwd_workspace_size": (C.c_size_t, [_I64, _I32]),
     "gs_render_bwd": (C.c_int, [C.POINTER(gs_params), C.POINTER(gs_projected), _P, _P, _P, _I32, _I64,
                                 C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, gs_grads, _I32, _P, _SZ, _P, _S]),

@@ -132,6 +132,9 @@ class Renderer:
                  pair_capacity: int | None = None, device="cuda", keep_keys: bool = False):
         self.s = settings or RasterSettings()
         self.n, self.sh_degree, self.views = int(n), int(sh_degree), views
+        # True when the device cameras are chosen on the device (slots filled by
+        # gs_select_views): the loss then reads each view's size from them
+        self.sizes_on_device = False
         self.cfg = self.s.struct(sh_degree)
         self.cfg_fwd = self.s.struct(sh_degree)
         self.cfg_fwd.pixels_per_thread = int(self.s.pixels_per_thread_fwd)
@@ -204,17 +207,20 @@ class Renderer:
         self.render_fwd(stream)
         return self.image
 
+    def _cams_dev(self):
+        return gsr.ptr(self.views.dev) if self.sizes_on_device else None
+
     def compute_loss(self, target: torch.Tensor, target_offsets=None, view_ids=None, with_grad=False,
                      stream=None) -> torch.Tensor:
         gsr.call("gs_loss", gsr.ptr(self.image), gsr.ptr(target), gsr.ptr(target_offsets), self.views.host,
-                 gsr.ptr(view_ids), self.views.n, float(self.s.lambda_ssim), gsr.ptr(self.loss_ws),
+                 self._cams_dev(), gsr.ptr(view_ids), self.views.n, float(self.s.lambda_ssim), gsr.ptr(self.loss_ws),
                  self.loss_ws_bytes, gsr.ptr(self.loss), gsr.ptr(self.dL_dimage) if with_grad else None,
                  gsr.stream_handle(stream))
         return self.loss
 
     def loss_backward(self, target: torch.Tensor, target_offsets=None, view_ids=None, stream=None) -> torch.Tensor:
         gsr.call("gs_loss_backward", gsr.ptr(self.image), gsr.ptr(target), gsr.ptr(target_offsets),
-                 self.views.host, gsr.ptr(view_ids), self.views.n, float(self.s.lambda_ssim),
+                 self.views.host, self._cams_dev(), gsr.ptr(view_ids), self.views.n, float(self.s.lambda_ssim),
                  gsr.ptr(self.loss_ws), self.loss_ws_bytes, gsr.ptr(self.dL_dimage), gsr.stream_handle(stream))
         return self.dL_dimage
 

@@ -1,9 +1,15 @@
 """Post-densification refinement loop with the SkipGS gate (Algorithm 1).
 
-One iteration: select the view of this iteration (device-side, from the
+One iteration: select the view(s) of this iteration (device-side, from the
 pre-drawn view sequence) -> project -> bin/sort -> render -> loss (value) ->
 gate decision -> [loss gradient -> raster and projection adjoint -> Adam]
-only when g = 1 -> per-view EMA update.  The backward branch issues
+only when g = 1 -> per-view EMA update.
+
+Batched form (views_per_step = B > 1): B views per iteration in B camera
+slots sized for the largest training view; each slot takes its view's pose,
+intrinsics and size on the device, the gate decides the B losses in order
+(reading (vii)), the adjoint runs for the views with g = 1 only, and Adam
+steps once if any did.  The backward branch issues
 gs_render_bwd then gs_adam_step; fused=True uses gs_render_bwd_adam (the
 projection adjoint and Adam in one kernel) instead.
 
@@ -25,27 +31,42 @@ from .raster import AdamState, Gate, GaussianModel, RasterSettings, Renderer, Vi
 
 
 class RefinementLoop:
-    def __init__(self, model: GaussianModel, train_cams: list, targets: torch.Tensor, view_seq,
+    def __init__(self, model: GaussianModel, train_cams: list, targets, view_seq,
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
-                 fused: bool = False):
+                 fused: bool = False, views_per_step: int = 1):
+        """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
+        [3, H_v, W_v] tensors, one per training view."""
+        import copy
         self.model = model
         self.fused = bool(fused)
         self.s = settings or RasterSettings()
         self.gated = bool(gated)
+        self.B = int(views_per_step)
         dev = model.flat.device
         self.n_train = len(train_cams)
-        self.slot = Views([train_cams[0]], self.s.tile, dev)
+        # B slots with the capacity of the largest training view
+        wmax = max(int(c.width) for c in train_cams)
+        hmax = max(int(c.height) for c in train_cams)
+        slot_cam = copy.copy(train_cams[0])
+        slot_cam.width, slot_cam.height = wmax, hmax
+        self.slot = Views([slot_cam] * self.B, self.s.tile, dev)
         self.poses = Views(train_cams, self.s.tile, dev)
         self.renderer = Renderer(model.n, model.sh_degree, self.slot, self.s, pair_capacity, dev)
-        t = targets.contiguous()
-        self.targets = t.view(-1)
-        per = t[0].numel()
-        self.target_offsets = torch.arange(self.n_train, dtype=torch.int64, device=dev) * per
+        self.renderer.sizes_on_device = True
+        if isinstance(targets, torch.Tensor):  # one stacked tensor: used in place (no copy)
+            t = targets.contiguous()
+            self.targets = t.view(-1)
+            self.target_offsets = torch.arange(t.shape[0], dtype=torch.int64, device=dev) * t[0].numel()
+        else:
+            sizes = [int(x.numel()) for x in targets]
+            self.targets = torch.cat([x.contiguous().view(-1) for x in targets]).to(dev)
+            self.target_offsets = torch.as_tensor(np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64),
+                                                  device=dev)
         self.seq = torch.as_tensor(np.asarray(view_seq, np.int32), device=dev)
         self.iter = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.view_ids = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.g = torch.zeros(1, dtype=torch.uint8, device=dev)
+        self.view_ids = torch.zeros(self.B, dtype=torch.int32, device=dev)
+        self.g = torch.zeros(self.B, dtype=torch.uint8, device=dev)
         self.any = torch.zeros(1, dtype=torch.int32, device=dev)
         self.gate = Gate(self.n_train, W, beta, eps, rho_lo, dev)
         self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
@@ -58,19 +79,23 @@ class RefinementLoop:
 
     # ---- pieces of one iteration
     def _front(self, s):
-        gsr.call("gs_select_views", gsr.ptr(self.seq), int(self.seq.numel()), gsr.ptr(self.iter), 1,
+        gsr.call("gs_select_views", gsr.ptr(self.seq), int(self.seq.numel()), gsr.ptr(self.iter), self.B,
                  gsr.ptr(self.view_ids), gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), gsr.stream_handle(s))
         self.renderer.forward(self.params, s)
         self.renderer.compute_loss(self.targets, self.target_offsets, self.view_ids, with_grad=False, stream=s)
 
     def _back(self, s, predicated: bool):
+        """predicated: the branch is issued unconditionally and each part checks
+        the device flags; otherwise it runs inside the gate's IF node (any g =
+        1), where only a batch still needs the per-view gate."""
         r = self.renderer
+        gate = self.g if (predicated or self.B > 1) and self.gated else None
         r.loss_backward(self.targets, self.target_offsets, self.view_ids, stream=s)
         if self.fused:
-            r.backward_adam(self.model, self.adam, view_gate=self.g if predicated else None,
-                            do_step=self.any if predicated else None, stream=s)
+            r.backward_adam(self.model, self.adam, view_gate=gate, do_step=self.any if predicated else None,
+                            stream=s)
         else:
-            r.backward(self.params, self.grads, view_gate=self.g if predicated else None, accumulate=False, stream=s)
+            r.backward(self.params, self.grads, view_gate=gate, accumulate=False, stream=s)
             self.adam.step(do_step=self.any if predicated else None, stream=s)
 
     def _update(self, s):
@@ -154,19 +179,21 @@ class RefinementLoop:
         self.gate.reset(self.stream)
 
     def evaluate(self, view_ids=None) -> np.ndarray:
-        """Loss of every training view (or the given ones) with the current parameters."""
-        ids = range(self.n_train) if view_ids is None else view_ids
-        seq = torch.as_tensor(np.asarray(list(ids), np.int32), device=self.model.flat.device)
+        """Loss of every training view (or the given ones) with the current
+        parameters, B views per forward pass."""
+        ids = list(range(self.n_train) if view_ids is None else view_ids)
+        n = len(ids)
+        seq = torch.as_tensor(np.asarray(ids, np.int32), device=self.model.flat.device)
         it = torch.zeros(1, dtype=torch.int64, device=seq.device)
-        vid = torch.zeros(1, dtype=torch.int32, device=seq.device)
-        out = torch.zeros(seq.numel(), dtype=torch.float32, device=seq.device)
+        vid = torch.zeros(self.B, dtype=torch.int32, device=seq.device)
+        out = torch.zeros(n + self.B, dtype=torch.float32, device=seq.device)
         s = self.stream
         with torch.cuda.stream(s):
-            for k in range(seq.numel()):
-                gsr.call("gs_select_views", gsr.ptr(seq), int(seq.numel()), gsr.ptr(it), 1, gsr.ptr(vid),
+            for k in range(0, n, self.B):
+                gsr.call("gs_select_views", gsr.ptr(seq), n, gsr.ptr(it), self.B, gsr.ptr(vid),
                          gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), gsr.stream_handle(s))
                 self.renderer.forward(self.params, s)
                 self.renderer.compute_loss(self.targets, self.target_offsets, vid, stream=s)
-                out[k:k + 1].copy_(self.renderer.loss)
+                out[k:k + self.B].copy_(self.renderer.loss)
         s.synchronize()
-        return out.cpu().numpy()
+        return out[:n].cpu().numpy()
