@@ -50,10 +50,97 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--ref-seconds", type=float, default=150.0, help="budget of the reference arm")
     ap.add_argument("--pre", type=int, default=5000, help="always-backward iterations before the measured loop")
+    ap.add_argument("--c4", action="store_true",
+                    help="batched workload instead of the default line: 8 ring views per iteration at mixed "
+                         "resolutions (640x360 .. 1600x1063), launch shape autotuned; prints its own JSON line")
     ap.add_argument("--stages-once", action="store_true",
                     help="run two eager iterations of every stage on one view of the workload and exit "
                          "(a small, fixed launch sequence for hardware-counter captures)")
     return ap.parse_args()
+
+
+def run_c4(args) -> None:
+    """Batched refinement: B = 8 views per iteration, each of the 200 ring
+    cameras at a resolution drawn from the four C4 sizes; launch shape chosen
+    by the autotuner; gated vs always-backward loops from the same
+    post-pre-phase snapshot (graph replays, CUDA events)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import autotune, build, raster
+    from paper_2603_08997_gb300.refine import RefinementLoop
+
+    build.build()
+    B = 8
+    K = args.steps if args.steps != 5000 else 300
+    pre_iters = args.pre if args.pre != 5000 else 300
+    gt, start, cams, seq = synth.case_c4_ring(n=args.n, n_views=args.views, n_iters=max(K, pre_iters) + 64,
+                                              views_per_step=B)
+    dev = torch.device("cuda", 0)
+    cap = 512 * 1024 * 1024
+    # targets: renders of the ground-truth scene at each camera's own size
+    mgt = raster.GaussianModel.from_scene(gt, dev)
+    targets = []
+    for cam in cams:
+        r = raster.Renderer(args.n, 3, raster.Views([cam], 16, dev), raster.RasterSettings(), 40 * args.n, dev)
+        r.forward(mgt.c_params())
+        targets.append(r.image.view(3, cam.height, cam.width).clone())
+        del r
+    torch.cuda.synchronize()
+    del mgt
+    torch.cuda.empty_cache()
+    model = raster.GaussianModel.from_scene(start, dev)
+    cands = tuple((t, b, 1, 2) for t in (8, 16, 32) for b in (128, 256))
+    st, tune_ms = autotune.autotune(model, cams, targets, candidates=cands, views_per_step=B, reps=2,
+                                    pair_capacity=cap)
+    pre = RefinementLoop(model, cams, targets, synth.pre_sequence(pre_iters * B, args.views), st, gated=False,
+                         pair_capacity=cap, views_per_step=B)
+    pre.capture()
+    for _ in range(pre_iters):
+        pre.step_graph()
+    init = pre.snapshot()
+    pre.close()
+    del pre
+
+    def timed(gated: bool):
+        loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, pair_capacity=cap, views_per_step=B)
+        loop.restore(init)
+        loop.capture()
+        for _ in range(args.warmup):
+            loop.step_graph()
+        loop.restore(init)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(loop.stream)
+        for _ in range(K):
+            loop.step_graph()
+        e1.record(loop.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        final = float(np.mean(loop.evaluate()))
+        gs = loop.gate.read(loop.stream)
+        status = int(loop.renderer.status.item())
+        loop.close()
+        return ms, final, gs, status
+
+    ms_full, loss_full, _, s_full = timed(False)
+    ms_gated, loss_gated, gs, s_gated = timed(True)
+    print(json.dumps({
+        "metric": "batched refinement: iters/s with 8 views per iteration (gated vs always-backward)",
+        "value": K / (ms_gated * 1e-3), "unit": "iters/s", "views_per_s": B * K / (ms_gated * 1e-3),
+        "full_bwd_iters_per_s": K / (ms_full * 1e-3), "gated_speedup": ms_full / ms_gated,
+        "steps": K, "views_per_step": B, "pre_iterations": pre_iters,
+        "gate": {"decisions": gs["t"], "backward_views": gs["b"], "rho_cum": gs["b"] / max(gs["t"], 1)},
+        "final_loss_gated": loss_gated, "final_loss_full": loss_full,
+        "final_loss_rel_diff": (loss_gated - loss_full) / loss_full,
+        "autotuned": {"tile": st.tile, "batch": st.batch, "pixels_per_thread_fwd": st.pixels_per_thread_fwd,
+                      "pixels_per_thread_bwd": st.pixels_per_thread,
+                      "candidates_ms": {f"{t}/{b}/{pf}/{pb}": v for (t, b, pf, pb), v in tune_ms.items()}},
+        "device_status": [s_full, s_gated], "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.n // 1000000}M Gaussians SH3, {args.views} ring views at resolutions drawn "
+                               "from 640x360/980x545/1297x840/1600x1063, 8 views per iteration",
+                   "n_gaussians": args.n}}))
 
 
 def stages_once(args) -> None:
@@ -382,6 +469,9 @@ def main():
         return
     if args.stages_once:
         stages_once(args)
+        return
+    if args.c4:
+        run_c4(args)
         return
 
     import numpy as np

@@ -271,6 +271,25 @@ def case_c4(seed: int = 0, n_views_per_launch: int = 8, n_ring: int = 200):
     return cams, picks.astype(np.int32)
 
 
+def case_c4_ring(seed: int = 0, n: int = 3_000_000, n_views: int = 200, n_iters: int = 500,
+                 views_per_step: int = 8, start_scale: float = 0.2):
+    """Batched workload: the C3 scenes, every ring camera with a resolution drawn
+    from C4_RESOLUTIONS (60 degree horizontal field of view at its width), and
+    a view sequence of n_iters * views_per_step draws.  Returns (ground-truth
+    scene, start scene, cameras, view sequence)."""
+    gt = scene_ball(n, seed, sh_degree=3, opacity_std=1.5)
+    start = perturb_scene(gt, seed + 1, start_scale)
+    rng = np.random.default_rng(seed + 3)
+    res = rng.choice(len(C4_RESOLUTIONS), size=n_views)
+    cams = []
+    for c, r in zip(ring_cameras(n_views, 1297, 840, seed + 2), res):
+        w, h = C4_RESOLUTIONS[int(r)]
+        f = (w / 2.0) / math.tan(math.radians(60.0) / 2.0)
+        cams.append(Camera(c.R.copy(), c.t.copy(), f, f, w / 2.0, h / 2.0, w, h, c.znear))
+    seq = view_sequence(n_iters * views_per_step, n_views, seed)
+    return gt, start, cams, seq
+
+
 def case_c5(seed: int = 0, n: int = 6_000_000, n_views: int = 4):
     scene = scene_ball(n, seed, sh_degree=3, opacity_std=1.5)
     cams = ring_cameras(n_views, 1920, 1080, seed + 2)

@@ -110,3 +110,21 @@ def test_batched_loop_runs_and_gates():
             assert np.isfinite(model.flat.cpu().numpy()).all()
         loop.close()
     assert gpu_util.rel_err(one[1], one[0]) < 1e-6
+
+
+def test_autotune_picks_a_timed_candidate():
+    from paper_2603_08997_gb300 import autotune
+    gpu_util.lib()
+    scene, _, _ = synth.case_c1(n=1500)
+    cams = _cams()
+    rng = np.random.default_rng(6)
+    targets = [torch.from_numpy(rng.uniform(0, 1, (3, h, w)).astype(np.float32)).cuda() for w, h in SIZES]
+    model = raster.GaussianModel.from_scene(scene)
+    cands = ((8, 64, 1, 2), (16, 256, 1, 2), (32, 128, 2, 2))
+    autotune._cache.clear()
+    st, times = autotune.autotune(model, cams, targets, candidates=cands, views_per_step=3, reps=2)
+    assert set(times) == set(cands) and all(np.isfinite(t) and t > 0 for t in times.values())
+    assert (st.tile, st.batch, st.pixels_per_thread_fwd, st.pixels_per_thread) == min(times, key=times.get)
+    st2, times2 = autotune.autotune(model, cams, targets, candidates=cands, views_per_step=3)
+    assert times2 == {} and st2 == st  # cached
+    autotune._cache.clear()
