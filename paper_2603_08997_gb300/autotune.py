@@ -104,9 +104,14 @@ def autotune(model: GaussianModel, cams: list, targets, base: RasterSettings | N
     offs = torch.tensor([sum(sizes[:i]) for i in range(len(sizes))], dtype=torch.int64, device=flat.device)
     times = {}
     for cand in candidates:
-        times[tuple(cand)] = _time_candidate(model, cams, flat, offs, settings_of(base, cand), views_per_step, reps,
-                                             pair_capacity)
+        try:
+            times[tuple(cand)] = _time_candidate(model, cams, flat, offs, settings_of(base, cand), views_per_step,
+                                                 reps, pair_capacity)
+        except gsr.GsError:  # a shape this workload cannot use (e.g. too many tiles per view)
+            times[tuple(cand)] = float("inf")
         torch.cuda.empty_cache()
+    if all(t == float("inf") for t in times.values()):
+        raise RuntimeError("autotune: no candidate launch shape runs this workload")
     best = min(times, key=times.get)
     _cache[key] = list(best)
     save_cache(cache_path)
