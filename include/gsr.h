@@ -324,10 +324,13 @@ typedef struct {
  * gs_param_layout): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
  * p -= lr m_hat / (sqrt(v_hat) + eps); zero_grad != 0 also sets g = 0.
  * dev_step (int64, device) counts executed steps and is incremented.
- * dev_do_step (nullable, int32 device): when it holds 0 nothing changes. */
+ * dev_do_step (nullable, int32 device): when it holds 0 nothing changes.
+ * norms2 (nullable, 2 doubles, device): the step adds sum g^2 and
+ * sum (p_new - p_old)^2 over all scalars to norms2[0] and norms2[1]
+ * (telemetry of gradient and update norms; the caller resets them). */
 gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t n, int32_t sh_degree,
                        const gs_adam_config *cfg /* host */, const int32_t *dev_do_step, int64_t *dev_step,
-                       int32_t zero_grad, cudaStream_t stream);
+                       int32_t zero_grad, double *norms2, cudaStream_t stream);
 
 /* The backward pass and the optimizer step of Algorithm 1 in one call: the
  * adjoint of gs_render_bwd, after which every parameter of the flat buffer
@@ -421,6 +424,14 @@ gs_status gs_graph_destroy(gs_graph graph);
  * than the slot's capacity is the caller's error. */
 gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
                           const gs_camera *pose_src, gs_camera *slots, cudaStream_t stream);
+
+/* Per-iteration log for graph replay: with k = (*iter - 1) mod cap (iter as
+ * advanced by gs_select_views), writes loss_log[k n + j] = loss[j] and
+ * g_log[k n + j] = g[j] for j < n; if norms2 and norm_log are given, also
+ * norm_log[2k .. 2k+1] = norms2[0..1] and then norms2 = 0 (the telemetry of
+ * gs_adam_step for this iteration; 0 when no step ran).  All device memory. */
+gs_status gs_log_step(const int64_t *iter, int32_t n, const float *loss, const uint8_t *g, double *norms2,
+                      float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -20,9 +20,11 @@ __device__ __forceinline__ int group_of(int64_t e, const Groups &G) {
     return ((e - G.o_sh) % G.K3) < 3 ? 4 : 5;
 }
 
+template <bool NORMS>
 __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                                                    float *__restrict__ v, Groups G, gs_adam_config cfg,
-                                                   const int32_t *do_step, const int64_t *step, int zero_grad) {
+                                                   const int32_t *do_step, const int64_t *step, int zero_grad,
+                                                   double *__restrict__ norms2) {
     if (do_step && *do_step == 0) return;
     __shared__ float s_lr[6];
     __shared__ float s_ibc2;
@@ -32,6 +34,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     const float ibc2 = s_ibc2;
     const int64_t nvec = G.total / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float sg = 0.f, sd = 0.f;  // sum of g^2 and of (p_new - p_old)^2 over this thread's scalars
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nvec; c += stride) {
         float4 pp = reinterpret_cast<float4 *>(p)[c];
         const float4 gg = reinterpret_cast<const float4 *>(g)[c];
@@ -40,7 +43,14 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
         float *pe = &pp.x, *me = &mm.x, *ve = &vv.x;
         const float *ge = &gg.x;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) adam_update(pe[u], me[u], ve[u], ge[u], s_lr[group_of(4 * c + u, G)], b1, b2, ibc2, eps);
+        for (int u = 0; u < 4; ++u) {
+            const float p0 = pe[u];
+            adam_update(pe[u], me[u], ve[u], ge[u], s_lr[group_of(4 * c + u, G)], b1, b2, ibc2, eps);
+            if (NORMS) {
+                sg += ge[u] * ge[u];
+                sd += (pe[u] - p0) * (pe[u] - p0);
+            }
+        }
         reinterpret_cast<float4 *>(p)[c] = pp;
         reinterpret_cast<float4 *>(m)[c] = mm;
         reinterpret_cast<float4 *>(v)[c] = vv;
@@ -49,11 +59,38 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     // scalar tail
     for (int64_t e = 4 * nvec + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < G.total; e += stride) {
         float pe = p[e], me = m[e], ve = v[e];
-        adam_update(pe, me, ve, g[e], s_lr[group_of(e, G)], b1, b2, ibc2, eps);
+        const float p0 = pe, ge = g[e];
+        adam_update(pe, me, ve, ge, s_lr[group_of(e, G)], b1, b2, ibc2, eps);
+        if (NORMS) {
+            sg += ge * ge;
+            sd += (pe - p0) * (pe - p0);
+        }
         p[e] = pe;
         m[e] = me;
         v[e] = ve;
         if (zero_grad) g[e] = 0.f;
+    }
+    if (NORMS) {  // block sums, one double atomic per block and quantity
+        __shared__ float s_red[2][8];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sg += __shfl_xor_sync(0xffffffffu, sg, off);
+            sd += __shfl_xor_sync(0xffffffffu, sd, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_red[0][threadIdx.x >> 5] = sg;
+            s_red[1][threadIdx.x >> 5] = sd;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                a += s_red[0][w];
+                b += s_red[1][w];
+            }
+            atomicAdd(norms2, a);
+            atomicAdd(norms2 + 1, b);
+        }
     }
 }
 
@@ -65,7 +102,7 @@ __global__ void adam_count_kernel(const int32_t *do_step, int64_t *step) {
 
 extern "C" gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t n, int32_t sh_degree,
                                   const gs_adam_config *cfg, const int32_t *dev_do_step, int64_t *dev_step,
-                                  int32_t zero_grad, cudaStream_t stream) {
+                                  int32_t zero_grad, double *norms2, cudaStream_t stream) {
     if (!params || !grads || !m || !v || !cfg || !dev_step || n < 0 || sh_degree < 0 || sh_degree > 3)
         return GS_ERR_INVALID_ARG;
     if (((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) & 15) return GS_ERR_INVALID_ARG;
@@ -78,7 +115,12 @@ extern "C" gs_status gs_adam_step(float *params, float *grads, float *m, float *
     if (n > 0) {
         int64_t blocks = ceil_div(G.total / 4 + 1, 256);
         if (blocks > 152 * 8) blocks = 152 * 8;
-        adam_kernel<<<(unsigned)blocks, 256, 0, stream>>>(params, grads, m, v, G, *cfg, dev_do_step, dev_step, zero_grad);
+        if (norms2)
+            adam_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(params, grads, m, v, G, *cfg, dev_do_step,
+                                                                    dev_step, zero_grad, norms2);
+        else
+            adam_kernel<false><<<(unsigned)blocks, 256, 0, stream>>>(params, grads, m, v, G, *cfg, dev_do_step,
+                                                                     dev_step, zero_grad, nullptr);
         GS_TRY_LAUNCH();
     }
     adam_count_kernel<<<1, 1, 0, stream>>>(dev_do_step, dev_step);

@@ -62,9 +62,33 @@ __global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t
     *iter = it + 1;
 }
 
+__global__ void log_step_kernel(const int64_t *iter, int n, const float *loss, const uint8_t *g, double *norms2,
+                                float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap) {
+    const int64_t it = *iter - 1;
+    const int64_t k = ((it % cap) + cap) % cap;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        loss_log[k * n + j] = loss[j];
+        g_log[k * n + j] = g[j];
+    }
+    if (threadIdx.x == 0 && norms2 && norm_log) {
+        norm_log[2 * k] = norms2[0];
+        norm_log[2 * k + 1] = norms2[1];
+        norms2[0] = 0.0;
+        norms2[1] = 0.0;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+gs_status gs_log_step(const int64_t *iter, int32_t n, const float *loss, const uint8_t *g, double *norms2,
+                      float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap, cudaStream_t stream) {
+    if (!iter || n <= 0 || !loss || !g || !loss_log || !g_log || cap <= 0) return GS_ERR_INVALID_ARG;
+    log_step_kernel<<<1, 32, 0, stream>>>(iter, n, loss, g, norms2, loss_log, g_log, norm_log, cap);
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}
 
 gs_status gs_graph_begin(cudaStream_t stream) {
     if (!stream) return GS_ERR_INVALID_ARG;  // the legacy default stream cannot be captured

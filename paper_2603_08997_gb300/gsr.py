@@ -96,7 +96,8 @@ _PROTOS = {
     "gs_render_bwd_adam": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(gs_projected), _P, _P, _P, _I32, _I64,
                                      C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, C.POINTER(gs_adam_config), _P,
                                      _P, _P, _SZ, _P, _S]),
-    "gs_adam_step": (C.c_int, [_P, _P, _P, _P, _I64, _I32, C.POINTER(gs_adam_config), _P, _P, _I32, _S]),
+    "gs_adam_step": (C.c_int, [_P, _P, _P, _P, _I64, _I32, C.POINTER(gs_adam_config), _P, _P, _I32, _P, _S]),
+    "gs_log_step": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P, _I64, _S]),
     "skipgs_gate_state_size": (C.c_size_t, [_I32]),
     "skipgs_gate_init": (C.c_int, [C.POINTER(gs_gate_config), _P, _S]),
     "skipgs_gate_decide": (C.c_int, [_P, _P, _P, _I32, _P, _P, C.POINTER(C.c_uint64), _P, _S]),

@@ -287,11 +287,14 @@ class AdamState:
             self.cfg.lr[i] = float(lr[i])
         self.cfg.beta1, self.cfg.beta2, self.cfg.eps = float(beta1), float(beta2), float(eps)
 
-    def step(self, do_step: torch.Tensor | None = None, zero_grad: bool = False, stream=None) -> None:
+    def step(self, do_step: torch.Tensor | None = None, zero_grad: bool = False, norms2: torch.Tensor | None = None,
+             stream=None) -> None:
+        """norms2: optional float64[2] device tensor that receives sum g^2 and
+        sum (p_new - p_old)^2 of this step (added to it)."""
         m = self.model
         gsr.call("gs_adam_step", gsr.ptr(m.flat), gsr.ptr(self.grad), gsr.ptr(self.m), gsr.ptr(self.v), m.n,
                  m.sh_degree, C.byref(self.cfg), gsr.ptr(do_step), gsr.ptr(self.step_count), int(bool(zero_grad)),
-                 gsr.stream_handle(stream))
+                 gsr.ptr(norms2), gsr.stream_handle(stream))
 
 
 class Gate:

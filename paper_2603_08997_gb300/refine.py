@@ -34,7 +34,7 @@ class RefinementLoop:
     def __init__(self, model: GaussianModel, train_cams: list, targets, view_seq,
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
-                 fused: bool = False, views_per_step: int = 1):
+                 fused: bool = False, views_per_step: int = 1, log_capacity: int = 0):
         """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
         [3, H_v, W_v] tensors, one per training view."""
         import copy
@@ -75,7 +75,16 @@ class RefinementLoop:
         self.stream = torch.cuda.Stream(device=dev)
         self.body_stream = torch.cuda.Stream(device=dev)
         self.graph = None
-        self.loss_log = None
+        # per-iteration log (losses, decisions, gradient and update norms), filled
+        # on the device inside the step; log_capacity iterations, then it wraps
+        self.log_cap = int(log_capacity)
+        if self.log_cap > 0:
+            self.loss_log = torch.zeros(self.log_cap * self.B, dtype=torch.float32, device=dev)
+            self.g_log = torch.zeros(self.log_cap * self.B, dtype=torch.uint8, device=dev)
+            self.norm_log = torch.zeros(2 * self.log_cap, dtype=torch.float64, device=dev)
+            self.norms2 = torch.zeros(2, dtype=torch.float64, device=dev)
+        else:
+            self.loss_log = self.g_log = self.norm_log = self.norms2 = None
 
     # ---- pieces of one iteration
     def _front(self, s):
@@ -96,10 +105,26 @@ class RefinementLoop:
                             stream=s)
         else:
             r.backward(self.params, self.grads, view_gate=gate, accumulate=False, stream=s)
-            self.adam.step(do_step=self.any if predicated else None, stream=s)
+            self.adam.step(do_step=self.any if predicated else None, norms2=self.norms2, stream=s)
 
     def _update(self, s):
         self.gate.update(self.view_ids, self.renderer.loss, stream=s)
+        if self.log_cap > 0:
+            gsr.call("gs_log_step", gsr.ptr(self.iter), self.B, gsr.ptr(self.renderer.loss), gsr.ptr(self.g),
+                     gsr.ptr(self.norms2), gsr.ptr(self.loss_log), gsr.ptr(self.g_log), gsr.ptr(self.norm_log),
+                     self.log_cap, gsr.stream_handle(s))
+
+    def read_log(self, iters: int) -> dict:
+        """The last `iters` (<= log_capacity) logged iterations, oldest first:
+        losses [iters, B], decisions [iters, B], sum g^2 and sum dp^2 [iters]."""
+        assert 0 < iters <= self.log_cap
+        torch.cuda.synchronize()
+        it = int(self.iter.item())
+        idx = [(k % self.log_cap) for k in range(it - iters, it)]
+        L = self.loss_log.view(self.log_cap, self.B).cpu().numpy()[idx]
+        G = self.g_log.view(self.log_cap, self.B).cpu().numpy()[idx]
+        Nm = self.norm_log.view(self.log_cap, 2).cpu().numpy()[idx]
+        return dict(loss=L, g=G, grad_sq=Nm[:, 0], update_sq=Nm[:, 1])
 
     # ---- eager
     def step_eager(self) -> None:

@@ -265,3 +265,21 @@ def test_backward_mixed_pixels_per_thread():
         res.append(g.cpu().numpy())
     for g in res[1:]:
         assert gpu_util.rel_err(g, res[0]) < 1e-6
+
+
+def test_adam_norms_telemetry():
+    """gs_adam_step's optional norms: sum g^2 and sum (p_new - p_old)^2."""
+    gpu_util.lib()
+    scene, _ = synth.scene_tiny(500, seed=9, sh_degree=3)
+    model = raster.GaussianModel.from_scene(scene)
+    adam = raster.AdamState(model)
+    rng = np.random.default_rng(1)
+    adam.grad.copy_(torch.from_numpy(rng.normal(0, 1e-3, adam.grad.numel()).astype(np.float32)))
+    g = adam.grad.double().clone()
+    p0 = model.flat.double().clone()
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    adam.step(norms2=norms)
+    torch.cuda.synchronize()
+    want = [float((g * g).sum()), float(((model.flat.double() - p0) ** 2).sum())]
+    got = norms.cpu().numpy()
+    assert abs(got[0] - want[0]) <= 1e-5 * want[0] and abs(got[1] - want[1]) <= 1e-4 * want[1]
