@@ -51,7 +51,7 @@ def test_loop_decisions_replay_bit_exact(B):
     targets = _targets(gt, cams, raster, dev)
     model = raster.GaussianModel.from_scene(start, dev)
     W = 500 if B == 1 else 300
-    loop = RefinementLoop(model, cams, targets, seq, gated=True, W=W, views_per_step=B, pair_capacity=24 * gt.n,
+    loop = RefinementLoop(model, cams, targets, seq, gated=True, W=W, views_per_step=B, pair_capacity=24 * gt.n * B,
                           log_capacity=ITERS)
     loop.capture()
     for _ in range(ITERS):
