@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--c4", action="store_true",
                     help="batched workload instead of the default line: 8 ring views per iteration at mixed "
                          "resolutions (640x360 .. 1600x1063), launch shape autotuned; prints its own JSON line")
+    ap.add_argument("--rho-sweep", action="store_true",
+                    help="NEXT-1: gated loop for rho_lo in (no budget, 0.3, 0.5, 0.7, 0.9) against the "
+                         "always-backward loop; prints its own JSON line")
     ap.add_argument("--stages-once", action="store_true",
                     help="run two eager iterations of every stage on one view of the workload and exit "
                          "(a small, fixed launch sequence for hardware-counter captures)")
@@ -141,6 +144,100 @@ def run_c4(args) -> None:
         "config": {"workload": f"{args.n // 1000000}M Gaussians SH3, {args.views} ring views at resolutions drawn "
                                "from 640x360/980x545/1297x840/1600x1063, 8 views per iteration",
                    "n_gaussians": args.n}}))
+
+
+def setup_c3(args, dev):
+    """The C3 workload: ground-truth targets rendered on the GPU, the start
+    scene, and the untimed always-backward pre-phase (stand-in for
+    densification) whose end state both timed loops start from.  Returns
+    (model, cameras, targets, view sequence, snapshot, settings, capacity,
+    start scene)."""
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import raster
+    from paper_2603_08997_gb300.refine import RefinementLoop
+
+    seq_len = max(args.steps, 5000)
+    gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=seq_len,
+                                         width=args.width, height=args.height)
+    st = raster.RasterSettings()
+    cap = 24 * args.n
+    # targets: renders of the ground-truth scene (device-resident)
+    mgt = raster.GaussianModel.from_scene(gt, dev)
+    slot = raster.Views([cams[0]], st.tile, dev)
+    rgt = raster.Renderer(args.n, 3, slot, st, cap, dev)
+    targets = torch.empty((args.views, 3, args.height, args.width), dtype=torch.float32, device=dev)
+    for v, cam in enumerate(cams):
+        rgt.views = raster.Views([cam], st.tile, dev)
+        rgt.forward(mgt.c_params())
+        targets[v].copy_(rgt.image.view(3, args.height, args.width))
+    torch.cuda.synchronize()
+    del mgt, rgt
+    model = raster.GaussianModel.from_scene(start, dev)
+    # the measured loops start from the pre-phase's end state, parameters and
+    # Adam moments carried over
+    pre = RefinementLoop(model, cams, targets, synth.pre_sequence(max(args.pre, 1), args.views), st,
+                         gated=False, pair_capacity=cap)
+    pre.capture()
+    for _ in range(args.pre):
+        pre.step_graph()
+    init = pre.snapshot()
+    pre.close()
+    del pre
+    return model, cams, targets, seq, init, st, cap, start
+
+
+def run_rho_sweep(args) -> None:
+    """NEXT-1: the gated loop from the same snapshot for several budget floors
+    rho_lo (rho_lo < 0: no budget, Table 4's ablation): realised rho_cum,
+    iterations/s and final loss, plus the always-backward reference; the
+    gated runs log the per-iteration gradient and update norms."""
+    import numpy as np
+    import torch
+
+    from paper_2603_08997_gb300 import build
+    from paper_2603_08997_gb300.refine import RefinementLoop
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    model, cams, targets, seq, init, st, cap, _ = setup_c3(args, dev)
+    K = args.steps
+
+    def run(gated: bool, rho_lo: float):
+        loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, rho_lo=rho_lo, pair_capacity=cap,
+                              log_capacity=K)
+        loop.restore(init)
+        loop.capture()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(loop.stream)
+        for _ in range(K):
+            loop.step_graph()
+        e1.record(loop.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        log = loop.read_log(K)
+        final = float(np.mean(loop.evaluate()))
+        gs = loop.gate.read(loop.stream)
+        loop.close()
+        tenth = max(1, K // 10)
+        stepped = log["g"][:, 0] > 0
+        gn = np.sqrt(log["grad_sq"][stepped]) if stepped.any() else np.zeros(1)
+        un = np.sqrt(log["update_sq"][stepped]) if stepped.any() else np.zeros(1)
+        return {"rho_lo": rho_lo if gated else None, "gated": gated, "iters_per_s": K / (ms * 1e-3),
+                "rho_cum": gs["b"] / max(gs["t"], 1), "rho_min": gs["rho_min"], "final_loss": final,
+                "grad_norm_first_tenth": float(np.mean(gn[:tenth])), "grad_norm_last_tenth": float(np.mean(gn[-tenth:])),
+                "update_norm_first_tenth": float(np.mean(un[:tenth])),
+                "update_norm_last_tenth": float(np.mean(un[-tenth:]))}
+
+    rows = [run(False, 0.5)] + [run(True, r) for r in (-1.0, 0.3, 0.5, 0.7, 0.9)]
+    full = rows[0]
+    for r in rows[1:]:
+        r["speedup"] = r["iters_per_s"] / full["iters_per_s"]
+        r["final_loss_rel_diff"] = (r["final_loss"] - full["final_loss"]) / full["final_loss"]
+    print(json.dumps({"metric": "rho_lo sweep of the gated refinement loop (NEXT-1)", "steps": K,
+                      "workload": WORKLOAD, "rows": rows}))
 
 
 def stages_once(args) -> None:
@@ -473,6 +570,9 @@ def main():
     if args.c4:
         run_c4(args)
         return
+    if args.rho_sweep:
+        run_rho_sweep(args)
+        return
 
     import numpy as np
     import torch
@@ -489,35 +589,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     K, W = args.steps, args.warmup
-    seq_len = max(K, 5000)
-    gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=seq_len,
-                                         width=args.width, height=args.height)
     dev = torch.device("cuda", local)
-    st = raster.RasterSettings()
-    cap = 24 * args.n
-    # targets: renders of the ground-truth scene (device-resident)
-    mgt = raster.GaussianModel.from_scene(gt, dev)
-    slot = raster.Views([cams[0]], st.tile, dev)
-    rgt = raster.Renderer(args.n, 3, slot, st, cap, dev)
-    targets = torch.empty((args.views, 3, args.height, args.width), dtype=torch.float32, device=dev)
-    for v, cam in enumerate(cams):
-        one = raster.Views([cam], st.tile, dev)
-        rgt.views = one
-        rgt.forward(mgt.c_params())
-        targets[v].copy_(rgt.image.view(3, args.height, args.width))
-    torch.cuda.synchronize()
-    del mgt, rgt
-    model = raster.GaussianModel.from_scene(start, dev)
-    # untimed pre-phase (stand-in for densification): the measured loop starts
-    # from its end state, parameters and Adam moments carried over
-    pre = RefinementLoop(model, cams, targets, synth.pre_sequence(max(args.pre, 1), args.views), st,
-                         gated=False, pair_capacity=cap)
-    pre.capture()
-    for _ in range(args.pre):
-        pre.step_graph()
-    init = pre.snapshot()
-    pre.close()
-    del pre
+    model, cams, targets, seq, init, st, cap, start = setup_c3(args, dev)
 
     def timed_loop(gated: bool):
         loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, pair_capacity=cap)
