@@ -210,15 +210,24 @@ def run_rho_sweep(args) -> None:
         loop.restore(init)
         loop.capture()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(loop.stream)
-        for _ in range(K):
-            loop.step_graph()
-        e1.record(loop.stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        log = loop.read_log(K)
-        final = float(np.mean(loop.evaluate()))
+        # timed in segments ending at the final-loss checkpoints K-3s .. K (as
+        # the headline loops); the evaluations between segments are not timed
+        seg = max(1, min(250, K // 4))
+        marks = sorted({m for m in (K - 3 * seg, K - 2 * seg, K - seg, K) if m > 0})
+        ms, done, evals = 0.0, 0, []
+        for mark in marks:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(loop.stream)
+            for _ in range(mark - done):
+                loop.step_graph()
+            e1.record(loop.stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done = mark
+            if mark == K:
+                log = loop.read_log(K)
+            evals.append(float(np.mean(loop.evaluate())))
+        final = float(np.mean(evals))
         gs = loop.gate.read(loop.stream)
         loop.close()
         tenth = max(1, K // 10)
