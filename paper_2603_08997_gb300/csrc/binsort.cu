@@ -574,6 +574,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     __shared__ ushort4 s_er[WIN];    // the window's rectangles
     __shared__ uint32_t s_eg[WIN];   // Gaussian indices
     __shared__ int s_pre[WIN + 1];   // first pair of each entry
+    __shared__ uint32_t s_tj[SC_THREADS * SC_Q];  // first sub-window: (tile << 8 | entry) per pair
     __shared__ uint32_t s_warp[32];
     if (*sort_count == 0) return;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
@@ -607,9 +608,8 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
         if (threadIdx.x == 0) s_pre[WIN] = (int)tot_u;
         __syncthreads();
         const int tot = (int)tot_u;
-        // pass A: entry masks per tile (the walk's start in the first
-        // sub-window is kept for pass B)
-        PairWalk first;
+        // pass A: entry masks per tile (the first sub-window's pairs are also
+        // recorded for pass B)
         for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
             const int cnt = min(SC_THREADS * SC_Q, tot - sw);
             const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
@@ -617,9 +617,9 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             if (p0 < p1) {
                 PairWalk it;
                 it.start(p0, s_pre, s_er, WIN, vt.tx);
-                if (sw == 0) first = it;
                 for (int p = p0;; ++p) {
                     atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
+                    if (sw == 0) s_tj[p] = ((uint32_t)it.t << 8) | (uint32_t)it.jj;  // for pass B
                     if (p + 1 >= p1) break;
                     it.next(p, s_pre, s_er, vt.tx);
                 }
@@ -637,30 +637,34 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             for (int k = 0; k < SC_Q; ++k) last_t[k] = -1;
             if (p0 < p1) {
                 PairWalk it;
-                if (sw == 0) it = first; else it.start(p0, s_pre, s_er, WIN, vt.tx);
+                if (sw != 0) it.start(p0, s_pre, s_er, WIN, vt.tx);
 #pragma unroll
                 for (int k = 0; k < SC_Q; ++k) {
                     const int p = p0 + k;
                     if (p >= p1) break;
-                    if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
-                    const int jw = it.jj / WB, jb = it.jj % WB;
+                    int t, jj;
+                    if (sw == 0) {  // the first sub-window's pairs were recorded by pass A
+                        const uint32_t tj = s_tj[p];
+                        t = (int)(tj >> 8);
+                        jj = (int)(tj & 0xffu);
+                    } else {
+                        if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
+                        t = it.t;
+                        jj = it.jj;
+                    }
+                    const int jw = jj / WB, jb = jj % WB;
                     uint32_t below = 0, all = 0;
-                    bool higher = false;
 #pragma unroll
                     for (int wd = 0; wd < NW; ++wd) {
-                        const W m = s_mask[it.t * NW + wd];
+                        const W m = s_mask[t * NW + wd];
                         const uint32_t pc = (uint32_t)__popc((uint32_t)m);
                         all += pc;
                         if (wd < jw) below += pc;
-                        if (wd == jw) {
-                            below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
-                            higher |= (jb + 1 < WB) && (m >> (jb + 1)) != 0;
-                        }
-                        if (wd > jw) higher |= m != 0;
+                        if (wd == jw) below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
                     }
-                    vals[s_off[it.t] + below] = s_eg[it.jj];
-                    if (!higher) {
-                        last_t[k] = it.t;
+                    vals[s_off[t] + below] = s_eg[jj];
+                    if (below + 1 == all) {  // the tile's last pair of the window
+                        last_t[k] = t;
                         last_n[k] = all;
                     }
                 }
