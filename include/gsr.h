@@ -121,6 +121,9 @@ typedef struct {
     float *rec;              /* [V*N][12] */
     int32_t *rect;           /* [V*N][4]  */
     int32_t *tiles_touched;  /* [V*N]     */
+    uint32_t *depth_key;     /* [V*N] or NULL: float32 bits of the depth, 0xffffffff when culled */
+    uint16_t *rect16;        /* [V*N][4] or NULL (8-byte aligned): rect as (x0, y0, width, height) in tiles,
+                                all 0 when culled */
 } gs_projected;
 
 /* State the forward pass saves for the backward pass (caller-owned):
@@ -190,7 +193,9 @@ size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capac
  * clipped to the view's tile grid; entries with tiles_touched <= 0 emit
  * nothing.  More pairs than pair_capacity: GS_ERR_CAPACITY in dev_status,
  * the full count in *dev_pair_count, ranges left empty, vals untouched.
- * Only the tile geometry of cams is read. */
+ * Only the tile geometry of cams is read.  If proj->depth_key and
+ * proj->rect16 are set (written by gs_project with the same cfg) the sort
+ * reads them instead of deriving them from rec, rect and tiles_touched. */
 gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n,
                       int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg /* host */,
                       void *workspace, size_t workspace_bytes, uint64_t *keys, uint32_t *vals,

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             const int li = warp * 32 * RS_ITEMS + r * 32 + lane;
             const bool valid = li < n_tile;
             k[r] = valid ? keys_in[base + li] : 0u;
-            v[r] = valid ? vals_in[base + li] : 0u;
+            v[r] = valid ? (vals_in ? vals_in[base + li] : (uint32_t)(base + li)) : 0u;  // no values: the index
             const int d = valid ? (int)((k[r] >> shift) & mask) : RADIX + lane;
             // lanes with the same digit: intersect one ballot per digit bit
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -223,14 +223,22 @@ int rs_blocks(int64_t cap) {
 // Stable LSD sort of (key, value) pairs on the low `bits` bits of the keys.
 // Ping-pongs between (ka, va) and (kb, vb); returns 0 when the result is in
 // (ka, va), 1 when it is in (kb, vb).
+// If k0 is given, the first pass reads its keys from k0 (left unchanged) with
+// each key's index as its value, instead of from (ka, va).
 int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int64_t *d_count, int64_t cap,
-               int bits, uint32_t *counts, cudaStream_t stream) {
+               int bits, uint32_t *counts, cudaStream_t stream, const uint32_t *k0 = nullptr) {
     const int G = rs_blocks(cap);
     int cur = 0;
     for (int shift = 0; shift < bits; shift += RADIX_BITS) {
         const int nb = bits - shift < RADIX_BITS ? bits - shift : RADIX_BITS;
         const uint32_t mask = (1u << nb) - 1u;
-        uint32_t *ki = cur ? kb : ka, *vi = cur ? vb : va, *ko = cur ? ka : kb, *vo = cur ? va : vb;
+        const uint32_t *ki = cur ? kb : ka;
+        const uint32_t *vi = cur ? vb : va;
+        if (shift == 0 && k0) {
+            ki = k0;
+            vi = nullptr;
+        }
+        uint32_t *ko = cur ? ka : kb, *vo = cur ? va : vb;
         uint32_t *totals = counts + (size_t)RADIX * RS_MAX_BLOCKS;
         rs_upsweep<<<G, RS_THREADS, 0, stream>>>(ki, d_count, cap, shift, mask, counts);
         rs_scan<<<RADIX, RS_THREADS, 0, stream>>>(counts, G, totals);
@@ -349,6 +357,15 @@ __global__ void bin_rects(const int4 *__restrict__ rect, const int32_t *__restri
 // (ty + 1) grid, and prefix sums along rows, then columns, give every tile the
 // number of the chunk's rectangles covering it (four shared atomics per entry
 // instead of one per pair, and no divergence on large rectangles).
+// The same from the packed rectangles gs_project wrote (already clipped).
+__global__ void bin_rects16(const ushort4 *__restrict__ rect16, const uint32_t *__restrict__ order,
+                            const gs_camera *__restrict__ cams, BinGeom g, int64_t total, ushort4 *__restrict__ srect) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const ViewTiles vt = view_tiles(cams[i / g.n], g.tile);
+    srect[i] = view_fits(vt, g.tiles, g.max_vt) ? rect16[order[i]] : make_ushort4(0, 0, 0, 0);
+}
+
 __global__ void __launch_bounds__(COUNT_THREADS) bin_count(const ushort4 *__restrict__ srect,
                                                            const gs_camera *__restrict__ cams, BinGeom g,
                                                            uint32_t *__restrict__ M, uint32_t *__restrict__ G1,
@@ -826,10 +843,15 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     }
     const BinGeom g = bin_geom(n, total_tiles, cfg->tile, (int)mvt);
     // 1. depth order of all (view, Gaussian) entries, then grouped by view
-    depth_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(proj->rec, proj->tiles_touched, total,
-                                                                         w.dk[0], w.dv[0]);
-    GS_TRY_LAUNCH();
-    int sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream);
+    int sel;
+    if (proj->depth_key) {  // written by gs_project
+        sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream, proj->depth_key);
+    } else {
+        depth_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(proj->rec, proj->tiles_touched, total,
+                                                                             w.dk[0], w.dv[0]);
+        GS_TRY_LAUNCH();
+        sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream);
+    }
     GS_TRY_LAUNCH();
     if (n_views > 1) {
         view_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(w.dv[sel], total, n, w.dk[sel]);
@@ -843,8 +865,12 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     // 2. counting sort of the pairs by tile, in depth order
     const size_t smem = sizeof(uint32_t) * (size_t)mvt;
     GS_TRY(bin_smem_attributes());
-    bin_rects<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(rect, proj->tiles_touched, order, cams, g, total,
-                                                                 w.srect);
+    if (proj->rect16)  // written by gs_project
+        bin_rects16<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(
+            reinterpret_cast<const ushort4 *>(proj->rect16), order, cams, g, total, w.srect);
+    else
+        bin_rects<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(rect, proj->tiles_touched, order, cams, g,
+                                                                     total, w.srect);
     GS_TRY_LAUNCH();
     GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
     const unsigned n_chunks = (unsigned)(g.n_c * n_views);

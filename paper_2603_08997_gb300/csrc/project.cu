@@ -10,7 +10,9 @@ namespace {
 template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_camera *__restrict__ cams,
                                                       gs_raster_config cfg, float *__restrict__ rec,
-                                                      int4 *__restrict__ rect, int32_t *__restrict__ touched) {
+                                                      int4 *__restrict__ rect, int32_t *__restrict__ touched,
+                                                      uint32_t *__restrict__ depth_key,
+                                                      ushort4 *__restrict__ rect16) {
     __shared__ gs_camera s_cam;
     const int v = blockIdx.y;
     if (threadIdx.x == 0) s_cam = cams[v];
@@ -54,6 +56,8 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
         out[2] = make_float4(0.f, __int_as_float(0x7f800000), 0.f, 0.f);
         rect[e] = make_int4(0, 0, -1, -1);
         touched[e] = 0;
+        if (depth_key) depth_key[e] = 0xffffffffu;  // culled entries sort last
+        if (rect16) rect16[e] = make_ushort4(0, 0, 0, 0);
         return;
     }
     // conic factor U with Q = U^T U (upper Cholesky of Sigma2D^-1)
@@ -92,6 +96,10 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
     out[2] = make_float4(fmaxf(col[2], 0.f), g.p[2], rx, ry);
     rect[e] = make_int4(x0, y0, x1, y1);
     touched[e] = (x1 - x0 + 1) * (y1 - y0 + 1);
+    if (depth_key) depth_key[e] = __float_as_uint(g.p[2]);  // positive depth: bit order = value order
+    if (rect16)
+        rect16[e] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)(x1 - x0 + 1),
+                                 (unsigned short)(y1 - y0 + 1));
 }
 
 }  // namespace
@@ -159,11 +167,13 @@ gs_status gs_project(const gs_params *params, const gs_camera *cams, int32_t n_v
     if ((K3 % 4 == 0) && ((uintptr_t)params->sh & 15)) return GS_ERR_INVALID_ARG;
     dim3 grid((unsigned)ceil_div(params->n, 256), (unsigned)n_views);
     int4 *rect = reinterpret_cast<int4 *>(out.rect);
+    if ((uintptr_t)out.rect16 & 7) return GS_ERR_INVALID_ARG;
+    ushort4 *r16 = reinterpret_cast<ushort4 *>(out.rect16);
     switch (params->sh_degree) {
-        case 0: project_kernel<0><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched); break;
-        case 1: project_kernel<1><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched); break;
-        case 2: project_kernel<2><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched); break;
-        default: project_kernel<3><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched); break;
+        case 0: project_kernel<0><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
+        case 1: project_kernel<1><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
+        case 2: project_kernel<2><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
+        default: project_kernel<3><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
     }
     GS_TRY_LAUNCH();
     return GS_OK;

@@ -46,7 +46,8 @@ class gs_grads(C.Structure):
 
 
 class gs_projected(C.Structure):
-    _fields_ = [("rec", C.c_void_p), ("rect", C.c_void_p), ("tiles_touched", C.c_void_p)]
+    _fields_ = [("rec", C.c_void_p), ("rect", C.c_void_p), ("tiles_touched", C.c_void_p), ("depth_key", C.c_void_p),
+                ("rect16", C.c_void_p)]
 
 
 class gs_fwd_saved(C.Structure):

@@ -146,6 +146,11 @@ class Renderer:
         self.rec = torch.empty(V * n * 12, dtype=torch.float32, device=dev)
         self.rect = torch.empty(V * n * 4, dtype=torch.int32, device=dev)
         self.touched = torch.empty(V * n, dtype=torch.int32, device=dev)
+        # depth keys and packed rectangles written by gs_project for gs_bin_sort;
+        # valid only after project() (records set by other means clear the flag)
+        self.depth_key = torch.empty(V * n, dtype=torch.int32, device=dev)
+        self.rect16 = torch.empty(V * n * 4, dtype=torch.int16, device=dev)
+        self.aux_valid = False
         self.vals = torch.empty(max(self.cap, 1), dtype=torch.int32, device=dev)
         self.keys = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev) if keep_keys else None
         self.ranges = torch.empty(2 * T, dtype=torch.int32, device=dev)
@@ -168,9 +173,11 @@ class Renderer:
         self.loss = torch.zeros(V, dtype=torch.float32, device=dev)
 
     # --- structs
-    def c_proj(self) -> gsr.gs_projected:
+    def c_proj(self, with_aux: bool | None = None) -> gsr.gs_projected:
         p = gsr.gs_projected()
         p.rec, p.rect, p.tiles_touched = self.rec.data_ptr(), self.rect.data_ptr(), self.touched.data_ptr()
+        if self.aux_valid if with_aux is None else with_aux:
+            p.depth_key, p.rect16 = self.depth_key.data_ptr(), self.rect16.data_ptr()
         return p
 
     def c_saved(self) -> gsr.gs_fwd_saved:
@@ -183,7 +190,8 @@ class Renderer:
     # --- pipeline steps (each one C-ABI call)
     def project(self, params: gsr.gs_params, stream=None) -> None:
         gsr.call("gs_project", C.byref(params), gsr.ptr(self.views.dev), self.views.n, C.byref(self.cfg),
-                 self.c_proj(), gsr.ptr(self.status), gsr.stream_handle(stream))
+                 self.c_proj(with_aux=True), gsr.ptr(self.status), gsr.stream_handle(stream))
+        self.aux_valid = True
 
     def bin_sort(self, stream=None) -> None:
         proj = self.c_proj()

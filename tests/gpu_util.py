@@ -82,6 +82,7 @@ def set_projected(renderer: raster.Renderer, dev: dict) -> None:
     renderer.rec.copy_(dev["rec"])
     renderer.rect.copy_(dev["rect"])
     renderer.touched.copy_(dev["touched"])
+    renderer.aux_valid = False  # bin_sort derives depth keys and rectangles from these records
 
 
 def rel_err(a, b) -> float:

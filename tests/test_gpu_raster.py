@@ -252,3 +252,22 @@ def test_tile_order_is_a_permutation_by_work_and_changes_nothing():
             assert np.all(np.diff(group) <= 0)
     for a, b in zip(*out):
         assert torch.equal(a, b)
+
+
+def test_bin_sort_from_projection_keys_equals_from_records():
+    """gs_bin_sort reading the depth keys and packed rectangles gs_project
+    wrote gives the same pairs and ranges as deriving them from the records."""
+    scene, _, cam, _ = synth.case_c2(n=50_000)
+    r = _renderer([cam], scene.n, sh_degree=3)
+    model = raster.GaussianModel.from_scene(scene)
+    r.project(model.c_params())
+    out = []
+    for aux in (True, False):
+        r.aux_valid = aux
+        r.bin_sort()
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        out.append(_sorted_pairs(r))
+    assert out[0][0] == out[1][0] > 0
+    for a, b in zip(out[0][1:], out[1][1:]):
+        assert np.array_equal(a, b)
