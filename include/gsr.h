@@ -96,8 +96,8 @@ typedef struct {
  * floor (a pixel stops before a Gaussian that would take T below it);
  * bg: background colour added with the final transmittance; tile: 8, 16 or
  * 32 (pixels per tile side); batch: Gaussians staged in shared memory per step
- * (64, 128 or 256); sh_degree: 0..3; pixels_per_thread: 1 or 2 (block shape of
- * the compositing kernels; results do not depend on it). */
+ * (64, 128 or 256); sh_degree: 0..3; pixels_per_thread: 1, 2, or 4 with tile
+ * >= 16 (block shape of the compositing kernels; results do not depend on it). */
 typedef struct {
     float lowpass, alpha_max, alpha_min, t_min;
     float bg[3];

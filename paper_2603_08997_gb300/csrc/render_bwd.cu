@@ -1,6 +1,6 @@
 // gs_render_bwd: analytic adjoint of gs_render_fwd and gs_project.
 //
-// Raster adjoint (one CTA per tile, PPT = 1 or 2 pixels per thread; each
+// Raster adjoint (one CTA per tile, PPT = 1, 2 or 4 pixels per thread; each
 // warp walks only the staged records whose support box reaches its pixel
 // block, marked per batch with one ballot per warp and 32 records).  With
 // A_k = sum_{j>k} c_j a_j T_j + T_end bg (the colour behind contributor k),
@@ -637,6 +637,8 @@ gs_status launch_bwd_ppt(int ppt, int batch, int64_t total_tiles, cudaStream_t s
                          const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
                          const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate,
                          float4 *g2d) {
+    if constexpr (TILE >= 16)
+        if (ppt == 4) return launch_bwd<TILE, 4>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
     if (ppt == 2) return launch_bwd<TILE, 2>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
     return launch_bwd<TILE, 1>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
 }
@@ -685,7 +687,8 @@ gs_status raster_bwd_impl(int64_t n, const gs_projected *proj, const uint32_t *v
     GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
     const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2) return GS_ERR_INVALID_ARG;
+    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2 && cfg->pixels_per_thread != 4) return GS_ERR_INVALID_ARG;
+    if (cfg->pixels_per_thread == 4 && cfg->tile < 16) return GS_ERR_INVALID_ARG;  // a warp needs 8 x 16 pixels
     switch (cfg->tile) {
         case 8: return launch_bwd_ppt<8>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
         case 16: return launch_bwd_ppt<16>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);

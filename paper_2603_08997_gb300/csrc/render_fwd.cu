@@ -1,6 +1,6 @@
 // gs_render_fwd: Eq. (blend) / Eq. (alpha), front-to-back compositing.
 //
-// One CTA per tile, PPT pixels per thread (1 or 2), each warp an 8 x 4 PPT
+// One CTA per tile, PPT pixels per thread (1, 2 or 4), each warp an 8 x 4 PPT
 // pixel block.  The tile's depth-ordered list is
 // consumed `BATCH` Gaussians at a time: the CTA gathers the batch's packed
 // records into shared memory (one coalesced 48-byte record per Gaussian) and
@@ -173,6 +173,8 @@ template <int TILE>
 gs_status launch_fwd_ppt(int ppt, int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
                          const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
                          const gs_raster_config &cfg, float *image, gs_fwd_saved s) {
+    if constexpr (TILE >= 16)
+        if (ppt == 4) return launch_fwd<TILE, 4>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
     if (ppt == 2) return launch_fwd<TILE, 2>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
     return launch_fwd<TILE, 1>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
 }
@@ -192,7 +194,8 @@ extern "C" gs_status gs_render_fwd(const gs_projected *proj, int64_t n, const ui
     if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
     const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2) return GS_ERR_INVALID_ARG;
+    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2 && cfg->pixels_per_thread != 4) return GS_ERR_INVALID_ARG;
+    if (cfg->pixels_per_thread == 4 && cfg->tile < 16) return GS_ERR_INVALID_ARG;  // a warp needs 8 x 16 pixels
     switch (cfg->tile) {
         case 8: return launch_fwd_ppt<8>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
         case 16: return launch_fwd_ppt<16>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
