@@ -198,13 +198,13 @@ def test_render_end_to_end_c2_like():
 def test_pixels_per_thread_is_bit_invariant(tile):
     """The per-pixel arithmetic does not depend on how pixels map to threads:
     images, final transmittance, last-contributor counts and checkpoints are
-    bit-identical for 1 and 2 pixels per thread."""
+    bit-identical for 1, 2 and (tiles of 16 or more) 4 pixels per thread."""
     sizes = [(150, 97), (41, 70)]
     cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
     recs = [synth.projected_records(4000, w, h, seed=41 + v) for v, (w, h) in enumerate(sizes)]
     dev, _ = gpu_util.records(recs, cams, tile)
     out = []
-    for ppt in (1, 2):
+    for ppt in ((1, 2) if tile < 16 else (1, 2, 4)):
         r = _renderer(cams, 4000, tile=tile, batch=64, ppt=ppt)
         gpu_util.set_projected(r, dev)
         r.ckpt.fill_(-1.0)
@@ -213,8 +213,9 @@ def test_pixels_per_thread_is_bit_invariant(tile):
         torch.cuda.synchronize()
         assert int(r.status.item()) == 0
         out.append([t.clone().cpu() for t in (r.image, r.T_final, r.n_last, r.ckpt)])
-    for a, b in zip(*out):
-        assert torch.equal(a, b)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert torch.equal(a, b)
 
 
 def test_tile_order_is_a_permutation_by_work_and_changes_nothing():
