@@ -204,7 +204,7 @@ def test_fused_backward_adam_equals_separate_calls(deg):
     torch.testing.assert_close(v1, v0, rtol=1e-5, atol=1e-14)
 
 
-@pytest.mark.parametrize("tile,ppt", [(16, 2), (8, 2), (32, 2), (16, 1)])
+@pytest.mark.parametrize("tile,ppt", [(16, 2), (8, 2), (32, 2), (16, 1), (16, 4), (32, 4)])
 def test_raster_bwd_g2d_against_oracle(tile, ppt):
     """gs_raster_bwd alone, on synthetic records both sides share: the per-view
     per-Gaussian gradients wrt (mean2D, conic a b c, opacity, colour)."""
