@@ -171,7 +171,8 @@ int64_t gs_ckpt_slots(int64_t pair_capacity, int64_t total_tiles, int32_t batch)
  * can hold: the bounding box of the ellipse dp^T Q dp <= c with
  * c = 2 ln(opacity / alpha_min), i.e. half-extents r_x = sqrt(c Sigma2D_xx),
  * r_y = sqrt(c Sigma2D_yy), inflated by x1.0001 + 0.001 px for float32
- * rounding (stored in the record's last two floats). */
+ * rounding (stored in the record's last two floats).  Every parameter array
+ * must start on a 16-byte boundary (the groups of gs_param_layout do). */
 gs_status gs_project(const gs_params *params /* host */, const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg /* host */, gs_projected out,
                      int32_t *dev_status, cudaStream_t stream);
 

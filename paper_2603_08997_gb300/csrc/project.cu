@@ -1,34 +1,23 @@
 // gs_project: Eq. (cov), Eq. (proj), SH colour and the conservative tile
-// rectangle, one thread per (Gaussian, view).  HBM-bound: ~236 B of parameters
-// read and 68 B written per Gaussian at SH degree 3.
+// rectangle, one thread per Gaussian over all views.  HBM-bound: ~236 B of
+// parameters read once and 80 B written per (Gaussian, view) at SH degree 3.
 #include "common.cuh"
 
 using namespace gsr;
 
 namespace {
 
+// One (Gaussian, view): Eq. (cov), Eq. (proj), colour, support rectangle.
+// mu, ls, q, logit: the Gaussian's parameters; f: its 3K SH coefficients.
 template <int DEG>
-__global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_camera *__restrict__ cams,
-                                                      gs_raster_config cfg, float *__restrict__ rec,
-                                                      int4 *__restrict__ rect, int32_t *__restrict__ touched,
-                                                      uint32_t *__restrict__ depth_key,
-                                                      ushort4 *__restrict__ rect16) {
-    __shared__ gs_camera s_cam;
-    const int v = blockIdx.y;
-    if (threadIdx.x == 0) s_cam = cams[v];
-    __syncthreads();
-    const int64_t n = prm.n;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const gs_camera &c = s_cam;
-    const int64_t e = (int64_t)v * n + i;
+__device__ __forceinline__ void project_one(const float (&mu)[3], const float (&ls)[3], float4 q, float logit,
+                                            const float *f, const gs_camera &c, const gs_raster_config &cfg,
+                                            int64_t e, float *__restrict__ rec, int4 *__restrict__ rect,
+                                            int32_t *__restrict__ touched, uint32_t *__restrict__ depth_key,
+                                            ushort4 *__restrict__ rect16) {
     float4 *out = reinterpret_cast<float4 *>(rec + e * kRecFloats);
-
-    const float mu[3] = {prm.means[3 * i], prm.means[3 * i + 1], prm.means[3 * i + 2]};
-    const float ls[3] = {prm.log_scales[3 * i], prm.log_scales[3 * i + 1], prm.log_scales[3 * i + 2]};
-    const float4 q = reinterpret_cast<const float4 *>(prm.quats)[i];
     ProjState g;
-    project_state(mu, ls, q, prm.opacity_logit[i], c, cfg.lowpass, g);
+    project_state(mu, ls, q, logit, c, cfg.lowpass, g);
     bool culled = g.culled || !(g.o >= cfg.alpha_min);
     float rx = 0.f, ry = 0.f;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
@@ -74,23 +63,8 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
     float Y[16];
     sh_basis(DEG, d[0], d[1], d[2], Y);
     float col[3] = {0.5f, 0.5f, 0.5f};
-    const float *f = prm.sh + (int64_t)i * (3 * K);
-    if constexpr ((3 * K) % 4 == 0) {
-        const float4 *f4 = reinterpret_cast<const float4 *>(f);
 #pragma unroll
-        for (int j = 0; j < (3 * K) / 4; ++j) {
-            const float4 t = f4[j];
-            const float tv[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = 4 * j + u;
-                col[idx % 3] += tv[u] * Y[idx / 3];
-            }
-        }
-    } else {
-#pragma unroll
-        for (int idx = 0; idx < 3 * K; ++idx) col[idx % 3] += f[idx] * Y[idx / 3];
-    }
+    for (int idx = 0; idx < 3 * K; ++idx) col[idx % 3] += f[idx] * Y[idx / 3];
     out[0] = make_float4(g.mean2d[0], g.mean2d[1], u00, u01);
     out[1] = make_float4(u11, g.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
     out[2] = make_float4(fmaxf(col[2], 0.f), g.p[2], rx, ry);
@@ -100,6 +74,62 @@ __global__ void __launch_bounds__(256) project_kernel(gs_params prm, const gs_ca
     if (rect16)
         rect16[e] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)(x1 - x0 + 1),
                                  (unsigned short)(y1 - y0 + 1));
+}
+
+// One block of PB Gaussians: their parameter slices are staged once into
+// shared memory with coalesced 16-byte loads, then each thread projects its
+// Gaussian into every view (the parameters are read from DRAM once however
+// many views there are).
+template <int DEG>
+__global__ void __launch_bounds__(PB) project_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
+                                                     gs_raster_config cfg, float *__restrict__ rec,
+                                                     int4 *__restrict__ rect, int32_t *__restrict__ touched,
+                                                     uint32_t *__restrict__ depth_key,
+                                                     ushort4 *__restrict__ rect16) {
+    using G = ParamGroups<DEG>;
+    extern __shared__ float s_par[];  // [TOT * PB]
+    __shared__ gs_camera s_cams[kStagedViews];
+    if (threadIdx.x < n_views && threadIdx.x < kStagedViews) s_cams[threadIdx.x] = cams[threadIdx.x];
+    const int64_t n = prm.n;
+    const int64_t i0 = (int64_t)blockIdx.x * PB;
+    const int nb = (int)min((int64_t)PB, n - i0);
+    const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
+    if (nb == PB)
+        stage_block_full<DEG>(src, i0, s_par);
+    else
+        stage_partial<DEG>(src, i0, nb, s_par);
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t >= nb) return;
+    const float *P0 = s_par + G::off(0, PB) + G::P(0) * t;
+    const float *P1 = s_par + G::off(1, PB) + G::P(1) * t;
+    const float *P2 = s_par + G::off(2, PB) + G::P(2) * t;
+    const float logit = s_par[G::off(3, PB) + G::P(3) * t];
+    const float *f = s_par + G::off(4, PB) + G::P(4) * t;
+    const float mu[3] = {P0[0], P0[1], P0[2]};
+    const float ls[3] = {P1[0], P1[1], P1[2]};
+    const float4 q = make_float4(P2[0], P2[1], P2[2], P2[3]);
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera &c = v < kStagedViews ? s_cams[v] : cams[v];
+        project_one<DEG>(mu, ls, q, logit, f, c, cfg, (int64_t)v * n + i0 + t, rec, rect, touched, depth_key,
+                         rect16);
+    }
+}
+
+template <int DEG>
+gs_status launch_project(const gs_params &prm, const gs_camera *cams, int n_views, const gs_raster_config &cfg,
+                         float *rec, int4 *rect, int32_t *touched, uint32_t *depth_key, ushort4 *rect16,
+                         cudaStream_t stream) {
+    constexpr size_t smem = sizeof(float) * ParamGroups<DEG>::TOT * PB;
+    static bool attr_set = false;  // raise the dynamic shared-memory limit once per instantiation
+    if (!attr_set && smem > 48 * 1024) {
+        GS_TRY(cudaFuncSetAttribute(project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    project_kernel<DEG><<<(unsigned)ceil_div(prm.n, (int64_t)PB), PB, smem, stream>>>(prm, cams, n_views, cfg, rec, rect,
+                                                                                     touched, depth_key, rect16);
+    GS_TRY_LAUNCH();
+    return GS_OK;
 }
 
 }  // namespace
@@ -165,18 +195,18 @@ gs_status gs_project(const gs_params *params, const gs_camera *cams, int32_t n_v
         return GS_ERR_INVALID_ARG;
     const int K3 = 3 * (params->sh_degree + 1) * (params->sh_degree + 1);
     if ((K3 % 4 == 0) && ((uintptr_t)params->sh & 15)) return GS_ERR_INVALID_ARG;
-    dim3 grid((unsigned)ceil_div(params->n, 256), (unsigned)n_views);
+    if (((uintptr_t)params->means | (uintptr_t)params->log_scales | (uintptr_t)params->opacity_logit |
+         (uintptr_t)params->sh) & 15)
+        return GS_ERR_INVALID_ARG;  // staged with 16-byte loads (gs_param_layout aligns every group)
     int4 *rect = reinterpret_cast<int4 *>(out.rect);
     if ((uintptr_t)out.rect16 & 7) return GS_ERR_INVALID_ARG;
     ushort4 *r16 = reinterpret_cast<ushort4 *>(out.rect16);
     switch (params->sh_degree) {
-        case 0: project_kernel<0><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
-        case 1: project_kernel<1><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
-        case 2: project_kernel<2><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
-        default: project_kernel<3><<<grid, 256, 0, stream>>>(*params, cams, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16); break;
+        case 0: return launch_project<0>(*params, cams, n_views, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16, stream);
+        case 1: return launch_project<1>(*params, cams, n_views, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16, stream);
+        case 2: return launch_project<2>(*params, cams, n_views, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16, stream);
+        default: return launch_project<3>(*params, cams, n_views, *cfg, out.rec, rect, out.tiles_touched, out.depth_key, r16, stream);
     }
-    GS_TRY_LAUNCH();
-    return GS_OK;
 }
 
 }  // extern "C"

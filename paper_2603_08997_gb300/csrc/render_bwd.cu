@@ -254,53 +254,8 @@ struct AdamFuse {
     const int64_t *step;
 };
 
-// Group strides (floats per Gaussian) and the staged layout in shared memory:
-// per Gaussian each group is padded to an odd stride P(g), so the 32 threads
-// of a warp touching "their" element k hit 32 different banks.
 template <int DEG>
-struct Groups {
-    static constexpr int K = (DEG + 1) * (DEG + 1);
-    __host__ __device__ static constexpr int S(int g) { return g == 0 ? 3 : (g == 1 ? 3 : (g == 2 ? 4 : (g == 3 ? 1 : 3 * K))); }
-    __host__ __device__ static constexpr int P(int g) { return S(g) | 1; }
-    static constexpr int TOT = P(0) + P(1) + P(2) + P(3) + P(4);  // padded floats per Gaussian
-    __host__ __device__ static constexpr int off(int g, int nb) {
-        return g == 0 ? 0
-             : (g == 1 ? P(0) * nb
-             : (g == 2 ? (P(0) + P(1)) * nb : (g == 3 ? (P(0) + P(1) + P(2)) * nb : (P(0) + P(1) + P(2) + P(3)) * nb)));
-    }
-    // linear index k of a group's contiguous global slice -> padded shared index
-    __host__ __device__ static constexpr int pad(int g, int k) { return (k / S(g)) * P(g) + k % S(g); }
-};
-
-constexpr int PB = 128;  // Gaussians (and threads) per projection-adjoint block
-constexpr int kStagedViews = 16;  // cameras copied to shared memory per block
-
-template <int DEG>
-constexpr size_t proj_bwd_smem() { return sizeof(float) * 2 * Groups<DEG>::TOT * PB; }
-
-// Copy the float4 chunks [0, C4) of a global slice into the padded shared
-// layout; every load of the thread is issued before the first store.
-template <int DEG, int g, int C4>
-__device__ __forceinline__ void stage_full(const float *__restrict__ sp, float *dp) {
-    using G = Groups<DEG>;
-    constexpr int J = (C4 + PB - 1) / PB;
-    float4 x[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        const int c = threadIdx.x + j * PB;
-        if (c < C4) x[j] = reinterpret_cast<const float4 *>(sp)[c];
-    }
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        const int c = threadIdx.x + j * PB;
-        if (c < C4) {
-            dp[G::pad(g, 4 * c)] = x[j].x;
-            dp[G::pad(g, 4 * c + 1)] = x[j].y;
-            dp[G::pad(g, 4 * c + 2)] = x[j].z;
-            dp[G::pad(g, 4 * c + 3)] = x[j].w;
-        }
-    }
-}
+constexpr size_t proj_bwd_smem() { return sizeof(float) * 2 * ParamGroups<DEG>::TOT * PB; }
 
 // Adam over the float4 chunks [0, C4) of a full block's slice of group g:
 // all m and v loads of the thread first, then the updates and stores.
@@ -308,7 +263,7 @@ template <int DEG, int g, int C4>
 __device__ __forceinline__ void adam_full(float *__restrict__ P, float *__restrict__ M, float *__restrict__ V,
                                           const float *sp, const float *sg, const float *lr_t, float ibc2,
                                           const gs_adam_config &cfg) {
-    using G = Groups<DEG>;
+    using G = ParamGroups<DEG>;
     constexpr int K3 = 3 * G::K;
     constexpr int J = (C4 + PB - 1) / PB;
     float4 m4[J], v4[J];
@@ -353,7 +308,7 @@ template <int DEG, int MODE>
 __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
                                                       const uint8_t *__restrict__ view_gate, gs_raster_config cfg,
                                                       const float4 *__restrict__ g2d, gs_grads gr, AdamFuse af) {
-    using G = Groups<DEG>;
+    using G = ParamGroups<DEG>;
     constexpr int K = G::K;
     extern __shared__ float smem[];
     float *s_par = smem;                  // [TOT * PB], group-major slices
@@ -371,27 +326,9 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     const int nb = (int)min((int64_t)PB, n - i0);
     const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
     if (nb == PB) {
-        stage_full<DEG, 0, 3 * PB / 4>(src[0] + 3 * i0, s_par + G::off(0, PB));
-        stage_full<DEG, 1, 3 * PB / 4>(src[1] + 3 * i0, s_par + G::off(1, PB));
-        stage_full<DEG, 2, PB>(src[2] + 4 * i0, s_par + G::off(2, PB));
-        stage_full<DEG, 3, PB / 4>(src[3] + i0, s_par + G::off(3, PB));
-        stage_full<DEG, 4, 3 * K * PB / 4>(src[4] + (int64_t)3 * K * i0, s_par + G::off(4, PB));
-    } else
-#pragma unroll
-    for (int g = 0; g < 5; ++g) {
-        const int cnt = G::S(g) * nb;
-        const float *sp = src[g] + (int64_t)G::S(g) * i0;  // 16-byte aligned: i0 is a multiple of PB
-        float *dp = s_par + G::off(g, PB);
-        const int cnt4 = cnt >> 2;
-#pragma unroll 4
-        for (int c = threadIdx.x; c < cnt4; c += PB) {
-            const float4 x = reinterpret_cast<const float4 *>(sp)[c];
-            dp[G::pad(g, 4 * c)] = x.x;
-            dp[G::pad(g, 4 * c + 1)] = x.y;
-            dp[G::pad(g, 4 * c + 2)] = x.z;
-            dp[G::pad(g, 4 * c + 3)] = x.w;
-        }
-        for (int k = 4 * cnt4 + threadIdx.x; k < cnt; k += PB) dp[G::pad(g, k)] = sp[k];
+        stage_block_full<DEG>(src, i0, s_par);
+    } else {
+        stage_partial<DEG>(src, i0, nb, s_par);
     }
     for (int k = threadIdx.x; k < G::TOT * PB; k += PB) s_grd[k] = 0.f;
     __syncthreads();
