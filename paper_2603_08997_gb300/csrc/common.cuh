@@ -381,4 +381,16 @@ __device__ __forceinline__ void stage_partial(const float *const (&src)[5], int6
     }
 }
 
+
+// Asynchronous 16-byte global -> shared copies (cp.async, bypassing L1) and
+// their group bookkeeping, for staging the next batch while the current one
+// is processed.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 }  // namespace gsr

@@ -3,10 +3,11 @@
 // One CTA per tile, PPT pixels per thread (1, 2 or 4), each warp an 8 x 4 PPT
 // pixel block.  The tile's depth-ordered list is
 // consumed `BATCH` Gaussians at a time: the CTA gathers the batch's packed
-// records into shared memory (one coalesced 48-byte record per Gaussian) and
-// marks, per warp, the records whose support box reaches the warp's pixel
-// block (one ballot per warp and 32 records); every warp then walks only its
-// marked records, in order.  At the start of every batch each pixel
+// records into shared memory (one 48-byte record per Gaussian, copied
+// asynchronously one batch ahead into a second buffer) and marks, per warp,
+// the records whose support box reaches the warp's pixel block (one ballot
+// per warp and 32 records); every warp then walks only its marked records,
+// in order.  At the start of every batch each pixel
 // stores its transmittance into the checkpoint slot
 //   slot(tile, b) = floor(range_start / BATCH) + tile + b
 // (TILE * TILE floats, row-major over the tile's pixels), which the backward pass uses to rebuild T without dividing across batches.
@@ -30,9 +31,10 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
     constexpr int NT = TILE * TILE;        // pixels per tile (checkpoint slot size)
     constexpr int NTH = TILE * TILE / PPT; // threads
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
-    __shared__ float4 s_a[BATCH];
-    __shared__ float4 s_b[BATCH];
-    __shared__ float4 s_c[BATCH];
+    constexpr int R = (BATCH + NTH - 1) / NTH;  // batch slots per thread
+    __shared__ float4 s_a[2][BATCH];  // double buffer: batch b + 1 arrives while batch b is composited
+    __shared__ float4 s_b[2][BATCH];
+    __shared__ float4 s_c[2][BATCH];
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     const int64_t tile = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
     const int v = view_of_tile(cams, n_views, tile);
@@ -69,33 +71,62 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
     for (int k = 0; k < PPT; ++k) {
         T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; done[k] = !inside[k];
     }
+    // Gaussian indices of this thread's slots of batch bb (0xffffffff past the list)
+    auto load_index = [&](int64_t bb, uint32_t (&gi)[R]) {
+        const int64_t b0 = (int64_t)rg.x + bb * BATCH;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int kk = threadIdx.x + r * NTH;
+            gi[r] = (bb < nb && kk < BATCH && b0 + kk < (int64_t)rg.y) ? vals[b0 + kk] : 0xffffffffu;
+        }
+    };
+    // start the copies of this thread's records of a batch into buffer buf
+    auto issue = [&](const uint32_t (&gi)[R], int buf) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int kk = threadIdx.x + r * NTH;
+            if (kk < BATCH && gi[r] != 0xffffffffu) {
+                const float4 *src = recv + (int64_t)gi[r] * 3;
+                cp_async16(&s_a[buf][kk], src);
+                cp_async16(&s_b[buf][kk], src + 1);
+                cp_async16(&s_c[buf][kk], src + 2);
+            }
+        }
+        cp_async_commit();
+    };
+    uint32_t gi[R];
+    load_index(0, gi);
+    issue(gi, 0);
+    load_index(1, gi);  // indices of the next batch, one batch ahead of its copies
     for (int64_t b = 0; b < nb; ++b) {
         bool all_done = true;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) all_done &= done[k];
-        if (__syncthreads_count(!all_done) == 0) break;
+        if (__syncthreads_count(!all_done) == 0) break;  // every warp is also past batch b - 1
         if (slot0 + b < ckpt_slots) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
                 if (inside[k]) ckpt[(slot0 + b) * NT + lp[k]] = T[k];
         }
+        const int buf = (int)(b & 1);
+        if (b + 1 < nb) {
+            issue(gi, buf ^ 1);
+            load_index(b + 2, gi);
+            cp_async_wait<1>();  // this thread's copies of batch b have landed
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
         const int64_t b0 = (int64_t)rg.x + b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
         for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
             const bool valid = kk < cnt;
-            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
-            if (valid) {
-                const uint32_t g = vals[b0 + kk];
-                const float4 *r = recv + (int64_t)g * 3;
-                ra = r[0];
-                rc = r[2];
-                s_a[kk] = ra;
-                s_b[kk] = r[1];
-                s_c[kk] = rc;
-            }
+            const float4 ra = valid ? s_a[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 rc = valid ? s_c[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
             overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rc, tx * TILE, ty * TILE);
         }
         __syncthreads();
+        const float4 *s_a_b = s_a[buf], *s_b_b = s_b[buf], *s_c_b = s_c[buf];
         if (!all_done) {
             bool alive = true;
             for (int wd = 0; wd < NWORD && alive; ++wd) {
@@ -104,7 +135,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
                 while (m) {
                     const int j = wd * 32 + __ffs(m) - 1;
                     m &= m - 1;
-                    const float4 sa = s_a[j], sb = s_b[j], sc = s_c[j];
+                    const float4 sa = s_a_b[j], sb = s_b_b[j], sc = s_c_b[j];
                     alive = false;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
@@ -129,6 +160,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
             }
         }
     }
+    cp_async_wait<0>();  // no copy into this block's shared memory outlives it
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!inside[k]) continue;
