@@ -75,11 +75,10 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     constexpr int NT = TILE * TILE;
     constexpr int NTH = TILE * TILE / PPT;
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
-    constexpr int R = (BATCH + NTH - 1) / NTH;  // batch slots per thread
-    __shared__ float4 s_a[2][BATCH];  // double buffer: batch b - 1 arrives while batch b is processed
-    __shared__ float4 s_b[2][BATCH];
-    __shared__ float4 s_c[2][BATCH];
-    __shared__ uint32_t s_g[2][BATCH];
+    __shared__ float4 s_a[BATCH];
+    __shared__ float4 s_b[BATCH];
+    __shared__ float4 s_c[BATCH];
+    __shared__ uint32_t s_g[BATCH];
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     __shared__ float s_acc[BATCH][9];
     __shared__ int s_max;
@@ -134,57 +133,27 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
         A2[k] = T_end[k] * cfg.bg[2];
     }
 
-    const int nbb = (max_last + BATCH - 1) / BATCH;  // batches visited, last to first
-    // Gaussian indices of this thread's slots of batch bb (0xffffffff outside)
-    auto load_index = [&](int bb, uint32_t (&gi)[R]) {
-        const int64_t b0 = (int64_t)rg.x + (int64_t)bb * BATCH;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int kk = threadIdx.x + r * NTH;
-            gi[r] = (bb >= 0 && bb < nbb && kk < BATCH && b0 + kk < (int64_t)rg.y) ? vals[b0 + kk] : 0xffffffffu;
-        }
-    };
-    // start the copies of this thread's records of a batch into buffer buf
-    auto issue = [&](const uint32_t (&gi)[R], int buf) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int kk = threadIdx.x + r * NTH;
-            if (kk < BATCH && gi[r] != 0xffffffffu) {
-                const float4 *src = recv + (int64_t)gi[r] * 3;
-                cp_async16(&s_a[buf][kk], src);
-                cp_async16(&s_b[buf][kk], src + 1);
-                cp_async16(&s_c[buf][kk], src + 2);
-                s_g[buf][kk] = gi[r];
-            }
-        }
-        cp_async_commit();
-    };
-    uint32_t gi[R];
-    load_index(nbb - 1, gi);
-    issue(gi, (nbb - 1) & 1);
-    load_index(nbb - 2, gi);  // indices of the next batch, one batch ahead of its copies
-    for (int b = nbb - 1; b >= 0; --b) {
-        __syncthreads();  // the previous batch's flush is done with its buffer
-        const int buf = b & 1;
-        if (b > 0) {
-            issue(gi, buf ^ 1);
-            load_index(b - 2, gi);
-            cp_async_wait<1>();  // this thread's copies of batch b have landed
-        } else {
-            cp_async_wait<0>();
-        }
+    for (int b = (max_last + BATCH - 1) / BATCH - 1; b >= 0; --b) {
         __syncthreads();
         const int64_t b0 = (int64_t)rg.x + (int64_t)b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
         for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
             const bool valid = kk < cnt;
-            const float4 ra = valid ? s_a[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 rc = valid ? s_c[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+            if (valid) {
+                const uint32_t g = vals[b0 + kk];
+                const float4 *r = recv + (int64_t)g * 3;
+                ra = r[0];
+                rc = r[2];
+                s_a[kk] = ra;
+                s_b[kk] = r[1];
+                s_c[kk] = rc;
+                s_g[kk] = g;
+            }
             overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rc, tx * TILE, ty * TILE);
         }
         for (int kk = threadIdx.x; kk < BATCH * 9; kk += NTH) (&s_acc[0][0])[kk] = 0.f;
         __syncthreads();
-        const float4 *s_a_b = s_a[buf], *s_b_b = s_b[buf], *s_c_b = s_c[buf];
         const int lo = b * BATCH;
         int jstart[PPT];
         float T[PPT];
@@ -212,7 +181,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
             const int bit = 31 - __clz(m);
             m &= ~(1u << bit);
             const int j = wd * 32 + bit;
-            const float4 sa = s_a_b[j], sb = s_b_b[j], sc = s_c_b[j];
+            const float4 sa = s_a[j], sb = s_b[j], sc = s_c[j];
             float gv[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) gv[q] = 0.f;
@@ -267,7 +236,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
 #pragma unroll
             for (int q = 0; q < 9; ++q) nz |= a[q] != 0.f;
             if (!nz) continue;
-            float4 *dst = g2d + ((int64_t)v * n + s_g[buf][kk]) * 3;
+            float4 *dst = g2d + ((int64_t)v * n + s_g[kk]) * 3;
             atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
             atomicAdd(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
             atomicAdd(&dst[2].x, a[8]);
