@@ -588,7 +588,7 @@ def main():
 
     import synth
     from paper_2603_08997_gb300 import build, gsr, raster
-    from paper_2603_08997_gb300.refine import RefinementLoop
+    from paper_2603_08997_gb300.refine import HostTargets, RefinementLoop
 
     build.build()
     torch.cuda.set_device(local)
@@ -667,11 +667,10 @@ def main():
         g_host = torch.empty(K, dtype=torch.uint8).pin_memory()
         seq_np = np.asarray(seq)
 
+        feeder = HostTargets(loop, host_targets, seq_np)
+
         def e2e_step(k):
-            v = int(seq_np[k % len(seq_np)])
-            with torch.cuda.stream(loop.stream):
-                slot_target[0].copy_(host_targets[v], non_blocking=True)
-            loop.step_graph()
+            feeder.step()  # target from pinned host memory, copied while the previous iteration runs
             with torch.cuda.stream(loop.stream):
                 loss_host[k:k + 1].copy_(loop.renderer.loss, non_blocking=True)
                 g_host[k:k + 1].copy_(loop.g, non_blocking=True)
@@ -679,6 +678,7 @@ def main():
         for k in range(W):
             e2e_step(k)
         loop.restore(init)
+        feeder.reset()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(K):

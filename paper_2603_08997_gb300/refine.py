@@ -222,3 +222,53 @@ class RefinementLoop:
                 out[k:k + self.B].copy_(self.renderer.loss)
         s.synchronize()
         return out[:n].cpu().numpy()
+
+
+class HostTargets:
+    """Feeds a one-view-per-iteration RefinementLoop from per-view targets in
+    pinned host memory.  The loop must have been built with a single device
+    target slot that every view maps to (target_offsets all 0).  The target
+    of iteration k + 1 is copied host -> device into a staging buffer on a
+    copy stream while iteration k runs; at the start of iteration k + 1 it is
+    moved into the slot with a device copy on the loop's stream, so the host
+    transfer overlaps the previous iteration instead of preceding this one."""
+
+    def __init__(self, loop: RefinementLoop, host_targets, view_seq):
+        assert loop.B == 1, "one view per iteration"
+        self.loop = loop
+        self.host = host_targets
+        self.seq = np.asarray(view_seq)
+        self.slot = loop.targets
+        self.stage = [torch.empty_like(self.slot) for _ in range(2)]
+        self.copy_stream = torch.cuda.Stream(device=self.slot.device)
+        self.ready = [torch.cuda.Event(), torch.cuda.Event()]
+        self.free = [torch.cuda.Event(), torch.cuda.Event()]
+        self.k = 0
+
+    def reset(self) -> None:
+        """Back to iteration 0 (with the loop's restore/reset)."""
+        torch.cuda.synchronize()
+        self.k = 0
+
+    def _prefetch(self, k: int) -> None:
+        b = k % 2
+        v = int(self.seq[k % len(self.seq)])
+        with torch.cuda.stream(self.copy_stream):
+            self.copy_stream.wait_event(self.free[b])  # the slot copy out of this buffer is done
+            self.stage[b].copy_(self.host[v].reshape(-1), non_blocking=True)
+            self.ready[b].record(self.copy_stream)
+
+    def step(self) -> None:
+        """One iteration (graph replay) with its target fed from the host."""
+        k = self.k
+        if k == 0:
+            self._prefetch(0)
+        self._prefetch(k + 1)
+        ls = self.loop.stream
+        b = k % 2
+        ls.wait_event(self.ready[b])
+        with torch.cuda.stream(ls):
+            self.slot.copy_(self.stage[b], non_blocking=True)
+        self.free[b].record(ls)
+        self.loop.step_graph()
+        self.k += 1

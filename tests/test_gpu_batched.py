@@ -128,3 +128,39 @@ def test_autotune_picks_a_timed_candidate():
     st2, times2 = autotune.autotune(model, cams, targets, candidates=cands, views_per_step=3)
     assert times2 == {} and st2 == st  # cached
     autotune._cache.clear()
+
+
+def test_host_targets_feed_equals_device_targets():
+    """Targets fed from pinned host memory one iteration ahead (HostTargets)
+    give the same per-iteration losses and decisions as device targets."""
+    from paper_2603_08997_gb300.refine import HostTargets
+    gpu_util.lib()
+    scene, _, _ = synth.case_c1(n=1500)
+    cams = [synth.camera_pinhole(64.0, 64.0, 32.0, 32.0, 64, 64) for _ in range(3)]
+    for k, c in enumerate(cams):  # three poses: small rotations about y
+        a = 0.05 * k
+        c.R = np.array([[np.cos(a), 0, np.sin(a)], [0, 1, 0], [-np.sin(a), 0, np.cos(a)]], np.float32)
+    rng = np.random.default_rng(8)
+    tg = torch.from_numpy(rng.uniform(0, 1, (3, 3, 64, 64)).astype(np.float32))
+    seq = rng.integers(0, 3, size=40).astype(np.int32)
+    logs = []
+    for host in (False, True):
+        model = raster.GaussianModel.from_scene(scene)
+        if host:
+            slot = torch.empty((1, 3, 64, 64), dtype=torch.float32, device="cuda")
+            loop = RefinementLoop(model, cams, slot, seq, gated=True, W=6, log_capacity=40)
+            loop.target_offsets = torch.zeros(3, dtype=torch.int64, device="cuda")
+            feeder = HostTargets(loop, tg.pin_memory(), seq)
+            loop.capture()
+            for _ in range(40):
+                feeder.step()
+        else:
+            loop = RefinementLoop(model, cams, tg.cuda(), seq, gated=True, W=6, log_capacity=40)
+            loop.capture()
+            for _ in range(40):
+                loop.step_graph()
+        torch.cuda.synchronize()
+        logs.append(loop.read_log(40))
+        loop.close()
+    assert np.array_equal(logs[0]["loss"], logs[1]["loss"])
+    assert np.array_equal(logs[0]["g"], logs[1]["g"])
