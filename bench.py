@@ -250,8 +250,9 @@ def run_rho_sweep(args) -> None:
 
 
 def stages_once(args) -> None:
-    """Two eager forward + backward iterations of every stage on view 0 of the
-    workload's scene (perturbed start, ground-truth target), for counters."""
+    """Two eager forward + backward iterations of every stage (and of the
+    unfused projection adjoint + Adam) on view 0 of the workload's scene
+    (perturbed start, ground-truth target), for counters."""
     import torch
 
     import synth
@@ -272,7 +273,8 @@ def stages_once(args) -> None:
         r.compute_loss(target)
         r.loss_backward(target)
         r.raster_bwd()
-        r.project_bwd(p, gr)
+        r.project_bwd_adam(m, adam)  # the loop's backward branch
+        r.project_bwd(p, gr)         # its unfused alternative
         adam.step()
     torch.cuda.synchronize()
     print(json.dumps({"stages_once": True, "status": int(r.status.item()), "pairs": int(r.pair_count.item())}))
@@ -423,7 +425,8 @@ def run_reference(args) -> None:
 # ------------------------------------------------------------ GPU arm
 
 PEAK_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
-BACKWARD_STAGES = ("loss_bwd", "raster_bwd", "project_bwd", "adam")
+BACKWARD_STAGES = ("loss_bwd", "raster_bwd", "project_bwd_adam")
+UNFUSED_STAGES = ("project_bwd", "adam")  # the loop's fused=False alternative to project_bwd_adam
 
 
 def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
@@ -442,7 +445,7 @@ def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
         "raster_bwd": lambda: r.raster_bwd(stream=s),
         "project_bwd": lambda: r.project_bwd(params, grads, stream=s),
         "adam": lambda: adam.step(stream=s),
-        "project_bwd_adam": lambda: r.backward_adam(loop.model, adam, stream=s),  # fused alternative
+        "project_bwd_adam": lambda: r.project_bwd_adam(loop.model, adam, stream=s),
     }
     out = {}
     with torch.cuda.stream(s):
@@ -457,12 +460,9 @@ def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
             torch.cuda.synchronize()
             out[name] = {"ms": e0.elapsed_time(e1) / reps}
     loop.restore(snap)
-    # the fused call includes its raster adjoint: its own cost is the difference
-    out["project_bwd_adam"]["ms"] = max(out["project_bwd_adam"]["ms"] - out["raster_bwd"]["ms"], 0.0)
     tot = 0.0
     for name, v in out.items():
-        v["weight"] = (0.0 if name == "project_bwd_adam" else b_frac) if name in BACKWARD_STAGES + ("project_bwd_adam",) \
-            else 1.0
+        v["weight"] = 0.0 if name in UNFUSED_STAGES else (b_frac if name in BACKWARD_STAGES else 1.0)
         tot += v["weight"] * v["ms"]
     for v in out.values():
         v["share"] = v["weight"] * v["ms"] / tot
@@ -504,7 +504,9 @@ def roofline_of(stages: dict, loop, args) -> dict:
         "raster_bwd": ("alu", 40.0 * evals, "FLOP: 40 per evaluated pair"),
         "project_bwd": ("hbm", N * (236 + 48 + 236), "bytes: 520 B per Gaussian"),
         "adam": ("hbm", 28 * params, "bytes: 28 B per parameter (read p, g, m, v; write p, m, v)"),
-        "project_bwd_adam": ("hbm", N * (48 + 236) + 24 * params, "bytes: 284 B per Gaussian + 24 B per parameter"),
+        "project_bwd_adam": ("hbm", N * 48 * r.views.n + 24 * params,
+                             "bytes: 48 B of 2D gradients per (view, Gaussian) + 24 B per parameter "
+                             "(read p, m, v; write p, m, v)"),
     }
     name = max(stages, key=lambda k: stages[k]["share"])
     bound, units, note = work[name]

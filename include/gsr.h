@@ -342,15 +342,27 @@ gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t 
  * adjoint of gs_render_bwd, after which every parameter of the flat buffer
  * (gs_param_layout; quats, m and v 16-byte aligned) takes one Adam step with
  * the gradient just computed, without storing the gradient.  Equal to
- * gs_render_bwd (accumulate = 0) followed by gs_adam_step; dev_do_step and
- * dev_step as in gs_adam_step, view_gate as in gs_render_bwd. */
+ * gs_render_bwd (accumulate = 0) followed by gs_adam_step; dev_do_step,
+ * dev_step and norms2 (nullable) as in gs_adam_step, view_gate as in
+ * gs_render_bwd.  The projection adjoint and the Adam step run in one kernel,
+ * so the parameter gradients never reach DRAM. */
 gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
                              const gs_projected *proj /* host */, const uint32_t *vals, const uint32_t *ranges,
                              const gs_camera *cams, int32_t n_views, int64_t total_tiles,
                              const gs_raster_config *cfg /* host */, gs_fwd_saved saved, const float *dL_dimage,
                              const uint8_t *view_gate, const gs_adam_config *adam /* host */,
-                             const int32_t *dev_do_step, int64_t *dev_step, void *workspace, size_t workspace_bytes,
-                             int32_t *dev_status, cudaStream_t stream);
+                             const int32_t *dev_do_step, int64_t *dev_step, double *norms2, void *workspace,
+                             size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream);
+
+/* The second half of gs_render_bwd_adam on its own: the projection adjoint of
+ * the 2D gradients that gs_raster_bwd left in g2d (layout and alignment as
+ * there), fused with the Adam step as above.  gs_raster_bwd followed by this
+ * call equals gs_render_bwd_adam. */
+gs_status gs_project_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                              const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg /* host */,
+                              const float *g2d, const uint8_t *view_gate, const gs_adam_config *adam /* host */,
+                              const int32_t *dev_do_step, int64_t *dev_step, double *norms2, int32_t *dev_status,
+                              cudaStream_t stream);
 
 /* ----------------------------------------------------------- SkipGS gate */
 

@@ -501,23 +501,6 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
     }
 }
 
-// Exclusive scan, in place, of the first n words of s (one block, each
-// thread a contiguous run).
-__device__ __forceinline__ void block_scan_table(uint32_t *s, int n, uint32_t *warp_sums) {
-    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
-    uint32_t sum = 0;
-    for (int t = lo; t < hi; ++t) sum += s[t];
-    uint32_t total;
-    uint32_t run = block_exclusive_scan(sum, warp_sums, &total);
-    for (int t = lo; t < hi; ++t) {
-        const uint32_t x = s[t];
-        s[t] = run;
-        run += x;
-    }
-    __syncthreads();
-}
-
 // One block per chunk.  The chunk's first slot per tile is held in shared
 // memory (s_off).  The block takes its entries WIN at a time (a window, WIN =
 // the bits of one tile's entry mask); the window's pairs, in order (entry,

@@ -60,13 +60,17 @@ __device__ __forceinline__ void adam_update(float &p, float &m, float &v, float 
     p -= lr_t * m * rcp_approx(sqrt_approx(v) * ibc2 + eps);
 }
 
-// Per-step Adam scalars from the executed-step counter (computed once per block).
+// Per-step Adam scalars from the executed-step counter (computed once per
+// block).  The bias corrections 1 - beta^t are formed in single precision as
+// -expm1(t log1p(beta - 1)): beta - 1 is exact for beta in [0.5, 1), and both
+// functions keep the small differences (t = 1, beta2 = 0.999) to a few ulp,
+// without the long double-precision pow chain a block would wait on.
 __device__ __forceinline__ void adam_scalars(const gs_adam_config &cfg, int64_t executed, float *lr_t, float *ibc2) {
-    const double t = (double)(executed + 1);
-    const double bc1 = 1.0 - pow((double)cfg.beta1, t);
-    const double bc2 = 1.0 - pow((double)cfg.beta2, t);
-    for (int k = 0; k < 6; ++k) lr_t[k] = (float)((double)cfg.lr[k] / bc1);
-    *ibc2 = (float)(1.0 / sqrt(bc2));
+    const float t = (float)(executed + 1);
+    const float bc1 = -expm1f(t * log1pf(cfg.beta1 - 1.f));
+    const float bc2 = -expm1f(t * log1pf(cfg.beta2 - 1.f));
+    for (int k = 0; k < 6; ++k) lr_t[k] = cfg.lr[k] / bc1;
+    *ibc2 = 1.f / sqrtf(bc2);
 }
 
 // First error wins.
@@ -323,20 +327,21 @@ constexpr int PB = 128;  // Gaussians (and threads) per staged block
 constexpr int kStagedViews = 16;  // cameras copied to shared memory per block
 
 // Copy the float4 chunks [0, C4) of a global slice into the padded shared
-// layout; every load of the thread is issued before the first store.
-template <int DEG, int g, int C4>
-__device__ __forceinline__ void stage_full(const float *__restrict__ sp, float *dp) {
+// layout, NT threads cooperating (this one is `lane`); every load of the
+// thread is issued before the first store.
+template <int DEG, int g, int C4, int NT>
+__device__ __forceinline__ void stage_full(const float *__restrict__ sp, float *dp, int lane) {
     using G = ParamGroups<DEG>;
-    constexpr int J = (C4 + PB - 1) / PB;
+    constexpr int J = (C4 + NT - 1) / NT;
     float4 x[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        const int c = threadIdx.x + j * PB;
+        const int c = lane + j * NT;
         if (c < C4) x[j] = reinterpret_cast<const float4 *>(sp)[c];
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        const int c = threadIdx.x + j * PB;
+        const int c = lane + j * NT;
         if (c < C4) {
             dp[G::pad(g, 4 * c)] = x[j].x;
             dp[G::pad(g, 4 * c + 1)] = x[j].y;
@@ -346,39 +351,51 @@ __device__ __forceinline__ void stage_full(const float *__restrict__ sp, float *
     }
 }
 
-// All five groups of a full block of PB Gaussians starting at i0.
-template <int DEG>
-__device__ __forceinline__ void stage_block_full(const float *const (&src)[5], int64_t i0, float *s_par) {
+// All five groups of NG Gaussians starting at i0 (NG threads, NG a multiple
+// of 4 so that every slice is a whole number of float4 chunks).
+template <int DEG, int NG>
+__device__ __forceinline__ void stage_group_full(const float *const (&src)[5], int64_t i0, float *s_par, int lane) {
     using G = ParamGroups<DEG>;
     constexpr int K = G::K;
-    stage_full<DEG, 0, 3 * PB / 4>(src[0] + 3 * i0, s_par + G::off(0, PB));
-    stage_full<DEG, 1, 3 * PB / 4>(src[1] + 3 * i0, s_par + G::off(1, PB));
-    stage_full<DEG, 2, PB>(src[2] + 4 * i0, s_par + G::off(2, PB));
-    stage_full<DEG, 3, PB / 4>(src[3] + i0, s_par + G::off(3, PB));
-    stage_full<DEG, 4, 3 * K * PB / 4>(src[4] + (int64_t)3 * K * i0, s_par + G::off(4, PB));
+    stage_full<DEG, 0, 3 * NG / 4, NG>(src[0] + 3 * i0, s_par + G::off(0, NG), lane);
+    stage_full<DEG, 1, 3 * NG / 4, NG>(src[1] + 3 * i0, s_par + G::off(1, NG), lane);
+    stage_full<DEG, 2, NG, NG>(src[2] + 4 * i0, s_par + G::off(2, NG), lane);
+    stage_full<DEG, 3, NG / 4, NG>(src[3] + i0, s_par + G::off(3, NG), lane);
+    stage_full<DEG, 4, 3 * K * NG / 4, NG>(src[4] + (int64_t)3 * K * i0, s_par + G::off(4, NG), lane);
 }
 
-// The same for the last, partial block of nb < PB Gaussians (slices start on
-// 16-byte boundaries: i0 is a multiple of PB and groups are 256-byte aligned).
-template <int DEG>
-__device__ __forceinline__ void stage_partial(const float *const (&src)[5], int64_t i0, int nb, float *s_par) {
+// The same for a partial group of nb < NG Gaussians (slices start on 16-byte
+// boundaries: i0 is a multiple of NG, NG of 4, and groups are 256-byte aligned).
+template <int DEG, int NG>
+__device__ __forceinline__ void stage_group_partial(const float *const (&src)[5], int64_t i0, int nb, float *s_par,
+                                                    int lane) {
     using G = ParamGroups<DEG>;
 #pragma unroll
     for (int g = 0; g < 5; ++g) {
         const int cnt = G::S(g) * nb;
         const float *sp = src[g] + (int64_t)G::S(g) * i0;
-        float *dp = s_par + G::off(g, PB);
+        float *dp = s_par + G::off(g, NG);
         const int cnt4 = cnt >> 2;
 #pragma unroll 4
-        for (int c = threadIdx.x; c < cnt4; c += PB) {
+        for (int c = lane; c < cnt4; c += NG) {
             const float4 x = reinterpret_cast<const float4 *>(sp)[c];
             dp[G::pad(g, 4 * c)] = x.x;
             dp[G::pad(g, 4 * c + 1)] = x.y;
             dp[G::pad(g, 4 * c + 2)] = x.z;
             dp[G::pad(g, 4 * c + 3)] = x.w;
         }
-        for (int k = 4 * cnt4 + threadIdx.x; k < cnt; k += PB) dp[G::pad(g, k)] = sp[k];
+        for (int k = 4 * cnt4 + lane; k < cnt; k += NG) dp[G::pad(g, k)] = sp[k];
     }
+}
+
+// A whole block of PB Gaussians, PB threads.
+template <int DEG>
+__device__ __forceinline__ void stage_block_full(const float *const (&src)[5], int64_t i0, float *s_par) {
+    stage_group_full<DEG, PB>(src, i0, s_par, threadIdx.x);
+}
+template <int DEG>
+__device__ __forceinline__ void stage_partial(const float *const (&src)[5], int64_t i0, int nb, float *s_par) {
+    stage_group_partial<DEG, PB>(src, i0, nb, s_par, threadIdx.x);
 }
 
 
@@ -392,5 +409,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Bulk prefetch of a global range into L2 (no completion to wait on).  The
+// address must be 16-byte aligned and `bytes` a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void *gmem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
 
 }  // namespace gsr

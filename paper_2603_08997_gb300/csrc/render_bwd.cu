@@ -252,24 +252,26 @@ struct AdamFuse {
     gs_adam_config cfg;
     const int32_t *do_step;
     const int64_t *step;
+    double *norms2;  // optional: sum of g^2 and of (p_new - p_old)^2 are added here
 };
 
 template <int DEG>
 constexpr size_t proj_bwd_smem() { return sizeof(float) * 2 * ParamGroups<DEG>::TOT * PB; }
 
-// Adam over the float4 chunks [0, C4) of a full block's slice of group g:
-// all m and v loads of the thread first, then the updates and stores.
+// Adam over the float4 chunks [0, C4) of a full warp's slice of group g:
+// all m and v loads of the lane first, then the updates and stores; the
+// lane's sums of g^2 and (p_new - p_old)^2 are added to ng and nd.
 template <int DEG, int g, int C4>
 __device__ __forceinline__ void adam_full(float *__restrict__ P, float *__restrict__ M, float *__restrict__ V,
                                           const float *sp, const float *sg, const float *lr_t, float ibc2,
-                                          const gs_adam_config &cfg) {
+                                          const gs_adam_config &cfg, int lane, float &ng, float &nd) {
     using G = ParamGroups<DEG>;
     constexpr int K3 = 3 * G::K;
-    constexpr int J = (C4 + PB - 1) / PB;
+    constexpr int J = (C4 + 31) / 32;
     float4 m4[J], v4[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        const int c = threadIdx.x + j * PB;
+        const int c = lane + j * 32;
         if (c < C4) {
             m4[j] = reinterpret_cast<const float4 *>(M)[c];
             v4[j] = reinterpret_cast<const float4 *>(V)[c];
@@ -277,7 +279,7 @@ __device__ __forceinline__ void adam_full(float *__restrict__ P, float *__restri
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        const int c = threadIdx.x + j * PB;
+        const int c = lane + j * 32;
         if (c < C4) {
             float4 p4;
             float *pm = &m4[j].x, *pv = &v4[j].x, *pp = &p4.x;
@@ -286,9 +288,12 @@ __device__ __forceinline__ void adam_full(float *__restrict__ P, float *__restri
                 const int k = 4 * c + u;
                 const int lr = g < 4 ? g : ((k % K3) < 3 ? 4 : 5);
                 const int ks = G::pad(g, k);
-                float p = sp[ks];
-                adam_update(p, pm[u], pv[u], sg[ks], lr_t[lr], cfg.beta1, cfg.beta2, ibc2, cfg.eps);
+                const float p0 = sp[ks], gk = sg[ks];
+                float p = p0;
+                adam_update(p, pm[u], pv[u], gk, lr_t[lr], cfg.beta1, cfg.beta2, ibc2, cfg.eps);
                 pp[u] = p;
+                ng += gk * gk;
+                nd += (p - p0) * (p - p0);
             }
             reinterpret_cast<float4 *>(P)[c] = p4;
             reinterpret_cast<float4 *>(M)[c] = m4[j];
@@ -297,13 +302,16 @@ __device__ __forceinline__ void adam_full(float *__restrict__ P, float *__restri
     }
 }
 
-// Projection adjoint, staged through shared memory.  The block copies the
-// parameter slices of its PB Gaussians (contiguous in every group) into
-// shared memory with coalesced loads; each thread chains its Gaussian's 2D
-// gradients (all views) to parameter gradients, accumulated in its own
-// shared slots; the block then sweeps its slices again, coalesced, to store
-// the gradients (MODE 0 overwrite, 1 add) or to apply Adam (MODE 2) without
-// ever storing them.
+// Projection adjoint, staged through shared memory one warp at a time: each
+// warp copies the parameter slices of its WG = 32 Gaussians (contiguous in
+// every group) into its own shared region with coalesced loads; each lane
+// chains its Gaussian's 2D gradients (all views) to parameter gradients,
+// accumulated in its own shared slots; the warp then sweeps its slices again,
+// coalesced, to store the gradients (MODE 0 overwrite, 1 add) or to apply
+// Adam (MODE 2) without ever storing them.  Warps synchronise only among
+// their own lanes, so one warp's sweep overlaps another's chain rule.
+constexpr int WG = 32;
+
 template <int DEG, int MODE>
 __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
                                                       const uint8_t *__restrict__ view_gate, gs_raster_config cfg,
@@ -311,8 +319,6 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     using G = ParamGroups<DEG>;
     constexpr int K = G::K;
     extern __shared__ float smem[];
-    float *s_par = smem;                  // [TOT * PB], group-major slices
-    float *s_grd = smem + G::TOT * PB;    // same layout
     __shared__ float s_lr[6];
     __shared__ float s_ibc2;
     __shared__ gs_camera s_cams[kStagedViews];
@@ -321,31 +327,56 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
         if (threadIdx.x == 0) adam_scalars(af.cfg, *af.step, s_lr, &s_ibc2);
     }
     if (threadIdx.x < n_views && threadIdx.x < kStagedViews) s_cams[threadIdx.x] = cams[threadIdx.x];
-    const int64_t n = prm.n;
-    const int64_t i0 = (int64_t)blockIdx.x * PB;
-    const int nb = (int)min((int64_t)PB, n - i0);
-    const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
-    if (nb == PB) {
-        stage_block_full<DEG>(src, i0, s_par);
-    } else {
-        stage_partial<DEG>(src, i0, nb, s_par);
-    }
-    for (int k = threadIdx.x; k < G::TOT * PB; k += PB) s_grd[k] = 0.f;
     __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t n = prm.n;
+    const int64_t i0 = (int64_t)blockIdx.x * PB + WG * (threadIdx.x >> 5);
+    float ng = 0.f, nd = 0.f;  // MODE 2: this lane's sums of g^2 and (p_new - p_old)^2
+    // the warp's work; a return ends this warp's part, not the block
+    [&]() {
+    if (i0 >= n) return;
+    const int nb = (int)min((int64_t)WG, n - i0);
+    float *s_par = smem + (threadIdx.x >> 5) * 2 * G::TOT * WG;  // [TOT * WG], group-major slices
+    float *s_grd = s_par + G::TOT * WG;                           // same layout
+    if constexpr (MODE == 2) {
+        // A full warp asks L2 for its Adam moments (and its 2D gradients) up
+        // front, so that the HBM reads of the final sweep overlap the chain
+        // rule instead of following it.  Slices are 16-byte aligned: group
+        // offsets are 64-float aligned and i0 is a multiple of WG.
+        if (nb == WG) {
+            if (lane < 10) {
+                const int g = lane >> 1;  // selects, not an indexed parameter array (no local copy)
+                const int64_t og = g == 0 ? af.o[0] : g == 1 ? af.o[1] : g == 2 ? af.o[2] : g == 3 ? af.o[3] : af.o[4];
+                const int sg = g < 2 ? 3 : g == 2 ? 4 : g == 3 ? 1 : 3 * K;
+                const float *base = (lane & 1) ? af.v : af.m;
+                prefetch_l2(base + og + (int64_t)sg * i0, (uint32_t)(sizeof(float) * sg * WG));
+            }
+            for (int v = lane - 10; v >= 0 && v < n_views; v += 22)
+                if (!view_gate || view_gate[v]) prefetch_l2(g2d + ((int64_t)v * n + i0) * 3, (uint32_t)(3 * sizeof(float4) * WG));
+        }
+    }
+    const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
+    if (nb == WG) {
+        stage_group_full<DEG, WG>(src, i0, s_par, lane);
+    } else {
+        stage_group_partial<DEG, WG>(src, i0, nb, s_par, lane);
+    }
+    for (int k = lane; k < G::TOT * WG / 4; k += 32) reinterpret_cast<float4 *>(s_grd)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
 
-    const int t = threadIdx.x;
+    const int t = lane;
     if (t < nb) {
         const int64_t i = i0 + t;
-        const float *P0 = s_par + G::off(0, PB) + G::P(0) * t;
-        const float *P1 = s_par + G::off(1, PB) + G::P(1) * t;
-        const float *P2 = s_par + G::off(2, PB) + G::P(2) * t;
-        const float logit = s_par[G::off(3, PB) + G::P(3) * t];
-        const float *f = s_par + G::off(4, PB) + G::P(4) * t;
-        float *D0 = s_grd + G::off(0, PB) + G::P(0) * t;
-        float *D1 = s_grd + G::off(1, PB) + G::P(1) * t;
-        float *D2 = s_grd + G::off(2, PB) + G::P(2) * t;
-        float *D3 = s_grd + G::off(3, PB) + G::P(3) * t;
-        float *DF = s_grd + G::off(4, PB) + G::P(4) * t;
+        const float *P0 = s_par + G::off(0, WG) + G::P(0) * t;
+        const float *P1 = s_par + G::off(1, WG) + G::P(1) * t;
+        const float *P2 = s_par + G::off(2, WG) + G::P(2) * t;
+        const float logit = s_par[G::off(3, WG) + G::P(3) * t];
+        const float *f = s_par + G::off(4, WG) + G::P(4) * t;
+        float *D0 = s_grd + G::off(0, WG) + G::P(0) * t;
+        float *D1 = s_grd + G::off(1, WG) + G::P(1) * t;
+        float *D2 = s_grd + G::off(2, WG) + G::P(2) * t;
+        float *D3 = s_grd + G::off(3, WG) + G::P(3) * t;
+        float *DF = s_grd + G::off(4, WG) + G::P(4) * t;
         const float mu[3] = {P0[0], P0[1], P0[2]};
         const float ls[3] = {P1[0], P1[1], P1[2]};
         const float4 q4 = make_float4(P2[0], P2[1], P2[2], P2[3]);
@@ -471,37 +502,37 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
             for (int a = 0; a < 4; ++a) D2[a] += (dqn[a] - g.qn[a] * qd) * g.qinv;
         }
     }
-    __syncthreads();
-    // coalesced sweep over the block's slices
+    __syncwarp();
+    // coalesced sweep over the warp's slices
     if constexpr (MODE == 2) {
         const float ibc2 = s_ibc2;
-        if (nb == PB) {
-            adam_full<DEG, 0, 3 * PB / 4>(af.p + af.o[0] + 3 * i0, af.m + af.o[0] + 3 * i0, af.v + af.o[0] + 3 * i0,
-                                         s_par + G::off(0, PB), s_grd + G::off(0, PB), s_lr, ibc2, af.cfg);
-            adam_full<DEG, 1, 3 * PB / 4>(af.p + af.o[1] + 3 * i0, af.m + af.o[1] + 3 * i0, af.v + af.o[1] + 3 * i0,
-                                         s_par + G::off(1, PB), s_grd + G::off(1, PB), s_lr, ibc2, af.cfg);
-            adam_full<DEG, 2, PB>(af.p + af.o[2] + 4 * i0, af.m + af.o[2] + 4 * i0, af.v + af.o[2] + 4 * i0,
-                                  s_par + G::off(2, PB), s_grd + G::off(2, PB), s_lr, ibc2, af.cfg);
-            adam_full<DEG, 3, PB / 4>(af.p + af.o[3] + i0, af.m + af.o[3] + i0, af.v + af.o[3] + i0,
-                                      s_par + G::off(3, PB), s_grd + G::off(3, PB), s_lr, ibc2, af.cfg);
+        if (nb == WG) {
+            adam_full<DEG, 0, 3 * WG / 4>(af.p + af.o[0] + 3 * i0, af.m + af.o[0] + 3 * i0, af.v + af.o[0] + 3 * i0,
+                                         s_par + G::off(0, WG), s_grd + G::off(0, WG), s_lr, ibc2, af.cfg, lane, ng, nd);
+            adam_full<DEG, 1, 3 * WG / 4>(af.p + af.o[1] + 3 * i0, af.m + af.o[1] + 3 * i0, af.v + af.o[1] + 3 * i0,
+                                         s_par + G::off(1, WG), s_grd + G::off(1, WG), s_lr, ibc2, af.cfg, lane, ng, nd);
+            adam_full<DEG, 2, WG>(af.p + af.o[2] + 4 * i0, af.m + af.o[2] + 4 * i0, af.v + af.o[2] + 4 * i0,
+                                  s_par + G::off(2, WG), s_grd + G::off(2, WG), s_lr, ibc2, af.cfg, lane, ng, nd);
+            adam_full<DEG, 3, WG / 4>(af.p + af.o[3] + i0, af.m + af.o[3] + i0, af.v + af.o[3] + i0,
+                                      s_par + G::off(3, WG), s_grd + G::off(3, WG), s_lr, ibc2, af.cfg, lane, ng, nd);
             const int64_t o4 = af.o[4] + (int64_t)3 * K * i0;
-            adam_full<DEG, 4, 3 * K * PB / 4>(af.p + o4, af.m + o4, af.v + o4, s_par + G::off(4, PB),
-                                              s_grd + G::off(4, PB), s_lr, ibc2, af.cfg);
+            adam_full<DEG, 4, 3 * K * WG / 4>(af.p + o4, af.m + o4, af.v + o4, s_par + G::off(4, WG),
+                                              s_grd + G::off(4, WG), s_lr, ibc2, af.cfg, lane, ng, nd);
             return;
         }
 #pragma unroll
         for (int g = 0; g < 5; ++g) {
             const int cnt = G::S(g) * nb;
             const int64_t e0 = af.o[g] + (int64_t)G::S(g) * i0;
-            const float *sp = s_par + G::off(g, PB);
-            const float *sg = s_grd + G::off(g, PB);
-            // float4 chunks (e0 is 16-byte aligned: group offsets are 64-float aligned, i0 a multiple of PB)
+            const float *sp = s_par + G::off(g, WG);
+            const float *sg = s_grd + G::off(g, WG);
+            // float4 chunks (e0 is 16-byte aligned: group offsets are 64-float aligned, i0 a multiple of WG)
             const int cnt4 = cnt >> 2;
             float4 *P4 = reinterpret_cast<float4 *>(af.p + e0);
             float4 *M4 = reinterpret_cast<float4 *>(af.m + e0);
             float4 *V4 = reinterpret_cast<float4 *>(af.v + e0);
 #pragma unroll 2
-            for (int c = threadIdx.x; c < cnt4; c += PB) {
+            for (int c = lane; c < cnt4; c += 32) {
                 float4 m4 = M4[c], v4 = V4[c], p4;
                 float *pm = &m4.x, *pv = &v4.x, *pp4 = &p4.x;
 #pragma unroll
@@ -509,19 +540,25 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
                     const int k = 4 * c + u;
                     const int lr = g < 4 ? g : ((k % (3 * K)) < 3 ? 4 : 5);
                     const int ks = G::pad(g, k);
-                    float p = sp[ks];
-                    adam_update(p, pm[u], pv[u], sg[ks], s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+                    const float p0 = sp[ks], gk = sg[ks];
+                    float p = p0;
+                    adam_update(p, pm[u], pv[u], gk, s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
                     pp4[u] = p;
+                    ng += gk * gk;
+                    nd += (p - p0) * (p - p0);
                 }
                 P4[c] = p4;
                 M4[c] = m4;
                 V4[c] = v4;
             }
-            for (int k = 4 * cnt4 + threadIdx.x; k < cnt; k += PB) {
+            for (int k = 4 * cnt4 + lane; k < cnt; k += 32) {
                 const int lr = g < 4 ? g : ((k % (3 * K)) < 3 ? 4 : 5);
                 const int ks = G::pad(g, k);
-                float p = sp[ks], m = af.m[e0 + k], v = af.v[e0 + k];
-                adam_update(p, m, v, sg[ks], s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+                const float p0 = sp[ks], gk = sg[ks];
+                float p = p0, m = af.m[e0 + k], v = af.v[e0 + k];
+                adam_update(p, m, v, gk, s_lr[lr], af.cfg.beta1, af.cfg.beta2, ibc2, af.cfg.eps);
+                ng += gk * gk;
+                nd += (p - p0) * (p - p0);
                 af.p[e0 + k] = p;
                 af.m[e0 + k] = m;
                 af.v[e0 + k] = v;
@@ -534,10 +571,35 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
         for (int g = 0; g < 5; ++g) {
             const int cnt = G::S(g) * nb;
             float *dp = dst[g] + (int64_t)G::S(g) * i0;
-            const float *sg = s_grd + G::off(g, PB);
-            for (int k = threadIdx.x; k < cnt; k += PB) {
+            const float *sg = s_grd + G::off(g, WG);
+            for (int k = lane; k < cnt; k += 32) {
                 if constexpr (MODE == 1) dp[k] += sg[G::pad(g, k)];
                 else dp[k] = sg[G::pad(g, k)];
+            }
+        }
+    }
+    }();
+    if constexpr (MODE == 2) {
+        if (af.norms2) {  // block sums, one double atomic per block and quantity
+            __shared__ float s_red[2][PB / 32];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                ng += __shfl_xor_sync(0xffffffffu, ng, off);
+                nd += __shfl_xor_sync(0xffffffffu, nd, off);
+            }
+            if (lane == 0) {
+                s_red[0][threadIdx.x >> 5] = ng;
+                s_red[1][threadIdx.x >> 5] = nd;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double a = 0.0, b = 0.0;
+                for (int w = 0; w < PB / 32; ++w) {
+                    a += s_red[0][w];
+                    b += s_red[1][w];
+                }
+                atomicAdd(af.norms2, a);
+                atomicAdd(af.norms2 + 1, b);
             }
         }
     }
@@ -735,43 +797,72 @@ gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t
                                    grads, accumulate, af, stream);
 }
 
+// The flat-buffer view of the parameters and the fused Adam arguments.
+static gs_status fused_args(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                            const gs_raster_config *cfg, const gs_adam_config *adam, const int32_t *dev_do_step,
+                            int64_t *dev_step, double *norms2, gs_params *prm, AdamFuse *af) {
+    if (!flat_params || !m || !v || !adam || !dev_step || n < 0 || n >= ((int64_t)1 << 31) || sh_degree < 0 ||
+        sh_degree > 3 || cfg == nullptr || cfg->sh_degree != sh_degree)
+        return GS_ERR_INVALID_ARG;
+    if (((uintptr_t)flat_params | (uintptr_t)m | (uintptr_t)v) & 15) return GS_ERR_INVALID_ARG;
+    if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f && adam->eps >= 0.f))
+        return GS_ERR_INVALID_ARG;
+    *af = AdamFuse{};
+    af->p = flat_params;
+    af->m = m;
+    af->v = v;
+    param_offsets(n, sh_degree, af->o);
+    af->cfg = *adam;
+    af->do_step = dev_do_step;
+    af->step = dev_step;
+    af->norms2 = norms2;
+    prm->means = flat_params + af->o[0];
+    prm->log_scales = flat_params + af->o[1];
+    prm->quats = flat_params + af->o[2];
+    prm->opacity_logit = flat_params + af->o[3];
+    prm->sh = flat_params + af->o[4];
+    prm->n = n;
+    prm->sh_degree = sh_degree;
+    return GS_OK;
+}
+
 gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
                              const gs_projected *proj, const uint32_t *vals, const uint32_t *ranges,
                              const gs_camera *cams, int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg,
                              gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate,
                              const gs_adam_config *adam, const int32_t *dev_do_step, int64_t *dev_step,
-                             void *workspace, size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
+                             double *norms2, void *workspace, size_t workspace_bytes, int32_t *dev_status,
+                             cudaStream_t stream) {
     (void)dev_status;
-    if (!flat_params || !m || !v || !adam || !dev_step || n < 0 || n >= ((int64_t)1 << 31) || sh_degree < 0 ||
-        sh_degree > 3 || cfg == nullptr || cfg->sh_degree != sh_degree)
-        return GS_ERR_INVALID_ARG;
+    gs_params prm;
+    AdamFuse af;
+    gs_status st = fused_args(flat_params, m, v, n, sh_degree, cfg, adam, dev_do_step, dev_step, norms2, &prm, &af);
+    if (st != GS_OK) return st;
     if (!proj || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0) return GS_ERR_INVALID_ARG;
     if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
-    if (((uintptr_t)flat_params | (uintptr_t)m | (uintptr_t)v | (uintptr_t)proj->rec) & 15) return GS_ERR_INVALID_ARG;
-    if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f && adam->eps >= 0.f))
-        return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
     if (n == 0) return GS_OK;
-    AdamFuse af{};
-    af.p = flat_params;
-    af.m = m;
-    af.v = v;
-    param_offsets(n, sh_degree, af.o);
-    af.cfg = *adam;
-    af.do_step = dev_do_step;
-    af.step = dev_step;
-    gs_params prm;
-    prm.means = flat_params + af.o[0];
-    prm.log_scales = flat_params + af.o[1];
-    prm.quats = flat_params + af.o[2];
-    prm.opacity_logit = flat_params + af.o[3];
-    prm.sh = flat_params + af.o[4];
-    prm.n = n;
-    prm.sh_degree = sh_degree;
     gs_grads none{};
     return render_bwd_impl<true>(&prm, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
                                  view_gate, none, 0, af, workspace, stream);
+}
+
+gs_status gs_project_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                              const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg, const float *g2d,
+                              const uint8_t *view_gate, const gs_adam_config *adam, const int32_t *dev_do_step,
+                              int64_t *dev_step, double *norms2, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    gs_params prm;
+    AdamFuse af;
+    gs_status st = fused_args(flat_params, m, v, n, sh_degree, cfg, adam, dev_do_step, dev_step, norms2, &prm, &af);
+    if (st != GS_OK) return st;
+    if (!cams || !g2d || n_views <= 0 || ((uintptr_t)g2d & 15)) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    gs_grads none{};
+    return project_bwd_impl<true>(&prm, cams, n_views, cfg, reinterpret_cast<const float4 *>(g2d), view_gate, none, 0,
+                                  af, stream);
 }
 
 }  // extern "C"

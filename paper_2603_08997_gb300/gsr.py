@@ -96,7 +96,9 @@ _PROTOS = {
                                  _P, _S]),
     "gs_render_bwd_adam": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(gs_projected), _P, _P, _P, _I32, _I64,
                                      C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, C.POINTER(gs_adam_config), _P,
-                                     _P, _P, _SZ, _P, _S]),
+                                     _P, _P, _P, _SZ, _P, _S]),
+    "gs_project_bwd_adam": (C.c_int, [_P, _P, _P, _I64, _I32, _P, _I32, C.POINTER(gs_raster_config), _P, _P,
+                                      C.POINTER(gs_adam_config), _P, _P, _P, _P, _S]),
     "gs_adam_step": (C.c_int, [_P, _P, _P, _P, _I64, _I32, C.POINTER(gs_adam_config), _P, _P, _I32, _P, _S]),
     "gs_log_step": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P, _I64, _S]),
     "skipgs_gate_state_size": (C.c_size_t, [_I32]),

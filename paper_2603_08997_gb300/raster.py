@@ -261,15 +261,26 @@ class Renderer:
 
     def backward_adam(self, model: "GaussianModel", adam: "AdamState", dL_dimage: torch.Tensor | None = None,
                       view_gate: torch.Tensor | None = None, do_step: torch.Tensor | None = None,
-                      stream=None) -> None:
-        """Backward pass and Adam step in one call (gs_render_bwd_adam)."""
+                      norms2: torch.Tensor | None = None, stream=None) -> None:
+        """Backward pass and Adam step in one call (gs_render_bwd_adam); norms2
+        (2 float64, optional) receives the sums of g^2 and of the squared update."""
         proj = self.c_proj()
         dl = self.dL_dimage if dL_dimage is None else dL_dimage
         gsr.call("gs_render_bwd_adam", gsr.ptr(model.flat), gsr.ptr(adam.m), gsr.ptr(adam.v), model.n,
                  model.sh_degree, C.byref(proj), gsr.ptr(self.vals), gsr.ptr(self.ranges), gsr.ptr(self.views.dev),
                  self.views.n, self.views.total_tiles, C.byref(self.cfg), self.c_saved(), gsr.ptr(dl),
-                 gsr.ptr(view_gate), C.byref(adam.cfg), gsr.ptr(do_step), gsr.ptr(adam.step_count),
+                 gsr.ptr(view_gate), C.byref(adam.cfg), gsr.ptr(do_step), gsr.ptr(adam.step_count), gsr.ptr(norms2),
                  gsr.ptr(self.bwd_ws), self.bwd_ws_bytes, gsr.ptr(self.status), gsr.stream_handle(stream))
+
+    def project_bwd_adam(self, model: "GaussianModel", adam: "AdamState", view_gate: torch.Tensor | None = None,
+                         do_step: torch.Tensor | None = None, norms2: torch.Tensor | None = None,
+                         stream=None) -> None:
+        """Projection adjoint of the 2D gradients in self.bwd_ws fused with the
+        Adam step (gs_project_bwd_adam): raster_bwd then this = backward_adam."""
+        gsr.call("gs_project_bwd_adam", gsr.ptr(model.flat), gsr.ptr(adam.m), gsr.ptr(adam.v), model.n,
+                 model.sh_degree, gsr.ptr(self.views.dev), self.views.n, C.byref(self.cfg), gsr.ptr(self.bwd_ws),
+                 gsr.ptr(view_gate), C.byref(adam.cfg), gsr.ptr(do_step), gsr.ptr(adam.step_count), gsr.ptr(norms2),
+                 gsr.ptr(self.status), gsr.stream_handle(stream))
 
     # --- helpers for inspection (synchronise)
     def image_of(self, v: int = 0) -> torch.Tensor:

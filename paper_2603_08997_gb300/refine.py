@@ -9,9 +9,10 @@ Batched form (views_per_step = B > 1): B views per iteration in B camera
 slots sized for the largest training view; each slot takes its view's pose,
 intrinsics and size on the device, the gate decides the B losses in order
 (reading (vii)), the adjoint runs for the views with g = 1 only, and Adam
-steps once if any did.  The backward branch issues
-gs_render_bwd then gs_adam_step; fused=True uses gs_render_bwd_adam (the
-projection adjoint and Adam in one kernel) instead.
+steps once if any did.  The backward branch issues gs_render_bwd_adam (the
+raster adjoint, then the projection adjoint and Adam in one kernel, so the
+parameter gradients never reach DRAM); fused=False issues gs_render_bwd then
+gs_adam_step instead.
 
 `step_graph` replays the iteration as one CUDA graph: the bracketed branch is
 an IF conditional node that the gate kernel sets on the device, so no value
@@ -34,7 +35,7 @@ class RefinementLoop:
     def __init__(self, model: GaussianModel, train_cams: list, targets, view_seq,
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
-                 fused: bool = False, views_per_step: int = 1, log_capacity: int = 0):
+                 fused: bool = True, views_per_step: int = 1, log_capacity: int = 0):
         """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
         [3, H_v, W_v] tensors, one per training view."""
         import copy
@@ -102,7 +103,7 @@ class RefinementLoop:
         r.loss_backward(self.targets, self.target_offsets, self.view_ids, stream=s)
         if self.fused:
             r.backward_adam(self.model, self.adam, view_gate=gate, do_step=self.any if predicated else None,
-                            stream=s)
+                            norms2=self.norms2, stream=s)
         else:
             r.backward(self.params, self.grads, view_gate=gate, accumulate=False, stream=s)
             self.adam.step(do_step=self.any if predicated else None, norms2=self.norms2, stream=s)

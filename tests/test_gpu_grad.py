@@ -179,29 +179,39 @@ def test_autograd_function_matches_oracle():
 
 @pytest.mark.parametrize("deg", [3, 0, 2])
 def test_fused_backward_adam_equals_separate_calls(deg):
-    """gs_render_bwd_adam = gs_render_bwd followed by gs_adam_step, over two steps."""
-    scene, cam = synth.scene_tiny(300, seed=2, sh_degree=deg)
+    """gs_render_bwd_adam, and gs_raster_bwd + gs_project_bwd_adam, equal
+    gs_render_bwd followed by gs_adam_step over two steps, telemetry included.
+    1500 Gaussians: full warps and a partial last warp of the fused sweep."""
+    scene, cam = synth.scene_tiny(1500 + 13, seed=2, sh_degree=deg)
     target = torch.from_numpy(np.random.default_rng(3).uniform(0, 1, (3, cam.height, cam.width)).astype(np.float32))
     target = target.cuda().view(-1)
     out = []
-    for fused in (False, True):
+    for form in ("separate", "fused", "split"):
         r, model = _setup(scene, cam)
         adam = raster.AdamState(model)
+        norms = torch.zeros(2, dtype=torch.float64, device="cuda")
         for _ in range(2):
             r.forward(model.c_params())
             r.compute_loss(target, with_grad=True)
-            if fused:
-                r.backward_adam(model, adam)
+            if form == "fused":
+                r.backward_adam(model, adam, norms2=norms)
+            elif form == "split":
+                r.raster_bwd()
+                r.project_bwd_adam(model, adam, norms2=norms)
             else:
                 r.backward(model.c_params(), model.c_grads(adam.grad))
-                adam.step()
+                adam.step(norms2=norms)
         torch.cuda.synchronize()
-        out.append((model.flat.clone(), adam.m.clone(), adam.v.clone(), int(adam.step_count.item())))
-    (p0, m0, v0, s0), (p1, m1, v1, s1) = out
-    assert s0 == s1 == 2
-    torch.testing.assert_close(p1, p0, rtol=1e-6, atol=1e-7)
-    torch.testing.assert_close(m1, m0, rtol=1e-5, atol=1e-10)
-    torch.testing.assert_close(v1, v0, rtol=1e-5, atol=1e-14)
+        out.append((model.flat.clone(), adam.m.clone(), adam.v.clone(), int(adam.step_count.item()),
+                    norms.cpu().numpy()))
+    p0, m0, v0, s0, n0 = out[0]
+    assert n0[0] > 0 and n0[1] > 0
+    for p1, m1, v1, s1, n1 in out[1:]:
+        assert s0 == s1 == 2
+        torch.testing.assert_close(p1, p0, rtol=1e-6, atol=1e-7)
+        torch.testing.assert_close(m1, m0, rtol=1e-5, atol=1e-10)
+        torch.testing.assert_close(v1, v0, rtol=1e-5, atol=1e-14)
+        np.testing.assert_allclose(n1, n0, rtol=1e-4)
 
 
 @pytest.mark.parametrize("tile,ppt", [(16, 2), (8, 2), (32, 2), (16, 1), (16, 4), (32, 4)])
