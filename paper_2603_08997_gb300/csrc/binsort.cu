@@ -602,12 +602,31 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             s_eg[threadIdx.x] = gi;
             area = (int)r.z * r.w;
         }
-        uint32_t tot_u;
-        const int pre = (int)block_exclusive_scan((uint32_t)area, s_warp, &tot_u);
-        if (threadIdx.x < WIN) s_pre[threadIdx.x] = pre;
-        if (threadIdx.x == 0) s_pre[WIN] = (int)tot_u;
+        // the window's pair prefix: a warp scan in the WIN / 32 warps holding
+        // entries, their totals through shared memory (one barrier).  The
+        // barrier also orders the previous window's mask clearing and slot
+        // advances before this window's pass A.
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int inc = area;
+        if (threadIdx.x < WIN) {  // whole warps
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += y;
+            }
+            if (lane == 31) s_warp[warp] = (uint32_t)inc;
+        }
         __syncthreads();
-        const int tot = (int)tot_u;
+        int before = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < WIN / 32; ++w) {
+            const int x = (int)s_warp[w];
+            before += w < warp ? x : 0;
+            tot += x;
+        }
+        if (threadIdx.x < WIN) s_pre[threadIdx.x] = before + inc - area;
+        if (threadIdx.x == 0) s_pre[WIN] = tot;
+        __syncthreads();
         // pass A: entry masks per tile (the first sub-window's pairs are also
         // recorded for pass B)
         for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
@@ -653,10 +672,22 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                         jj = it.jj;
                     }
                     const int jw = jj / WB, jb = jj % WB;
+                    W mw[NW];
+                    if constexpr (NW == 4) {  // the tile's four words in one 16-byte load
+                        static_assert(sizeof(W) == 4, "four 32-bit mask words");
+                        const uint4 q4 = *reinterpret_cast<const uint4 *>(s_mask + t * NW);
+                        mw[0] = q4.x;
+                        mw[1] = q4.y;
+                        mw[2] = q4.z;
+                        mw[3] = q4.w;
+                    } else {
+#pragma unroll
+                        for (int wd = 0; wd < NW; ++wd) mw[wd] = s_mask[t * NW + wd];
+                    }
                     uint32_t below = 0, all = 0;
 #pragma unroll
                     for (int wd = 0; wd < NW; ++wd) {
-                        const W m = s_mask[t * NW + wd];
+                        const W m = mw[wd];
                         const uint32_t pc = (uint32_t)__popc((uint32_t)m);
                         all += pc;
                         if (wd < jw) below += pc;
@@ -670,6 +701,9 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                 }
             }
             __syncthreads();
+            // No barrier after the advances: a tile advanced here has no pair in
+            // a later sub-window of this window, and the next window's first
+            // barrier orders them before its pass A.
 #pragma unroll
             for (int k = 0; k < SC_Q; ++k) {
                 if (last_t[k] >= 0) {
@@ -678,7 +712,6 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                     for (int wd = 0; wd < NW; ++wd) s_mask[last_t[k] * NW + wd] = 0;
                 }
             }
-            __syncthreads();
         }
     }
 }
