@@ -148,11 +148,16 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
         uint32_t k[RS_ITEMS], v[RS_ITEMS], lr[RS_ITEMS];
         int dg[RS_ITEMS];
 #pragma unroll
-        for (int r = 0; r < RS_ITEMS; ++r) {
+        for (int r = 0; r < RS_ITEMS; ++r) {  // every load of the thread first
             const int li = warp * 32 * RS_ITEMS + r * 32 + lane;
             const bool valid = li < n_tile;
             k[r] = valid ? keys_in[base + li] : 0u;
             v[r] = valid ? (vals_in ? vals_in[base + li] : (uint32_t)(base + li)) : 0u;  // no values: the index
+        }
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            const int li = warp * 32 * RS_ITEMS + r * 32 + lane;
+            const bool valid = li < n_tile;
             const int d = valid ? (int)((k[r] >> shift) & mask) : RADIX + lane;
             // lanes with the same digit: intersect one ballot per digit bit
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
