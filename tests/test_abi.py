@@ -67,6 +67,32 @@ def test_host_side_checks(lib):
     assert lib.skipgs_gate_init(C.byref(cfg), C.c_void_p(16), None) == gsr.GS_ERR_INVALID_ARG
 
 
+def test_fused_adjoint_adam_argument_checks(lib):
+    """gs_project_bwd_adam refuses bad arguments before any launch: missing
+    buffers, unaligned moments, degree mismatch, beta outside [0, 1)."""
+    from paper_2603_08997_gb300 import gsr
+    rc = gsr.gs_raster_config()
+    rc.sh_degree = 3
+    ac = gsr.gs_adam_config()
+    ac.beta1, ac.beta2, ac.eps = 0.9, 0.999, 1e-15
+    P = C.c_void_p
+    fn = lib.gs_project_bwd_adam
+
+    def call(flat=256, m=512, v=768, deg=3, cfg=rc, adam=ac, step=1024, g2d=2048):
+        return fn(P(flat) if flat else None, P(m) if m else None, P(v), 100, deg, P(4096), 1, C.byref(cfg), P(g2d),
+                  None, C.byref(adam), None, P(step) if step else None, None, None, None)
+
+    assert call(flat=0) == gsr.GS_ERR_INVALID_ARG
+    assert call(m=0) == gsr.GS_ERR_INVALID_ARG
+    assert call(step=0) == gsr.GS_ERR_INVALID_ARG
+    assert call(m=520) == gsr.GS_ERR_INVALID_ARG      # moments not 16-byte aligned
+    assert call(g2d=2052) == gsr.GS_ERR_INVALID_ARG   # 2D gradients not 16-byte aligned
+    assert call(deg=2) == gsr.GS_ERR_INVALID_ARG      # degree differs from the raster config
+    bad = gsr.gs_adam_config()
+    bad.beta1, bad.beta2, bad.eps = 0.9, 1.0, 1e-15
+    assert call(adam=bad) == gsr.GS_ERR_INVALID_ARG
+
+
 def test_workspace_too_small_is_refused(lib):
     from paper_2603_08997_gb300 import gsr
     proj = gsr.gs_projected(16, 16, 16)
