@@ -3,7 +3,9 @@
 // SSIM uses an 11x11 Gaussian window (sigma 1.5, separable), zero padding,
 // C1 = 0.01^2, C2 = 0.03^2.  One CTA computes a 32x16 output tile: it stages
 // the tile plus a 5-pixel halo of image and target in shared memory, filters
-// rows then columns, and evaluates the SSIM map.  Window sums are taken of
+// rows (a thread computes 4 adjacent outputs of a row, so each staged value
+// is loaded once per thread) then columns (2 adjacent rows per thread), and
+// evaluates the SSIM map.  Window sums are taken of
 // values shifted by the tile's centre value (exact for a window whose weights
 // sum to 1, padded pixels included), which keeps the variance terms
 // E[x^2] - E[x]^2 well conditioned in float32.
@@ -22,6 +24,8 @@ using namespace gsr;
 namespace {
 
 constexpr int LTW = 32, LTH = 16, HALO = 5, LW = LTW + 2 * HALO, LH = LTH + 2 * HALO;
+static_assert(LTW == 32 && LTH == 16 && LH * (LTW / 4) <= 256,
+              "a 32 x 8 block: 4-column row strips and 2-row column strips cover the tile");
 constexpr float SSIM_C1 = 0.0001f;  // (0.01)^2
 constexpr float SSIM_C2 = 0.0009f;  // (0.03)^2
 
@@ -66,7 +70,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__
                                                        float *__restrict__ dmaps, double2 *__restrict__ partials) {
     __shared__ float sx[LH][LW];
     __shared__ float sy[LH][LW];
-    __shared__ float hs[5][LH][LTW];
+    __shared__ __align__(16) float hs[5][LH][LTW];
     __shared__ double red[2][8];
     view_size(cam_dev, W, H);
     const float *tgt = target_base(target, target_offsets, view_ids, v, pix_offset);
@@ -82,61 +86,87 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float *__restrict__
     for (int ch = 0; ch < 3; ++ch) {
         const float *X = img + ch * hw, *Yp = tgt + ch * hw;
         const float shx = X[(int64_t)ccy * W + ccx], shy = Yp[(int64_t)ccy * W + ccx];
-        for (int idx = tid; idx < LH * LW; idx += 256) {
-            const int r = idx / LW, c = idx % LW;
-            const int gx = bx0 + c - HALO, gy = by0 + r - HALO;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const int64_t p = (int64_t)gy * W + gx;
-            sx[r][c] = (in ? X[p] : 0.f) - shx;
-            sy[r][c] = (in ? Yp[p] : 0.f) - shy;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < LH * LTW; idx += 256) {
-            const int r = idx / LTW, c = idx % LTW;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
-#pragma unroll
-            for (int t = 0; t < 11; ++t) {
-                const float w = win.w[t], xv = sx[r][c + t], yv = sy[r][c + t];
-                a0 += w * xv;
-                a1 += w * yv;
-                a2 += w * xv * xv;
-                a3 += w * yv * yv;
-                a4 += w * xv * yv;
-            }
-            hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2; hs[3][r][c] = a3; hs[4][r][c] = a4;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int r = threadIdx.y + 8 * half, c = threadIdx.x;
-            const int gx = bx0 + c, gy = by0 + r;
-            if (gx < W && gy < H) {
-                float m0 = 0.f, m1 = 0.f, e2 = 0.f, f2 = 0.f, exy = 0.f;
-#pragma unroll
-                for (int t = 0; t < 11; ++t) {
-                    const float w = win.w[t];
-                    m0 += w * hs[0][r + t][c];
-                    m1 += w * hs[1][r + t][c];
-                    e2 += w * hs[2][r + t][c];
-                    f2 += w * hs[3][r + t][c];
-                    exy += w * hs[4][r + t][c];
-                }
-                const float sxx = e2 - m0 * m0, syy = f2 - m1 * m1, sxy = exy - m0 * m1;
-                const float mx = m0 + shx, my = m1 + shy;
-                const float A1 = 2.f * mx * my + SSIM_C1, A2 = 2.f * sxy + SSIM_C2;
-                const float B1 = mx * mx + my * my + SSIM_C1, B2 = sxx + syy + SSIM_C2;
-                const float iD = 1.f / (B1 * B2);
-                const float m = A1 * A2 * iD;
-                const float P2 = -m / B2;
-                const float P3 = 2.f * A1 * iD;
-                const float dmu = (2.f * my * A2 - 2.f * mx * m * B2) * iD;
-                const float P1 = dmu - 2.f * mx * P2 - my * P3;
+        for (int r = threadIdx.y; r < LH; r += 8) {
+            for (int c = threadIdx.x; c < LW; c += 32) {
+                const int gx = bx0 + c - HALO, gy = by0 + r - HALO;
+                const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
                 const int64_t p = (int64_t)gy * W + gx;
-                dmaps[(0 * 3 + ch) * hw + p] = P1;
-                dmaps[(1 * 3 + ch) * hw + p] = P2;
-                dmaps[(2 * 3 + ch) * hw + p] = P3;
-                ssim_acc += m;
-                l1_acc += fabsf(X[p] - Yp[p]);
+                sx[r][c] = (in ? X[p] : 0.f) - shx;
+                sy[r][c] = (in ? Yp[p] : 0.f) - shy;
+            }
+        }
+        __syncthreads();
+        // rows: a thread filters 4 adjacent outputs of one row from 14 inputs
+        // (each input and its products loaded and formed once)
+        if (tid < LH * (LTW / 4)) {
+            const int r = tid / (LTW / 4), c0 = 4 * (tid % (LTW / 4));
+            float acc[4][5];
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[o][q] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 14; ++j) {
+                const float xv = sx[r][c0 + j], yv = sy[r][c0 + j];
+                const float in5[5] = {xv, yv, xv * xv, yv * yv, xv * yv};
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int t = j - o;
+                    if (t >= 0 && t < 11) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) acc[o][q] += win.w[t] * in5[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                *reinterpret_cast<float4 *>(&hs[q][r][c0]) = make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
+        }
+        __syncthreads();
+        // columns: a thread filters 2 adjacent output rows of one column
+        {
+            const int c = threadIdx.x, r0 = 2 * threadIdx.y;
+            float mm[2][5];
+#pragma unroll
+            for (int o = 0; o < 2; ++o)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) mm[o][q] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                float h[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) h[q] = hs[q][r0 + j][c];
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const int t = j - o;
+                    if (t >= 0 && t < 11) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) mm[o][q] += win.w[t] * h[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int gx = bx0 + c, gy = by0 + r0 + o;
+                if (gx < W && gy < H) {
+                    const float m0 = mm[o][0], m1 = mm[o][1], e2 = mm[o][2], f2 = mm[o][3], exy = mm[o][4];
+                    const float sxx = e2 - m0 * m0, syy = f2 - m1 * m1, sxy = exy - m0 * m1;
+                    const float mx = m0 + shx, my = m1 + shy;
+                    const float A1 = 2.f * mx * my + SSIM_C1, A2 = 2.f * sxy + SSIM_C2;
+                    const float B1 = mx * mx + my * my + SSIM_C1, B2 = sxx + syy + SSIM_C2;
+                    const float iD = 1.f / (B1 * B2);
+                    const float m = A1 * A2 * iD;
+                    const float P2 = -m / B2;
+                    const float P3 = 2.f * A1 * iD;
+                    const float dmu = (2.f * my * A2 - 2.f * mx * m * B2) * iD;
+                    const float P1 = dmu - 2.f * mx * P2 - my * P3;
+                    const int64_t p = (int64_t)gy * W + gx;
+                    dmaps[(0 * 3 + ch) * hw + p] = P1;
+                    dmaps[(1 * 3 + ch) * hw + p] = P2;
+                    dmaps[(2 * 3 + ch) * hw + p] = P3;
+                    ssim_acc += m;
+                    l1_acc += fabsf(X[p] - Yp[p]);
+                }
             }
         }
         __syncthreads();
@@ -190,7 +220,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__
                                                        const gs_camera *__restrict__ cam_dev, float lambda, Win win,
                                                        const float *__restrict__ dmaps, float *__restrict__ grad) {
     __shared__ float sp[3][LH][LW];
-    __shared__ float hs[3][LH][LTW];
+    __shared__ __align__(16) float hs[3][LH][LTW];
     view_size(cam_dev, W, H);
     const float *tgt = target_base(target, target_offsets, view_ids, v, pix_offset);
     const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -199,47 +229,72 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float *__restrict__
     const int64_t hw = (int64_t)W * H;
     const float inv_n = 1.f / (3.f * (float)hw);
     for (int ch = 0; ch < 3; ++ch) {
-        for (int idx = tid; idx < LH * LW; idx += 256) {
-            const int r = idx / LW, c = idx % LW;
-            const int gx = bx0 + c - HALO, gy = by0 + r - HALO;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const int64_t p = (int64_t)gy * W + gx;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) sp[q][r][c] = in ? dmaps[(q * 3 + ch) * hw + p] : 0.f;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < LH * LTW; idx += 256) {
-            const int r = idx / LTW, c = idx % LTW;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll
-            for (int t = 0; t < 11; ++t) {
-                const float w = win.w[t];
-                a0 += w * sp[0][r][c + t];
-                a1 += w * sp[1][r][c + t];
-                a2 += w * sp[2][r][c + t];
-            }
-            hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int r = threadIdx.y + 8 * half, c = threadIdx.x;
-            const int gx = bx0 + c, gy = by0 + r;
-            if (gx < W && gy < H) {
-                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-#pragma unroll
-                for (int t = 0; t < 11; ++t) {
-                    const float w = win.w[t];
-                    f0 += w * hs[0][r + t][c];
-                    f1 += w * hs[1][r + t][c];
-                    f2 += w * hs[2][r + t][c];
-                }
+        for (int r = threadIdx.y; r < LH; r += 8) {
+            for (int c = threadIdx.x; c < LW; c += 32) {
+                const int gx = bx0 + c - HALO, gy = by0 + r - HALO;
+                const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
                 const int64_t p = (int64_t)gy * W + gx;
-                const float xv = img[ch * hw + p], yv = tgt[ch * hw + p];
-                const float dssim = (f0 + 2.f * xv * f1 + yv * f2) * inv_n;
-                const float diff = xv - yv;
-                const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-                grad[ch * hw + p] = (1.f - lambda) * sgn * inv_n - lambda * dssim;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) sp[q][r][c] = in ? dmaps[(q * 3 + ch) * hw + p] : 0.f;
+            }
+        }
+        __syncthreads();
+        // rows: 4 adjacent outputs of one row per thread
+        if (tid < LH * (LTW / 4)) {
+            const int r = tid / (LTW / 4), c0 = 4 * (tid % (LTW / 4));
+            float acc[4][3];
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc[o][q] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 14; ++j) {
+                const float in3[3] = {sp[0][r][c0 + j], sp[1][r][c0 + j], sp[2][r][c0 + j]};
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int t = j - o;
+                    if (t >= 0 && t < 11) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) acc[o][q] += win.w[t] * in3[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                *reinterpret_cast<float4 *>(&hs[q][r][c0]) = make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
+        }
+        __syncthreads();
+        // columns: 2 adjacent output rows of one column per thread
+        {
+            const int c = threadIdx.x, r0 = 2 * threadIdx.y;
+            float ff[2][3];
+#pragma unroll
+            for (int o = 0; o < 2; ++o)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) ff[o][q] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                const float h[3] = {hs[0][r0 + j][c], hs[1][r0 + j][c], hs[2][r0 + j][c]};
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const int t = j - o;
+                    if (t >= 0 && t < 11) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) ff[o][q] += win.w[t] * h[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int gx = bx0 + c, gy = by0 + r0 + o;
+                if (gx < W && gy < H) {
+                    const int64_t p = (int64_t)gy * W + gx;
+                    const float xv = img[ch * hw + p], yv = tgt[ch * hw + p];
+                    const float dssim = (ff[o][0] + 2.f * xv * ff[o][1] + yv * ff[o][2]) * inv_n;
+                    const float diff = xv - yv;
+                    const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+                    grad[ch * hw + p] = (1.f - lambda) * sgn * inv_n - lambda * dssim;
+                }
             }
         }
         __syncthreads();

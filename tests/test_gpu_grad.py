@@ -277,6 +277,59 @@ def test_backward_mixed_pixels_per_thread():
         assert gpu_util.rel_err(g, res[0]) < 1e-6
 
 
+@pytest.mark.parametrize("t0", [0, 1, 99, 2999, 29999])
+def test_adam_bias_correction_at_step_counts(t0):
+    """One Adam step after t0 executed steps (random moments) against the FP64
+    oracle: the bias corrections 1 - beta^t hold from t = 1, where they are
+    small differences, to t = 30000, where they are 1."""
+    gpu_util.lib()
+    scene, _ = synth.scene_tiny(64, seed=5, sh_degree=1)
+    model = raster.GaussianModel.from_scene(scene)
+    cfg = AdamConfig()
+    adam = raster.AdamState(model, lr=cfg.lrs(), beta1=cfg.beta1, beta2=cfg.beta2, eps=cfg.eps)
+    # the kernel receives the betas as float32 (gs_adam_config): the oracle
+    # takes the same values, so 1 - beta2 agrees beyond the 1e-5 that
+    # float32(0.999) differs from 0.999 by
+    cfg = AdamConfig(beta1=float(np.float32(cfg.beta1)), beta2=float(np.float32(cfg.beta2)), eps=cfg.eps)
+    rng = np.random.default_rng(10 + t0)
+    n, K = scene.n, scene.sh.shape[1]
+    lr = {"means": cfg.lr_means, "log_scales": cfg.lr_log_scales, "quats": cfg.lr_quats,
+          "opacity_logit": cfg.lr_opacity,
+          "sh": np.where((np.arange(3 * K * n) % (3 * K)) < 3, cfg.lr_sh_dc, cfg.lr_sh_rest)}
+    model.flat.zero_()  # p = 0: the float32 result carries the update to full relative precision
+    pv, mv, vv, gv = (model.group_views(x) for x in (model.flat, adam.m, adam.v, adam.grad))
+    state = {}
+    for k in GROUPS:
+        shape = tuple(pv[k].shape)
+        g = rng.normal(0, 1e-3, shape).astype(np.float32)
+        m = (rng.normal(0, 1e-3, shape) if t0 else np.zeros(shape)).astype(np.float32)
+        v = (rng.uniform(1e-10, 1e-5, shape) if t0 else np.zeros(shape)).astype(np.float32)
+        gv[k].copy_(torch.from_numpy(g))
+        mv[k].copy_(torch.from_numpy(m))
+        vv[k].copy_(torch.from_numpy(v))
+        state[k] = (pv[k].double().cpu().numpy().ravel(), g.astype(np.float64).ravel(), m.astype(np.float64).ravel(),
+                    v.astype(np.float64).ravel())
+    adam.step_count.fill_(t0)
+    adam.step()
+    torch.cuda.synchronize()
+    assert int(adam.step_count.item()) == t0 + 1
+    for k in GROUPS:
+        p0, g, m, v = state[k]
+        p1, m1, v1, _ = adam_step(p0, g, m, v, t0, lr[k], cfg)
+        got = pv[k].double().cpu().numpy().ravel()
+        # moments: a few float32 roundings of the two terms (the sum may cancel)
+        m_tol = 4e-7 * (cfg.beta1 * np.abs(m) + (1 - cfg.beta1) * np.abs(g))
+        v_tol = 4e-7 * (cfg.beta2 * v + (1 - cfg.beta2) * g * g)
+        # update: 2e-5 of itself (SFU square root and reciprocal, bias
+        # corrections) plus what the first moment's rounding carries
+        t = t0 + 1
+        den = np.sqrt(v1 / (1 - cfg.beta2 ** t)) + cfg.eps
+        p_tol = 2e-5 * np.abs(p1) + lr[k] * m_tol / (1 - cfg.beta1 ** t) / den
+        assert np.all(np.abs(got - p1) <= p_tol)
+        assert np.all(np.abs(mv[k].double().cpu().numpy().ravel() - m1) <= m_tol)
+        assert np.all(np.abs(vv[k].double().cpu().numpy().ravel() - v1) <= v_tol)
+
+
 def test_adam_norms_telemetry():
     """gs_adam_step's optional norms: sum g^2 and sum (p_new - p_old)^2."""
     gpu_util.lib()
