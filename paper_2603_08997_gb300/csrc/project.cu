@@ -79,13 +79,16 @@ __device__ __forceinline__ void project_one(const float (&mu)[3], const float (&
 // One block of PB Gaussians: their parameter slices are staged once into
 // shared memory with coalesced 16-byte loads, then each thread projects its
 // Gaussian into every view (the parameters are read from DRAM once however
-// many views there are).
+// many views there are).  On entry a block also asks L2 for the parameter
+// slices of the block `ahead` / PB positions later (one resident wave of
+// blocks ahead), so a block's staging loads find their lines in L2 instead
+// of waiting on DRAM while the wave before it computes.
 template <int DEG>
 __global__ void __launch_bounds__(PB) project_kernel(gs_params prm, const gs_camera *__restrict__ cams, int n_views,
                                                      gs_raster_config cfg, float *__restrict__ rec,
                                                      int4 *__restrict__ rect, int32_t *__restrict__ touched,
                                                      uint32_t *__restrict__ depth_key,
-                                                     ushort4 *__restrict__ rect16) {
+                                                     ushort4 *__restrict__ rect16, int64_t ahead) {
     using G = ParamGroups<DEG>;
     extern __shared__ float s_par[];  // [TOT * PB]
     __shared__ gs_camera s_cams[kStagedViews];
@@ -94,6 +97,18 @@ __global__ void __launch_bounds__(PB) project_kernel(gs_params prm, const gs_cam
     const int64_t i0 = (int64_t)blockIdx.x * PB;
     const int nb = (int)min((int64_t)PB, n - i0);
     const float *src[5] = {prm.means, prm.log_scales, prm.quats, prm.opacity_logit, prm.sh};
+    {
+        // slices of a full block start on 16-byte boundaries (groups 256-byte
+        // aligned, i0 + ahead a multiple of PB)
+        const int64_t j0 = i0 + ahead;
+        if (threadIdx.x < 5 && ahead > 0 && j0 + PB <= n) {
+            const int g = threadIdx.x;  // selects, not an indexed array (no local copy)
+            const float *sp = g == 0 ? prm.means : g == 1 ? prm.log_scales : g == 2 ? prm.quats
+                            : g == 3 ? prm.opacity_logit : prm.sh;
+            const int sg = g < 2 ? 3 : g == 2 ? 4 : g == 3 ? 1 : 3 * G::K;
+            prefetch_l2(sp + (int64_t)sg * j0, (uint32_t)(sizeof(float) * sg * PB));
+        }
+    }
     if (nb == PB)
         stage_block_full<DEG>(src, i0, s_par);
     else
@@ -126,8 +141,18 @@ gs_status launch_project(const gs_params &prm, const gs_camera *cams, int n_view
         GS_TRY(cudaFuncSetAttribute(project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set = true;
     }
+    // one resident wave of blocks, in Gaussians (the prefetch distance);
+    // computed once per instantiation on the first call's device
+    static int64_t ahead = -1;
+    if (ahead < 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        GS_TRY(cudaGetDevice(&dev));
+        GS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel<DEG>, PB, smem));
+        ahead = (int64_t)per_sm * sms * PB;
+    }
     project_kernel<DEG><<<(unsigned)ceil_div(prm.n, (int64_t)PB), PB, smem, stream>>>(prm, cams, n_views, cfg, rec, rect,
-                                                                                     touched, depth_key, rect16);
+                                                                                     touched, depth_key, rect16, ahead);
     GS_TRY_LAUNCH();
     return GS_OK;
 }
