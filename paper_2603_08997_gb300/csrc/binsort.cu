@@ -253,8 +253,6 @@ int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int
     return cur;
 }
 
-int radix_passes(int bits) { return (bits + RADIX_BITS - 1) / RADIX_BITS; }
-
 // depth keys: float32 bits of the depth (positive, so the bit patterns order
 // like the values); culled entries sort last and emit nothing.
 __global__ void depth_keys_kernel(const float *__restrict__ rec, const int32_t *__restrict__ touched, int64_t total,
@@ -885,7 +883,10 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     const int4 *rect = reinterpret_cast<const int4 *>(proj->rect);
     // 2. counting sort of the pairs by tile, in depth order
     const size_t smem = sizeof(uint32_t) * (size_t)mvt;
-    GS_TRY(bin_smem_attributes());
+    {
+        const gs_status st = bin_smem_attributes();
+        if (st != GS_OK) return st;
+    }
     if (proj->rect16)  // written by gs_project
         bin_rects16<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(
             reinterpret_cast<const ushort4 *>(proj->rect16), order, cams, g, total, w.srect);

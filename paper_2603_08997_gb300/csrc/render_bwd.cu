@@ -17,9 +17,11 @@
 // values), summed per Gaussian in shared memory, and added once per
 // (Gaussian, tile) to a per-view buffer with float4 vector atomics.
 //
-// Projection adjoint: one thread per Gaussian chains those 2D gradients
+// Projection adjoint: one lane per Gaussian chains those 2D gradients
 // through Eq. (proj), Eq. (cov), the SH colour and the sigmoid to the
-// parameters, summing the views.
+// parameters, summing the views; each warp stages and sweeps its own 32
+// Gaussians.  The sweep either stores the parameter gradients or applies the
+// Adam step to them directly (gs_render_bwd_adam, gs_project_bwd_adam).
 #include "common.cuh"
 
 using namespace gsr;
