@@ -460,6 +460,13 @@ def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
             torch.cuda.synchronize()
             out[name] = {"ms": e0.elapsed_time(e1) / reps}
     loop.restore(snap)
+    return weigh_stages(out, b_frac)
+
+
+def weigh_stages(out: dict, b_frac: float) -> dict:
+    """Each stage's weight in a gated iteration (1 every step, b_frac for the
+    backward branch, 0 for the unfused alternative the loop does not run) and
+    its share of the weighted sum; `out` maps stage -> {"ms": ...}."""
     tot = 0.0
     for name, v in out.items():
         v["weight"] = 0.0 if name in UNFUSED_STAGES else (b_frac if name in BACKWARD_STAGES else 1.0)
@@ -471,7 +478,7 @@ def stage_times(loop, targets, b_frac: float, reps: int = 10) -> dict:
 
 def roofline_of(stages: dict, loop, args) -> dict:
     """Roofline of the stage with the largest share of the gated iteration.
-    Algorithmic work per launch (stated in the design doc): HBM stages count bytes
+    Algorithmic work per launch: HBM stages count bytes
     a launch must move; compositing stages count FLOPs per evaluated
     (pixel, Gaussian) pair, with the evaluated pairs counted as sum(n_last)."""
     import json as _json
