@@ -49,8 +49,12 @@ def test_roofline_names_the_largest_share_and_divides_algorithmic_work_by_time()
 
 
 def test_stored_traffic_only_for_matching_sources(monkeypatch):
+    import json
+    import os
+    stored = json.load(open(os.path.join(bench.ROOT, "profiles", "stage_traffic_3M.json")))
+    monkeypatch.setattr(bench, "sources_sha256", lambda: stored["sources_sha256"])
     got, note = bench.stage_traffic("bin_sort")
-    assert got is not None and got > 0, note  # the committed capture matches the committed kernels
+    assert got == float(stored["per_launch_bytes"]["bin_sort"]) and got > 0, note
     monkeypatch.setattr(bench, "sources_sha256", lambda: "0" * 64)
     got, note = bench.stage_traffic("bin_sort")
     assert got is None and "changed" in note
