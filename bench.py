@@ -345,12 +345,15 @@ def oracle_sample_step(scene, cam, frac: float, seed: int = 0):
     key = ("proj_full", id(cam))
     if key not in scene.extra:
         scene.extra[key] = oracle.project(scene, cam, rc)  # sample selection only, untimed
-    pr = scene.extra[key]
-    m = pr["mean2d"]
-    sel = np.nonzero((pr["touched"] > 0) & (m[:, 0] > x0 - 16) & (m[:, 0] < x0 + cw + 16) &
-                     (m[:, 1] > y0 - 16) & (m[:, 1] < y0 + ch + 16))[0]
-    sub = synth.Scene(scene.means[sel], scene.log_scales[sel], scene.quats[sel], scene.opacity_logit[sel],
-                      scene.sh[sel])
+    skey = ("sample", id(cam), cw, ch)  # the crop's Gaussians, untimed, reused by later steps of one size
+    if skey not in scene.extra:
+        pr = scene.extra[key]
+        m = pr["mean2d"]
+        sel = np.nonzero((pr["touched"] > 0) & (m[:, 0] > x0 - 16) & (m[:, 0] < x0 + cw + 16) &
+                         (m[:, 1] > y0 - 16) & (m[:, 1] < y0 + ch + 16))[0]
+        scene.extra[skey] = synth.Scene(scene.means[sel], scene.log_scales[sel], scene.quats[sel],
+                                        scene.opacity_logit[sel], scene.sh[sel])
+    sub = scene.extra[skey]
     target = np.random.default_rng(seed).uniform(0, 1, (3, ch, cw))
     from oracle.adam import AdamConfig, adam_step, lr_vector
     cfg = AdamConfig()
