@@ -340,12 +340,17 @@ gs_status gs_adam_step(float *params, float *grads, float *m, float *v, int64_t 
 
 /* The backward pass and the optimizer step of Algorithm 1 in one call: the
  * adjoint of gs_render_bwd, after which every parameter of the flat buffer
- * (gs_param_layout; quats, m and v 16-byte aligned) takes one Adam step with
- * the gradient just computed, without storing the gradient.  Equal to
- * gs_render_bwd (accumulate = 0) followed by gs_adam_step; dev_do_step,
- * dev_step and norms2 (nullable) as in gs_adam_step, view_gate as in
- * gs_render_bwd.  The projection adjoint and the Adam step run in one kernel,
- * so the parameter gradients never reach DRAM. */
+ * (gs_param_layout) takes one Adam step with the gradient just computed,
+ * without storing the gradient.  Equal to gs_render_bwd (accumulate = 0)
+ * followed by gs_adam_step; dev_do_step, dev_step and norms2 (nullable) as in
+ * gs_adam_step, view_gate as in gs_render_bwd.  The projection adjoint and the
+ * Adam step run in one kernel, so the parameter gradients never reach DRAM.
+ * flat_params, m and v: device, caller-owned, gs_param_layout(n, sh_degree)
+ * floats each, 16-byte aligned, updated in place.  workspace: device, at least
+ * gs_render_bwd_workspace_size(n, n_views) bytes, 16-byte aligned (the 2D
+ * gradients).  Returns GS_ERR_INVALID_ARG (null or unaligned pointers,
+ * sh_degree outside 0..3 or unlike cfg->sh_degree, beta outside [0, 1),
+ * eps < 0) or GS_ERR_WORKSPACE before any launch. */
 gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
                              const gs_projected *proj /* host */, const uint32_t *vals, const uint32_t *ranges,
                              const gs_camera *cams, int32_t n_views, int64_t total_tiles,
@@ -355,9 +360,10 @@ gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, 
                              size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream);
 
 /* The second half of gs_render_bwd_adam on its own: the projection adjoint of
- * the 2D gradients that gs_raster_bwd left in g2d (layout and alignment as
- * there), fused with the Adam step as above.  gs_raster_bwd followed by this
- * call equals gs_render_bwd_adam. */
+ * the 2D gradients that gs_raster_bwd left in g2d (device, layout and
+ * alignment as there), fused with the Adam step as above.  gs_raster_bwd
+ * followed by this call equals gs_render_bwd_adam.  Argument checks as for
+ * gs_render_bwd_adam (GS_ERR_INVALID_ARG before any launch). */
 gs_status gs_project_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
                               const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg /* host */,
                               const float *g2d, const uint8_t *view_gate, const gs_adam_config *adam /* host */,
