@@ -39,7 +39,8 @@ WORKLOAD = ("3M Gaussians SH3, 200 jittered-ring views 1297x840, post-densificat
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--steps", type=int, default=1000,
+                    help="timed iterations: the last K of the --iters-iteration post-densification loop")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
     ap.add_argument("--n", type=int, default=3_000_000)
@@ -50,6 +51,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--ref-seconds", type=float, default=150.0, help="budget of the reference arm")
     ap.add_argument("--pre", type=int, default=5000, help="always-backward iterations before the measured loop")
+    ap.add_argument("--iters", type=int, default=5000,
+                    help="length of each measured post-densification loop (both arms run all of it; the last "
+                         "--steps iterations are timed)")
     ap.add_argument("--c4", action="store_true",
                     help="batched workload instead of the default line: 8 ring views per iteration at mixed "
                          "resolutions (640x360 .. 1600x1063), launch shape autotuned; prints its own JSON line")
@@ -158,7 +162,7 @@ def setup_c3(args, dev):
     from paper_2603_08997_gb300 import raster
     from paper_2603_08997_gb300.refine import RefinementLoop
 
-    seq_len = max(args.steps, 5000)
+    seq_len = max(args.steps, getattr(args, "iters", 5000), 5000)
     gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=seq_len,
                                          width=args.width, height=args.height)
     st = raster.RasterSettings()
@@ -202,40 +206,27 @@ def run_rho_sweep(args) -> None:
     build.build()
     dev = torch.device("cuda", 0)
     model, cams, targets, seq, init, st, cap, _ = setup_c3(args, dev)
-    K = args.steps
+    K = max(args.iters, args.steps)  # the whole loop is timed here
 
     def run(gated: bool, rho_lo: float):
         loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, rho_lo=rho_lo, pair_capacity=cap,
                               log_capacity=K)
         loop.restore(init)
         loop.capture()
-        torch.cuda.synchronize()
-        # timed in segments ending at the final-loss checkpoints K-3s .. K (as
-        # the headline loops); the evaluations between segments are not timed
-        seg = max(1, min(250, K // 4))
-        marks = sorted({m for m in (K - 3 * seg, K - 2 * seg, K - seg, K) if m > 0})
-        ms, done, evals = 0.0, 0, []
-        for mark in marks:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(loop.stream)
-            for _ in range(mark - done):
-                loop.step_graph()
-            e1.record(loop.stream)
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-            done = mark
-            if mark == K:
-                log = loop.read_log(K)
-            evals.append(float(np.mean(loop.evaluate())))
-        final = float(np.mean(evals))
-        gs = loop.gate.read(loop.stream)
+        res = run_measured_loop(loop, plan_loop(K, K))
+        log = loop.read_log(K)
+        final = float(np.mean(res["evals"]))
+        gs = res["gate_end"]
         loop.close()
         tenth = max(1, K // 10)
-        stepped = log["g"][:, 0] > 0
+        stepped = log["g"][:, 0] > 0 if gated else np.ones(K, bool)
         gn = np.sqrt(log["grad_sq"][stepped]) if stepped.any() else np.zeros(1)
         un = np.sqrt(log["update_sq"][stepped]) if stepped.any() else np.zeros(1)
-        return {"rho_lo": rho_lo if gated else None, "gated": gated, "iters_per_s": K / (ms * 1e-3),
-                "rho_cum": gs["b"] / max(gs["t"], 1), "rho_min": gs["rho_min"], "final_loss": final,
+        # the always-backward loop runs every backward pass; its gate still
+        # decides (and would have skipped where g = 0), reported separately
+        return {"rho_lo": rho_lo if gated else None, "gated": gated, "iters_per_s": K / (res["ms_loop"] * 1e-3),
+                "backward_passes": gs["b"] if gated else K, "rho_cum": gs["b"] / max(gs["t"], 1) if gated else 1.0,
+                "gate_open_rate": gs["b"] / max(gs["t"], 1), "rho_min": gs["rho_min"], "final_loss": final,
                 "grad_norm_first_tenth": float(np.mean(gn[:tenth])), "grad_norm_last_tenth": float(np.mean(gn[-tenth:])),
                 "update_norm_first_tenth": float(np.mean(un[:tenth])),
                 "update_norm_last_tenth": float(np.mean(un[-tenth:]))}
@@ -328,9 +319,9 @@ class ClockSampler:
 
 def oracle_sample_step(scene, cam, frac: float, seed: int = 0):
     """One oracle refinement iteration on a bounded sample of the workload: the
-    crop of the view covering `frac` of its pixels (centred) with the Gaussians
-    whose projected centres fall in it (plus a 16-pixel border), against a
-    seeded target.  Returns (seconds, pixels of the crop)."""
+    crop of the view covering `frac` of its pixels (centred) with every
+    Gaussian whose support box reaches it, against a seeded target.  Returns
+    (seconds, pixels of the crop)."""
     import numpy as np
 
     import oracle
@@ -348,9 +339,11 @@ def oracle_sample_step(scene, cam, frac: float, seed: int = 0):
     skey = ("sample", id(cam), cw, ch)  # the crop's Gaussians, untimed, reused by later steps of one size
     if skey not in scene.extra:
         pr = scene.extra[key]
-        m = pr["mean2d"]
-        sel = np.nonzero((pr["touched"] > 0) & (m[:, 0] > x0 - 16) & (m[:, 0] < x0 + cw + 16) &
-                         (m[:, 1] > y0 - 16) & (m[:, 1] < y0 + ch + 16))[0]
+        m, r = pr["mean2d"], pr["radius"]
+        # every Gaussian whose support box (mean2D +- half-extents) reaches the
+        # crop, wherever its centre lies
+        sel = np.nonzero((pr["touched"] > 0) & (m[:, 0] + r[:, 0] >= x0) & (m[:, 0] - r[:, 0] <= x0 + cw) &
+                         (m[:, 1] + r[:, 1] >= y0) & (m[:, 1] - r[:, 1] <= y0 + ch))[0]
         scene.extra[skey] = synth.Scene(scene.means[sel], scene.log_scales[sel], scene.quats[sel],
                                         scene.opacity_logit[sel], scene.sh[sel])
     sub = scene.extra[skey]
@@ -388,13 +381,29 @@ def cpu_baseline(args, scene, cam, budget_s: float) -> dict:
     its = (pix / full_px) / total
     return {"value": its, "unit": "iters/s", "cores": cores, "kind": "oracle",
             "sample": f"{runs} oracle iteration(s) on a centred crop of {pix // runs} px of view 0 "
-                      f"({100.0 * pix / runs / full_px:.1f}% of 1297x840) with the Gaussians over it; "
+                      f"({100.0 * pix / runs / full_px:.1f}% of 1297x840) with every Gaussian whose support "
+                      f"box reaches it; "
                       f"{total:.1f} s CPU wall time, scaled to the full view by the pixel fraction"}
 
 
+def workload_config(args, plan: dict, world: int) -> dict:
+    """The `config` object of the bench line (both arms print the same one)."""
+    return {"workload": WORKLOAD, "n_gaussians": args.n, "views": args.views, "width": args.width,
+            "height": args.height, "loop_iterations": plan["iters"],
+            "timed": f"the last {plan['K']} of {plan['iters']} post-densification iterations "
+                     f"(t = {plan['start'] + 1}..{plan['iters']})",
+            "parallelism": "replicas" if world > 1 else "1 GPU",
+            "l2": "inputs larger than L2 (2.8 GB of parameters and Adam state, 2.6 GB of targets)"}
+
+
 def run_reference(args) -> None:
+    """The oracle arm: each step one FP64 oracle refinement iteration on a
+    bounded crop of the workload's view (the same crop size every step, sized
+    so the whole run takes about --ref-seconds), scaled to full-view
+    iterations/s by the pixel fraction."""
     import synth
     K, W = args.steps, args.warmup
+    plan = plan_loop(max(args.iters, args.steps), args.steps)
     gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=max(K, 1),
                                          width=args.width, height=args.height)
     cam = cams[int(seq[0])]
@@ -413,21 +422,55 @@ def run_reference(args) -> None:
         pix += px
     value = (pix / (args.width * args.height)) / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
-            "steps": K, "warmup": W, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "steps": K, "warmup": W, "ms_per_step": 1000.0 * total / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views": args.views,
-                       "width": args.width, "height": args.height},
+            "value_def": "full-view iterations/s: the crop's pixel fraction per timed second; ms_per_step is the "
+                         "wall time of one timed sample step",
+            "config": workload_config(args, plan, 1),
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: one FP64 oracle iteration on a centred crop covering "
-                                       f"{100 * frac:.3f}% of the view's pixels with the Gaussians over it, "
-                                       f"scaled to the full view by the pixel fraction"},
+                                       f"{100 * frac:.3f}% of the view's pixels with every Gaussian whose support "
+                                       f"box reaches it, scaled to the full view by the pixel fraction"},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------ GPU arm
 
-PEAK_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
+# FP32 work per (pixel, Gaussian) pair of the compositing kernels, counted from
+# the operations Eq. (alpha) and Eq. (blend) and their adjoint need (a fused
+# multiply-add counts two):
+#   evaluating alpha' at a pixel inside the support box: offset (2), |U dp|^2
+#   (7), exponent scale and opacity (2), clamp and cut-off tests (2) = 13, plus
+#   one exponential on the special-function unit;
+#   forward, per contributing pair: 1 - alpha', T (1 - alpha') and its test,
+#   alpha' T, three colour FMAs = 10;
+#   adjoint, per contributing pair: T rebuilt (2 + a reciprocal), weight (1),
+#   colour gradients (6), dL/dalpha' (14), colour-behind suffix sums (6),
+#   opacity, mean2D and conic gradients (23), and the nine sums over pixels
+#   per Gaussian (9) = 61.
+FLOP_EVAL, FLOP_FWD_CONTRIB, FLOP_BWD_CONTRIB = 13, 10, 61
+
+
+def peak_alu_tflops(sm_count: int, sm_mhz: float) -> float:
+    """FP32 peak from unit counts and the clock: SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def device_alu_peak(peaks: dict):
+    """(TFLOP/s, note) for the current device: its SM count and the maximum SM
+    clock the driver measured (else 2070 MHz, the part's maximum)."""
+    sms = 152
+    try:
+        import torch
+        if torch.cuda.is_available():
+            sms = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        pass
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return peak_alu_tflops(sms, mhz), f"derived FP32 peak: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz"
+
+
 BACKWARD_STAGES = ("loss_bwd", "raster_bwd", "project_bwd_adam")
 UNFUSED_STAGES = ("project_bwd", "adam")  # the loop's fused=False alternative to project_bwd_adam
 
@@ -479,11 +522,36 @@ def weigh_stages(out: dict, b_frac: float) -> dict:
     return out
 
 
-def roofline_of(stages: dict, loop, args) -> dict:
-    """Roofline of the stage with the largest share of the gated iteration.
-    Algorithmic work per launch: HBM stages count bytes
-    a launch must move; compositing stages count FLOPs per evaluated
-    (pixel, Gaussian) pair, with the evaluated pairs counted as sum(n_last)."""
+def atomic_probe_rate(n_records: int, n_updates: int, reps: int = 3) -> float:
+    """Peak rate (updates/s) of the raster adjoint's global atomic pattern -
+    two float4 and one float reduction per update into scattered 48-byte
+    records (gs_atomic_probe) - over a buffer of n_records records; best of
+    `reps` launches timed with CUDA events."""
+    import torch
+    from paper_2603_08997_gb300 import gsr
+    buf = torch.zeros(n_records * 12, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    best = float("inf")
+    gsr.call("gs_atomic_probe", gsr.ptr(buf), n_records, n_updates, gsr.stream_handle(s))
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        gsr.call("gs_atomic_probe", gsr.ptr(buf), n_records, n_updates, gsr.stream_handle(s))
+        e1.record(s)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del buf
+    return n_updates / best
+
+
+def roofline_of(stages: dict, loop, args, census: dict | None = None, atomic_peak: float | None = None) -> dict:
+    """Roofline of the stage with the largest share of the gated iteration, and
+    of every stage.  Algorithmic work per launch: HBM stages count the bytes a
+    launch must move; the compositing kernels count FP32 operations per
+    (pixel, Gaussian) pair the method needs (FLOP_* above) over the pairs the
+    work census found: evaluations inside support boxes and contributing
+    pairs.  The raster adjoint also reports its global atomic rate against the
+    probe's peak, and the bytes its pairs move through L2."""
     import json as _json
     peaks = {}
     try:
@@ -492,13 +560,17 @@ def roofline_of(stages: dict, loop, args) -> dict:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_note = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback 6.8 TB/s"
+    alu_peak, alu_note = device_alu_peak(peaks)
     r = loop.renderer
     N = r.n
     E = N * r.views.n
     P = int(r.pair_count.item())
     px = r.views.total_pixels
-    evals = float(r.n_last.double().sum().item())
     T = r.views.total_tiles
+    if census is None:  # no census: every list position up to n_last, all contributing (an upper bound)
+        ev = float(r.n_last.double().sum().item())
+        census = dict(sum_n_last=ev, evaluated=ev, contributing=ev, tile_pairs=P, staged=P)
+    ev, con = float(census["evaluated"]), float(census["contributing"])
     chunk = max(1024, -(-(-(-N // 304)) // 256) * 256)  # entries per chunk of the tile counting sort
     n_c = -(-N // chunk) * r.views.n
     params = loop.model.flat.numel()
@@ -508,16 +580,48 @@ def roofline_of(stages: dict, loop, args) -> dict:
                      "bytes: 148 B per (view, Gaussian) entry (depth keys 16, four radix passes 80, clipped "
                      "rectangles 32, counting 8, placement 12) + 4 B per (Gaussian, tile) pair + 16 B per "
                      "(chunk, tile) count-matrix cell + 8 B per tile range"),
-        "render_fwd": ("alu", 12.0 * evals, "FLOP: 12 per evaluated pair"),
+        "render_fwd": ("alu", FLOP_EVAL * ev + FLOP_FWD_CONTRIB * con,
+                       f"FLOP: {FLOP_EVAL} per evaluated (pixel, Gaussian) pair inside its support box "
+                       f"({ev:.4g}) + {FLOP_FWD_CONTRIB} per contributing pair ({con:.4g}), from the work census"),
         "loss": ("hbm", 60 * px, "bytes: 60 B per pixel"),
         "loss_bwd": ("hbm", 72 * px, "bytes: 72 B per pixel"),
-        "raster_bwd": ("alu", 40.0 * evals, "FLOP: 40 per evaluated pair"),
+        "raster_bwd": ("alu", FLOP_EVAL * ev + FLOP_BWD_CONTRIB * con,
+                       f"FLOP: {FLOP_EVAL} per evaluated pair ({ev:.4g}) + {FLOP_BWD_CONTRIB} per contributing "
+                       f"pair ({con:.4g}), from the work census"),
         "project_bwd": ("hbm", N * (236 + 48 + 236), "bytes: 520 B per Gaussian"),
         "adam": ("hbm", 28 * params, "bytes: 28 B per parameter (read p, g, m, v; write p, m, v)"),
         "project_bwd_adam": ("hbm", N * 48 * r.views.n + 24 * params,
                              "bytes: 48 B of 2D gradients per (view, Gaussian) + 24 B per parameter "
                              "(read p, m, v; write p, m, v)"),
     }
+
+    def frac_of(k):
+        w = work[k]
+        a = (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12)
+        return a, a / (hbm if w[0] == "hbm" else alu_peak)
+
+    all_stages = {}
+    for k, w in work.items():
+        if k not in stages:
+            continue
+        a, f = frac_of(k)
+        all_stages[k] = {"bound": w[0], "achieved": a, "frac": f, "ms": stages[k]["ms"]}
+    # the raster adjoint: global atomics (three instructions per (tile,
+    # Gaussian) pair with a contributor) against the probe's peak, and the
+    # bytes its pairs move (40 B record re-read per staged entry, 36 B of
+    # atomic read-modify-write per contributing (tile, Gaussian) pair), which
+    # L2 serves
+    if "raster_bwd" in stages:
+        t_b = stages["raster_bwd"]["ms"] * 1e-3
+        tp = float(census["tile_pairs"])
+        at = {"updates_per_s": tp / t_b, "atomic_instructions_per_launch": 3 * tp}
+        if atomic_peak:
+            at.update(peak_updates_per_s=atomic_peak, frac=tp / t_b / atomic_peak,
+                      peak_note="gs_atomic_probe: the same three-atomic update at hashed records of a "
+                                "[N][12]-float buffer, best of 3 launches")
+        l2_bytes = 40.0 * float(census["staged"]) + 36.0 * tp
+        all_stages["raster_bwd"].update(atomic=at, pair_bytes_per_launch=l2_bytes,
+                                        pair_bytes_gbs=l2_bytes / t_b / 1e9)
     name = max(stages, key=lambda k: stages[k]["share"])
     bound, units, note = work[name]
     traffic, traffic_note = stage_traffic(name)
@@ -525,14 +629,11 @@ def roofline_of(stages: dict, loop, args) -> dict:
     if bound == "hbm":
         achieved, peak, unit, pk_note = units / t / 1e9, hbm, "GB/s", hbm_note
     else:
-        achieved, peak, unit = units / t / 1e12, PEAK_ALU_TFLOPS, "TFLOP/s"
-        pk_note = "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
+        achieved, peak, unit, pk_note = units / t / 1e12, alu_peak, "TFLOP/s", alu_note
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": traffic, "traffic_note": traffic_note, "work_per_launch": units, "work_def": note, "launch_ms": t * 1e3,
-            "share_of_gated_iteration": stages[name]["share"], "peak_note": pk_note,
-            "all_stages": {k: {"bound": w[0], "achieved": (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12),
-                               "frac": (w[1] / (stages[k]["ms"] * 1e-3)) / (1e9 if w[0] == "hbm" else 1e12) /
-                               (hbm if w[0] == "hbm" else PEAK_ALU_TFLOPS)} for k, w in work.items()}}
+            "traffic": traffic, "traffic_note": traffic_note, "work_per_launch": units, "work_def": note,
+            "launch_ms": t * 1e3, "share_of_gated_iteration": stages[name]["share"], "peak_note": pk_note,
+            "census": census, "all_stages": all_stages}
 
 
 def sources_sha256() -> str:
@@ -576,6 +677,80 @@ def job_value(steps: int, world: int, t_max: float) -> float:
     return steps * world / t_max
 
 
+def plan_loop(iters: int, K: int) -> dict:
+    """Where one measured loop stops.  The loop runs `iters` iterations from
+    the post-pre-phase snapshot; its last K form the timed window.  The
+    final-loss checkpoints sit at iters - 3s, iters - 2s, iters - s and iters
+    (s = min(250, iters // 4)); the all-view evaluations there are not timed,
+    so the window is split where a checkpoint falls inside it.
+    Returns {"iters", "K", "start", "marks", "evals"}: run to each mark in
+    turn; the window is [start, iters)."""
+    iters = max(1, int(iters))
+    K = max(1, min(int(K), iters))
+    start = iters - K
+    seg = max(1, min(250, iters // 4))
+    evals = sorted({m for m in (iters - 3 * seg, iters - 2 * seg, iters - seg, iters) if m > 0})
+    marks = sorted(({start} if start > 0 else set()) | set(evals))
+    return {"iters": iters, "K": K, "start": start, "marks": marks, "evals": evals}
+
+
+def backward_split(ms_full: float, ms_gated: float, iters: int, n_bwd: int, min_skip_frac: float = 0.1):
+    """Forward and backward ms per view from two loops over the same `iters`
+    iterations, one always-backward (t_full = iters (f + b)) and one gated with
+    n_bwd backward passes (t_gated = iters f + n_bwd b).  The system is only
+    determined when the gated loop skipped enough of them: with fewer than
+    min_skip_frac * iters skips the difference is timing noise and (None, None)
+    comes back."""
+    skipped = iters - n_bwd
+    if iters <= 0 or skipped < max(1.0, min_skip_frac * iters):
+        return None, None
+    b = (ms_full - ms_gated) / skipped
+    f = ms_full / iters - b
+    return f, b
+
+
+def run_measured_loop(loop, plan: dict, dist=None, on_window=None) -> dict:
+    """Runs a restored, captured RefinementLoop through plan_loop's marks
+    (graph replays; CUDA events on the loop's stream around every segment).
+    Returns the window's and the whole loop's device ms, the gate counters at
+    the window's start and end, and the final-loss evaluations."""
+    import numpy as np
+    import torch
+    done, ms_all, ms_win, evals = 0, 0.0, 0.0, []
+    g0 = {"t": 0, "b": 0}
+    wall0 = None
+    for mark in plan["marks"]:
+        in_window = done >= plan["start"]
+        torch.cuda.synchronize()
+        if in_window and done == plan["start"]:
+            if dist:
+                dist.barrier()
+            if on_window:
+                on_window()
+            wall0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(loop.stream)
+        for _ in range(mark - done):
+            loop.step_graph()
+        e1.record(loop.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ms_all += ms
+        if in_window:
+            ms_win += ms
+        done = mark
+        if mark == plan["start"]:
+            g0 = loop.gate.read(loop.stream)
+        if mark in plan["evals"]:
+            evals.append(float(np.mean(loop.evaluate())))
+    if dist:
+        dist.barrier()
+    g1 = loop.gate.read(loop.stream)
+    return {"ms_window": ms_win, "ms_loop": ms_all, "gate_start": g0, "gate_end": g1, "evals": evals,
+            "wall_window": time.perf_counter() - wall0 if wall0 is not None else None,
+            "status": int(loop.renderer.status.item())}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -598,8 +773,7 @@ def main():
     import numpy as np
     import torch
 
-    import synth
-    from paper_2603_08997_gb300 import build, gsr, raster
+    from paper_2603_08997_gb300 import build
     from paper_2603_08997_gb300.refine import HostTargets, RefinementLoop
 
     build.build()
@@ -609,59 +783,44 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    K, W = args.steps, args.warmup
+    W = args.warmup
+    plan = plan_loop(max(args.iters, args.steps), args.steps)
+    K, iters = plan["K"], plan["iters"]
     dev = torch.device("cuda", local)
     model, cams, targets, seq, init, st, cap, start = setup_c3(args, dev)
 
-    def timed_loop(gated: bool):
+    def measured(gated: bool):
         loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, pair_capacity=cap)
         loop.restore(init)
         loop.capture()
-        for _ in range(W):
+        for _ in range(W):  # untimed warm-up replays (graph upload), then back to the snapshot
             loop.step_graph()
         loop.restore(init)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
         clock = ClockSampler(local) if (gated and rank == 0) else None
-        # timed in segments that end at the final-loss checkpoints K-3s, K-2s,
-        # K-s and K; the all-view evaluations between segments are not timed
-        seg = max(1, min(250, K // 4))
-        marks = sorted({m for m in (K - 3 * seg, K - 2 * seg, K - seg, K) if m > 0})
-        ms, done, evals = 0.0, 0, []
-        t0 = time.perf_counter()
-        for mark in marks:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_push("timed_gated" if gated else "timed_full")
-            e0.record(loop.stream)
-            for _ in range(mark - done):
-                loop.step_graph()
-            e1.record(loop.stream)
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_pop()
-            ms += e0.elapsed_time(e1)
-            done = mark
-            if mark >= K - 3 * seg:
-                evals.append(float(np.mean(loop.evaluate())))
-        wall = time.perf_counter() - t0
-        clocks = clock.stop() if clock else None
-        gs = loop.gate.read(loop.stream)
-        status = int(loop.renderer.status.item())
-        final = float(np.mean(evals))
-        return loop, ms, wall, gs, status, final, clocks
+        torch.cuda.nvtx.range_push("loop_gated" if gated else "loop_full")
+        res = run_measured_loop(loop, plan, dist)
+        torch.cuda.nvtx.range_pop()
+        res["clocks"] = clock.stop() if clock else None
+        return loop, res
 
-    full, ms_full, wall_full, gs_full, st_full, loss_full, _ = timed_loop(False)
+    full, r_full = measured(False)
     kc_full = full.kernels_per_step
     full.close()
-    gated, ms_gated, wall_gated, gs_gated, st_gated, loss_gated, clocks = timed_loop(True)
+    del full
+    gated, r_gated = measured(True)
     kc_gated = gated.kernels_per_step
+    b_loop = r_gated["gate_end"]["b"]
+    b_win = b_loop - r_gated["gate_start"]["b"]
 
     # per-stage timing on the loop's stream (CUDA events, after the timed loops),
     # weighted by how often each stage runs in the gated loop
-    stages = stage_times(gated, targets, b_frac=gs_gated["b"] / K)
-    roofline = roofline_of(stages, gated, args)
-    # end-to-end through the C ABI with host-resident targets
+    stages = stage_times(gated, targets, b_frac=b_loop / iters)
+    census = gated.renderer.census(gated.stream)
+    atomic_peak = atomic_probe_rate(args.n, max(census["tile_pairs"], 1 << 20))
+    roofline = roofline_of(stages, gated, args, census, atomic_peak)
+    # end to end through the C ABI with host-resident targets: the same loop,
+    # each step's target copied from pinned host memory, loss and decision
+    # copied back; wall clock over the same window
     e2e = None
     if not args.no_e2e:
         host_targets = targets.cpu().pin_memory()
@@ -675,11 +834,9 @@ def main():
         loop.target_offsets = torch.zeros(len(cams), dtype=torch.int64, device=dev)
         loop.restore(init)
         loop.capture()
-        loss_host = torch.empty(K, dtype=torch.float32).pin_memory()
-        g_host = torch.empty(K, dtype=torch.uint8).pin_memory()
-        seq_np = np.asarray(seq)
-
-        feeder = HostTargets(loop, host_targets, seq_np)
+        loss_host = torch.empty(iters + W, dtype=torch.float32).pin_memory()
+        g_host = torch.empty(iters + W, dtype=torch.uint8).pin_memory()
+        feeder = HostTargets(loop, host_targets, np.asarray(seq))
 
         def e2e_step(k):
             feeder.step()  # target from pinned host memory, copied while the previous iteration runs
@@ -691,46 +848,60 @@ def main():
             e2e_step(k)
         loop.restore(init)
         feeder.reset()
+        for k in range(plan["start"]):
+            e2e_step(k)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
-        for k in range(K):
+        for k in range(plan["start"], iters):
             e2e_step(k)
         torch.cuda.synchronize()
         wall_e2e = time.perf_counter() - t0
-        e2e = {"value": K / wall_e2e, "unit": "iters/s",
-               "h2d_bytes_per_step": 3 * args.height * args.width * 4, "d2h_bytes_per_step": 4 + 1}
+        e2e = {"value": K * world / aggregate_time(wall_e2e, dist, dev), "unit": "iters/s",
+               "h2d_bytes_per_step": 3 * args.height * args.width * 4, "d2h_bytes_per_step": 4 + 1,
+               "timed": f"wall clock over the last {K} of {iters} iterations, targets from pinned host memory"}
         loop.close()
 
     # aggregate over ranks: max time
-    t_gated = aggregate_time(ms_gated * 1e-3, dist, dev)
+    t_gated = aggregate_time(r_gated["ms_window"] * 1e-3, dist, dev)
+    t_full = aggregate_time(r_full["ms_window"] * 1e-3, dist, dev)
     if dist:
         dist.barrier()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    b = gs_gated["b"]
-    it_full = K / (ms_full * 1e-3)
-    it_gated = job_value(K, 1, t_gated)
-    t_bwd = (ms_full - ms_gated) / max(K - b, 1)          # ms per backward (per view)
-    t_fwd_ms = ms_full / K - t_bwd
-    launches = kc_gated[0] * K + kc_gated[1] * b
+    it_full = job_value(K, world, t_full)
+    it_gated = job_value(K, world, t_gated)
+    f_reg, b_reg = backward_split(r_full["ms_loop"], r_gated["ms_loop"], iters, b_loop)
+    bwd_stage = sum(stages[k]["ms"] for k in BACKWARD_STAGES)
+    fwd_stage = sum(stages[k]["ms"] for k in ("project", "bin_sort", "render_fwd", "loss"))
+    launches = kc_gated[0] * K + kc_gated[1] * b_win
+    loss_gated, loss_full = float(np.mean(r_gated["evals"])), float(np.mean(r_full["evals"]))
     line = {
-        "metric": METRIC, "value": job_value(K, world, t_gated), "unit": "iters/s", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": ms_gated / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": it_gated, "unit": "iters/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_gated * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views": args.views, "width": args.width,
-                   "height": args.height, "iterations_timed": K, "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (2.8 GB of parameters and Adam state, 2.6 GB of targets)"},
-        "full_bwd_iters_per_s": it_full * world, "gated_speedup": it_gated / it_full,
-        "bwd_ms_per_view": t_bwd, "fwd_ms_per_view": t_fwd_ms,
-        "backward_passes": b, "rho_cum": b / K, "rho_min": gs_gated["rho_min"],
+        "config": workload_config(args, plan, world),
+        "full_bwd_iters_per_s": it_full, "gated_speedup": it_gated / it_full,
+        "gate_in_warmup": plan["start"] < 500 + 1,
+        "backward_passes": b_win, "rho_cum_window": b_win / K, "rho_cum": b_loop / iters,
+        "rho_min": r_gated["gate_end"]["rho_min"],
+        "bwd_ms_per_view": bwd_stage, "fwd_ms_per_view": fwd_stage,
+        "bwd_fwd_def": "stage times (CUDA events): backward = loss_bwd + raster_bwd + project_bwd_adam, "
+                       "forward = project + bin_sort + render_fwd + loss",
+        "bwd_ms_per_view_loop": b_reg, "fwd_ms_per_view_loop": f_reg,
+        "loop": {"iterations": iters, "gated_iters_per_s": iters / (r_gated["ms_loop"] * 1e-3),
+                 "full_bwd_iters_per_s": iters / (r_full["ms_loop"] * 1e-3),
+                 "speedup": r_full["ms_loop"] / r_gated["ms_loop"], "backward_passes": b_loop,
+                 "rho_cum": b_loop / iters, "ms": {"gated": r_gated["ms_loop"], "full": r_full["ms_loop"]}},
         "final_loss_gated": loss_gated, "final_loss_full": loss_full,
-        "final_loss_def": "mean over all 200 views, averaged over the checkpoints at K-750, K-500, K-250, K",
+        "final_loss_def": "mean over all %d views, averaged over the checkpoints after iterations %s" % (
+            args.views, ", ".join(str(m) for m in plan["evals"])),
         "final_loss_rel_diff": (loss_gated - loss_full) / loss_full,
-        "device_status": [st_full, st_gated],
-        "wall_s": {"full": wall_full, "gated": wall_gated},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+        "device_status": [r_full["status"], r_gated["status"]],
+        "clocks": r_gated["clocks"], "e2e": e2e, "gpu_launches": launches,
         "kernels_per_step": {"always": kc_gated[0], "backward_branch": kc_gated[1],
                              "full_loop": kc_full[0] + kc_full[1]},
         "roofline": roofline,

@@ -213,8 +213,11 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
  * are capped: n * n_views <= 262144 entries and
  * gs_bin_sort_workspace_size(...) <= 16 MB; larger requests return
  * GS_ERR_WORKSPACE and launch nothing.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call
+ * Each call outside stream capture looks up the array's device address with
+ * the device current; a call during capture reuses the address of the last
+ * call outside capture on that device, so make one call before any stream
+ * capture, and again after the device's context was reset (cudaDeviceReset
+ * invalidates the address a captured graph holds: capture again).  Every call
  * shares the one array: calls that overlap on the GPU (different streams, or
  * other threads) race and must be serialised by the caller.  Nothing in the
  * array needs to start at zero: each call overwrites all scratch it reads.
@@ -456,6 +459,96 @@ gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, in
  * gs_adam_step for this iteration; 0 when no step ran).  All device memory. */
 gs_status gs_log_step(const int64_t *iter, int32_t n, const float *loss, const uint8_t *g, double *norms2,
                       float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap, cudaStream_t stream);
+
+/* ------------------------------------------------- adaptive density control */
+
+/* Adaptive density control (Sec. 3, Preliminaries): during the densification
+ * phase (iterations 0..T_d) Gaussians with a high view-space positional
+ * gradient are cloned when small and split when large, and near-transparent
+ * ones (alpha < eps_alpha) are pruned; after T_d the set is fixed.  The paper
+ * states the rules qualitatively; the thresholds are the caller's.
+ * Thresholds in the units the decision compares, so it is a float32
+ * comparison only: grad_thr on the mean view-space gradient norm (pixels),
+ * log_size_thr on the largest log-scale, logit_prune_thr on the opacity logit
+ * (opacity < eps_alpha <=> logit < log(eps_alpha / (1 - eps_alpha)));
+ * log_split_shrink: split children's log-scales are reduced by it (log 1.6 in
+ * the vanilla scheme). */
+typedef struct {
+    float grad_thr, log_size_thr, logit_prune_thr, log_split_shrink;
+} gs_densify_config;
+
+enum { GS_DENSIFY_KEEP = 0, GS_DENSIFY_CLONE = 1, GS_DENSIFY_SPLIT = 2, GS_DENSIFY_PRUNE = 3 };
+
+/* The gradient statistic, after a backward pass: for every view v (with
+ * view_gate[v] != 0 when view_gate, device u8[n_views], is given) and every
+ * Gaussian i visible in v (tiles_touched[v * n + i] > 0, as gs_project wrote),
+ * accum[i] += |(g2d.x, g2d.y)| - the norm of dL/dmean2D that gs_raster_bwd or
+ * gs_render_bwd_adam left in g2d (device, [n_views][n][12] floats, 16-byte
+ * aligned) - and denom[i] += 1.  accum: device float[n], denom: device
+ * int32[n], both caller-owned and updated in place (zero them to start). */
+gs_status gs_densify_accumulate(const float *g2d, const int32_t *tiles_touched, int64_t n, int32_t n_views,
+                                const uint8_t *view_gate, float *accum, int32_t *denom, cudaStream_t stream);
+
+/* Scratch bytes of gs_densify_decide for n Gaussians. */
+size_t gs_densify_workspace_size(int64_t n);
+
+/* One action per Gaussian into action[n] (device u8): with avg = accum /
+ * denom (one float32 division; 0 when denom = 0): GS_DENSIFY_PRUNE when the
+ * opacity logit < logit_prune_thr; else, when avg >= grad_thr,
+ * GS_DENSIFY_SPLIT if the largest log-scale > log_size_thr and
+ * GS_DENSIFY_CLONE otherwise; else GS_DENSIFY_KEEP.  Then offsets[n + 1]
+ * (device int64): the exclusive scan of the outputs per Gaussian (keep 1,
+ * clone 2, split 2, prune 0), so offsets[n] is the new count - read it to
+ * size the buffers of gs_densify_apply.  flat_params: gs_param_layout(n,
+ * sh_degree).  GS_ERR_WORKSPACE below gs_densify_workspace_size(n). */
+gs_status gs_densify_decide(const float *flat_params, int64_t n, int32_t sh_degree, const float *accum,
+                            const int32_t *denom, const gs_densify_config *cfg /* host */, uint8_t *action,
+                            int64_t *offsets, void *workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* The output set, in input order (a Gaussian's outputs consecutive, at
+ * offsets[i]): keep copies the Gaussian with its Adam moments; clone writes
+ * the Gaussian (moments kept) and then an identical copy (moments zero);
+ * split writes two children (moments zero) at mean + R(q / |q|) (exp(log_s)
+ * * z_k), k = 0, 1, with z = noise[i][k][0..3) (device float [n][2][3],
+ * standard normal draws, the caller's), log-scales reduced by
+ * log_split_shrink, rotation, opacity and SH copied; prune writes nothing.
+ * src_*: gs_param_layout(n, sh_degree) floats each; dst_*: caller-allocated
+ * gs_param_layout(n_out, sh_degree) floats each, n_out = offsets[n] (else
+ * GS_ERR_INVALID_ARG in dev_status and nothing is written).  The step count
+ * of the optimizer is the caller's and carries on; the statistics of the new
+ * set start at zero (the caller's arrays for n_out). */
+gs_status gs_densify_apply(const float *src_params, const float *src_m, const float *src_v, int64_t n,
+                           int32_t sh_degree, const uint8_t *action, const int64_t *offsets, const float *noise,
+                           const gs_densify_config *cfg /* host */, float *dst_params, float *dst_m, float *dst_v,
+                           int64_t n_out, int32_t *dev_status, cudaStream_t stream);
+
+/* ----------------------------------------------------------- measurement */
+
+/* Work census of one forward pass (not on the refinement path; for stating
+ * throughput per unit of algorithmic work).  Inputs as gs_render_fwd after
+ * it ran (records, vals, ranges, cams, n_last = saved.n_last), cfg->tile and
+ * the alpha constants as used there.  Writes counts[5] (device, uint64,
+ * overwritten): [0] sum over pixels of n_last; [1] (pixel, Gaussian) pairs
+ * before the pixel's last contributor whose support box (mean2D +- (rx, ry))
+ * contains the pixel centre - the evaluations of Eq. (alpha) the pass needs;
+ * [2] contributing pairs (alpha' >= alpha_min, Eq. blend); [3] (tile,
+ * Gaussian) pairs with a contributing pixel - the raster adjoint issues
+ * three global atomic instructions for each; [4] list entries up to each
+ * tile's largest n_last.  GS_ERR_INVALID_ARG for null or unaligned pointers
+ * before any launch.  The paper has no counterpart. */
+gs_status gs_raster_census(const gs_projected *proj /* host */, int64_t n, const uint32_t *vals,
+                           const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                           const gs_raster_config *cfg /* host */, const int32_t *n_last,
+                           unsigned long long *counts, cudaStream_t stream);
+
+/* Throughput probe of scattered global reductions: n_updates updates, each
+ * two float4 and one float atomic add into one of n_records 48-byte records
+ * of buf (device, 16-byte aligned, [n_records][12] floats, contents
+ * perturbed by ~1e-30 per update) chosen by a multiplicative hash of the
+ * update's index - the pattern the raster adjoint uses for its per-Gaussian
+ * 2D gradients.  Timing it gives the atomic peak the adjoint's rate is
+ * compared with.  The paper has no counterpart. */
+gs_status gs_atomic_probe(float *buf, int64_t n_records, int64_t n_updates, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

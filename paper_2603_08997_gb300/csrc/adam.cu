@@ -114,7 +114,8 @@ extern "C" gs_status gs_adam_step(float *params, float *grads, float *m, float *
     Groups G{o[1], o[2], o[3], o[4], o[5], 3 * K};
     if (n > 0) {
         int64_t blocks = ceil_div(G.total / 4 + 1, 256);
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        const int64_t resident = (int64_t)device_sm_count() * 8;  // 8 blocks of 256 threads per SM
+        if (blocks > resident) blocks = resident;
         if (norms2)
             adam_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(params, grads, m, v, G, *cfg, dev_do_step,
                                                                     dev_step, zero_grad, norms2);

@@ -812,17 +812,17 @@ constexpr int kMaxViewTiles = 20480;
 // Raise the dynamic shared-memory limit of the table kernels to the largest
 // table, once per device (before any stream capture, on the first call).
 gs_status bin_smem_attributes() {
-    static bool done[64] = {};
-    int dev = 0;
-    GS_TRY(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
+    static bool done[kMaxDevices] = {};
+    const int dev = cached_device_index();
+    if (dev < 0) return GS_ERR_UNSUPPORTED;
+    if (done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bytes + 8));
     GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(96 * 1024)));
     GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(ScatterMask<uint32_t, 1>::bytes_per_tile * kMaxViewTiles)));
-    if (dev >= 0 && dev < 64) done[dev] = true;
+    done[dev] = true;
     return GS_OK;
 }
 
@@ -940,7 +940,6 @@ constexpr size_t kNoAllocBytes = (size_t)16 << 20;        // the whole scratch
 // One copy per device that loads the library, held until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
 void *g_noalloc_ptr[kMaxDevices] = {};
 
 }  // namespace
@@ -953,12 +952,16 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, const gs_came
     if (n * n_views > kNoAllocMaxEntries) return GS_ERR_WORKSPACE;
     if (total_tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
     if (bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr) > kNoAllocBytes) return GS_ERR_WORKSPACE;
-    int dev = 0;
-    GS_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
-    if (!g_noalloc_ptr[dev]) {
-        // Host code cannot use the array's name as a device address: look the
-        // address up once per device, with that device current.
+    const int dev = cached_device_index();
+    if (dev < 0) return GS_ERR_UNSUPPORTED;
+    // Host code cannot use the array's name as a device address: look the
+    // address up with the device current.  Outside stream capture it is looked
+    // up on every call (so a context torn down and recreated, e.g. after
+    // cudaDeviceReset, gets the new address); during capture the address of
+    // the last call outside capture on this device is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GS_TRY(cudaStreamIsCapturing(stream, &cap));
+    if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
         void *p = nullptr;
         GS_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         g_noalloc_ptr[dev] = p;

@@ -18,6 +18,28 @@
 
 namespace gsr {
 
+// Host-side values that the CUDA runtime keeps per device (function
+// attributes, occupancy, SM count) are cached per device index.
+constexpr int kMaxDevices = 64;
+
+// The current device, or -1 when it cannot be queried or is beyond the cache.
+inline int cached_device_index() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return dev;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+inline int device_sm_count() {
+    static int sms[kMaxDevices] = {};
+    const int dev = cached_device_index();
+    if (dev >= 0 && sms[dev] > 0) return sms[dev];
+    int d = dev < 0 ? 0 : dev, n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 1;
+    if (dev >= 0) sms[dev] = n;
+    return n;
+}
+
 constexpr int kRecFloats = 12;   // packed projected record (see gsr.h)
 constexpr int kG2d = 12;         // per-Gaussian 2D gradient slots: dmean(2) dconic(3) dopac(1) drgb(3) pad(3)
 

@@ -136,20 +136,22 @@ gs_status launch_project(const gs_params &prm, const gs_camera *cams, int n_view
                          float *rec, int4 *rect, int32_t *touched, uint32_t *depth_key, ushort4 *rect16,
                          cudaStream_t stream) {
     constexpr size_t smem = sizeof(float) * ParamGroups<DEG>::TOT * PB;
-    static bool attr_set = false;  // raise the dynamic shared-memory limit once per instantiation
-    if (!attr_set && smem > 48 * 1024) {
+    // per device: the shared-memory limit is raised once, and the prefetch
+    // distance is one resident wave of blocks, in Gaussians
+    static bool attr_set[kMaxDevices] = {};
+    static int64_t ahead_of[kMaxDevices] = {};
+    const int dev = cached_device_index();
+    if (dev < 0) return GS_ERR_UNSUPPORTED;
+    if (!attr_set[dev] && smem > 48 * 1024) {
         GS_TRY(cudaFuncSetAttribute(project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+        attr_set[dev] = true;
     }
-    // one resident wave of blocks, in Gaussians (the prefetch distance);
-    // computed once per instantiation on the first call's device
-    static int64_t ahead = -1;
-    if (ahead < 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        GS_TRY(cudaGetDevice(&dev));
-        GS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t ahead = ahead_of[dev];
+    if (ahead <= 0) {
+        int per_sm = 0;
         GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_kernel<DEG>, PB, smem));
-        ahead = (int64_t)per_sm * sms * PB;
+        ahead = (int64_t)per_sm * device_sm_count() * PB;
+        ahead_of[dev] = ahead;
     }
     project_kernel<DEG><<<(unsigned)ceil_div(prm.n, (int64_t)PB), PB, smem, stream>>>(prm, cams, n_views, cfg, rec, rect,
                                                                                      touched, depth_key, rect16, ahead);

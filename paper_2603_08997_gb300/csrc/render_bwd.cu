@@ -195,7 +195,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                 if (ae.alpha < amin) continue;
                 contrib = true;
                 const float om = __fsub_rn(1.f, ae.alpha);
-                const float inv = rcp_approx(om);  // 1 - alpha >= 0.01
+                // correctly rounded (unbiased): T is rebuilt through up to a batch of
+                // these factors, so a biased approximate reciprocal would drift
+                const float inv = __frcp_rn(om);  // 1 - alpha >= 0.01
                 const float Tk = T[k] * inv;
                 const float wgt = ae.alpha * Tk;
                 const float c0 = sb.z, c1 = sb.w, c2 = sc.x;
@@ -649,10 +651,12 @@ gs_status launch_proj_bwd_mode(unsigned blocks, cudaStream_t stream, const gs_pa
                                int n_views, const uint8_t *gate, const gs_raster_config &cfg, const float4 *g2d,
                                const gs_grads &gr, const AdamFuse &af) {
     constexpr size_t smem = proj_bwd_smem<DEG>();
-    static bool attr_set = false;  // raise the dynamic shared-memory limit once per instantiation
-    if (!attr_set) {
+    static bool attr_set[kMaxDevices] = {};  // the shared-memory limit is raised once per device
+    const int dev = cached_device_index();
+    if (dev < 0) return GS_ERR_UNSUPPORTED;
+    if (!attr_set[dev]) {
         GS_TRY(cudaFuncSetAttribute(proj_bwd_kernel<DEG, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+        attr_set[dev] = true;
     }
     proj_bwd_kernel<DEG, MODE><<<blocks, PB, smem, stream>>>(prm, cams, n_views, gate, cfg, g2d, gr, af);
     GS_TRY_LAUNCH();

@@ -59,6 +59,14 @@ class gs_adam_config(C.Structure):
     _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class gs_densify_config(C.Structure):
+    _fields_ = [("grad_thr", C.c_float), ("log_size_thr", C.c_float), ("logit_prune_thr", C.c_float),
+                ("log_split_shrink", C.c_float)]
+
+
+GS_DENSIFY_KEEP, GS_DENSIFY_CLONE, GS_DENSIFY_SPLIT, GS_DENSIFY_PRUNE = range(4)
+
+
 class gs_gate_config(C.Structure):
     _fields_ = [("W", C.c_int32), ("beta", C.c_double), ("eps", C.c_double), ("rho_lo", C.c_double),
                 ("n_views", C.c_int32)]
@@ -115,6 +123,14 @@ _PROTOS = {
     "gs_graph_kernel_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "gs_graph_destroy": (C.c_int, [C.c_void_p]),
     "gs_select_views": (C.c_int, [_P, _I64, _P, _I32, _P, _P, _P, _S]),
+    "gs_raster_census": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
+                                   _P, _P, _S]),
+    "gs_atomic_probe": (C.c_int, [_P, _I64, _I64, _S]),
+    "gs_densify_accumulate": (C.c_int, [_P, _P, _I64, _I32, _P, _P, _P, _S]),
+    "gs_densify_workspace_size": (C.c_size_t, [_I64]),
+    "gs_densify_decide": (C.c_int, [_P, _I64, _I32, _P, _P, C.POINTER(gs_densify_config), _P, _P, _P, _SZ, _S]),
+    "gs_densify_apply": (C.c_int, [_P, _P, _P, _I64, _I32, _P, _P, _P, C.POINTER(gs_densify_config), _P, _P, _P,
+                                   _I64, _P, _S]),
 }
 
 _lib = None

@@ -10,6 +10,7 @@ arithmetic step runs in libgsr's kernels:
 from __future__ import annotations
 
 import ctypes as C
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -282,6 +283,19 @@ class Renderer:
                  gsr.ptr(view_gate), C.byref(adam.cfg), gsr.ptr(do_step), gsr.ptr(adam.step_count), gsr.ptr(norms2),
                  gsr.ptr(self.status), gsr.stream_handle(stream))
 
+    def census(self, stream=None) -> dict:
+        """Work of the last forward pass (gs_raster_census; synchronises):
+        sum of n_last, support-box evaluations, contributing pairs, (tile,
+        Gaussian) pairs with a contributor, staged list entries."""
+        counts = torch.zeros(5, dtype=torch.int64, device=self.image.device)
+        proj = self.c_proj()
+        gsr.call("gs_raster_census", C.byref(proj), self.n, gsr.ptr(self.vals), gsr.ptr(self.ranges),
+                 gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg),
+                 gsr.ptr(self.n_last), gsr.ptr(counts), gsr.stream_handle(stream))
+        torch.cuda.synchronize()  # the census ran on `stream`, not necessarily the current one
+        c = [int(x) for x in counts.cpu().tolist()]
+        return dict(sum_n_last=c[0], evaluated=c[1], contributing=c[2], tile_pairs=c[3], staged=c[4])
+
     # --- helpers for inspection (synchronise)
     def image_of(self, v: int = 0) -> torch.Tensor:
         return self.views.image_view(self.image, v)
@@ -351,3 +365,69 @@ class Gate:
         gsr.call("skipgs_gate_read", gsr.ptr(self.state), out, C.byref(rho), gsr.stream_handle(stream))
         return dict(t=out[0], b=out[1], n_w=out[2], n_w1=out[3], calibrated=out[4], errors=out[5], n_views=out[6],
                     rho_min=rho.value)
+
+
+def densify_config(grad_thr: float, max_scale: float, eps_alpha: float = 0.005,
+                   split_factor: float = 1.6) -> gsr.gs_densify_config:
+    """Thresholds of adaptive density control in the units gs_densify_decide
+    compares: the mean view-space gradient norm (pixels), the largest scale
+    (as a log-scale) and the opacity (as a logit); split children's scales
+    are divided by split_factor (as a log)."""
+    c = gsr.gs_densify_config()
+    c.grad_thr = float(grad_thr)
+    c.log_size_thr = float(math.log(max_scale))
+    c.logit_prune_thr = float(math.log(eps_alpha / (1.0 - eps_alpha))) if eps_alpha > 0 else -float("inf")
+    c.log_split_shrink = float(math.log(split_factor))
+    return c
+
+
+class DensityStats:
+    """The densification statistic of N Gaussians (device): the summed norm of
+    dL/dmean2D over the views each was visible in, and that view count."""
+
+    def __init__(self, n: int, device="cuda"):
+        self.n = int(n)
+        self.accum = torch.zeros(self.n, dtype=torch.float32, device=device)
+        self.denom = torch.zeros(self.n, dtype=torch.int32, device=device)
+
+    def accumulate(self, renderer: "Renderer", view_gate: torch.Tensor | None = None, stream=None) -> None:
+        """After a backward pass of `renderer` (its 2D gradients in the workspace)."""
+        gsr.call("gs_densify_accumulate", gsr.ptr(renderer.bwd_ws), gsr.ptr(renderer.touched), self.n,
+                 renderer.views.n, gsr.ptr(view_gate), gsr.ptr(self.accum), gsr.ptr(self.denom),
+                 gsr.stream_handle(stream))
+
+    def reset(self) -> None:
+        self.accum.zero_()
+        self.denom.zero_()
+
+
+def densify_decide(model: GaussianModel, stats: DensityStats, cfg: gsr.gs_densify_config, stream=None):
+    """Actions (u8[N]) and output offsets (int64[N+1]) on the device."""
+    n = model.n
+    dev = model.flat.device
+    action = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ws_bytes = int(gsr.lib().gs_densify_workspace_size(n))
+    ws = torch.empty(max(ws_bytes, 16), dtype=torch.uint8, device=dev)
+    gsr.call("gs_densify_decide", gsr.ptr(model.flat), n, model.sh_degree, gsr.ptr(stats.accum),
+             gsr.ptr(stats.denom), C.byref(cfg), gsr.ptr(action), gsr.ptr(offsets), gsr.ptr(ws), ws_bytes,
+             gsr.stream_handle(stream))
+    return action[:n], offsets
+
+
+def densify(model: GaussianModel, adam: "AdamState", stats: DensityStats, cfg: gsr.gs_densify_config,
+            noise: torch.Tensor, status: torch.Tensor | None = None, stream=None):
+    """One density-control step: decide, read the new count (synchronises),
+    allocate the resized parameter and Adam buffers, write the output set.
+    noise: device float [N, 2, 3] standard normal draws for split children.
+    Returns (model, adam, action) of the new set (statistics: new zeros)."""
+    action, offsets = densify_decide(model, stats, cfg, stream)
+    n_out = int(offsets[model.n].item())
+    new = GaussianModel(n_out, model.sh_degree, model.flat.device)
+    new_adam = AdamState(new)
+    new_adam.cfg = adam.cfg
+    new_adam.step_count.copy_(adam.step_count)
+    gsr.call("gs_densify_apply", gsr.ptr(model.flat), gsr.ptr(adam.m), gsr.ptr(adam.v), model.n, model.sh_degree,
+             gsr.ptr(action), gsr.ptr(offsets), gsr.ptr(noise), C.byref(cfg), gsr.ptr(new.flat), gsr.ptr(new_adam.m),
+             gsr.ptr(new_adam.v), n_out, gsr.ptr(status), gsr.stream_handle(stream))
+    return new, new_adam, action

@@ -28,16 +28,19 @@ import numpy as np
 import torch
 
 from . import gsr
-from .raster import AdamState, Gate, GaussianModel, RasterSettings, Renderer, Views
+from .raster import AdamState, DensityStats, Gate, GaussianModel, RasterSettings, Renderer, Views, densify
 
 
 class RefinementLoop:
     def __init__(self, model: GaussianModel, train_cams: list, targets, view_seq,
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
-                 fused: bool = True, views_per_step: int = 1, log_capacity: int = 0):
+                 fused: bool = True, views_per_step: int = 1, log_capacity: int = 0,
+                 adam: AdamState | None = None, stats: DensityStats | None = None):
         """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
-        [3, H_v, W_v] tensors, one per training view."""
+        [3, H_v, W_v] tensors, one per training view.  adam: an existing
+        optimizer state of `model` to continue (else a fresh one).  stats: the
+        densification statistic, accumulated after every backward pass."""
         import copy
         self.model = model
         self.fused = bool(fused)
@@ -70,7 +73,11 @@ class RefinementLoop:
         self.g = torch.zeros(self.B, dtype=torch.uint8, device=dev)
         self.any = torch.zeros(1, dtype=torch.int32, device=dev)
         self.gate = Gate(self.n_train, W, beta, eps, rho_lo, dev)
-        self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
+        if adam is not None:
+            self.adam = adam
+        else:
+            self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
+        self.stats = stats
         self.params = model.c_params()
         self.grads = model.c_grads(self.adam.grad)
         self.stream = torch.cuda.Stream(device=dev)
@@ -107,6 +114,9 @@ class RefinementLoop:
         else:
             r.backward(self.params, self.grads, view_gate=gate, accumulate=False, stream=s)
             self.adam.step(do_step=self.any if predicated else None, norms2=self.norms2, stream=s)
+        if self.stats is not None:  # the 2D gradients are still in the workspace
+            self.stats.accumulate(r, view_gate=self.g if (predicated or self.B > 1) and self.gated else None,
+                                  stream=s)
 
     def _update(self, s):
         self.gate.update(self.view_ids, self.renderer.loss, stream=s)
@@ -273,3 +283,68 @@ class HostTargets:
         self.free[b].record(ls)
         self.loop.step_graph()
         self.k += 1
+
+
+def densification_phase(model: GaussianModel, train_cams: list, targets, view_seq, iters: int, cfg,
+                        settings: RasterSettings | None = None, interval: int = 100, start: int = 500,
+                        until: int | None = None, noise_seed: int = 0, capacity_per_gaussian: int = 24,
+                        max_gaussians: int | None = None, adam: AdamState | None = None, on_step=None):
+    """Iterations 0..iters of always-backward refinement with adaptive density
+    control (Sec. 3, the phase before T_d): the statistic accumulates after
+    every backward pass, and at every multiple of `interval` in [start,
+    until) (until = iters) the set is cloned, split and pruned by
+    gs_densify_decide / gs_densify_apply and the statistic restarts.  Between
+    two density steps N is fixed and the iterations replay one captured
+    graph.  When a step would grow the set beyond max_gaussians it only
+    prunes.  Split noise: standard normal draws from a seeded CUDA generator.
+    Returns (model, adam, history); history rows are (iteration, n_before,
+    clones, splits, prunes, n_after)."""
+    from . import gsr
+    st = settings or RasterSettings()
+    until = iters if until is None else until
+    dev = model.flat.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(noise_seed))
+    adam = adam if adam is not None else AdamState(model)
+    stats = DensityStats(model.n, dev)
+    steps = [k for k in range(max(start, interval), min(until, iters) + 1, interval) if k > 0]
+    history, it = [], 0
+    for end in steps + ([iters] if not steps or steps[-1] < iters else []):
+        if end > it:
+            loop = RefinementLoop(model, train_cams, targets, view_seq, st, gated=False,
+                                  pair_capacity=capacity_per_gaussian * model.n, adam=adam, stats=stats)
+            loop.iter.fill_(it)
+            loop.capture()
+            for _ in range(end - it):
+                loop.step_graph()
+            loop.close()
+            torch.cuda.synchronize()
+            status = int(loop.renderer.status.item())
+            if status != 0:
+                raise gsr.GsError("densification_phase", status)
+            del loop
+            it = end
+        if end in steps:
+            noise = torch.randn((model.n, 2, 3), generator=gen, device=dev, dtype=torch.float32)
+            c = cfg
+            if max_gaussians is not None:
+                action, offsets = densify_decide_count(model, stats, cfg)
+                if offsets > max_gaussians:  # prune only
+                    c = gsr.gs_densify_config(float("inf"), cfg.log_size_thr, cfg.logit_prune_thr,
+                                              cfg.log_split_shrink)
+            n0 = model.n
+            model, adam, action = densify(model, adam, stats, c, noise)
+            counts = torch.bincount(action.long(), minlength=4).cpu().tolist()
+            history.append((it, n0, counts[1], counts[2], counts[3], model.n))
+            if on_step is not None:
+                on_step(history[-1])
+            stats = DensityStats(model.n, dev)
+            del noise
+    return model, adam, history
+
+
+def densify_decide_count(model: GaussianModel, stats: DensityStats, cfg):
+    """(actions, new count) of a density step without applying it (synchronises)."""
+    from .raster import densify_decide
+    action, offsets = densify_decide(model, stats, cfg)
+    return action, int(offsets[model.n].item())

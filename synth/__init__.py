@@ -9,5 +9,5 @@ from .scenes import (  # noqa: F401
     camera_pinhole, camera_look_at, ring_cameras,
     scene_cube, scene_ball, perturb_scene, scene_tiny,
     case_c1, case_c2, case_c3, case_c4, case_c4_ring, case_c5, view_sequence,
-    C4_RESOLUTIONS, projected_records, dl_dimage, pre_sequence,
+    C4_RESOLUTIONS, projected_records, opaque_stack_records, dl_dimage, pre_sequence,
 )

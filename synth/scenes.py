@@ -324,6 +324,33 @@ def projected_records(n: int, width: int, height: int, seed: int = 0, tie_frac: 
                 opacity=opacity.astype(F32), rgb=rgb.astype(F32), depth=depth, box=box.astype(F32), culled=culled)
 
 
+def opaque_stack_records(n: int, width: int, height: int, clamp_at=(40, 230), seed: int = 0) -> dict:
+    """A deep stack of screen-space Gaussians over a small image, for the
+    adjoint's transmittance rebuild: every Gaussian covers the whole image,
+    record i lies at depth 1 + i / 100 (so the list order is the index order);
+    the records at positions `clamp_at` are wide (sigma 400 px) and nearly
+    opaque (opacity U(0.997, 0.9995)), so alpha' reaches the 0.99 clamp at every
+    pixel; the others have sigma 60 px and opacity U(0.006, 0.02).  Layout as
+    projected_records."""
+    rng = np.random.default_rng(seed)
+    mean2d = np.stack([rng.uniform(0.3 * width, 0.7 * width, n), rng.uniform(0.3 * height, 0.7 * height, n)], 1)
+    s1 = np.full(n, 60.0)
+    opacity = rng.uniform(0.006, 0.02, n)
+    for k in clamp_at:
+        if k < n:
+            s1[k] = 400.0
+            opacity[k] = rng.uniform(0.997, 0.9995)
+    s2 = s1 / rng.uniform(1.0, 1.5, n)
+    theta = rng.uniform(0.0, np.pi, n)
+    rgb = rng.uniform(0.0, 1.0, (n, 3))
+    depth = (1.0 + np.arange(n) / 100.0).astype(F32)
+    half = 3.5 * s1
+    box = np.stack([mean2d[:, 0] - half, mean2d[:, 0] + half, mean2d[:, 1] - half, mean2d[:, 1] + half], 1)
+    return dict(mean2d=mean2d.astype(F32), sigma1=s1.astype(F32), sigma2=s2.astype(F32), theta=theta.astype(F32),
+                opacity=opacity.astype(F32), rgb=rgb.astype(F32), depth=depth, box=box.astype(F32),
+                culled=np.zeros(n, bool))
+
+
 def dl_dimage(width: int, height: int, seed: int = 0) -> np.ndarray:
     """A random upstream gradient dL/dimage [3,H,W] (a linear functional of the image)."""
     return np.random.default_rng(seed).normal(0.0, 1.0, (3, height, width)).astype(F32)

@@ -101,3 +101,16 @@ def cosine(a, b) -> float:
 def gpu_grads(model: raster.GaussianModel, flat: torch.Tensor) -> dict:
     v = model.group_views(flat)
     return {k: t.double().cpu().numpy() for k, t in v.items()}
+
+
+def l1_tie_mask(oracle_image, target, margin=None, tau: float = 1e-4) -> np.ndarray:
+    """Values [3,H,W] where the L1 derivative sign(C - C_hat) is not determined
+    at the render's float32 precision: |C - C_hat| <= tau in the oracle's own
+    image (tau = the end-to-end per-pixel reach of float32 rendering), plus
+    every channel of the pixels the oracle flags near a cut-off.  Both sides
+    of an end-to-end gradient test zero dL/dimage there, so the comparison
+    covers what is unique (the oracle's input never comes from the GPU)."""
+    m = np.abs(np.asarray(oracle_image, np.float64) - np.asarray(target, np.float64)) <= tau
+    if margin is not None:
+        m |= np.asarray(margin, bool)[None]
+    return m

@@ -35,17 +35,50 @@ def test_roofline_names_the_largest_share_and_divides_algorithmic_work_by_time()
                                                       ("loss", 0.05), ("loss_bwd", 0.05),
                                                       ("raster_bwd", 0.3), ("project_bwd", 0.0), ("adam", 0.0),
                                                       ("project_bwd_adam", 0.2))}
-    rf = bench.roofline_of(stages, loop, None)
+    census = dict(sum_n_last=50000, evaluated=30000, contributing=20000, tile_pairs=4000, staged=6000)
+    rf = bench.roofline_of(stages, loop, None, census, atomic_peak=8e9)
     assert rf["kernel"] == "raster_bwd" and rf["bound"] == "alu" and rf["unit"] == "TFLOP/s"
-    # 40 FLOP per evaluated pair over 1 ms
-    assert rf["achieved"] == pytest.approx(40.0 * 50000.0 / 1e-3 / 1e12)
+    # 13 FLOP per evaluated pair + 61 per contributing pair, over 1 ms
+    assert rf["achieved"] == pytest.approx((13 * 30000 + 61 * 20000) / 1e-3 / 1e12)
     assert rf["frac"] == pytest.approx(rf["achieved"] / rf["peak"])
+    fwd = rf["all_stages"]["render_fwd"]
+    assert fwd["achieved"] == pytest.approx((13 * 30000 + 10 * 20000) / 1e-3 / 1e12)
+    at = rf["all_stages"]["raster_bwd"]["atomic"]
+    assert at["updates_per_s"] == pytest.approx(4000 / 1e-3)
+    assert at["frac"] == pytest.approx(4000 / 1e-3 / 8e9)
+    assert rf["all_stages"]["raster_bwd"]["pair_bytes_per_launch"] == pytest.approx(40 * 6000 + 36 * 4000)
     stages["raster_bwd"]["share"] = 0.0
     stages["project_bwd_adam"].update(ms=2.0, share=0.25)
-    rf = bench.roofline_of(stages, loop, None)
+    rf = bench.roofline_of(stages, loop, None, census)
     assert rf["kernel"] == "project_bwd_adam" and rf["bound"] == "hbm" and rf["unit"] == "GB/s"
     want = (1000 * 48 + 24 * 59 * 1000) / 2e-3 / 1e9  # 2D gradients + (p, m, v) read and written
     assert rf["achieved"] == pytest.approx(want)
+
+
+def test_alu_peak_follows_the_device():
+    assert bench.peak_alu_tflops(152, 2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.peak_alu_tflops(76, 2070.0) == pytest.approx(bench.peak_alu_tflops(152, 2070.0) / 2)
+
+
+def test_plan_times_the_last_steps_of_the_whole_loop():
+    p = bench.plan_loop(5000, 20)
+    assert p["start"] == 4980 and p["K"] == 20 and p["marks"][-1] == 5000
+    assert p["evals"] == [4250, 4500, 4750, 5000]
+    assert 4980 in p["marks"] and all(m > 0 for m in p["marks"]) and p["marks"] == sorted(set(p["marks"]))
+    # a window longer than one checkpoint segment is split at the checkpoints inside it
+    p = bench.plan_loop(5000, 1000)
+    assert p["start"] == 4000 and p["marks"] == [4000, 4250, 4500, 4750, 5000]
+    # the whole loop timed
+    p = bench.plan_loop(100, 500)
+    assert p["start"] == 0 and p["K"] == 100 and p["marks"] == [25, 50, 75, 100]
+
+
+def test_backward_split_needs_skipped_backward_passes():
+    # every iteration ran the backward pass: the split is undetermined, not noise / 1
+    assert bench.backward_split(1000.0, 1002.0, 20, 20) == (None, None)
+    assert bench.backward_split(1000.0, 990.0, 100, 95) == (None, None)  # 5% skipped < 10%
+    f, b = bench.backward_split(5000 * 2.7, 5000 * 1.24 + 3300 * 1.46, 5000, 3300)
+    assert b == pytest.approx(1.46) and f == pytest.approx(1.24)
 
 
 def test_stored_traffic_only_for_matching_sources(monkeypatch):

@@ -81,6 +81,48 @@ def test_batch_matches_views_alone():
     assert gpu_util.rel_err(grad.cpu().numpy(), want) < 1e-5
 
 
+def test_batch_slot_against_oracle():
+    """One slot of a batch (a view chosen on the device into a slot larger than
+    itself, between two other views) against the FP64 oracle directly: image
+    within 1e-5, loss within 1e-5, and the gradient of that slot alone (the
+    other slots' gates closed) within the gradient bar."""
+    import oracle
+    gpu_util.lib()
+    scene, _, _ = synth.case_c1(n=1500)
+    cams = _cams()
+    rng = np.random.default_rng(6)
+    targets = [rng.uniform(0, 1, (3, h, w)).astype(np.float32) for w, h in SIZES]
+    order = [2, 1, 0]
+    r, vid = _slots(scene, cams, order)
+    flat_t = torch.from_numpy(np.concatenate([t.ravel() for t in targets])).cuda()
+    offs = torch.tensor(np.concatenate([[0], np.cumsum([t.size for t in targets])[:-1]]), dtype=torch.int64,
+                        device="cuda")
+    model = raster.GaussianModel.from_scene(scene)
+    grad = torch.zeros_like(model.flat)
+    gate = torch.tensor([0, 1, 0], dtype=torch.uint8, device="cuda")  # slot 1 holds view 1 (48x40)
+    r.forward(model.c_params())
+    r.compute_loss(flat_t, offs, vid, with_grad=True)
+    r.backward(model.c_params(), model.c_grads(grad), view_gate=gate)
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    v = order[1]
+    w, h = SIZES[v]
+    rc = oracle.RasterConfig()
+    f = oracle.forward(scene, cams[v], rc, margin_rel=1e-4)
+    off = r.views.pix_offsets[1]
+    img = r.image[3 * off:3 * off + 3 * w * h].view(3, h, w).cpu().numpy()
+    ok = ~f["margin"].astype(bool)[None].repeat(3, 0)
+    assert f["margin"].mean() < 0.01
+    assert np.abs(img - f["image"])[ok].max() <= 1e-5 * np.abs(f["image"]).max()
+    L, dL = oracle.loss_and_grad(f["image"], targets[v])
+    assert abs(float(r.loss[1].item()) - L) <= 1e-5 * L
+    og = oracle.backward(scene, cams[v], rc, f, dL)
+    gg = gpu_util.gpu_grads(model, grad)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        assert gpu_util.rel_err(gg[k], og[k]) < 1e-4, (k, gpu_util.rel_err(gg[k], og[k]))
+        assert gpu_util.cosine(gg[k], og[k]) > 0.9999, k
+
+
 def test_batched_loop_runs_and_gates():
     """Eager and graph forms of one batched iteration agree; over 20 graph
     iterations the gate counts 2 decisions per iteration and Adam steps at

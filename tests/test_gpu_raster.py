@@ -96,17 +96,33 @@ def test_bin_sort_capacity_overflow_and_empty():
     assert float(r2.image.abs().max().item()) == 0.0
 
 
-def _compare_images(img, ref, margin, tol=1e-5):
+def _compare_images(img, ref, margin, tol=1e-5, cap=0.002, outliers=0.0):
+    """Pixels against the oracle's:
+    - normwise within tol relative, over all pixels and over the pixels the
+      oracle does not flag as within its margin of a cut-off (alpha' near
+      alpha_min or alpha_max, T (1 - alpha') near t_min);
+    - per unflagged pixel within tol of the image's peak, except at most
+      `outliers` of the pixels, which stay within 10 tol (end to end, the
+      projection's float32 rounding of ill-conditioned footprints moves
+      alphas by up to ~1e-4 relative; stage-wise, records are shared exactly
+      and outliers = 0);
+    - flagged pixels fewer than `cap` of the image.
+    Returns (flagged, outlier) pixel counts."""
     img = np.asarray(img, np.float64)
     ref = np.asarray(ref, np.float64)
-    mask = margin.astype(bool)[None].repeat(3, 0)
-    assert mask.mean() < 0.01
+    flagged = margin.astype(bool)
+    assert flagged.mean() < cap, (int(flagged.sum()), flagged.size)
+    mask = flagged[None].repeat(3, 0)
     d = np.abs(img - ref)
     d[mask] = 0.0
     peak = np.abs(ref).max()
-    assert d.max() <= tol * peak, (d.max(), peak)
+    over = d.max(0) > tol * peak
+    assert over.mean() <= outliers, (int(over.sum()), d.max() / peak)
+    assert d.max() <= 10 * tol * peak, (d.max(), peak)
     nd = np.linalg.norm(np.where(mask, 0.0, img - ref))
     assert nd <= tol * np.linalg.norm(ref), nd / np.linalg.norm(ref)
+    assert np.linalg.norm(img - ref) <= tol * np.linalg.norm(ref), np.linalg.norm(img - ref) / np.linalg.norm(ref)
+    return int(flagged.sum()), int(over.sum())
 
 
 @pytest.mark.parametrize("tile,batch,ppt", [(16, 256, 2), (8, 64, 2), (32, 128, 2), (16, 128, 1), (8, 256, 1),
@@ -144,14 +160,21 @@ def test_render_end_to_end_c1(tile, ppt):
     torch.cuda.synchronize()
     assert int(r.status.item()) == 0
     # end to end, the projection's float32 rounding moves alphas by up to ~1e-4
-    # relative for ill-conditioned footprints: flag pixels within that of a cut-off
+    # relative for ill-conditioned footprints (test_projection_c2: conic error
+    # below 1e-6 (1 + cond)): flag pixels within that of a cut-off
     o = oracle.forward(scene, cam, oracle.RasterConfig(tile=tile), margin_rel=1e-4)
-    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])
+    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"], cap=0.01, outliers=1e-4)
 
 
-def test_projection_c2_like():
-    """Projection of an SH-degree-3 unit-ball scene seen by the C2 camera."""
-    scene, _, cam, _ = synth.case_c2(n=50_000)
+def test_projection_c2():
+    """Projection of the full C2 scene (200,000 Gaussians SH3, 980x545).
+    The conic's float32 error grows with the condition number of Sigma2D (it
+    is the inverse of a matrix rounded to float32): relative error at most
+    1e-6 (1 + cond) for every footprint, and 1e-5 where cond <= 10.  Culling
+    disagrees only where the oracle's wider rectangle inflation (x1.001 +
+    0.01 px against x1.0001 + 0.001 px) keeps a Gaussian whose exact support
+    reaches no pixel centre."""
+    scene, _, cam, _ = synth.case_c2()
     r = _renderer([cam], scene.n, sh_degree=3)
     model = raster.GaussianModel.from_scene(scene)
     r.project(model.c_params())
@@ -161,8 +184,14 @@ def test_projection_c2_like():
     touched = r.touched.cpu().numpy()
     o = oracle.project(scene, cam, oracle.RasterConfig())
     vis = (o["touched"] > 0) & (touched > 0)
-    # culling agrees except within float rounding of a threshold
-    assert ((o["touched"] > 0) != (touched > 0)).sum() <= 5
+    r_ex = (o["radius"] - 0.01) / 1.001  # the oracle's exact support extents
+    m = o["mean2d"]
+    ex = np.stack([np.maximum(np.ceil(m[:, 0] - r_ex[:, 0] - 0.5), 0), np.maximum(np.ceil(m[:, 1] - r_ex[:, 1] - 0.5), 0),
+                   np.minimum(np.floor(m[:, 0] + r_ex[:, 0] - 0.5), cam.width - 1),
+                   np.minimum(np.floor(m[:, 1] + r_ex[:, 1] - 0.5), cam.height - 1)], 1)
+    exact_empty = (ex[:, 0] > ex[:, 2]) | (ex[:, 1] > ex[:, 3])
+    differ = (o["touched"] > 0) != (touched > 0)
+    assert np.all(differ <= ((o["touched"] > 0) & exact_empty)), np.nonzero(differ & ~exact_empty)[0][:10]
     np.testing.assert_allclose(rec[vis, 0:2], o["mean2d"][vis], rtol=1e-6, atol=1e-4)
     np.testing.assert_allclose(rec[vis, 9], o["depth"][vis], rtol=1e-6)
     np.testing.assert_allclose(rec[vis, 5], o["opacity"][vis], rtol=1e-5)
@@ -171,27 +200,31 @@ def test_projection_c2_like():
     Q = np.stack([U[:, 0] ** 2, U[:, 0] * U[:, 1], U[:, 1] ** 2 + U[:, 2] ** 2], 1)
     Qo = o["conic"][vis]
     err = np.linalg.norm(Q - Qo, axis=1) / np.linalg.norm(Qo, axis=1)
-    assert np.median(err) < 1e-6 and err.max() < 1e-3
-    # the GPU rectangle contains the exact support box (the oracle's extents
-    # before the oracle's own inflation, r -> 1.001 r + 0.01)
-    r_ex = (o["radius"][vis] - 0.01) / 1.001
-    m = o["mean2d"][vis]
-    ex = np.stack([np.maximum(np.ceil(m[:, 0] - r_ex[:, 0] - 0.5), 0) // 16,
-                   np.maximum(np.ceil(m[:, 1] - r_ex[:, 1] - 0.5), 0) // 16,
-                   np.minimum(np.floor(m[:, 0] + r_ex[:, 0] - 0.5), cam.width - 1) // 16,
-                   np.minimum(np.floor(m[:, 1] + r_ex[:, 1] - 0.5), cam.height - 1) // 16], 1)
+    cov = o["cov2d"][vis]
+    tr, det = cov[:, 0] + cov[:, 2], cov[:, 0] * cov[:, 2] - cov[:, 1] ** 2
+    disc = np.sqrt(np.maximum(tr * tr / 4 - det, 0.0))
+    cond = (tr / 2 + disc) / (tr / 2 - disc)
+    assert np.all(err <= 1e-6 * (1.0 + cond)), (err.max(), cond[np.argmax(err / (1 + cond))])
+    well = cond <= 10.0
+    assert well.mean() > 0.5 and err[well].max() <= 1e-5, err[well].max()
+    # the GPU rectangle contains the exact support box
     gr = rect[vis]
-    assert ((gr[:, 0] <= ex[:, 0]) & (gr[:, 1] <= ex[:, 1]) & (gr[:, 2] >= ex[:, 2]) & (gr[:, 3] >= ex[:, 3])).all()
+    exv = ex[vis] // 16
+    assert ((gr[:, 0] <= exv[:, 0]) & (gr[:, 1] <= exv[:, 1]) & (gr[:, 2] >= exv[:, 2]) & (gr[:, 3] >= exv[:, 3])).all()
 
 
-def test_render_end_to_end_c2_like():
-    scene, _, cam, _ = synth.case_c2(n=60_000)
-    r = _renderer([cam], scene.n, sh_degree=3)
+def test_render_end_to_end_c2():
+    """The full C2 scene rendered end to end; flagged pixels (within 1e-4 of a
+    cut-off, the projection's float32 reach) below 1% of the image, pixels
+    beyond 1e-5 of the peak at most 0.01% (each within 1e-4)."""
+    scene, _, cam, _ = synth.case_c2()
+    r = _renderer([cam], scene.n, sh_degree=3, cap=24 * scene.n)
     model = raster.GaussianModel.from_scene(scene)
     r.forward(model.c_params())
     torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
     o = oracle.forward(scene, cam, oracle.RasterConfig(), margin_rel=1e-4)
-    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])
+    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"], cap=0.01, outliers=1e-4)
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
