@@ -60,6 +60,13 @@ def parse():
     ap.add_argument("--rho-sweep", action="store_true",
                     help="NEXT-1: gated loop for rho_lo in (no budget, 0.3, 0.5, 0.7, 0.9) against the "
                          "always-backward loop; prints its own JSON line")
+    ap.add_argument("--densify", action="store_true",
+                    help="NEXT-3: densification phase from a sparse start, then gated vs always-backward post phase")
+    ap.add_argument("--densify-iters", type=int, default=3000, help="length of the densification phase")
+    ap.add_argument("--prune", action="store_true",
+                    help="NEXT-4: opacity prune + compaction at eps_alpha in (0.005, 0.05, 0.2), then SkipGS")
+    ap.add_argument("--c2", action="store_true", help="C2: 200k-Gaussian fwd+bwd+Adam iteration timing")
+    ap.add_argument("--c5", action="store_true", help="C5: 6M Gaussians, 4x1080p fwd+bwd batch timing and memory")
     ap.add_argument("--stages-once", action="store_true",
                     help="run two eager iterations of every stage on one view of the workload and exit "
                          "(a small, fixed launch sequence for hardware-counter captures)")
@@ -238,6 +245,246 @@ def run_rho_sweep(args) -> None:
         r["final_loss_rel_diff"] = (r["final_loss"] - full["final_loss"]) / full["final_loss"]
     print(json.dumps({"metric": "rho_lo sweep of the gated refinement loop (NEXT-1)", "steps": K,
                       "workload": WORKLOAD, "rows": rows}))
+
+
+def gated_vs_full(model, cams, targets, seq, st, cap, plan, adam=None, W=3):
+    """The post-densification loop from the model's current state (and
+    optional Adam state), always-backward then gated, both from the same
+    snapshot, each run through plan_loop's marks (whole loop timed).
+    Returns {"full": result, "gated": result} as run_measured_loop gives."""
+    import torch
+    from paper_2603_08997_gb300.refine import RefinementLoop
+    base = RefinementLoop(model, cams, targets, seq, st, gated=False, pair_capacity=cap, adam=adam)
+    init = base.snapshot()
+    base.close()
+    del base
+    out = {}
+    for gated in (False, True):
+        loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, pair_capacity=cap, adam=adam)
+        loop.restore(init)
+        loop.capture()
+        for _ in range(W):
+            loop.step_graph()
+        loop.restore(init)
+        res = run_measured_loop(loop, plan)
+        res["kernels_per_step"] = loop.kernels_per_step
+        loop.close()
+        out["gated" if gated else "full"] = res
+        torch.cuda.synchronize()
+    return out
+
+
+def loop_summary(r: dict, iters: int) -> dict:
+    f, g = r["full"], r["gated"]
+    lf, lg = float(sum(f["evals"]) / len(f["evals"])), float(sum(g["evals"]) / len(g["evals"]))
+    return {"full_iters_per_s": iters / (f["ms_loop"] * 1e-3), "gated_iters_per_s": iters / (g["ms_loop"] * 1e-3),
+            "speedup": f["ms_loop"] / g["ms_loop"], "rho_cum": g["gate_end"]["b"] / iters,
+            "final_loss_full": lf, "final_loss_gated": lg, "final_loss_rel_diff": (lg - lf) / lf,
+            "device_status": [f["status"], g["status"]]}
+
+
+def run_densify(args) -> None:
+    """NEXT-3: a densification phase before T_d, then the post phase.  The
+    start is a sparse perturbed subset (a third) of the 3M ground truth;
+    always-backward refinement with adaptive density control every 100
+    iterations from iteration 500 (clone / split / prune, Sec. 3) up to
+    --densify-iters, the set capped at --n; then the gated and the
+    always-backward post-densification loops of --iters iterations from the
+    densified state (parameters and Adam moments carried over)."""
+    import math
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import build, raster
+    from paper_2603_08997_gb300.refine import densification_phase
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    gt, _, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=max(args.iters, args.densify_iters),
+                                     width=args.width, height=args.height)
+    st = raster.RasterSettings()
+    mgt = raster.GaussianModel.from_scene(gt, dev)
+    rgt = raster.Renderer(args.n, 3, raster.Views([cams[0]], st.tile, dev), st, 24 * args.n, dev)
+    targets = torch.empty((args.views, 3, args.height, args.width), dtype=torch.float32, device=dev)
+    for v, cam in enumerate(cams):
+        rgt.views = raster.Views([cam], st.tile, dev)
+        rgt.forward(mgt.c_params())
+        targets[v].copy_(rgt.image.view(3, args.height, args.width))
+    torch.cuda.synchronize()
+    del mgt, rgt
+    n0 = args.n // 3
+    start = synth.sparse_start(gt, n0, seed=11)
+    del gt
+    model = raster.GaussianModel.from_scene(start, dev)
+    # thresholds: the vanilla 2e-4 on the NDC-space gradient, in pixels
+    # (d/dpx = d/dndc * 2 / W); 1% of the scene extent (1.1 x the camera
+    # radius 3); opacity 0.005
+    grad_thr = 2e-4 * 2.0 / args.width
+    cfg = raster.densify_config(grad_thr=grad_thr, max_scale=0.01 * 1.1 * 3.0, eps_alpha=0.005)
+    pre_seq = synth.pre_sequence(args.densify_iters, args.views)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    model, adam, hist = densification_phase(model, cams, targets, pre_seq, args.densify_iters, cfg, st,
+                                            interval=100, start=500, max_gaussians=args.n,
+                                            capacity_per_gaussian=48)
+    torch.cuda.synchronize()
+    t_d = time.perf_counter() - t0
+    iters = max(args.iters, 1)
+    r = gated_vs_full(model, cams, targets, seq, st, 48 * model.n, plan_loop(iters, iters), adam=adam)
+    print(json.dumps({
+        "metric": "densification phase then post phase (NEXT-3): gated vs always-backward iters/s",
+        "densify": {"start_gaussians": n0, "iterations": args.densify_iters, "interval": 100, "from": 500,
+                    "grad_thr_px": grad_thr, "max_scale": 0.033, "eps_alpha": 0.005, "cap": args.n,
+                    "wall_s": t_d, "iters_per_s_wall": args.densify_iters / t_d,
+                    "history": [dict(zip(("iteration", "n_before", "clone", "split", "prune", "n_after"), h))
+                                for h in hist]},
+        "post": dict(loop_summary(r, iters), iterations=iters, n_gaussians=model.n),
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sparse perturbed third of the 3M-Gaussian SH3 scene, 200 ring views 1297x840, "
+                               "density control then SkipGS W=500 beta=0.95 eps=1e-8 rho_lo=0.5"}}))
+
+
+def run_prune(args) -> None:
+    """NEXT-4: an opacity-threshold prune (alpha < eps_alpha, Sec. 3) with
+    compaction of the parameters and Adam moments before the post phase,
+    then SkipGS on top: for each threshold, the gated and always-backward
+    loops on the pruned set against the unpruned ones (same snapshot, same
+    view sequence)."""
+    import torch
+
+    from paper_2603_08997_gb300 import build, raster
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    model, cams, targets, seq, init, st, cap, _ = setup_c3(args, dev)
+    iters = max(args.iters, 1)
+    plan = plan_loop(iters, iters)
+    adam = raster.AdamState(model)
+
+    def load(snap):
+        model.flat.copy_(snap["flat"])
+        adam.m.copy_(snap["m"])
+        adam.v.copy_(snap["v"])
+        adam.step_count.copy_(snap["step"])
+
+    rows = []
+    load(init)
+    rows.append(dict(loop_summary(gated_vs_full(model, cams, targets, seq, st, cap, plan, adam=adam), iters),
+                     eps_alpha=None, n_gaussians=model.n))
+    for eps in (0.005, 0.05, 0.2):
+        load(init)
+        stats = raster.DensityStats(model.n, dev)
+        cfg = raster.densify_config(grad_thr=float("inf"), max_scale=1.0, eps_alpha=eps)
+        noise = torch.zeros((model.n, 2, 3), dtype=torch.float32, device=dev)
+        pm, pa, action = raster.densify(model, adam, stats, cfg, noise)
+        del stats, noise
+        torch.cuda.synchronize()
+        rows.append(dict(loop_summary(gated_vs_full(pm, cams, targets, seq, st, cap, plan, adam=pa), iters),
+                         eps_alpha=eps, n_gaussians=pm.n))
+        del pm, pa
+        torch.cuda.empty_cache()
+    base_full = rows[0]["full_iters_per_s"]
+    base_loss = rows[0]["final_loss_full"]
+    for r in rows:
+        r["gated_speedup_vs_unpruned_full"] = r["gated_iters_per_s"] / base_full
+        r["full_speedup_vs_unpruned_full"] = r["full_iters_per_s"] / base_full
+        r["final_loss_gated_vs_unpruned_full"] = (r["final_loss_gated"] - base_loss) / base_loss
+    print(json.dumps({"metric": "opacity prune + compaction, then SkipGS (NEXT-4)", "iterations": iters,
+                      "workload": WORKLOAD, "rows": rows, "dtype": "f32", "data": "synthetic"}))
+
+
+def run_c2(args) -> None:
+    """C2: one view of the 200,000-Gaussian SH3 unit-ball scene at 980x545, a
+    forward + loss + backward + Adam iteration (the always-backward loop as a
+    captured graph, 1 view per iteration), target = render of a perturbed copy
+    plus N(0, 0.01) noise; per-stage times and the peak device memory."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import build, raster
+    from paper_2603_08997_gb300.refine import RefinementLoop
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    scene, tscene, cam, noise = synth.case_c2()
+    st = raster.RasterSettings()
+    mt = raster.GaussianModel.from_scene(tscene, dev)
+    rt = raster.Renderer(scene.n, 3, raster.Views([cam], st.tile, dev), st, 48 * scene.n, dev)
+    rt.forward(mt.c_params())
+    target = (rt.image.view(1, 3, cam.height, cam.width) + torch.from_numpy(noise).to(dev)).contiguous()
+    del mt, rt
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    model = raster.GaussianModel.from_scene(scene, dev)
+    K = max(args.steps, 1)
+    loop = RefinementLoop(model, [cam], target, np.zeros(K + args.warmup, np.int32), st, gated=False,
+                          pair_capacity=48 * scene.n)
+    loop.capture()
+    for _ in range(max(args.warmup, 3)):
+        loop.step_graph()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(loop.stream)
+    for _ in range(K):
+        loop.step_graph()
+    e1.record(loop.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    stages = stage_times(loop, target, b_frac=1.0)
+    print(json.dumps({"metric": "C2 fwd+bwd+Adam iteration (200k Gaussians SH3, 980x545)", "value": 1000.0 / ms,
+                      "unit": "iters/s", "ms_per_iteration": ms, "steps": K,
+                      "stage_ms": {k: round(v["ms"], 4) for k, v in stages.items()},
+                      "pairs": int(loop.renderer.pair_count.item()), "status": int(loop.renderer.status.item()),
+                      "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                      "dtype": "f32", "data": "synthetic"}))
+
+
+def run_c5(args) -> None:
+    """C5: 6M Gaussians SH3, 4 views of 1920x1080 per batch through the
+    torch.autograd.Function path (render -> per-view loss -> backward with
+    per-tile transmittance checkpoints), targets = renders of a perturbed copy;
+    ms per batch for forward and backward, pairs, and the peak device memory
+    (parameters, gradients, pairs, checkpoints, images)."""
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import autograd, build, raster
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    scene, cams = synth.case_c5()
+    views = raster.Views(cams, 16, dev)
+    cap = 200_000_000 * len(cams)
+    r = raster.Renderer(scene.n, 3, views, raster.RasterSettings(), pair_capacity=cap, device=dev)
+    mt = raster.GaussianModel.from_scene(synth.perturb_scene(scene, 5, 0.2), dev)
+    r.forward(mt.c_params())
+    target = r.image.clone()
+    del mt
+    model = raster.GaussianModel.from_scene(scene, dev)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    flat = model.flat.clone().requires_grad_(True)
+    ms_f, ms_b = [], []
+    for k in range(max(args.warmup, 2) + max(args.steps, 1)):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        img = autograd.render(flat, model, r)
+        losses = autograd.photometric_loss(img, target, r)
+        e[1].record()
+        flat.grad = None
+        losses.sum().backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if k >= max(args.warmup, 2):
+            ms_f.append(e[0].elapsed_time(e[1]))
+            ms_b.append(e[1].elapsed_time(e[2]))
+    print(json.dumps({"metric": "C5 fwd+bwd per 4x1920x1080 batch (6M Gaussians SH3, autograd path)",
+                      "value": 1000.0 / (sum(ms_f) / len(ms_f) + sum(ms_b) / len(ms_b)), "unit": "batches/s",
+                      "fwd_ms": sum(ms_f) / len(ms_f), "bwd_ms": sum(ms_b) / len(ms_b), "batches": len(ms_f),
+                      "pairs": int(r.pair_count.item()), "status": int(r.status.item()),
+                      "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                      "param_bytes": int(model.flat.numel() * 4), "dtype": "f32", "data": "synthetic"}))
 
 
 def stages_once(args) -> None:
@@ -768,6 +1015,18 @@ def main():
         return
     if args.rho_sweep:
         run_rho_sweep(args)
+        return
+    if args.densify:
+        run_densify(args)
+        return
+    if args.c2:
+        run_c2(args)
+        return
+    if args.c5:
+        run_c5(args)
+        return
+    if args.prune:
+        run_prune(args)
         return
 
     import numpy as np

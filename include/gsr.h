@@ -460,6 +460,45 @@ gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, in
 gs_status gs_log_step(const int64_t *iter, int32_t n, const float *loss, const uint8_t *g, double *norms2,
                       float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap, cudaStream_t stream);
 
+/* ------------------------------------------------------------- autotuning */
+
+/* A launch shape of the rasterizer: tile side (8, 16, 32), staging batch (64,
+ * 128, 256) and pixels per thread of the forward and adjoint compositing
+ * kernels (1, 2, or 4 with tile >= 16).  Shapes change how the work maps to
+ * the GPU, not the results (the contribution set does not depend on the tile
+ * size; gradients equal up to the order of float atomics). */
+typedef struct {
+    int32_t tile, batch, pixels_per_thread_fwd, pixels_per_thread_bwd;
+} gs_launch_shape;
+
+/* Scratch bytes gs_autotune needs: the buffers of one rasterization
+ * pipeline over these views for the largest candidate (invalid candidates
+ * are ignored).  0 for invalid arguments. */
+size_t gs_autotune_workspace_size(int64_t n, int32_t sh_degree, const gs_camera *cams_host, int32_t n_views,
+                                  int64_t pair_capacity, const gs_launch_shape *cands, int32_t n_cands);
+
+/* Times each candidate shape on the caller's workload: one untimed, then
+ * `reps` timed iterations of gs_project -> gs_bin_sort -> gs_tile_order ->
+ * gs_render_fwd -> gs_loss (with its gradient, lambda_ssim) -> gs_render_bwd
+ * over all n_views views in one call, with CUDA events on `stream`
+ * (synchronises; not capturable).  params: device parameters (as gs_project);
+ * cams_host: the views (host; tile_offset and pix_offset are filled per
+ * candidate, the input is not modified); target: device, planar [3][H][W]
+ * per view in view order (the layout of gs_render_fwd's image, which does
+ * not depend on the tile); base: the rasterizer constants (tile, batch and
+ * pixels per thread are taken from each candidate).  Writes ms_per_iter[c]
+ * (host; +infinity for a candidate this workload cannot use: an invalid
+ * shape, a view with more tiles than the binning holds, more pairs than
+ * pair_capacity) and *best (host) = the fastest candidate's index.  All
+ * buffers are carved from `workspace` (device, 256-byte aligned, at least
+ * gs_autotune_workspace_size bytes, else GS_ERR_WORKSPACE); the library
+ * allocates nothing.  GS_ERR_UNSUPPORTED when no candidate runs. */
+gs_status gs_autotune(const gs_params *params /* host */, const gs_camera *cams_host, int32_t n_views,
+                      const float *target, const gs_raster_config *base /* host */, float lambda_ssim,
+                      const gs_launch_shape *cands /* host */, int32_t n_cands, int32_t reps, int64_t pair_capacity,
+                      void *workspace, size_t workspace_bytes, float *ms_per_iter /* host */,
+                      int32_t *best /* host */, cudaStream_t stream);
+
 /* ------------------------------------------------- adaptive density control */
 
 /* Adaptive density control (Sec. 3, Preliminaries): during the densification

@@ -5,14 +5,14 @@ per thread of the forward and adjoint kernels change how the work maps to
 the GPU but not what it computes: the contribution set is tile-size
 invariant (conservative support rectangles) and every configuration gives
 the same images and gradients up to the order of float atomics.  So the
-choice is made on speed alone: each candidate runs a few forward + loss +
-adjoint iterations on the caller's workload and the fastest wins.  Results
-are cached per workload signature (Gaussian count, SH degree, view sizes,
-views per step, candidate set), in memory and optionally in a JSON file.
+choice is made on speed alone, by gs_autotune (the C ABI): each candidate
+runs a few forward + loss + adjoint iterations on the caller's workload and
+the fastest wins.  This module sizes its workspace and caches the choice per
+workload signature (Gaussian count, SH degree, view sizes, views per step,
+candidate set), in memory and optionally in a JSON file.
 """
 from __future__ import annotations
 
-import copy
 import dataclasses
 import hashlib
 import json
@@ -21,7 +21,7 @@ import os
 import torch
 
 from . import gsr
-from .raster import GaussianModel, RasterSettings, Renderer, Views
+from .raster import GaussianModel, RasterSettings
 
 DEFAULT_CANDIDATES = tuple((t, b, pf, pb) for t in (8, 16, 32) for b in (64, 128, 256)
                            for pf, pb in ((1, 2), (1, 1), (2, 2)))
@@ -52,40 +52,33 @@ def settings_of(base: RasterSettings, cand) -> RasterSettings:
                                pixels_per_thread=int(pb))
 
 
-def _time_candidate(model: GaussianModel, cams: list, flat_targets, offsets, settings: RasterSettings,
-                    views_per_step: int, reps: int, pair_capacity) -> float:
-    wmax, hmax = max(c.width for c in cams), max(c.height for c in cams)
-    slot_cam = copy.copy(cams[0])
-    slot_cam.width, slot_cam.height = wmax, hmax
-    slots = Views([slot_cam] * views_per_step, settings.tile)
-    poses = Views(cams, settings.tile)
-    r = Renderer(model.n, model.sh_degree, slots, settings, pair_capacity)
-    r.sizes_on_device = True
-    dev = model.flat.device
-    seq = torch.arange(len(cams), dtype=torch.int32, device=dev)
-    it = torch.zeros(1, dtype=torch.int64, device=dev)
-    vid = torch.zeros(views_per_step, dtype=torch.int32, device=dev)
-    grad = torch.zeros_like(model.flat)
-    params, grads = model.c_params(), model.c_grads(grad)
-
-    def once():
-        gsr.call("gs_select_views", gsr.ptr(seq), len(cams), gsr.ptr(it), views_per_step, gsr.ptr(vid),
-                 gsr.ptr(poses.dev), gsr.ptr(slots.dev), None)
-        r.forward(params)
-        r.compute_loss(flat_targets, offsets, vid, with_grad=True)
-        r.backward(params, grads, accumulate=False)
-
-    once()
-    torch.cuda.synchronize()
-    if int(r.status.item()) != 0:
-        return float("inf")  # e.g. over the pair capacity: not a usable configuration
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        once()
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
+def time_candidates(model: GaussianModel, cams: list, targets, base: RasterSettings, candidates, reps: int,
+                    pair_capacity: int, stream=None) -> list:
+    """gs_autotune over the candidates: ms per iteration of each (inf where the
+    workload cannot use the shape), all views of `cams` rendered in one call.
+    targets: one [3, H_v, W_v] device tensor per camera."""
+    import ctypes as C
+    from .raster import camera_struct
+    n = len(candidates)
+    shapes = (gsr.gs_launch_shape * n)(*[gsr.gs_launch_shape(*map(int, c)) for c in candidates])
+    hcams = (gsr.gs_camera * len(cams))(*[camera_struct(c) for c in cams])
+    flat = torch.cat([t.contiguous().view(-1) for t in targets]).to(model.flat.device)
+    L = gsr.lib()
+    cap = int(pair_capacity)
+    ws_bytes = int(L.gs_autotune_workspace_size(model.n, model.sh_degree, hcams, len(cams), cap, shapes, n))
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=model.flat.device)
+    ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+    ms = (C.c_float * n)()
+    best = C.c_int32(-1)
+    cfg = base.struct(model.sh_degree)
+    code = L.gs_autotune(C.byref(model.c_params()), hcams, len(cams), gsr.ptr(flat), C.byref(cfg),
+                         float(base.lambda_ssim), shapes, n, int(reps), cap, C.c_void_p(ws_ptr), ws_bytes, ms,
+                         C.byref(best), gsr.stream_handle(stream))
+    if code == gsr.GS_ERR_UNSUPPORTED:
+        raise RuntimeError("autotune: no candidate launch shape runs this workload")
+    gsr.check("gs_autotune", code)
+    del ws
+    return [float(ms[i]) for i in range(n)]
 
 
 def autotune(model: GaussianModel, cams: list, targets, base: RasterSettings | None = None,
@@ -99,19 +92,12 @@ def autotune(model: GaussianModel, cams: list, targets, base: RasterSettings | N
     key = signature(model.n, model.sh_degree, [(c.width, c.height) for c in cams], views_per_step, candidates)
     if key in _cache:
         return settings_of(base, tuple(_cache[key])), {}
-    sizes = [int(t.numel()) for t in targets]
-    flat = torch.cat([t.contiguous().view(-1) for t in targets])
-    offs = torch.tensor([sum(sizes[:i]) for i in range(len(sizes))], dtype=torch.int64, device=flat.device)
-    times = {}
-    for cand in candidates:
-        try:
-            times[tuple(cand)] = _time_candidate(model, cams, flat, offs, settings_of(base, cand), views_per_step,
-                                                 reps, pair_capacity)
-        except gsr.GsError:  # a shape this workload cannot use (e.g. too many tiles per view)
-            times[tuple(cand)] = float("inf")
-        torch.cuda.empty_cache()
-    if all(t == float("inf") for t in times.values()):
-        raise RuntimeError("autotune: no candidate launch shape runs this workload")
+    # one multi-view call over the first views_per_step views stands for an iteration
+    k = max(1, min(int(views_per_step), len(cams)))
+    cap = int(pair_capacity) if pair_capacity else max(1 << 16, 24 * model.n * k)
+    ms = time_candidates(model, cams[:k], targets[:k], base, candidates, reps, cap)
+    times = {tuple(c): t for c, t in zip(candidates, ms)}
+    torch.cuda.empty_cache()
     best = min(times, key=times.get)
     _cache[key] = list(best)
     save_cache(cache_path)

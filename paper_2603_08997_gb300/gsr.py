@@ -59,6 +59,11 @@ class gs_adam_config(C.Structure):
     _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class gs_launch_shape(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("pixels_per_thread_fwd", C.c_int32),
+                ("pixels_per_thread_bwd", C.c_int32)]
+
+
 class gs_densify_config(C.Structure):
     _fields_ = [("grad_thr", C.c_float), ("log_size_thr", C.c_float), ("logit_prune_thr", C.c_float),
                 ("log_split_shrink", C.c_float)]
@@ -127,6 +132,11 @@ _PROTOS = {
                                    _P, _P, _S]),
     "gs_atomic_probe": (C.c_int, [_P, _I64, _I64, _S]),
     "gs_densify_accumulate": (C.c_int, [_P, _P, _I64, _I32, _P, _P, _P, _S]),
+    "gs_autotune_workspace_size": (C.c_size_t, [_I64, _I32, C.POINTER(gs_camera), _I32, _I64,
+                                                C.POINTER(gs_launch_shape), _I32]),
+    "gs_autotune": (C.c_int, [C.POINTER(gs_params), C.POINTER(gs_camera), _I32, _P, C.POINTER(gs_raster_config), _F32,
+                              C.POINTER(gs_launch_shape), _I32, _I32, _I64, _P, _SZ, C.POINTER(C.c_float),
+                              C.POINTER(C.c_int32), _S]),
     "gs_densify_workspace_size": (C.c_size_t, [_I64]),
     "gs_densify_decide": (C.c_int, [_P, _I64, _I32, _P, _P, C.POINTER(gs_densify_config), _P, _P, _P, _SZ, _S]),
     "gs_densify_apply": (C.c_int, [_P, _P, _P, _I64, _I32, _P, _P, _P, C.POINTER(gs_densify_config), _P, _P, _P,

@@ -191,6 +191,20 @@ def perturb_scene(scene: Scene, seed: int, scale: float = 1.0) -> Scene:
     return out
 
 
+def sparse_start(scene: Scene, n0: int, seed: int, perturb: float = 0.2, scale_boost: float = 1.44) -> Scene:
+    """The start of a densification phase: a random subset of n0 of the
+    scene's Gaussians (kept in index order), perturbed like perturb_scene x
+    perturb, with scales multiplied by scale_boost so the sparser set still
+    covers the volume (x1.44 ~ (3M / 1M)^(1/3) for a third of the Gaussians)."""
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(scene.n, size=n0, replace=False))
+    sub = Scene(scene.means[idx].copy(), scene.log_scales[idx].copy(), scene.quats[idx].copy(),
+                scene.opacity_logit[idx].copy(), scene.sh[idx].copy())
+    out = perturb_scene(sub, seed + 1, perturb)
+    out.log_scales = (out.log_scales + np.float32(math.log(scale_boost))).astype(F32)
+    return out
+
+
 def scene_tiny(n: int, seed: int, width: int = 32, height: int = 32, sh_degree: int = 1,
                depth=(2.0, 4.0), log_scale=(-2.6, 0.3)) -> tuple:
     """Small scene for brute-force and finite-difference checks: Gaussians spread over

@@ -102,3 +102,31 @@ def test_workspace_too_small_is_refused(lib):
     code = lib.gs_bin_sort(C.byref(proj), C.c_void_p(256), 1, 100, 4, 4, C.byref(rc), C.c_void_p(256), need - 1,
                            None, C.c_void_p(256), 1000, C.c_void_p(256), C.c_void_p(256), None, None)
     assert code == gsr.GS_ERR_WORKSPACE
+
+
+def test_autotune_host_checks(lib):
+    """gs_autotune sizes its workspace for the largest valid candidate and
+    refuses a missing or short workspace, and mismatched arguments, before
+    any launch."""
+    from paper_2603_08997_gb300 import gsr
+    cams = (gsr.gs_camera * 2)()
+    cams[0].width, cams[0].height, cams[1].width, cams[1].height = 130, 70, 64, 64
+    shapes = (gsr.gs_launch_shape * 3)(gsr.gs_launch_shape(8, 64, 1, 2), gsr.gs_launch_shape(32, 256, 2, 2),
+                                      gsr.gs_launch_shape(12, 64, 1, 1))  # the last is not a valid shape
+    big = lib.gs_autotune_workspace_size(1000, 3, cams, 2, 50000, shapes, 3)
+    small = lib.gs_autotune_workspace_size(1000, 3, cams, 2, 50000, shapes, 1)
+    only_invalid = lib.gs_autotune_workspace_size(1000, 3, cams, 2, 50000, C.byref(shapes[2]), 1)
+    assert big >= small > 0 and only_invalid == 0
+    assert lib.gs_autotune_workspace_size(1000, 4, cams, 2, 50000, shapes, 3) == 0
+    assert cams[1].tile_offset == 0  # the caller's cameras are not modified
+    p = gsr.gs_params()
+    p.n, p.sh_degree = 1000, 3
+    rc = gsr.gs_raster_config()
+    rc.sh_degree = 3
+    ms = (C.c_float * 3)()
+    best = C.c_int32()
+    args = (C.byref(p), cams, 2, C.c_void_p(256), C.byref(rc), 0.2, shapes, 3, 2, 50000)
+    assert lib.gs_autotune(*args, None, big, ms, C.byref(best), None) == gsr.GS_ERR_WORKSPACE
+    assert lib.gs_autotune(*args, C.c_void_p(1 << 20), big - 1, ms, C.byref(best), None) == gsr.GS_ERR_WORKSPACE
+    rc.sh_degree = 2
+    assert lib.gs_autotune(*args, C.c_void_p(1 << 20), big, ms, C.byref(best), None) == gsr.GS_ERR_INVALID_ARG
