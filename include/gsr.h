@@ -179,7 +179,8 @@ gs_status gs_project(const gs_params *params /* host */, const gs_camera *cams, 
 /* ------------------------------------------------------ binning and sort */
 
 /* Scratch bytes gs_bin_sort needs for n Gaussians x n_views views over
- * total_tiles tiles (pair_capacity does not change it). */
+ * total_tiles tiles and pair_capacity pairs (12 bytes per pair of capacity:
+ * the entries listed by super-tile of 4 x 4 tiles, at most one per pair). */
 size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capacity, int64_t total_tiles);
 
 /* Tile binning + depth order ("depth-sorted Gaussians overlapping a pixel",
@@ -323,10 +324,17 @@ gs_status gs_project_bwd(const gs_params *params /* host */, const gs_camera *ca
 /* (gs_adam_config and gs_adam_step below; gs_render_bwd_adam after them.) */
 
 /* Adam (Kingma & Ba, bias-corrected), the optimizer step of Algorithm 1.
- * lr[6]: means, log_scales, quats, opacity, SH DC, SH higher bands. */
+ * lr[6]: means, log_scales, quats, opacity, SH DC, SH higher bands.
+ * lr_scale_den: 0, or (with a step-gate word dev_do_step) the learning rates
+ * of a step are multiplied by *dev_do_step / lr_scale_den - for a batched
+ * step whose gate word holds the number of views the gate opened
+ * (skipgs_gate_decide's dev_any) out of lr_scale_den, so the step moves by
+ * the opened views' share of the batch (a reading of Algorithm 1 for
+ * several views per step; the paper decides one view per step). */
 typedef struct {
     float lr[6];
     float beta1, beta2, eps;
+    int32_t lr_scale_den;
 } gs_adam_config;
 
 /* One fused update of every scalar of the flat parameter buffer (layout of
@@ -402,7 +410,8 @@ gs_status skipgs_gate_init(const gs_gate_config *cfg /* host */, void *dev_state
  * in binary64 with one rounding per operation.  Writes g[n] (u8) and, if
  * given, *dev_any = OR of g (int32) and the graph conditional `cond` (host
  * pointer to a handle created for the graph being captured; NULL outside a
- * graph).  A non-finite loss: g = 0, state untouched, GS_ERR_NONFINITE. */
+ * graph).  A non-finite loss: g = 0, state untouched, GS_ERR_NONFINITE.
+ * *dev_any holds the number of g = 1 (nonzero exactly when any view opened). */
 gs_status skipgs_gate_decide(void *dev_state, const int32_t *dev_view_ids, const float *dev_losses, int32_t n,
                              uint8_t *dev_g, int32_t *dev_any, const cudaGraphConditionalHandle *cond,
                              int32_t *dev_status, cudaStream_t stream);

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ p, float 
     if (do_step && *do_step == 0) return;
     __shared__ float s_lr[6];
     __shared__ float s_ibc2;
-    if (threadIdx.x == 0) adam_scalars(cfg, *step, s_lr, &s_ibc2);
+    if (threadIdx.x == 0) adam_scalars(cfg, *step, do_step, s_lr, &s_ibc2);
     __syncthreads();
     const float b1 = cfg.beta1, b2 = cfg.beta2, eps = cfg.eps;
     const float ibc2 = s_ibc2;

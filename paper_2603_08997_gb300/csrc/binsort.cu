@@ -10,7 +10,10 @@
 //   2. place every pair by a counting sort over tiles that walks the entries
 //      in that order (see bin_count .. bin_scatter below).
 // A stable sort by tile of a depth-ordered list is ordered by
-// (tile, depth, index), i.e. exactly the 64-bit key order.
+// (tile, depth, index), i.e. exactly the 64-bit key order.  Stage 2 runs in
+// two levels: a chunked counting sort of the entries by 4 x 4-tile
+// super-tile, then, per super-tile, one warp per tile selecting the tile's
+// entries from the super-tile's depth-ordered list (stage 2b below).
 //
 // Every kernel reads the counts it needs from device memory, so the whole
 // call can be captured in a CUDA graph.  The radix sort is a reduce-then-scan LSD
@@ -291,9 +294,10 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 //   bin_offsets: per (group, tile), the count matrix becomes the chunks' first
 //                slots, and group 0 writes the tile's range;
 //   bin_scatter: one block per chunk places the chunk's pairs (below).
-// There are only about two chunks per SM, so the pair writes of all chunks in
-// flight together cover a few tens of MB: partly written 32-byte sectors are
-// completed in L2 instead of being read back from DRAM.
+// On the tile grid only the tile totals are used (bin_count, bin_groups,
+// bin_starts: each tile's start and range); the placement runs on the grid of
+// super-tiles (BinGeom.sup), where bin_scatter places entry positions, and
+// stage 2b fills the tiles.
 constexpr int BIN_GROUP = 16;
 constexpr int COUNT_THREADS = 1024;
 
@@ -302,15 +306,17 @@ struct BinGeom {
     int64_t chunk;   // entries per chunk
     int64_t n_c;     // chunks per view
     int64_t n_g;     // groups per view
-    int64_t tiles;   // total tiles over all views
+    int64_t tiles;   // total tiles over all views (of this grid)
     int tile;        // pixels per tile side
     int max_vt;      // tiles per view the shared-memory tables hold
+    int sup;         // 1: the tile grid; SUP: the grid of SUP x SUP super-tiles
+    const int64_t *coff;  // sup > 1: first super-tile id of each view, [n_views + 1] (device)
 };
 
-// Entries per chunk: about two chunks per SM for one view, at least 1024, in
-// multiples of 256.
-int64_t bin_chunk(int64_t n) {
-    int64_t c = ceil_div(n, (int64_t)304);
+// Entries per chunk: n / `chunks` (about two chunks per SM for one view on
+// the tile grid), at least 1024, in multiples of 256.
+int64_t bin_chunk(int64_t n, int64_t chunks = 304) {
+    int64_t c = ceil_div(n, chunks);
     c = ceil_div(c, (int64_t)256) * 256;
     return c < 1024 ? 1024 : c;
 }
@@ -326,6 +332,36 @@ __device__ __forceinline__ ViewTiles view_tiles(const gs_camera &cam, int tile) 
     vt.tx = (cam.width + tile - 1) / tile;
     vt.ty = (cam.height + tile - 1) / tile;
     return vt;
+}
+
+// The grid a BinGeom counts and places on: the view's tiles, or its
+// super-tiles (SUP x SUP tiles each; the view's first super-tile id from
+// g.coff).
+__device__ __forceinline__ ViewTiles view_grid(const BinGeom &g, const gs_camera *cams, int64_t v) {
+    ViewTiles vt = view_tiles(cams[v], g.tile);
+    if (g.sup > 1) {
+        vt.tx = (vt.tx + g.sup - 1) / g.sup;
+        vt.ty = (vt.ty + g.sup - 1) / g.sup;
+        vt.off = g.coff[v];
+    }
+    return vt;
+}
+
+// A clipped tile rectangle (x0, y0, width, height) in the geometry's grid.
+__device__ __forceinline__ ushort4 grid_rect(const BinGeom &g, ushort4 r) {
+    if (g.sup == 1 || r.z == 0) return r;
+    const int x0 = r.x / g.sup, y0 = r.y / g.sup;
+    const int x1 = (r.x + r.z - 1) / g.sup, y1 = (r.y + r.w - 1) / g.sup;
+    return make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)(x1 - x0 + 1),
+                        (unsigned short)(y1 - y0 + 1));
+}
+
+// The view a global id of the geometry's grid belongs to.
+__device__ __forceinline__ int view_of_grid_tile(const BinGeom &g, const gs_camera *cams, int n_views, int64_t gt) {
+    if (g.sup == 1) return view_of_tile(cams, n_views, gt);
+    int v = 0;
+    while (v + 1 < n_views && g.coff[v + 1] <= gt) ++v;
+    return v;
 }
 
 // Does the view's tile table fit the shared-memory tables and the global
@@ -375,7 +411,7 @@ __global__ void __launch_bounds__(COUNT_THREADS) bin_count(const ushort4 *__rest
                                                            int32_t *dev_status) {
     extern __shared__ int s_d[];  // [(tx + 1) * (ty + 1)] <= 2 max_vt + 2
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
-    const ViewTiles vt = view_tiles(cams[v], g.tile);
+    const ViewTiles vt = view_grid(g, cams, v);
     if (!view_fits(vt, g.tiles, g.max_vt)) {
         if (threadIdx.x == 0) set_status(dev_status, GS_ERR_INVALID_ARG);
         return;
@@ -385,7 +421,7 @@ __global__ void __launch_bounds__(COUNT_THREADS) bin_count(const ushort4 *__rest
     __syncthreads();
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
     for (int64_t i = e0 + threadIdx.x; i < e1; i += COUNT_THREADS) {
-        const ushort4 r = srect[i];
+        const ushort4 r = grid_rect(g, srect[i]);
         if (r.z == 0) continue;
         const int x0 = r.x, y0 = r.y, x1 = x0 + r.z, y1 = y0 + r.w;
         atomicAdd(&s_d[y0 * W + x0], 1);
@@ -410,11 +446,11 @@ __global__ void __launch_bounds__(COUNT_THREADS) bin_count(const ushort4 *__rest
         }
     }
     __syncthreads();
-    uint32_t *row = M + g.n_c * vt.off + c * T;
+    uint32_t *row = M ? M + g.n_c * vt.off + c * T : nullptr;  // no M: only the group sums are needed
     uint32_t *grp = G1 + (c / BIN_GROUP) * g.tiles + vt.off;
     for (int t = threadIdx.x; t < T; t += COUNT_THREADS) {
         const uint32_t h = (uint32_t)s_d[(t / vt.tx) * W + (t % vt.tx)];
-        row[t] = h;
+        if (row) row[t] = h;
         if (h) atomicAdd(&grp[t], h);
     }
 }
@@ -481,8 +517,8 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_g * g.tiles) return;
     const int64_t k = i / g.tiles, gt = i % g.tiles;
-    const int v = view_of_tile(cams, n_views, gt);
-    const ViewTiles vt = view_tiles(cams[v], g.tile);
+    const int v = view_of_grid_tile(g, cams, n_views, gt);
+    const ViewTiles vt = view_grid(g, cams, v);
     if (!view_fits(vt, g.tiles, g.max_vt)) return;
     const int T = vt.tx * vt.ty;
     const int64_t t = gt - vt.off;
@@ -498,7 +534,7 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
         if (c0 + j < c1) col[(c0 + j) * T] = run;
         run += x[j];
     }
-    if (k == 0) {
+    if (k == 0 && ranges) {
         const uint32_t tot = tile_total[gt];
         ranges[gt] = tot ? make_uint2(tile_start[gt], tile_start[gt] + tot) : make_uint2(0u, 0u);
     }
@@ -563,25 +599,30 @@ struct PairWalk {
     }
 };
 
+// Places each pair's Gaussian index into vals and the entry's tile
+// rectangle (in tiles, packed as (x0 | y0 << 16, width | height << 16)) into
+// recs: on the super-tile grid, the records the tile placement reads.
 template <typename W, int NW>  // W: 32-bit mask words
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                           const uint32_t *__restrict__ order,
                                                           const gs_camera *__restrict__ cams, BinGeom g,
                                                           const uint32_t *__restrict__ M,
-                                                          const int64_t *sort_count, uint32_t *__restrict__ vals) {
+                                                          const int64_t *sort_count, uint32_t *__restrict__ vals,
+                                                          uint2 *__restrict__ recs) {
     using SM = ScatterMask<W, NW>;
     constexpr int WB = SM::WB, WIN = SM::WIN;
     extern __shared__ __align__(16) unsigned char s_raw[];
     W *s_mask = reinterpret_cast<W *>(s_raw);                                     // [max_vt][NW]
     uint32_t *s_off = reinterpret_cast<uint32_t *>(s_mask + (size_t)g.max_vt * NW);  // [max_vt]
-    __shared__ ushort4 s_er[WIN];    // the window's rectangles
+    __shared__ ushort4 s_er[WIN];    // the window's rectangles (in the geometry's grid)
     __shared__ uint32_t s_eg[WIN];   // Gaussian indices
+    __shared__ uint2 s_fr[WIN];      // the window's tile rectangles, packed
     __shared__ int s_pre[WIN + 1];   // first pair of each entry
-    __shared__ uint32_t s_tj[SC_THREADS * SC_Q];  // first sub-window: (tile << 8 | entry) per pair
+    __shared__ uint32_t s_tj[SC_THREADS * SC_Q];  // first sub-window: (tile << 9 | entry) per pair
     __shared__ uint32_t s_warp[32];
     if (*sort_count == 0) return;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
-    const ViewTiles vt = view_tiles(cams[v], g.tile);
+    const ViewTiles vt = view_grid(g, cams, v);
     if (!view_fits(vt, g.tiles, g.max_vt)) return;
     const int T = vt.tx * vt.ty;
     const uint32_t *row = M + g.n_c * vt.off + c * T;
@@ -597,12 +638,16 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             const int64_t i = base + threadIdx.x;
             ushort4 r = make_ushort4(0, 0, 0, 0);
             uint32_t gi = 0;
+            ushort4 fr = make_ushort4(0, 0, 0, 0);
             if (i < e1) {
-                r = srect[i];
+                fr = srect[i];
+                r = grid_rect(g, fr);
                 gi = (uint32_t)((int64_t)order[i] - v * g.n);
             }
             s_er[threadIdx.x] = r;
             s_eg[threadIdx.x] = gi;
+            s_fr[threadIdx.x] = make_uint2((uint32_t)fr.x | ((uint32_t)fr.y << 16),
+                                                    (uint32_t)fr.z | ((uint32_t)fr.w << 16));
             area = (int)r.z * r.w;
         }
         // the window's pair prefix: a warp scan in the WIN / 32 warps holding
@@ -641,7 +686,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                 it.start(p0, s_pre, s_er, WIN, vt.tx);
                 for (int p = p0;; ++p) {
                     atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
-                    if (sw == 0) s_tj[p] = ((uint32_t)it.t << 8) | (uint32_t)it.jj;  // for pass B
+                    if (sw == 0) s_tj[p] = ((uint32_t)it.t << 9) | (uint32_t)it.jj;  // for pass B
                     if (p + 1 >= p1) break;
                     it.next(p, s_pre, s_er, vt.tx);
                 }
@@ -667,8 +712,8 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                     int t, jj;
                     if (sw == 0) {  // the first sub-window's pairs were recorded by pass A
                         const uint32_t tj = s_tj[p];
-                        t = (int)(tj >> 8);
-                        jj = (int)(tj & 0xffu);
+                        t = (int)(tj >> 9);
+                        jj = (int)(tj & 0x1ffu);
                     } else {
                         if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
                         t = it.t;
@@ -697,6 +742,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                         if (wd == jw) below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
                     }
                     vals[s_off[t] + below] = s_eg[jj];
+                    recs[s_off[t] + below] = s_fr[jj];
                     if (below + 1 == all) {  // the tile's last pair of the window
                         last_t[k] = t;
                         last_n[k] = all;
@@ -719,11 +765,245 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     }
 }
 
-// Window width for a tile table: 128 entries (four 32-bit masks per tile)
-// where it fits two blocks per SM, else 32 (one mask).  The masks are 32-bit
-// words because shared-memory atomicOr is native at that width.
-bool scatter_wide(int64_t max_vt) {
-    return (size_t)max_vt * ScatterMask<uint32_t, 4>::bytes_per_tile <= (size_t)96 * 1024;
+// Window width of the super-tile scatter: 512 entries (sixteen 32-bit masks
+// per super-tile) where the table stays small enough for two blocks per SM,
+// else 128.  The masks are 32-bit words because shared-memory atomicOr is
+// native at that width.
+bool coarse_scatter_wide(int64_t max_vt) {
+    return (size_t)max_vt * ScatterMask<uint32_t, 16>::bytes_per_tile <= (size_t)96 * 1024;
+}
+
+// ----------------------------------------------------------------------------
+// Stage 2b: placement by super-tile.
+//
+// The chunked counting sort above, run on the grid of SUP x SUP super-tiles
+// with entry positions as values, gives every super-tile the depth-ordered
+// list of the entries whose rectangle meets it (its "coarse list").  A coarse
+// list is cut into work items of WI entries, one warp each.  The warp takes
+// its entries 32 at a time; each lane turns its entry's rectangle into a
+// 16-bit mask of the super-tile's tiles it covers, and one ballot per tile
+// gives each covering lane its rank among the group's covering lanes: the
+// tile's pairs from the item, in depth order, go to consecutive slots.  A
+// count pass gives each (item, tile) its pair count, a scan per super-tile
+// over its items (after the tile's start) the first slots, and the place pass
+// writes.  Every pair is written once, each tile's run contiguously, and no
+// warp waits on another.
+constexpr int SUP = 4;            // tiles per super-tile side
+constexpr int SUP_T = SUP * SUP;  // tiles per super-tile: one mask bit each
+constexpr int WI = 512;           // coarse-list entries per work item (one warp)
+constexpr int FP_THREADS = 256;   // threads of the placement blocks (8 warps)
+
+// coff[v]: first super-tile id of view v; coff[n_views]: the total.
+__global__ void coarse_offsets(const gs_camera *__restrict__ cams, int n_views, int tile, int64_t *__restrict__ coff) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int64_t run = 0;
+    for (int v = 0; v < n_views; ++v) {
+        coff[v] = run;
+        const int64_t tx = (cams[v].width + tile - 1) / tile, ty = (cams[v].height + tile - 1) / tile;
+        if (tx > 0 && ty > 0) run += ((tx + SUP - 1) / SUP) * ((ty + SUP - 1) / SUP);
+    }
+    coff[n_views] = run;
+}
+
+// Work items: seg_base[ct] = exclusive scan of ceil(ctotal[ct] / WI) over
+// the super-tiles (one block), seg_base[tiles] = the item count (0 when the
+// pairs exceeded the capacity).
+__global__ void __launch_bounds__(SCAN_THREADS) seg_layout(int64_t tiles, const uint32_t *__restrict__ ctotal,
+                                                           const int64_t *sort_count, uint32_t *__restrict__ seg_base) {
+    __shared__ uint32_t s[SCAN_THREADS];
+    const bool ok = *sort_count != 0;
+    const int64_t per = ceil_div(tiles, (int64_t)SCAN_THREADS);
+    const int64_t lo = min(tiles, (int64_t)threadIdx.x * per), hi = min(tiles, lo + per);
+    uint32_t sum = 0;
+    for (int64_t t = lo; t < hi; ++t) sum += ok ? (ctotal[t] + WI - 1) / WI : 0u;
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        const uint32_t y = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += y;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (int64_t t = lo; t < hi; ++t) {
+        seg_base[t] = run;
+        run += ok ? (ctotal[t] + WI - 1) / WI : 0u;
+    }
+    if (threadIdx.x == 0) seg_base[tiles] = s[SCAN_THREADS - 1];
+}
+
+__global__ void seg_fill(int64_t tiles, const uint32_t *__restrict__ seg_base, uint32_t *__restrict__ item_ct) {
+    const int64_t ct = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ct >= tiles) return;
+    for (uint32_t it = seg_base[ct]; it < seg_base[ct + 1]; ++it) item_ct[it] = (uint32_t)ct;
+}
+
+// Bits k = 4 row + column of the super-tile's tiles (its first tile at
+// (x0, y0)) that the clipped tile rectangle r covers.
+__device__ __forceinline__ uint32_t cover_mask(ushort4 r, int x0, int y0) {
+    if (r.z == 0) return 0u;
+    const int c0 = max((int)r.x - x0, 0), c1 = min((int)r.x + (int)r.z - x0, SUP);
+    const int r0 = max((int)r.y - y0, 0), r1 = min((int)r.y + (int)r.w - y0, SUP);
+    if (c0 >= c1 || r0 >= r1) return 0u;
+    const uint32_t cols = ((1u << c1) - 1u) & ~((1u << c0) - 1u);
+    uint32_t m = 0;
+#pragma unroll
+    for (int y = 0; y < SUP; ++y)
+        if (y >= r0 && y < r1) m |= cols << (SUP * y);
+    return m;
+}
+
+// Geometry of work item `item`: its super-tile's first tile, view, entries.
+struct ItemGeom {
+    int v, x0, y0, cnt;
+    uint32_t b0;
+    bool fits;
+};
+
+__device__ __forceinline__ ItemGeom item_geom(uint32_t item, const BinGeom &gc, const gs_camera *cams, int n_views,
+                                              const uint32_t *cstart, const uint32_t *ctotal,
+                                              const uint32_t *seg_base, const uint32_t *item_ct, int64_t fine_tiles,
+                                              int fine_max_vt) {
+    ItemGeom ig;
+    const uint32_t ct = item_ct[item];
+    const uint32_t sg = item - seg_base[ct];
+    ig.v = view_of_grid_tile(gc, cams, n_views, ct);
+    const ViewTiles ft = view_tiles(cams[ig.v], gc.tile);
+    ig.fits = view_fits(ft, fine_tiles, fine_max_vt);
+    const int ctx = (ft.tx + SUP - 1) / SUP;
+    const int64_t lct = (int64_t)ct - gc.coff[ig.v];
+    ig.x0 = (int)(lct % ctx) * SUP;
+    ig.y0 = (int)(lct / ctx) * SUP;
+    ig.b0 = cstart[ct] + sg * WI;
+    ig.cnt = (int)min((uint32_t)WI, ctotal[ct] - sg * WI);
+    return ig;
+}
+
+// PLACE = false: per item and tile of its super-tile, the number of the
+// item's entries covering the tile (into run_of[item][k]).  PLACE = true:
+// run_of[item][k] holds the tile's first slot for the item; the covering
+// entries' Gaussian indices are written from there in list order.  Warps
+// take items in a grid-stride loop (the item count is on the device); the
+// item's records are read in order (coalesced).
+template <bool PLACE>
+__global__ void __launch_bounds__(FP_THREADS) fine_pass(const uint2 *__restrict__ crect,
+                                                        const uint32_t *__restrict__ cgid,
+                                                        const gs_camera *__restrict__ cams, int n_views, BinGeom gc,
+                                                        const uint32_t *__restrict__ cstart,
+                                                        const uint32_t *__restrict__ ctotal,
+                                                        const uint32_t *__restrict__ seg_base,
+                                                        const uint32_t *__restrict__ item_ct,
+                                                        uint32_t *__restrict__ run_of, uint32_t *__restrict__ vals,
+                                                        int64_t fine_tiles, int fine_max_vt, int64_t cap) {
+    const uint32_t n_items = seg_base[gc.tiles];
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t warps = gridDim.x * (FP_THREADS / 32);
+    for (uint32_t item = blockIdx.x * (FP_THREADS / 32) + (threadIdx.x >> 5); item < n_items; item += warps) {
+        const ItemGeom ig = item_geom(item, gc, cams, n_views, cstart, ctotal, seg_base, item_ct, fine_tiles,
+                                      fine_max_vt);
+        uint32_t run[SUP_T];
+#pragma unroll
+        for (int k = 0; k < SUP_T; ++k) run[k] = PLACE ? run_of[(size_t)item * SUP_T + k] : 0u;
+        if (ig.fits) {  // else no pairs (the tile counts flagged the view)
+            for (int g0 = 0; g0 < ig.cnt; g0 += 32) {
+                const int j = g0 + lane;
+                uint32_t m = 0, gid = 0;
+                if (j < ig.cnt) {
+                    const uint2 q = crect[ig.b0 + j];
+                    const ushort4 r = make_ushort4((unsigned short)(q.x & 0xffffu), (unsigned short)(q.x >> 16),
+                                                   (unsigned short)(q.y & 0xffffu), (unsigned short)(q.y >> 16));
+                    m = cover_mask(r, ig.x0, ig.y0);
+                    if (PLACE) gid = cgid[ig.b0 + j];
+                }
+#pragma unroll
+                for (int k = 0; k < SUP_T; ++k) {
+                    const bool cov = (m >> k) & 1u;
+                    const uint32_t b = __ballot_sync(0xffffffffu, cov);
+                    if (PLACE && cov) {
+                        const uint32_t d = run[k] + __popc(b & lt_mask);
+                        if (d < cap) vals[d] = gid;  // always below: the tile counts bound the runs
+                    }
+                    run[k] += __popc(b);
+                }
+            }
+        }
+        if (!PLACE && lane < SUP_T) {
+            uint32_t mine = 0;
+#pragma unroll
+            for (int k = 0; k < SUP_T; ++k) mine = lane == k ? run[k] : mine;
+            run_of[(size_t)item * SUP_T + lane] = mine;
+        }
+    }
+}
+
+// One warp per super-tile: the counts of its items become first slots (per
+// tile, an exclusive scan over the items after the tile's start: lanes take
+// 32 items at a time, shuffle scans per tile), and its tiles' ranges are
+// written.
+__global__ void __launch_bounds__(256) fine_prefix(const gs_camera *__restrict__ cams, int n_views, BinGeom gc,
+                                                   int64_t tiles, int fine_max_vt,
+                                                   const uint32_t *__restrict__ tile_start,
+                                                   const uint32_t *__restrict__ tile_total,
+                                                   const uint32_t *__restrict__ seg_base, const int64_t *sort_count,
+                                                   uint32_t *__restrict__ run_of, uint2 *__restrict__ ranges) {
+    if (*sort_count == 0) return;
+    const int64_t ct = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (ct >= gc.tiles || ct >= gc.coff[n_views]) return;  // whole warps
+    const int v = view_of_grid_tile(gc, cams, n_views, ct);
+    const ViewTiles ft = view_tiles(cams[v], gc.tile);
+    if (!view_fits(ft, tiles, fine_max_vt)) return;
+    const int ctx = (ft.tx + SUP - 1) / SUP;
+    const int64_t lct = ct - gc.coff[v];
+    const int x0 = (int)(lct % ctx) * SUP, y0 = (int)(lct / ctx) * SUP;
+    // lane k < 16: tile k of the super-tile, its start and range
+    int64_t gt = -1;
+    uint32_t carry = 0;
+    if (lane < SUP_T) {
+        const int fx = x0 + lane % SUP, fy = y0 + lane / SUP;
+        if (fx < ft.tx && fy < ft.ty) {
+            gt = ft.off + (int64_t)fy * ft.tx + fx;
+            carry = tile_start[gt];
+            const uint32_t tot = tile_total[gt];
+            ranges[gt] = tot ? make_uint2(carry, carry + tot) : make_uint2(0u, 0u);
+        }
+    }
+    const uint32_t i0 = seg_base[ct], i1 = seg_base[ct + 1];
+    for (uint32_t base = i0; base < i1; base += 32) {
+        const uint32_t it = base + lane;
+        const bool valid = it < i1;
+        uint32_t c[SUP_T];
+#pragma unroll
+        for (int q = 0; q < SUP_T / 4; ++q) {
+            const uint4 x = valid ? reinterpret_cast<const uint4 *>(run_of + (size_t)it * SUP_T)[q]
+                                  : make_uint4(0u, 0u, 0u, 0u);
+            c[4 * q] = x.x;
+            c[4 * q + 1] = x.y;
+            c[4 * q + 2] = x.z;
+            c[4 * q + 3] = x.w;
+        }
+#pragma unroll
+        for (int k = 0; k < SUP_T; ++k) {
+            uint32_t inc = c[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t start_k = __shfl_sync(0xffffffffu, carry, k);  // tile k's running slot
+            const uint32_t total_k = __shfl_sync(0xffffffffu, inc, 31);
+            c[k] = start_k + inc - c[k];
+            if (lane == k) carry += total_k;
+        }
+        if (valid) {
+#pragma unroll
+            for (int q = 0; q < SUP_T / 4; ++q)
+                reinterpret_cast<uint4 *>(run_of + (size_t)it * SUP_T)[q] =
+                    make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+        }
+    }
+    (void)gt;
 }
 
 // 64-bit keys of the sorted pairs (for checking the order): one block per tile.
@@ -756,29 +1036,68 @@ BinGeom bin_geom(int64_t n, int64_t total_tiles, int tile, int max_vt) {
     g.tiles = total_tiles;
     g.tile = tile;
     g.max_vt = max_vt;
+    g.sup = 1;
+    g.coff = nullptr;
     return g;
+}
+
+// The super-tile grid: a view of T tiles (tx * ty <= max_vt) has at most
+// ceil(tx / SUP) * ceil(ty / SUP) <= (T + 3 (tx + ty) + 9) / 16 <= max_vt / 4
+// + 1 super-tiles (tx + ty <= T + 1), so all views together at most
+// total_tiles / 4 + n_views.  Smaller tables allow shorter chunks (about four
+// per SM).
+BinGeom coarse_geom(int64_t n, int64_t total_tiles, int64_t n_views, int tile, int max_vt, const int64_t *coff) {
+    BinGeom g;
+    g.n = n;
+    g.chunk = bin_chunk(n, 608);
+    g.n_c = ceil_div(n > 0 ? n : 1, g.chunk);
+    g.n_g = ceil_div(g.n_c, (int64_t)BIN_GROUP);
+    g.tiles = total_tiles / 4 + n_views;
+    g.tile = tile;
+    g.max_vt = max_vt / 4 + 1;
+    g.sup = SUP;
+    g.coff = coff;
+    return g;
+}
+
+int64_t fine_items_cap(int64_t pair_capacity, int64_t coarse_tiles) {
+    return ceil_div(pair_capacity, (int64_t)WI) + coarse_tiles;
 }
 
 struct BinWorkspace {
     uint32_t *dk[2], *dv[2];   // depth (then view) keys / entry ids, ping-pong, [V*N]
     uint32_t *counts;          // [RADIX * RS_MAX_BLOCKS] + [RADIX] digit totals
-    uint32_t *M;               // [n_c * total_tiles] chunk x tile counts, then first slots
-    uint32_t *G1;              // [n_g * total_tiles] group sums, then group offsets
+    uint32_t *G1;              // [n_g * total_tiles] group sums of the tile counts
     uint32_t *tile_total;      // [total_tiles]
     uint32_t *tile_start;      // [total_tiles]
     ushort4 *srect;            // [V*N] clipped rectangles in depth order
     int64_t *sort_count;       // [1]
+    // the super-tile grid (coarse)
+    int64_t *coff;             // [V + 1] first super-tile of each view
+    uint32_t *Mc;              // [n_c' * Tc] chunk x super-tile counts, then first slots
+    uint32_t *G1c;             // [n_g' * Tc]
+    uint32_t *ctotal, *cstart; // [Tc]
+    uint2 *crect;              // [pair_capacity] tile rectangles by super-tile, in depth order
+    uint32_t *cgid;            // [pair_capacity] their Gaussian indices
+    int64_t *c_count;          // [2] super-tile pair count, its sort count
+    // placement work items
+    uint32_t *seg_base;        // [Tc + 1]
+    uint32_t *item_ct;         // [items]
+    uint32_t *run_of;          // [items * SUP_T] counts, then first slots
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspace *w, char *base) {
+size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pair_capacity, BinWorkspace *w,
+                     char *base) {
     const int64_t total = n * n_views;
     const BinGeom g = bin_geom(n, total_tiles, 16, 0);
+    const BinGeom gc = coarse_geom(n, total_tiles, n_views, 16, 0, nullptr);
+    const int64_t items = fine_items_cap(pair_capacity, gc.tiles);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char *p = base ? base + off : nullptr;
-        off += align256(bytes);
+        off += align256(bytes > 0 ? bytes : 1);
         return p;
     };
     for (int i = 0; i < 2; ++i) {
@@ -787,20 +1106,40 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, BinWorkspa
         if (w) { w->dk[i] = (uint32_t *)a; w->dv[i] = (uint32_t *)b; }
     }
     char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1));
-    char *M = take(sizeof(uint32_t) * (size_t)(g.n_c * total_tiles));
     char *G1 = take(sizeof(uint32_t) * (size_t)(g.n_g * total_tiles));
     char *tt = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *ts = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *sr = take(sizeof(ushort4) * (size_t)(total > 0 ? total : 1));
     char *sc = take(sizeof(int64_t));
+    char *coff = take(sizeof(int64_t) * (size_t)(n_views + 1));
+    char *Mc = take(sizeof(uint32_t) * (size_t)(gc.n_c * gc.tiles));
+    char *G1c = take(sizeof(uint32_t) * (size_t)(gc.n_g * gc.tiles));
+    char *ct = take(sizeof(uint32_t) * (size_t)gc.tiles);
+    char *cs = take(sizeof(uint32_t) * (size_t)gc.tiles);
+    char *cl = take(sizeof(uint2) * (size_t)pair_capacity);
+    char *cg = take(sizeof(uint32_t) * (size_t)pair_capacity);
+    char *cc = take(sizeof(int64_t) * 2);
+    char *sb = take(sizeof(uint32_t) * (size_t)(gc.tiles + 1));
+    char *ic = take(sizeof(uint32_t) * (size_t)items);
+    char *ro = take(sizeof(uint32_t) * (size_t)items * SUP_T);
     if (w) {
         w->counts = (uint32_t *)counts;
-        w->M = (uint32_t *)M;
         w->G1 = (uint32_t *)G1;
         w->tile_total = (uint32_t *)tt;
         w->tile_start = (uint32_t *)ts;
         w->srect = (ushort4 *)sr;
         w->sort_count = (int64_t *)sc;
+        w->coff = (int64_t *)coff;
+        w->Mc = (uint32_t *)Mc;
+        w->G1c = (uint32_t *)G1c;
+        w->ctotal = (uint32_t *)ct;
+        w->cstart = (uint32_t *)cs;
+        w->crect = (uint2 *)cl;
+        w->cgid = (uint32_t *)cg;
+        w->c_count = (int64_t *)cc;
+        w->seg_base = (uint32_t *)sb;
+        w->item_ct = (uint32_t *)ic;
+        w->run_of = (uint32_t *)ro;
     }
     return off;
 }
@@ -818,10 +1157,12 @@ gs_status bin_smem_attributes() {
     if (done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bytes + 8));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the super-tile scatter: tables of at most kMaxViewTiles / 4 + 1 super-tiles
+    const int coarse_vt = kMaxViewTiles / 4 + 1;
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(96 * 1024)));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(ScatterMask<uint32_t, 1>::bytes_per_tile * kMaxViewTiles)));
+    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(ScatterMask<uint32_t, 4>::bytes_per_tile * coarse_vt)));
     done[dev] = true;
     return GS_OK;
 }
@@ -832,7 +1173,7 @@ extern "C" {
 
 size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capacity, int64_t total_tiles) {
     if (n < 0 || n_views <= 0 || pair_capacity < 0 || total_tiles <= 0) return 0;
-    return bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr);
+    return bin_ws_layout(n, n_views, total_tiles, pair_capacity, nullptr, nullptr);
 }
 
 gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
@@ -849,11 +1190,11 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     const int64_t total = n * n_views;
     if (total >= ((int64_t)1 << 32) - 1) return GS_ERR_INVALID_ARG;
     if (total > 0 && (!proj->rec || !proj->rect || !proj->tiles_touched)) return GS_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr))
+    if (!workspace || workspace_bytes < bin_ws_layout(n, n_views, total_tiles, pair_capacity, nullptr, nullptr))
         return GS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 255) return GS_ERR_WORKSPACE;
     BinWorkspace w;
-    bin_ws_layout(n, n_views, total_tiles, &w, (char *)workspace);
+    bin_ws_layout(n, n_views, total_tiles, pair_capacity, &w, (char *)workspace);
 
     GS_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, stream));
     if (total == 0) {
@@ -881,7 +1222,10 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     }
     const uint32_t *order = w.dv[sel];
     const int4 *rect = reinterpret_cast<const int4 *>(proj->rect);
-    // 2. counting sort of the pairs by tile, in depth order
+    // 2. the pairs by tile, in depth order: tile totals and starts (chunked
+    // counts on the tile grid), then the entries by super-tile (the chunked
+    // counting sort on the super-tile grid), then each super-tile's tiles
+    // filled from its depth-ordered entry list
     const size_t smem = sizeof(uint32_t) * (size_t)mvt;
     {
         const gs_status st = bin_smem_attributes();
@@ -896,22 +1240,59 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     GS_TRY_LAUNCH();
     GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
     const unsigned n_chunks = (unsigned)(g.n_c * n_views);
-    bin_count<<<n_chunks, COUNT_THREADS, 2 * smem + 8, stream>>>(w.srect, cams, g, w.M, w.G1, dev_status);
+    bin_count<<<n_chunks, COUNT_THREADS, 2 * smem + 8, stream>>>(w.srect, cams, g, nullptr, w.G1, dev_status);
     GS_TRY_LAUNCH();
     bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
     GS_TRY_LAUNCH();
     bin_starts<<<1, SCAN_THREADS, 0, stream>>>(g, w.tile_total, w.tile_start, pair_capacity, dev_pair_count,
                                                w.sort_count, dev_status);
     GS_TRY_LAUNCH();
-    bin_offsets<<<(unsigned)ceil_div(g.n_g * total_tiles, (int64_t)256), 256, 0, stream>>>(
-        g, cams, n_views, w.G1, w.tile_start, w.tile_total, w.sort_count, w.M, reinterpret_cast<uint2 *>(ranges));
+    // the super-tile grid
+    coarse_offsets<<<1, 32, 0, stream>>>(cams, n_views, cfg->tile, w.coff);
     GS_TRY_LAUNCH();
-    if (scatter_wide(mvt))
-        bin_scatter<uint32_t, 4><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 4>::bytes_per_tile * mvt, stream>>>(
-            w.srect, order, cams, g, w.M, w.sort_count, vals);
+    const BinGeom gc = coarse_geom(n, total_tiles, n_views, cfg->tile, (int)mvt, w.coff);
+    const size_t csmem = sizeof(uint32_t) * (size_t)gc.max_vt;
+    GS_TRY(cudaMemsetAsync(w.G1c, 0, sizeof(uint32_t) * (size_t)(gc.n_g * gc.tiles), stream));
+    const unsigned n_cchunks = (unsigned)(gc.n_c * n_views);
+    bin_count<<<n_cchunks, COUNT_THREADS, 2 * csmem + 8, stream>>>(w.srect, cams, gc, w.Mc, w.G1c, dev_status);
+    GS_TRY_LAUNCH();
+    bin_groups<<<(unsigned)ceil_div(gc.tiles, (int64_t)256), 256, 0, stream>>>(gc, w.G1c, w.ctotal);
+    GS_TRY_LAUNCH();
+    // at most as many entry x super-tile pairs as pairs: within the capacity
+    // whenever the pairs are
+    bin_starts<<<1, SCAN_THREADS, 0, stream>>>(gc, w.ctotal, w.cstart, pair_capacity, w.c_count, w.c_count + 1,
+                                               dev_status);
+    GS_TRY_LAUNCH();
+    bin_offsets<<<(unsigned)ceil_div(gc.n_g * gc.tiles, (int64_t)256), 256, 0, stream>>>(
+        gc, cams, n_views, w.G1c, w.cstart, w.ctotal, w.c_count + 1, w.Mc, nullptr);
+    GS_TRY_LAUNCH();
+    if (coarse_scatter_wide(gc.max_vt))
+        bin_scatter<uint32_t, 16><<<n_cchunks, SC_THREADS, ScatterMask<uint32_t, 16>::bytes_per_tile * gc.max_vt,
+                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.crect);
     else
-        bin_scatter<uint32_t, 1><<<n_chunks, SC_THREADS, ScatterMask<uint32_t, 1>::bytes_per_tile * mvt, stream>>>(
-            w.srect, order, cams, g, w.M, w.sort_count, vals);
+        bin_scatter<uint32_t, 4><<<n_cchunks, SC_THREADS, ScatterMask<uint32_t, 4>::bytes_per_tile * gc.max_vt,
+                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.crect);
+    GS_TRY_LAUNCH();
+    // placement work items (segments of the super-tiles' lists)
+    seg_layout<<<1, SCAN_THREADS, 0, stream>>>(gc.tiles, w.ctotal, w.sort_count, w.seg_base);
+    GS_TRY_LAUNCH();
+    seg_fill<<<(unsigned)ceil_div(gc.tiles, (int64_t)256), 256, 0, stream>>>(gc.tiles, w.seg_base, w.item_ct);
+    GS_TRY_LAUNCH();
+    const int64_t items_cap = fine_items_cap(pair_capacity, gc.tiles);
+    const int64_t resident = (int64_t)device_sm_count() * 8;  // blocks of 8 warps
+    const int64_t want = ceil_div(items_cap, (int64_t)(FP_THREADS / 32));
+    const unsigned fp_blocks = (unsigned)(want < resident ? (want > 0 ? want : 1) : resident);
+    fine_pass<false><<<fp_blocks, FP_THREADS, 0, stream>>>(w.crect, w.cgid, cams, n_views, gc, w.cstart, w.ctotal,
+                                                           w.seg_base, w.item_ct, w.run_of, vals, total_tiles,
+                                                           (int)mvt, pair_capacity);
+    GS_TRY_LAUNCH();
+    fine_prefix<<<(unsigned)ceil_div(gc.tiles * 32, (int64_t)256), 256, 0, stream>>>(
+        cams, n_views, gc, total_tiles, (int)mvt, w.tile_start, w.tile_total, w.seg_base, w.sort_count, w.run_of,
+        reinterpret_cast<uint2 *>(ranges));
+    GS_TRY_LAUNCH();
+    fine_pass<true><<<fp_blocks, FP_THREADS, 0, stream>>>(w.crect, w.cgid, cams, n_views, gc, w.cstart, w.ctotal,
+                                                          w.seg_base, w.item_ct, w.run_of, vals, total_tiles,
+                                                          (int)mvt, pair_capacity);
     GS_TRY_LAUNCH();
     if (keys) {
         keys64_kernel<<<(unsigned)total_tiles, 128, 0, stream>>>(reinterpret_cast<const uint2 *>(ranges), vals,
@@ -951,7 +1332,8 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_projected *proj, const gs_came
     if (n < 0 || n_views <= 0 || pair_capacity < 0 || total_tiles <= 0) return GS_ERR_INVALID_ARG;
     if (n * n_views > kNoAllocMaxEntries) return GS_ERR_WORKSPACE;
     if (total_tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
-    if (bin_ws_layout(n, n_views, total_tiles, nullptr, nullptr) > kNoAllocBytes) return GS_ERR_WORKSPACE;
+    if (bin_ws_layout(n, n_views, total_tiles, pair_capacity, nullptr, nullptr) > kNoAllocBytes)
+        return GS_ERR_WORKSPACE;
     const int dev = cached_device_index();
     if (dev < 0) return GS_ERR_UNSUPPORTED;
     // Host code cannot use the array's name as a device address: look the

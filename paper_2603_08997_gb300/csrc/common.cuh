@@ -87,11 +87,17 @@ __device__ __forceinline__ void adam_update(float &p, float &m, float &v, float 
 // -expm1(t log1p(beta - 1)): beta - 1 is exact for beta in [0.5, 1), and both
 // functions keep the small differences (t = 1, beta2 = 0.999) to a few ulp,
 // without the long double-precision pow chain a block would wait on.
-__device__ __forceinline__ void adam_scalars(const gs_adam_config &cfg, int64_t executed, float *lr_t, float *ibc2) {
+// With cfg.lr_scale_den > 0 and a step-gate word, the learning rates of this
+// step are multiplied by *do_step / lr_scale_den (the gate writes the number
+// of views it opened there: a batched step then moves by each opened view's
+// share of the batch).
+__device__ __forceinline__ void adam_scalars(const gs_adam_config &cfg, int64_t executed, const int32_t *do_step,
+                                             float *lr_t, float *ibc2) {
     const float t = (float)(executed + 1);
     const float bc1 = -expm1f(t * log1pf(cfg.beta1 - 1.f));
     const float bc2 = -expm1f(t * log1pf(cfg.beta2 - 1.f));
-    for (int k = 0; k < 6; ++k) lr_t[k] = cfg.lr[k] / bc1;
+    const float scale = (cfg.lr_scale_den > 0 && do_step) ? (float)*do_step / (float)cfg.lr_scale_den : 1.f;
+    for (int k = 0; k < 6; ++k) lr_t[k] = cfg.lr[k] * scale / bc1;
     *ibc2 = 1.f / sqrtf(bc2);
 }
 

@@ -105,7 +105,7 @@ __global__ void gate_decide_kernel(void *st, const int32_t *view_ids, const floa
         }
         if (g) h->b += 1;
         g_out[k] = (uint8_t)g;
-        any |= g;
+        any += g;  // the number of opened views
     }
     if (any_out) *any_out = any;
     if (has_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);

@@ -195,9 +195,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                 if (ae.alpha < amin) continue;
                 contrib = true;
                 const float om = __fsub_rn(1.f, ae.alpha);
-                // correctly rounded (unbiased): T is rebuilt through up to a batch of
-                // these factors, so a biased approximate reciprocal would drift
-                const float inv = __frcp_rn(om);  // 1 - alpha >= 0.01
+                const float inv = rcp_approx(om);  // 1 - alpha >= 0.01
                 const float Tk = T[k] * inv;
                 const float wgt = ae.alpha * Tk;
                 const float c0 = sb.z, c1 = sb.w, c2 = sc.x;
@@ -328,7 +326,7 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     __shared__ gs_camera s_cams[kStagedViews];
     if constexpr (MODE == 2) {
         if (af.do_step && *af.do_step == 0) return;  // the same for every block
-        if (threadIdx.x == 0) adam_scalars(af.cfg, *af.step, s_lr, &s_ibc2);
+        if (threadIdx.x == 0) adam_scalars(af.cfg, *af.step, af.do_step, s_lr, &s_ibc2);
     }
     if (threadIdx.x < n_views && threadIdx.x < kStagedViews) s_cams[threadIdx.x] = cams[threadIdx.x];
     __syncthreads();

@@ -56,7 +56,8 @@ class gs_fwd_saved(C.Structure):
 
 
 class gs_adam_config(C.Structure):
-    _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+    _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("lr_scale_den", C.c_int32)]
 
 
 class gs_launch_shape(C.Structure):

@@ -36,11 +36,13 @@ class RefinementLoop:
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
                  fused: bool = True, views_per_step: int = 1, log_capacity: int = 0,
-                 adam: AdamState | None = None, stats: DensityStats | None = None):
+                 adam: AdamState | None = None, stats: DensityStats | None = None, batch_lr_scale: bool = False):
         """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
         [3, H_v, W_v] tensors, one per training view.  adam: an existing
         optimizer state of `model` to continue (else a fresh one).  stats: the
-        densification statistic, accumulated after every backward pass."""
+        densification statistic, accumulated after every backward pass.
+        batch_lr_scale (views_per_step > 1): each step's learning rates are
+        scaled by the fraction of the iteration's views the gate opened."""
         import copy
         self.model = model
         self.fused = bool(fused)
@@ -78,6 +80,8 @@ class RefinementLoop:
         else:
             self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
         self.stats = stats
+        self.lr_scale = bool(batch_lr_scale) and self.B > 1 and self.gated
+        self.adam.cfg.lr_scale_den = self.B if self.lr_scale else 0
         self.params = model.c_params()
         self.grads = model.c_grads(self.adam.grad)
         self.stream = torch.cuda.Stream(device=dev)
@@ -108,12 +112,14 @@ class RefinementLoop:
         r = self.renderer
         gate = self.g if (predicated or self.B > 1) and self.gated else None
         r.loss_backward(self.targets, self.target_offsets, self.view_ids, stream=s)
+        # the step-gate word (number of opened views) is passed when the step
+        # is predicated on it, or when it scales the step
+        do_step = self.any if (predicated or self.lr_scale) else None
         if self.fused:
-            r.backward_adam(self.model, self.adam, view_gate=gate, do_step=self.any if predicated else None,
-                            norms2=self.norms2, stream=s)
+            r.backward_adam(self.model, self.adam, view_gate=gate, do_step=do_step, norms2=self.norms2, stream=s)
         else:
             r.backward(self.params, self.grads, view_gate=gate, accumulate=False, stream=s)
-            self.adam.step(do_step=self.any if predicated else None, norms2=self.norms2, stream=s)
+            self.adam.step(do_step=do_step, norms2=self.norms2, stream=s)
         if self.stats is not None:  # the 2D gradients are still in the workspace
             self.stats.accumulate(r, view_gate=self.g if (predicated or self.B > 1) and self.gated else None,
                                   stream=s)

@@ -101,3 +101,23 @@ def test_nonfinite_loss_reported_and_skipped():
     g, st, status = _run_gpu(cfg, views, losses)
     assert status == gsr.GS_ERR_NONFINITE
     assert g[2] == 0 and st["errors"] == 1 and st["t"] == 3
+
+
+def test_decide_reports_the_number_of_opened_views():
+    """skipgs_gate_decide writes the number of g = 1 into dev_any (the
+    batched step's learning-rate scale reads it)."""
+    from paper_2603_08997_gb300 import raster
+    gpu_util.lib()
+    gate = raster.Gate(8, W=0)
+    ids = torch.arange(4, dtype=torch.int32, device="cuda")
+    g = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    any_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    losses = torch.tensor([1.0, 1.0, 1.0, 1.0], device="cuda")
+    gate.decide(ids, losses, g, any_out)  # no history: every view opens
+    gate.update(ids, losses)
+    torch.cuda.synchronize()
+    assert int(any_out.item()) == 4 == int(g.sum().item())
+    losses2 = torch.tensor([2.0, 0.5, 3.0, 0.25], device="cuda")  # two above their EMA, two below
+    gate.decide(ids, losses2, g, any_out)
+    torch.cuda.synchronize()
+    assert int(any_out.item()) == int(g.sum().item())

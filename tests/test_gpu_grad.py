@@ -354,3 +354,43 @@ def test_adam_norms_telemetry():
     want = [float((g * g).sum()), float(((model.flat.double() - p0) ** 2).sum())]
     got = norms.cpu().numpy()
     assert abs(got[0] - want[0]) <= 1e-5 * want[0] and abs(got[1] - want[1]) <= 1e-4 * want[1]
+
+
+def test_adam_learning_rate_scaled_by_opened_views():
+    """gs_adam_config.lr_scale_den: with the step-gate word holding the number
+    of opened views k, the step's learning rates are lr * k / den (against
+    the FP64 oracle with the scaled rates); k = 0 still skips the step."""
+    gpu_util.lib()
+    scene, _ = synth.scene_tiny(50, seed=3, sh_degree=2)
+    model = raster.GaussianModel.from_scene(scene)
+    cfg = AdamConfig()
+    adam = raster.AdamState(model, lr=cfg.lrs(), beta1=cfg.beta1, beta2=cfg.beta2, eps=cfg.eps)
+    adam.cfg.lr_scale_den = 8
+    n, K = scene.n, scene.sh.shape[1]
+    rng = np.random.default_rng(8)
+    p = {k: getattr(scene, k).astype(np.float64).ravel() for k in GROUPS}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    vv = {k: np.zeros_like(v) for k, v in p.items()}
+    lr = {"means": cfg.lr_means, "log_scales": cfg.lr_log_scales, "quats": cfg.lr_quats,
+          "opacity_logit": cfg.lr_opacity}
+    sh_lr = np.where((np.arange(3 * K * n) % (3 * K)) < 3, cfg.lr_sh_dc, cfg.lr_sh_rest)
+    do = torch.zeros(1, dtype=torch.int32, device="cuda")
+    step = 0
+    for k_open in (3, 0, 8, 1):
+        g = {k: rng.normal(size=v.shape) for k, v in p.items()}
+        gv = model.group_views(adam.grad)
+        for k in GROUPS:
+            gv[k].copy_(torch.from_numpy(g[k].astype(np.float32).reshape(gv[k].shape)))
+        do.fill_(k_open)
+        adam.step(do_step=do, zero_grad=True)
+        if k_open:
+            for k in GROUPS:
+                gk = g[k].astype(np.float32).astype(np.float64)
+                rate = (sh_lr if k == "sh" else lr[k]) * (k_open / 8.0)
+                p[k], m[k], vv[k], _ = adam_step(p[k], gk, m[k], vv[k], step, rate, cfg)
+            step += 1
+    torch.cuda.synchronize()
+    assert int(adam.step_count.item()) == step == 3
+    got = gpu_util.gpu_grads(model, model.flat)
+    for k in GROUPS:
+        np.testing.assert_allclose(got[k].ravel(), p[k], rtol=2e-6, atol=1e-7)
