@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--c4", action="store_true",
                     help="batched workload instead of the default line: 8 ring views per iteration at mixed "
                          "resolutions (640x360 .. 1600x1063), launch shape autotuned; prints its own JSON line")
+    ap.add_argument("--c4-slots", action="store_true",
+                    help="with --c4: every slot a grid of the largest view's size, a block per tile (the "
+                         "non-persistent form, for comparison)")
     ap.add_argument("--rho-sweep", action="store_true",
                     help="NEXT-1: gated loop for rho_lo in (no budget, 0.3, 0.5, 0.7, 0.9) against the "
                          "always-backward loop; prints its own JSON line")
@@ -108,6 +111,11 @@ def run_c4(args) -> None:
     cands = tuple((t, b, 1, 2) for t in (8, 16, 32) for b in (128, 256))
     st, tune_ms = autotune.autotune(model, cams, targets, candidates=cands, views_per_step=B, reps=2,
                                     pair_capacity=cap)
+    # the batch as one persistent launch per compositing stage: resident
+    # blocks take (view, tile) items longest-first from a device queue, each
+    # view with its own tile grid
+    import dataclasses
+    st = dataclasses.replace(st, persistent=not args.c4_slots)
     pre = RefinementLoop(model, cams, targets, synth.pre_sequence(pre_iters * B, args.views), st, gated=False,
                          pair_capacity=cap, views_per_step=B)
     pre.capture()
@@ -119,7 +127,7 @@ def run_c4(args) -> None:
 
     def timed(gated: bool, lr_scale: bool = False):
         loop = RefinementLoop(model, cams, targets, seq, st, gated=gated, pair_capacity=cap, views_per_step=B,
-                              batch_lr_scale=lr_scale)
+                              batch_lr_scale=lr_scale, compact_tiles=not args.c4_slots)
         loop.restore(init)
         loop.capture()
         for _ in range(args.warmup):
@@ -146,6 +154,8 @@ def run_c4(args) -> None:
         "unscaled_step": {"iters_per_s": K / (ms_g1 * 1e-3), "speedup": ms_full / ms_g1,
                           "rho_cum": gs1["b"] / max(gs1["t"], 1), "final_loss": loss_g1,
                           "final_loss_rel_diff": (loss_g1 - loss_full) / loss_full},
+        "launch": "block per tile, largest-view slots" if args.c4_slots else
+                  "persistent: resident blocks take (view, tile) items longest-first from a queue; per-view tile grids",
         "autotuned": {"tile": st.tile, "batch": st.batch, "pixels_per_thread_fwd": st.pixels_per_thread_fwd,
                       "pixels_per_thread_bwd": st.pixels_per_thread,
                       "candidates_ms": {f"{t}/{b}/{pf}/{pb}": v for (t, b, pf, pb), v in tune_ms.items()}},

@@ -141,6 +141,10 @@ typedef struct {
     const uint32_t *tile_order;  /* [total_tiles] visiting order of the tiles (gs_tile_order), or NULL for
                                     ascending tile id; a permutation of 0..total_tiles-1; results do not
                                     depend on it */
+    uint32_t *queue;             /* NULL: one block per tile; else a device word (4-byte aligned) through
+                                    which a persistent grid of resident blocks takes the tiles in
+                                    tile_order (reset by each compositing call, so the calls that share it
+                                    must be ordered on one stream); results do not depend on it */
 } gs_fwd_saved;
 
 /* --------------------------------------------------------------- layout */
@@ -455,11 +459,15 @@ gs_status gs_graph_destroy(gs_graph graph);
 /* Device-side view selection for graph replay: view_ids[k] =
  * seq[(*iter * n + k) mod seq_len] for k < n, then *iter += 1 (int64, device).
  * If pose_src and slots are given, slot k takes the pose, intrinsics, size and
- * near plane of pose_src[view_ids[k]] and keeps its own tile_offset and
- * pix_offset, so a captured step renders the selected views; a view larger
- * than the slot's capacity is the caller's error. */
+ * near plane of pose_src[view_ids[k]] and keeps its own pix_offset, so a
+ * captured step renders the selected views; a view larger than the slot's
+ * capacity is the caller's error.  tile = 0: each slot keeps its tile_offset
+ * (every slot a grid of the largest view's size); tile = 8, 16 or 32: each
+ * slot's tile_offset is recomputed so the selected views' own tile grids
+ * follow one another from slot 0's offset (the slots' total tile count still
+ * bounds them; the tiles past the last view's grid render nothing). */
 gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
-                          const gs_camera *pose_src, gs_camera *slots, cudaStream_t stream);
+                          const gs_camera *pose_src, gs_camera *slots, int32_t tile, cudaStream_t stream);
 
 /* Per-iteration log for graph replay: with k = (*iter - 1) mod cap (iter as
  * advanced by gs_select_views), writes loss_log[k n + j] = loss[j] and

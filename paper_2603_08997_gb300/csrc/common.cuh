@@ -113,6 +113,25 @@ __device__ inline int view_of_tile(const gs_camera *cams, int n_views, int64_t t
     return v;
 }
 
+// Work items of the compositing kernels (tiles, visited through the
+// longest-first tile order).  Without a queue each block takes the item of
+// its block index; with a queue (a device word, zero at launch) the kernel
+// runs persistently: a grid of resident blocks, each taking the next item
+// from the queue until none is left.  Called by every thread of the block.
+__device__ __forceinline__ uint32_t first_item(uint32_t *queue, uint32_t *s_item) {
+    if (!queue) return blockIdx.x;
+    if (threadIdx.x == 0) *s_item = atomicAdd(queue, 1u);
+    __syncthreads();
+    return *s_item;
+}
+__device__ __forceinline__ uint32_t next_item(uint32_t *queue, uint32_t *s_item) {
+    if (!queue) return 0xffffffffu;
+    __syncthreads();  // every thread has read the previous item
+    if (threadIdx.x == 0) *s_item = atomicAdd(queue, 1u);
+    __syncthreads();
+    return *s_item;
+}
+
 // Eq. (alpha) at one pixel, evaluated through the conic's Cholesky factor U
 // (Q = U^T U): dp^T Q dp = |U dp|^2 with z0 = u00 dx + u01 dy, z1 = u11 dy.
 // A sum of squares keeps the float32 rounding error near eps * sqrt(cond(Q)).

@@ -38,9 +38,10 @@ int64_t count_kernel_nodes(cudaGraph_t g) {
 }
 
 __global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t *iter, int n, int32_t *view_ids,
-                                    const gs_camera *pose_src, gs_camera *slots) {
+                                    const gs_camera *pose_src, gs_camera *slots, int tile) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int64_t it = *iter;
+    int64_t next_tile = slots ? slots[0].tile_offset : 0;  // compact layout: from the first slot's offset
     for (int k = 0; k < n; ++k) {
         const int64_t idx = (it * n + k) % seq_len;
         const int32_t vid = seq[idx];
@@ -57,6 +58,10 @@ __global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t
             dst.width = src.width;
             dst.height = src.height;
             dst.znear = src.znear;
+            if (tile > 0) {  // each view its own tile grid, packed after the previous slot's
+                dst.tile_offset = (int32_t)next_tile;
+                next_tile += (int64_t)((src.width + tile - 1) / tile) * ((src.height + tile - 1) / tile);
+            }
         }
     }
     *iter = it + 1;
@@ -181,9 +186,10 @@ gs_status gs_graph_destroy(gs_graph graph) {
 }
 
 gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
-                          const gs_camera *pose_src, gs_camera *slots, cudaStream_t stream) {
+                          const gs_camera *pose_src, gs_camera *slots, int32_t tile, cudaStream_t stream) {
     if (!seq || seq_len <= 0 || !iter || n <= 0 || !view_ids) return GS_ERR_INVALID_ARG;
-    select_views_kernel<<<1, 32, 0, stream>>>(seq, seq_len, iter, n, view_ids, pose_src, slots);
+    if (tile != 0 && tile != 8 && tile != 16 && tile != 32) return GS_ERR_INVALID_ARG;
+    select_views_kernel<<<1, 32, 0, stream>>>(seq, seq_len, iter, n, view_ids, pose_src, slots, tile);
     GS_TRY_LAUNCH();
     return GS_OK;
 }

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     const gs_camera *__restrict__ cams, int n_views, gs_raster_config cfg, const float *__restrict__ T_final,
     const int32_t *__restrict__ n_last, const float *__restrict__ ckpt, int64_t ckpt_slots,
     const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d,
-    const uint32_t *__restrict__ tile_order) {
+    const uint32_t *__restrict__ tile_order, uint32_t *queue, int64_t total_tiles) {
     constexpr int NT = TILE * TILE;
     constexpr int NTH = TILE * TILE / PPT;
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
@@ -84,9 +84,11 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     __shared__ float s_acc[BATCH][9];
     __shared__ int s_max;
-    const int64_t tile = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
+    __shared__ uint32_t s_item;
+    for (uint32_t item = first_item(queue, &s_item); item < (uint64_t)total_tiles; item = next_item(queue, &s_item)) {
+    const int64_t tile = tile_order ? (int64_t)tile_order[item] : (int64_t)item;
     const int v = view_of_tile(cams, n_views, tile);
-    if (view_gate && !view_gate[v]) return;
+    if (view_gate && !view_gate[v]) continue;  // uniform per block
     const gs_camera &cam = cams[v];
     const int tiles_x = (cam.width + TILE - 1) / TILE;
     const int64_t lt = tile - cam.tile_offset;
@@ -244,6 +246,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
             atomicAdd(&dst[2].x, a[8]);
         }
     }
+    }  // items
 }
 
 // Optimizer fused into the projection adjoint: the parameters live in one flat
@@ -611,20 +614,38 @@ template <int TILE, int PPT>
 gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
                      const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
                      const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate, float4 *g2d) {
-    const dim3 grid((unsigned)total_tiles);
+    dim3 grid((unsigned)total_tiles);
     constexpr int NTH = TILE * TILE / PPT;
+    if (s.queue) {  // persistent: the resident blocks (cached per device and staging batch size)
+        static int resident[3][kMaxDevices] = {};
+        const int bi = batch == 64 ? 0 : (batch == 128 ? 1 : 2);
+        const int dev = cached_device_index();
+        if (dev < 0) return GS_ERR_UNSUPPORTED;
+        if (resident[bi][dev] <= 0) {
+            int per_sm = 0;
+            if (batch == 64)
+                GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TILE, 64, PPT>, NTH, 0));
+            else if (batch == 128)
+                GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TILE, 128, PPT>, NTH, 0));
+            else
+                GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TILE, 256, PPT>, NTH, 0));
+            resident[bi][dev] = (per_sm > 0 ? per_sm : 1) * device_sm_count();
+        }
+        if ((int64_t)resident[bi][dev] < total_tiles) grid = dim3((unsigned)resident[bi][dev]);
+        GS_TRY(cudaMemsetAsync(s.queue, 0, sizeof(uint32_t), stream));
+    }
     switch (batch) {
         case 64:
             render_bwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                      s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order);
+                                                                      s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order, s.queue, total_tiles);
             break;
         case 128:
             render_bwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order);
+                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order, s.queue, total_tiles);
             break;
         case 256:
             render_bwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order);
+                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order, s.queue, total_tiles);
             break;
         default:
             return GS_ERR_UNSUPPORTED;

@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
                                                                        float *__restrict__ T_final,
                                                                        int32_t *__restrict__ n_last,
                                                                        float *__restrict__ ckpt, int64_t ckpt_slots,
-                                                                       const uint32_t *__restrict__ tile_order) {
+                                                                       const uint32_t *__restrict__ tile_order,
+                                                                       uint32_t *queue, int64_t total_tiles) {
     constexpr int NT = TILE * TILE;        // pixels per tile (checkpoint slot size)
     constexpr int NTH = TILE * TILE / PPT; // threads
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
@@ -36,7 +37,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
     __shared__ float4 s_b[2][BATCH];
     __shared__ float4 s_c[2][BATCH];
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
-    const int64_t tile = tile_order ? (int64_t)tile_order[blockIdx.x] : (int64_t)blockIdx.x;
+    __shared__ uint32_t s_item;
+    for (uint32_t item = first_item(queue, &s_item); item < (uint64_t)total_tiles; item = next_item(queue, &s_item)) {
+    const int64_t tile = tile_order ? (int64_t)tile_order[item] : (int64_t)item;
     const int v = view_of_tile(cams, n_views, tile);
     const gs_camera &cam = cams[v];
     const int tiles_x = (cam.width + TILE - 1) / TILE;
@@ -173,26 +176,54 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
         T_final[cam.pix_offset + pix] = T[k];
         n_last[cam.pix_offset + pix] = last[k];
     }
+    }  // items
+}
+
+// Grid of a compositing kernel: a block per tile, or (persistent, with a
+// queue) the blocks resident on the device at once (cached per device).
+template <typename K>
+gs_status item_grid(K kernel, int threads, int64_t total_tiles, bool persistent, int *cache, dim3 &grid) {
+    grid = dim3((unsigned)total_tiles);
+    if (!persistent) return GS_OK;
+    const int dev = cached_device_index();
+    if (dev < 0) return GS_ERR_UNSUPPORTED;
+    if (cache[dev] <= 0) {
+        int per_sm = 0;
+        GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
+        cache[dev] = (per_sm > 0 ? per_sm : 1) * device_sm_count();
+    }
+    if ((int64_t)cache[dev] < total_tiles) grid = dim3((unsigned)cache[dev]);
+    return GS_OK;
 }
 
 template <int TILE, int PPT>
 gs_status launch_fwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
                      const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
                      const gs_raster_config &cfg, float *image, gs_fwd_saved s) {
-    const dim3 grid((unsigned)total_tiles);
+    dim3 grid;
     constexpr int NTH = TILE * TILE / PPT;
+    static int resident[3][kMaxDevices] = {};  // per staging batch size
+    {
+        const int bi = batch == 64 ? 0 : (batch == 128 ? 1 : 2);
+        gs_status st = GS_OK;
+        if (batch == 64) st = item_grid(render_fwd_kernel<TILE, 64, PPT>, NTH, total_tiles, s.queue, resident[bi], grid);
+        else if (batch == 128) st = item_grid(render_fwd_kernel<TILE, 128, PPT>, NTH, total_tiles, s.queue, resident[bi], grid);
+        else st = item_grid(render_fwd_kernel<TILE, 256, PPT>, NTH, total_tiles, s.queue, resident[bi], grid);
+        if (st != GS_OK) return st;
+    }
+    if (s.queue) GS_TRY(cudaMemsetAsync(s.queue, 0, sizeof(uint32_t), stream));
     switch (batch) {
         case 64:
             render_fwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                      s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order);
+                                                                      s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order, s.queue, total_tiles);
             break;
         case 128:
             render_fwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order);
+                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order, s.queue, total_tiles);
             break;
         case 256:
             render_fwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order);
+                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order, s.queue, total_tiles);
             break;
         default:
             return GS_ERR_UNSUPPORTED;

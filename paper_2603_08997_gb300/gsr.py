@@ -52,7 +52,7 @@ class gs_projected(C.Structure):
 
 class gs_fwd_saved(C.Structure):
     _fields_ = [("T_final", C.c_void_p), ("n_last", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_slots", C.c_int64),
-                ("tile_order", C.c_void_p)]
+                ("tile_order", C.c_void_p), ("queue", C.c_void_p)]
 
 
 class gs_adam_config(C.Structure):
@@ -128,7 +128,7 @@ _PROTOS = {
     "gs_graph_launch": (C.c_int, [C.c_void_p, _S]),
     "gs_graph_kernel_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "gs_graph_destroy": (C.c_int, [C.c_void_p]),
-    "gs_select_views": (C.c_int, [_P, _I64, _P, _I32, _P, _P, _P, _S]),
+    "gs_select_views": (C.c_int, [_P, _I64, _P, _I32, _P, _P, _P, _I32, _S]),
     "gs_raster_census": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                    _P, _P, _S]),
     "gs_atomic_probe": (C.c_int, [_P, _I64, _I64, _S]),

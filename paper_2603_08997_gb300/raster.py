@@ -32,6 +32,7 @@ class RasterSettings:
     pixels_per_thread: int = 2      # raster adjoint
     pixels_per_thread_fwd: int = 1  # forward compositing
     longest_tiles_first: bool = True  # launch tiles by descending list length (gs_tile_order)
+    persistent: bool = False  # compositing kernels as a persistent grid taking tiles from a device queue
 
     def struct(self, sh_degree: int) -> gsr.gs_raster_config:
         c = gsr.gs_raster_config()
@@ -156,6 +157,7 @@ class Renderer:
         self.keys = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev) if keep_keys else None
         self.ranges = torch.empty(2 * T, dtype=torch.int32, device=dev)
         self.tile_order = torch.empty(T, dtype=torch.int32, device=dev) if self.s.longest_tiles_first else None
+        self.queue = torch.zeros(1, dtype=torch.int32, device=dev) if self.s.persistent else None
         self.pair_count = torch.zeros(1, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.image = torch.empty(3 * P, dtype=torch.float32, device=dev)
@@ -186,6 +188,7 @@ class Renderer:
         s.T_final, s.n_last, s.ckpt, s.ckpt_slots = (self.T_final.data_ptr(), self.n_last.data_ptr(),
                                                      self.ckpt.data_ptr(), self.ckpt_slots)
         s.tile_order = self.tile_order.data_ptr() if self.tile_order is not None else None
+        s.queue = self.queue.data_ptr() if self.queue is not None else None
         return s
 
     # --- pipeline steps (each one C-ABI call)

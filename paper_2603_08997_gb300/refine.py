@@ -36,13 +36,17 @@ class RefinementLoop:
                  settings: RasterSettings | None = None, gated: bool = True, W: int = 500, beta: float = 0.95,
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
                  fused: bool = True, views_per_step: int = 1, log_capacity: int = 0,
-                 adam: AdamState | None = None, stats: DensityStats | None = None, batch_lr_scale: bool = False):
+                 adam: AdamState | None = None, stats: DensityStats | None = None, batch_lr_scale: bool = False,
+                 compact_tiles: bool = False):
         """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
         [3, H_v, W_v] tensors, one per training view.  adam: an existing
         optimizer state of `model` to continue (else a fresh one).  stats: the
         densification statistic, accumulated after every backward pass.
         batch_lr_scale (views_per_step > 1): each step's learning rates are
-        scaled by the fraction of the iteration's views the gate opened."""
+        scaled by the fraction of the iteration's views the gate opened.
+        compact_tiles: the selected views' own tile grids are packed one after
+        another (gs_select_views with the tile size) instead of each slot
+        holding a grid of the largest view's size."""
         import copy
         self.model = model
         self.fused = bool(fused)
@@ -80,6 +84,7 @@ class RefinementLoop:
         else:
             self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
         self.stats = stats
+        self.select_tile = int(self.s.tile) if compact_tiles else 0
         self.lr_scale = bool(batch_lr_scale) and self.B > 1 and self.gated
         self.adam.cfg.lr_scale_den = self.B if self.lr_scale else 0
         self.params = model.c_params()
@@ -101,7 +106,8 @@ class RefinementLoop:
     # ---- pieces of one iteration
     def _front(self, s):
         gsr.call("gs_select_views", gsr.ptr(self.seq), int(self.seq.numel()), gsr.ptr(self.iter), self.B,
-                 gsr.ptr(self.view_ids), gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), gsr.stream_handle(s))
+                 gsr.ptr(self.view_ids), gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), self.select_tile,
+                 gsr.stream_handle(s))
         self.renderer.forward(self.params, s)
         self.renderer.compute_loss(self.targets, self.target_offsets, self.view_ids, with_grad=False, stream=s)
 
@@ -233,7 +239,7 @@ class RefinementLoop:
         with torch.cuda.stream(s):
             for k in range(0, n, self.B):
                 gsr.call("gs_select_views", gsr.ptr(seq), n, gsr.ptr(it), self.B, gsr.ptr(vid),
-                         gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), gsr.stream_handle(s))
+                         gsr.ptr(self.poses.dev), gsr.ptr(self.slot.dev), self.select_tile, gsr.stream_handle(s))
                 self.renderer.forward(self.params, s)
                 self.renderer.compute_loss(self.targets, self.target_offsets, vid, stream=s)
                 out[k:k + self.B].copy_(self.renderer.loss)

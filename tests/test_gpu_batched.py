@@ -32,26 +32,31 @@ def _single(scene, cam, target, dl=None):
     return r.image_of(0).cpu().numpy(), float(r.loss[0].item()), grad.cpu().numpy()
 
 
-def _slots(scene, cams, order):
+def _slots(scene, cams, order, compact=False, persistent=False):
     """A renderer over len(order) slots of the largest size, filled on the
-    device with the cameras of `order`."""
+    device with the cameras of `order` (compact: the views' own tile grids
+    packed one after another; persistent: compositing through a tile queue)."""
     import copy
     wmax, hmax = max(c.width for c in cams), max(c.height for c in cams)
     slot = copy.copy(cams[0])
     slot.width, slot.height = wmax, hmax
     slots = raster.Views([slot] * len(order), 16)
     poses = raster.Views(cams, 16)
-    r = raster.Renderer(scene.n, scene.sh_degree, slots)
+    r = raster.Renderer(scene.n, scene.sh_degree, slots, raster.RasterSettings(persistent=persistent))
     r.sizes_on_device = True
     seq = torch.tensor(order, dtype=torch.int32, device="cuda")
     it = torch.zeros(1, dtype=torch.int64, device="cuda")
     vid = torch.zeros(len(order), dtype=torch.int32, device="cuda")
     gsr.call("gs_select_views", gsr.ptr(seq), len(order), gsr.ptr(it), len(order), gsr.ptr(vid),
-             gsr.ptr(poses.dev), gsr.ptr(slots.dev), None)
+             gsr.ptr(poses.dev), gsr.ptr(slots.dev), 16 if compact else 0, None)
     return r, vid
 
 
-def test_batch_matches_views_alone():
+@pytest.mark.parametrize("compact,persistent", [(False, False), (True, True), (True, False), (False, True)])
+def test_batch_matches_views_alone(compact, persistent):
+    """Every view of a batch renders bit-identically to the view alone, with
+    the slots' tile grids sized for the largest view or packed per view, and
+    with one block per tile or a persistent grid taking tiles from a queue."""
     gpu_util.lib()
     scene, _, _ = synth.case_c1(n=1500)
     cams = _cams()
@@ -59,7 +64,7 @@ def test_batch_matches_views_alone():
     targets = [rng.uniform(0, 1, (3, h, w)).astype(np.float32) for w, h in SIZES]
     alone = [_single(scene, c, t) for c, t in zip(cams, targets)]
     order = [2, 0, 1]
-    r, vid = _slots(scene, cams, order)
+    r, vid = _slots(scene, cams, order, compact, persistent)
     flat_t = torch.from_numpy(np.concatenate([t.ravel() for t in targets])).cuda()
     offs = torch.tensor(np.concatenate([[0], np.cumsum([t.size for t in targets])[:-1]]), dtype=torch.int64,
                         device="cuda")
@@ -83,7 +88,8 @@ def test_batch_matches_views_alone():
 
 def test_batch_slot_against_oracle():
     """One slot of a batch (a view chosen on the device into a slot larger than
-    itself, between two other views) against the FP64 oracle directly: image
+    itself, between two other views; compact tile grids, persistent
+    compositing) against the FP64 oracle directly: image
     within 1e-5, loss within 1e-5, and the gradient of that slot alone (the
     other slots' gates closed) within the gradient bar."""
     import oracle
@@ -93,7 +99,7 @@ def test_batch_slot_against_oracle():
     rng = np.random.default_rng(6)
     targets = [rng.uniform(0, 1, (3, h, w)).astype(np.float32) for w, h in SIZES]
     order = [2, 1, 0]
-    r, vid = _slots(scene, cams, order)
+    r, vid = _slots(scene, cams, order, compact=True, persistent=True)
     flat_t = torch.from_numpy(np.concatenate([t.ravel() for t in targets])).cuda()
     offs = torch.tensor(np.concatenate([[0], np.cumsum([t.size for t in targets])[:-1]]), dtype=torch.int64,
                         device="cuda")
@@ -152,6 +158,33 @@ def test_batched_loop_runs_and_gates():
             assert np.isfinite(model.flat.cpu().numpy()).all()
         loop.close()
     assert gpu_util.rel_err(one[1], one[0]) < 1e-6
+
+
+def test_batched_loop_compact_persistent_equals_default():
+    """The batched loop with per-view packed tile grids and persistent
+    compositing takes the same decisions and steps as with largest-view slots
+    and a block per tile (parameters equal up to the order of float atomics)."""
+    gpu_util.lib()
+    scene, _, _ = synth.case_c1(n=1500)
+    cams = _cams()
+    rng = np.random.default_rng(5)
+    targets = [torch.from_numpy(rng.uniform(0, 1, (3, h, w)).astype(np.float32)) for w, h in SIZES]
+    seq = rng.integers(0, 3, size=60).astype(np.int32)
+    out = []
+    for compact in (False, True):
+        model = raster.GaussianModel.from_scene(scene)
+        st = raster.RasterSettings(persistent=compact)
+        loop = RefinementLoop(model, cams, targets, seq, st, gated=True, W=4, views_per_step=3, log_capacity=16,
+                              compact_tiles=compact, batch_lr_scale=True)
+        for _ in range(12):
+            loop.step_graph()
+        torch.cuda.synchronize()
+        assert int(loop.renderer.status.item()) == 0
+        log = loop.read_log(12)
+        out.append((model.flat.cpu().numpy(), log["g"], int(loop.adam.step_count.item())))
+        loop.close()
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+    assert gpu_util.rel_err(out[1][0], out[0][0]) < 1e-6
 
 
 def test_fused_and_unfused_loops_agree():

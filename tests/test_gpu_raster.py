@@ -288,6 +288,36 @@ def test_tile_order_is_a_permutation_by_work_and_changes_nothing():
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("tile,batch,ppt", [(16, 256, 1), (8, 64, 2), (32, 128, 2)])
+def test_persistent_compositing_is_bit_invariant(tile, batch, ppt):
+    """A persistent grid taking tiles from the queue gives the same image,
+    final transmittance, last-contributor counts and checkpoints as a block
+    per tile, and the same 2D gradients up to the order of float atomics."""
+    sizes = [(150, 97), (41, 70)]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(4000, w, h, seed=71 + v) for v, (w, h) in enumerate(sizes)]
+    dev, _ = gpu_util.records(recs, cams, tile)
+    dls = torch.from_numpy(np.concatenate([synth.dl_dimage(w, h, seed=3 + v).ravel()
+                                           for v, (w, h) in enumerate(sizes)])).cuda()
+    out = []
+    for persistent in (False, True):
+        gpu_util.lib()
+        st = raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt, pixels_per_thread_fwd=ppt,
+                                   persistent=persistent)
+        r = raster.Renderer(4000, 0, raster.Views(cams, tile), st)
+        gpu_util.set_projected(r, dev)
+        r.ckpt.fill_(-1.0)
+        r.bin_sort()
+        r.render_fwd()
+        g2d = r.raster_bwd(dL_dimage=dls).clone()
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        out.append([t.clone().cpu() for t in (r.image, r.T_final, r.n_last, r.ckpt)] + [g2d.cpu()])
+    for a, b in zip(out[0][:4], out[1][:4]):
+        assert torch.equal(a, b)
+    assert gpu_util.rel_err(out[1][4].double().numpy(), out[0][4].double().numpy()) < 1e-6
+
+
 def test_bin_sort_from_projection_keys_equals_from_records():
     """gs_bin_sort reading the depth keys and packed rectangles gs_project
     wrote gives the same pairs and ranges as deriving them from the records."""
