@@ -65,7 +65,11 @@ def parse():
                          "always-backward loop; prints its own JSON line")
     ap.add_argument("--densify", action="store_true",
                     help="NEXT-3: densification phase from a sparse start, then gated vs always-backward post phase")
-    ap.add_argument("--densify-iters", type=int, default=3000, help="length of the densification phase")
+    ap.add_argument("--densify-iters", type=int, default=5000, help="length of the densification phase")
+    ap.add_argument("--densify-grad", type=float, default=1e-8,
+                    help="gradient threshold of the density control, pixels (0: the vanilla 2e-4 NDC value in "
+                         "pixels, 3.1e-7 at 1297 px, which lies above the 99th percentile of this synthetic "
+                         "scene's statistic; 1e-8 lies between its 90th and 99th at the first density step)")
     ap.add_argument("--prune", action="store_true",
                     help="NEXT-4: opacity prune + compaction at eps_alpha in (0.005, 0.05, 0.2), then SkipGS")
     ap.add_argument("--c2", action="store_true", help="C2: 200k-Gaussian fwd+bwd+Adam iteration timing")
@@ -324,10 +328,10 @@ def run_densify(args) -> None:
     start = synth.sparse_start(gt, n0, seed=11)
     del gt
     model = raster.GaussianModel.from_scene(start, dev)
-    # thresholds: the vanilla 2e-4 on the NDC-space gradient, in pixels
-    # (d/dpx = d/dndc * 2 / W); 1% of the scene extent (1.1 x the camera
-    # radius 3); opacity 0.005
-    grad_thr = 2e-4 * 2.0 / args.width
+    # thresholds: the gradient threshold from --densify-grad (pixels; the
+    # vanilla 2e-4 on the NDC-space gradient is 2e-4 * 2 / W = 3.1e-7 here);
+    # 1% of the scene extent (1.1 x the camera radius 3); opacity 0.005
+    grad_thr = args.densify_grad if args.densify_grad > 0 else 2e-4 * 2.0 / args.width
     cfg = raster.densify_config(grad_thr=grad_thr, max_scale=0.01 * 1.1 * 3.0, eps_alpha=0.005)
     pre_seq = synth.pre_sequence(args.densify_iters, args.views)
     torch.cuda.synchronize()
@@ -344,8 +348,8 @@ def run_densify(args) -> None:
         "densify": {"start_gaussians": n0, "iterations": args.densify_iters, "interval": 100, "from": 500,
                     "grad_thr_px": grad_thr, "max_scale": 0.033, "eps_alpha": 0.005, "cap": args.n,
                     "wall_s": t_d, "iters_per_s_wall": args.densify_iters / t_d,
-                    "history": [dict(zip(("iteration", "n_before", "clone", "split", "prune", "n_after"), h))
-                                for h in hist]},
+                    "history": [dict(zip(("iteration", "n_before", "clone", "split", "prune", "n_after",
+                                          "grad_p50_p90_p99"), h)) for h in hist]},
         "post": dict(loop_summary(r, iters), iterations=iters, n_gaussians=model.n),
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "sparse perturbed third of the 3M-Gaussian SH3 scene, 200 ring views 1297x840, "

@@ -310,7 +310,8 @@ def densification_phase(model: GaussianModel, train_cams: list, targets, view_se
     graph.  When a step would grow the set beyond max_gaussians it only
     prunes.  Split noise: standard normal draws from a seeded CUDA generator.
     Returns (model, adam, history); history rows are (iteration, n_before,
-    clones, splits, prunes, n_after)."""
+    clones, splits, prunes, n_after, [median, 90th, 99th percentile of the
+    mean gradient norm over the Gaussians seen])."""
     from . import gsr
     st = settings or RasterSettings()
     until = iters if until is None else until
@@ -338,6 +339,11 @@ def densification_phase(model: GaussianModel, train_cams: list, targets, view_se
             it = end
         if end in steps:
             noise = torch.randn((model.n, 2, 3), generator=gen, device=dev, dtype=torch.float32)
+            # the statistic's distribution over the Gaussians seen so far (for the log)
+            seen = stats.denom > 0
+            avg = stats.accum[seen] / stats.denom[seen].float()
+            q = torch.quantile(avg[:1 << 24], torch.tensor([0.5, 0.9, 0.99], device=dev)).tolist() \
+                if avg.numel() else [0.0, 0.0, 0.0]
             c = cfg
             if max_gaussians is not None:
                 action, offsets = densify_decide_count(model, stats, cfg)
@@ -347,7 +353,7 @@ def densification_phase(model: GaussianModel, train_cams: list, targets, view_se
             n0 = model.n
             model, adam, action = densify(model, adam, stats, c, noise)
             counts = torch.bincount(action.long(), minlength=4).cpu().tolist()
-            history.append((it, n0, counts[1], counts[2], counts[3], model.n))
+            history.append((it, n0, counts[1], counts[2], counts[3], model.n, q))
             if on_step is not None:
                 on_step(history[-1])
             stats = DensityStats(model.n, dev)

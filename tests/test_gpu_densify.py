@@ -219,6 +219,6 @@ def test_densification_phase_grows_and_keeps_rendering():
     seq = np.zeros(200, np.int32)
     model2, adam2, hist = densification_phase(model, cams, targets, seq, iters=60, cfg=cfg, interval=20, start=20)
     assert len(hist) == 3
-    for (it, n0, c, s, p, n1) in hist:
+    for (it, n0, c, s, p, n1, q) in hist:
         assert n1 == n0 + c + s - p
     assert hist[0][2] > 0 and hist[-1][5] == model2.n and int(adam2.step_count.item()) == 60
