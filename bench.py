@@ -781,6 +781,24 @@ def weigh_stages(out: dict, b_frac: float) -> dict:
     return out
 
 
+def coarse_pairs(r, fallback: int) -> int:
+    """(entry, super-tile of 4 x 4 tiles) pairs of the last binning, from the
+    packed tile rectangles the projection wrote (x0, y0, width, height in
+    tiles); `fallback` (the pair count, an upper bound) when unavailable."""
+    try:
+        import torch
+        if not getattr(r, "aux_valid", False):
+            return int(fallback)
+        q = r.rect16.view(-1, 4).to(torch.int64)
+        w, h = q[:, 2], q[:, 3]
+        live = (w > 0) & (h > 0)
+        cx = (q[:, 0] + w - 1) // 4 - q[:, 0] // 4 + 1
+        cy = (q[:, 1] + h - 1) // 4 - q[:, 1] // 4 + 1
+        return int(torch.where(live, cx * cy, torch.zeros_like(cx)).sum().item())
+    except Exception:
+        return int(fallback)
+
+
 def atomic_probe_rate(n_records: int, n_updates: int, reps: int = 3) -> float:
     """Peak rate (updates/s) of the raster adjoint's global atomic pattern -
     two float4 and one float reduction per update into scattered 48-byte
@@ -830,15 +848,15 @@ def roofline_of(stages: dict, loop, args, census: dict | None = None, atomic_pea
         ev = float(r.n_last.double().sum().item())
         census = dict(sum_n_last=ev, evaluated=ev, contributing=ev, tile_pairs=P, staged=P)
     ev, con = float(census["evaluated"]), float(census["contributing"])
-    chunk = max(1024, -(-(-(-N // 304)) // 256) * 256)  # entries per chunk of the tile counting sort
-    n_c = -(-N // chunk) * r.views.n
+    Pc = coarse_pairs(r, P)
     params = loop.model.flat.numel()
     work = {
         "project": ("hbm", N * (236 + 68), "bytes: 236 B parameters read + 68 B record, rectangle, count written per Gaussian"),
-        "bin_sort": ("hbm", 148 * E + 4 * P + 16 * n_c * T + 8 * T,
-                     "bytes: 148 B per (view, Gaussian) entry (depth keys 16, four radix passes 80, clipped "
-                     "rectangles 32, counting 8, placement 12) + 4 B per (Gaussian, tile) pair + 16 B per "
-                     "(chunk, tile) count-matrix cell + 8 B per tile range"),
+        "bin_sort": ("hbm", 124 * E + 32 * Pc + 4 * P + 20 * T,
+                     f"bytes: 124 B per (view, Gaussian) entry (four radix passes 76, rectangle gather 20, tile "
+                     f"and super-tile counts 16, super-tile scatter reads 12) + 32 B per (entry, super-tile) pair "
+                     f"({Pc:.4g}: 12 B record written, read by the count and place passes) + 4 B per (Gaussian, "
+                     f"tile) pair ({P:.4g}) + 20 B per tile (totals, starts, range)"),
         "render_fwd": ("alu", FLOP_EVAL * ev + FLOP_FWD_CONTRIB * con,
                        f"FLOP: {FLOP_EVAL} per evaluated (pixel, Gaussian) pair inside its support box "
                        f"({ev:.4g}) + {FLOP_FWD_CONTRIB} per contributing pair ({con:.4g}), from the work census"),
@@ -968,11 +986,12 @@ def backward_split(ms_full: float, ms_gated: float, iters: int, n_bwd: int, min_
     return f, b
 
 
-def run_measured_loop(loop, plan: dict, dist=None, on_window=None) -> dict:
+def run_measured_loop(loop, plan: dict, dist=None, on_window=None, nvtx: str | None = None) -> dict:
     """Runs a restored, captured RefinementLoop through plan_loop's marks
     (graph replays; CUDA events on the loop's stream around every segment).
     Returns the window's and the whole loop's device ms, the gate counters at
-    the window's start and end, and the final-loss evaluations."""
+    the window's start and end, and the final-loss evaluations.  nvtx: name
+    of an NVTX range around each segment of the timed window only."""
     import numpy as np
     import torch
     done, ms_all, ms_win, evals = 0, 0.0, 0.0, []
@@ -988,11 +1007,15 @@ def run_measured_loop(loop, plan: dict, dist=None, on_window=None) -> dict:
                 on_window()
             wall0 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if nvtx and in_window:
+            torch.cuda.nvtx.range_push(nvtx)
         e0.record(loop.stream)
         for _ in range(mark - done):
             loop.step_graph()
         e1.record(loop.stream)
         torch.cuda.synchronize()
+        if nvtx and in_window:
+            torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1)
         ms_all += ms
         if in_window:
@@ -1068,9 +1091,7 @@ def main():
             loop.step_graph()
         loop.restore(init)
         clock = ClockSampler(local) if (gated and rank == 0) else None
-        torch.cuda.nvtx.range_push("loop_gated" if gated else "loop_full")
-        res = run_measured_loop(loop, plan, dist)
-        torch.cuda.nvtx.range_pop()
+        res = run_measured_loop(loop, plan, dist, nvtx="timed_gated" if gated else "timed_full")
         res["clocks"] = clock.stop() if clock else None
         return loop, res
 

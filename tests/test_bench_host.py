@@ -91,3 +91,15 @@ def test_stored_traffic_only_for_matching_sources(monkeypatch):
     monkeypatch.setattr(bench, "sources_sha256", lambda: "0" * 64)
     got, note = bench.stage_traffic("bin_sort")
     assert got is None and "changed" in note
+
+
+def test_coarse_pairs_count_super_tiles_of_each_rectangle():
+    """(entry, 4x4-tile super-tile) pairs from packed tile rectangles
+    (x0, y0, width, height): a rectangle inside one super-tile counts 1, one
+    straddling a super-tile edge in x and y counts 4; empty ones count 0."""
+    rect16 = torch.tensor([[0, 0, 4, 4], [3, 3, 2, 2], [5, 1, 8, 1], [0, 0, 0, 0], [7, 7, 1, 1]],
+                          dtype=torch.int16)
+    r = types.SimpleNamespace(aux_valid=True, rect16=rect16.view(-1))
+    # [0,3]x[0,3]: 1; [3,4]x[3,4]: 4; x [5,12] -> super-tiles 1..3, y 1 -> 0: 3; empty: 0; (7,7): 1
+    assert bench.coarse_pairs(r, 999) == 1 + 4 + 3 + 0 + 1
+    assert bench.coarse_pairs(types.SimpleNamespace(aux_valid=False), 999) == 999
