@@ -469,6 +469,19 @@ gs_status gs_graph_destroy(gs_graph graph);
 gs_status gs_select_views(const int32_t *seq, int64_t seq_len, int64_t *iter, int32_t n, int32_t *view_ids,
                           const gs_camera *pose_src, gs_camera *slots, int32_t tile, cudaStream_t stream);
 
+/* Per-view optimizer steps of a batched iteration (one reading of Algorithm 1
+ * for several views per step: the views of a batch are consecutive
+ * iterations whose forward passes share the batch's parameters, and each
+ * opened view takes its own Adam step, in slot order, on its own gradient).
+ * From the gate's decisions g[n] (device u8; may be NULL with all_open)
+ * writes gates[k][j] = 1 exactly when j == k and view k opened (or
+ * all_open), as the view_gate of slot k's gs_project_bwd_adam call, and
+ * do_steps[k] (int32) = whether view k opened (or all_open), as its
+ * dev_do_step.  n <= 1024.  The paper has no counterpart (it decides one
+ * view per iteration). */
+gs_status gs_view_steps(const uint8_t *g, int32_t n, int32_t all_open, uint8_t *gates, int32_t *do_steps,
+                        cudaStream_t stream);
+
 /* Per-iteration log for graph replay: with k = (*iter - 1) mod cap (iter as
  * advanced by gs_select_views), writes loss_log[k n + j] = loss[j] and
  * g_log[k n + j] = g[j] for j < n; if norms2 and norm_log are given, also

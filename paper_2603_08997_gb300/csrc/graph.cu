@@ -67,6 +67,17 @@ __global__ void select_views_kernel(const int32_t *seq, int64_t seq_len, int64_t
     *iter = it + 1;
 }
 
+// Per-view optimizer steps of a batched iteration: gates[k][j] = (j == k) and
+// view k opened (or all_open), do_steps[k] = view k opened (or all_open).
+__global__ void view_steps_kernel(const uint8_t *g, int n, int all_open, uint8_t *gates, int32_t *do_steps) {
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+        const int k = i / n, j = i % n;
+        const int open = all_open || (g && g[k]);
+        gates[i] = (uint8_t)(j == k && open);
+        if (j == 0) do_steps[k] = open;
+    }
+}
+
 __global__ void log_step_kernel(const int64_t *iter, int n, const float *loss, const uint8_t *g, double *norms2,
                                 float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap) {
     const int64_t it = *iter - 1;
@@ -86,6 +97,14 @@ __global__ void log_step_kernel(const int64_t *iter, int n, const float *loss, c
 }  // namespace
 
 extern "C" {
+
+gs_status gs_view_steps(const uint8_t *g, int32_t n, int32_t all_open, uint8_t *gates, int32_t *do_steps,
+                        cudaStream_t stream) {
+    if (n <= 0 || n > 1024 || !gates || !do_steps || (!g && !all_open)) return GS_ERR_INVALID_ARG;
+    view_steps_kernel<<<1, 256, 0, stream>>>(g, n, all_open ? 1 : 0, gates, do_steps);
+    GS_TRY_LAUNCH();
+    return GS_OK;
+}
 
 gs_status gs_log_step(const int64_t *iter, int32_t n, const float *loss, const uint8_t *g, double *norms2,
                       float *loss_log, uint8_t *g_log, double *norm_log, int64_t cap, cudaStream_t stream) {

@@ -129,6 +129,7 @@ _PROTOS = {
     "gs_graph_kernel_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "gs_graph_destroy": (C.c_int, [C.c_void_p]),
     "gs_select_views": (C.c_int, [_P, _I64, _P, _I32, _P, _P, _P, _I32, _S]),
+    "gs_view_steps": (C.c_int, [_P, _I32, _I32, _P, _P, _S]),
     "gs_raster_census": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                    _P, _P, _S]),
     "gs_atomic_probe": (C.c_int, [_P, _I64, _I64, _S]),

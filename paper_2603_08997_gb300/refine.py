@@ -37,7 +37,7 @@ class RefinementLoop:
                  eps: float = 1e-8, rho_lo: float = 0.5, lr=None, pair_capacity: int | None = None,
                  fused: bool = True, views_per_step: int = 1, log_capacity: int = 0,
                  adam: AdamState | None = None, stats: DensityStats | None = None, batch_lr_scale: bool = False,
-                 compact_tiles: bool = False):
+                 compact_tiles: bool = False, per_view_steps: bool = False):
         """targets: [n_train, 3, H, W] tensor (equal sizes) or a list of
         [3, H_v, W_v] tensors, one per training view.  adam: an existing
         optimizer state of `model` to continue (else a fresh one).  stats: the
@@ -46,7 +46,10 @@ class RefinementLoop:
         scaled by the fraction of the iteration's views the gate opened.
         compact_tiles: the selected views' own tile grids are packed one after
         another (gs_select_views with the tile size) instead of each slot
-        holding a grid of the largest view's size."""
+        holding a grid of the largest view's size.
+        per_view_steps (views_per_step > 1, fused backward): each opened view
+        of the batch takes its own Adam step in slot order (the always-backward
+        loop: every view), on its own gradient from the batch's forward pass."""
         import copy
         self.model = model
         self.fused = bool(fused)
@@ -85,6 +88,10 @@ class RefinementLoop:
             self.adam = AdamState(model, lr) if lr is not None else AdamState(model)
         self.stats = stats
         self.select_tile = int(self.s.tile) if compact_tiles else 0
+        self.per_view = bool(per_view_steps) and self.B > 1 and self.fused
+        if self.per_view:
+            self.view_gates = torch.zeros(self.B * self.B, dtype=torch.uint8, device=dev)
+            self.view_do = torch.zeros(self.B, dtype=torch.int32, device=dev)
         self.lr_scale = bool(batch_lr_scale) and self.B > 1 and self.gated
         self.adam.cfg.lr_scale_den = self.B if self.lr_scale else 0
         self.params = model.c_params()
@@ -121,7 +128,16 @@ class RefinementLoop:
         # the step-gate word (number of opened views) is passed when the step
         # is predicated on it, or when it scales the step
         do_step = self.any if (predicated or self.lr_scale) else None
-        if self.fused:
+        if self.per_view:
+            # the raster adjoint of the opened views, then one projection
+            # adjoint + Adam step per opened view, in slot order
+            gsr.call("gs_view_steps", gsr.ptr(self.g), self.B, int(not self.gated), gsr.ptr(self.view_gates),
+                     gsr.ptr(self.view_do), gsr.stream_handle(s))
+            r.raster_bwd(view_gate=gate, stream=s)
+            for k in range(self.B):
+                r.project_bwd_adam(self.model, self.adam, view_gate=self.view_gates[k * self.B:(k + 1) * self.B],
+                                   do_step=self.view_do[k:k + 1], norms2=self.norms2, stream=s)
+        elif self.fused:
             r.backward_adam(self.model, self.adam, view_gate=gate, do_step=do_step, norms2=self.norms2, stream=s)
         else:
             r.backward(self.params, self.grads, view_gate=gate, accumulate=False, stream=s)

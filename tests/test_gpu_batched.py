@@ -187,6 +187,51 @@ def test_batched_loop_compact_persistent_equals_default():
     assert gpu_util.rel_err(out[1][0], out[0][0]) < 1e-6
 
 
+@pytest.mark.parametrize("gated", [False, True])
+def test_per_view_steps_equal_an_explicit_sequence(gated):
+    """Per-view optimizer steps of a batch: the raster adjoint of the opened
+    views from the batch's forward pass, then for each opened view in slot
+    order the projection adjoint of its 2D gradients fused with one Adam
+    step (at the parameters as they stand).  Equal to the explicit sequence
+    of those calls, and the step count advances once per opened view."""
+    gpu_util.lib()
+    scene, _, _ = synth.case_c1(n=1500)
+    cams = _cams()
+    rng = np.random.default_rng(9)
+    targets = [torch.from_numpy(rng.uniform(0, 1, (3, h, w)).astype(np.float32)) for w, h in SIZES]
+    seq = np.array([2, 0, 1] * 4, np.int32)
+    model = raster.GaussianModel.from_scene(scene)
+    loop = RefinementLoop(model, cams, targets, seq, gated=gated, W=0, views_per_step=3, per_view_steps=True,
+                          compact_tiles=True)
+    flat0 = model.flat.clone()
+    loop.gate.decide(torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda"),
+                     torch.ones(3, device="cuda"), loop.g, loop.any)  # every view gets a history
+    loop.gate.update(torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda"), torch.ones(3, device="cuda") * 10)
+    loop.step_eager()
+    torch.cuda.synchronize()
+    g = loop.g.cpu().numpy().copy() if gated else np.ones(3, np.uint8)
+    assert int(loop.adam.step_count.item()) == int(g.sum())
+    got = model.flat.clone()
+    # the explicit sequence on a fresh copy of the same state
+    model2 = raster.GaussianModel.from_scene(scene)
+    model2.flat.copy_(flat0)
+    adam2 = raster.AdamState(model2)
+    r = loop.renderer
+    r.forward(model2.c_params())
+    r.compute_loss(loop.targets, loop.target_offsets, loop.view_ids, with_grad=True)
+    gate = torch.from_numpy(g).cuda()
+    r.raster_bwd(view_gate=gate)
+    for k in range(3):
+        if g[k]:
+            one = torch.zeros(3, dtype=torch.uint8, device="cuda")
+            one[k] = 1
+            r.project_bwd_adam(model2, adam2, view_gate=one)
+    torch.cuda.synchronize()
+    assert int(adam2.step_count.item()) == int(g.sum())
+    assert gpu_util.rel_err(got.cpu().numpy(), model2.flat.cpu().numpy()) < 1e-6
+    loop.close()
+
+
 def test_fused_and_unfused_loops_agree():
     """The loop's backward branch in its two forms (projection adjoint and Adam
     fused in one kernel; gradients stored, then the Adam kernel) gives the same
