@@ -74,6 +74,9 @@ def parse():
                     help="NEXT-4: opacity prune + compaction at eps_alpha in (0.005, 0.05, 0.2), then SkipGS")
     ap.add_argument("--c2", action="store_true", help="C2: 200k-Gaussian fwd+bwd+Adam iteration timing")
     ap.add_argument("--c5", action="store_true", help="C5: 6M Gaussians, 4x1080p fwd+bwd batch timing and memory")
+    ap.add_argument("--lists", default="coarse", choices=["coarse", "tile"],
+                    help="coarse: the binning writes super-tile lists and the compositing kernels filter each "
+                         "tile's entries from them; tile: per-tile lists (gs_bin_sort)")
     ap.add_argument("--stages-once", action="store_true",
                     help="run two eager iterations of every stage on one view of the workload and exit "
                          "(a small, fixed launch sequence for hardware-counter captures)")
@@ -195,7 +198,7 @@ def setup_c3(args, dev):
     seq_len = max(args.steps, getattr(args, "iters", 5000), 5000)
     gt, start, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=seq_len,
                                          width=args.width, height=args.height)
-    st = raster.RasterSettings()
+    st = raster.RasterSettings(coarse_lists=args.lists == "coarse")
     cap = 24 * args.n
     # targets: renders of the ground-truth scene (device-resident)
     mgt = raster.GaussianModel.from_scene(gt, dev)
@@ -325,7 +328,7 @@ def run_densify(args) -> None:
     dev = torch.device("cuda", 0)
     gt, _, cams, seq = synth.case_c3(n=args.n, n_views=args.views, n_iters=max(args.iters, args.densify_iters),
                                      width=args.width, height=args.height)
-    st = raster.RasterSettings()
+    st = raster.RasterSettings(coarse_lists=args.lists == "coarse")
     mgt = raster.GaussianModel.from_scene(gt, dev)
     rgt = raster.Renderer(args.n, 3, raster.Views([cams[0]], st.tile, dev), st, 24 * args.n, dev)
     targets = torch.empty((args.views, 3, args.height, args.width), dtype=torch.float32, device=dev)
@@ -431,7 +434,7 @@ def run_c2(args) -> None:
     build.build()
     dev = torch.device("cuda", 0)
     scene, tscene, cam, noise = synth.case_c2()
-    st = raster.RasterSettings()
+    st = raster.RasterSettings(coarse_lists=args.lists == "coarse")
     mt = raster.GaussianModel.from_scene(tscene, dev)
     rt = raster.Renderer(scene.n, 3, raster.Views([cam], st.tile, dev), st, 48 * scene.n, dev)
     rt.forward(mt.c_params())
@@ -522,7 +525,8 @@ def stages_once(args) -> None:
     build.build()
     gt, start, cams, _ = synth.case_c3(n=args.n, n_views=4, n_iters=10, width=args.width, height=args.height)
     views = raster.Views([cams[0]], 16)
-    r = raster.Renderer(args.n, 3, views, raster.RasterSettings(), pair_capacity=24 * args.n)
+    r = raster.Renderer(args.n, 3, views, raster.RasterSettings(coarse_lists=args.lists == "coarse"),
+                        pair_capacity=24 * args.n)
     r.forward(raster.GaussianModel.from_scene(gt).c_params())
     torch.cuda.synchronize()
     target = r.image.clone()
@@ -663,6 +667,8 @@ def workload_config(args, plan: dict, world: int) -> dict:
             "timed": f"the last {plan['K']} of {plan['iters']} post-densification iterations "
                      f"(t = {plan['start'] + 1}..{plan['iters']})",
             "parallelism": "replicas" if world > 1 else "1 GPU",
+            "lists": ("super-tile lists, each tile's entries filtered by the compositing kernels"
+                      if getattr(args, "lists", "tile") == "coarse" else "per-tile lists"),
             "l2": "inputs larger than L2 (2.8 GB of parameters and Adam state, 2.6 GB of targets)"}
 
 
@@ -863,11 +869,17 @@ def roofline_of(stages: dict, loop, args, census: dict | None = None, atomic_pea
     params = loop.model.flat.numel()
     work = {
         "project": ("hbm", N * (236 + 68), "bytes: 236 B parameters read + 68 B record, rectangle, count written per Gaussian"),
-        "bin_sort": ("hbm", 124 * E + 32 * Pc + 4 * P + 20 * T,
-                     f"bytes: 124 B per (view, Gaussian) entry (four radix passes 76, rectangle gather 20, tile "
-                     f"and super-tile counts 16, super-tile scatter reads 12) + 32 B per (entry, super-tile) pair "
-                     f"({Pc:.4g}: 12 B record written, read by the count and place passes) + 4 B per (Gaussian, "
-                     f"tile) pair ({P:.4g}) + 20 B per tile (totals, starts, range)"),
+        "bin_sort": (("hbm", 124 * E + 6 * Pc + 20 * T,
+                      f"bytes: 124 B per (view, Gaussian) entry (four radix passes 76, rectangle gather 20, tile "
+                      f"and super-tile counts 16, super-tile scatter reads 12) + 6 B per (entry, super-tile) pair "
+                      f"({Pc:.4g}: Gaussian index and covered-tile mask written; the compositing kernels filter the "
+                      f"tiles' entries from these lists, no (Gaussian, tile) pair is placed) + 20 B per tile "
+                      f"(totals, starts, range)") if getattr(r, "coarse", False) else
+                     ("hbm", 124 * E + 14 * Pc + 4 * P + 20 * T,
+                      f"bytes: 124 B per (view, Gaussian) entry (four radix passes 76, rectangle gather 20, tile "
+                      f"and super-tile counts 16, super-tile scatter reads 12) + 14 B per (entry, super-tile) pair "
+                      f"({Pc:.4g}: 6 B record written, the mask read by the count pass, both read by the place "
+                      f"pass) + 4 B per (Gaussian, tile) pair ({P:.4g}) + 20 B per tile (totals, starts, range)")),
         "render_fwd": ("alu", FLOP_EVAL * ev + FLOP_FWD_CONTRIB * con,
                        f"FLOP: {FLOP_EVAL} per evaluated (pixel, Gaussian) pair inside its support box "
                        f"({ev:.4g}) + {FLOP_FWD_CONTRIB} per contributing pair ({con:.4g}), from the work census"),

@@ -145,7 +145,39 @@ typedef struct {
                                     which a persistent grid of resident blocks takes the tiles in
                                     tile_order (reset by each compositing call, so the calls that share it
                                     must be ordered on one stream); results do not depend on it */
+    uint32_t *batch_pos;         /* [ckpt_slots] for the *_coarse calls (else ignored, may be NULL): per
+                                    checkpoint slot, the super-tile list position of the batch's first
+                                    Gaussian (written by gs_render_fwd_coarse, read by the adjoints) */
 } gs_fwd_saved;
+
+/* Super-tile lists, the output of gs_bin_sort_coarse and the input of the
+ * *_coarse compositing calls.  The (view, Gaussian) entries are listed once
+ * per super-tile of 4 x 4 tiles that their tile rectangle meets, in depth
+ * order, each as its Gaussian index and a 16-bit mask of the super-tile's
+ * tiles the rectangle covers (bit 4 * row + column, rows and columns counted
+ * from the super-tile's first tile).  A view's super-tiles cover its tile grid
+ * row-major in steps of 4 tiles (the last row and column may be partial);
+ * views follow one another.  A tile's list as gs_bin_sort writes it is
+ * exactly the entries of its super-tile's list with the tile's bit set, in
+ * the same order: the compositing kernels filter it out as they stage it and
+ * only as far as the tile's pixels need, so the tile lists are never
+ * written.  Caller-owned device buffers:
+ *   gid        [capacity] Gaussian index within its view;
+ *   mask       [capacity] covered tiles (16-byte aligned);
+ *   start      [total_tiles / 4 + n_views] first list entry of each super-tile;
+ *   count      [total_tiles / 4 + n_views] its number of entries (0 past the last super-tile);
+ *   view_first [n_views + 1] first super-tile of each view, then the super-tile total;
+ *   total      [1] number of entries of all lists (written also when above capacity);
+ *   capacity   at most 2^32 - 65536. */
+typedef struct {
+    uint32_t *gid;
+    uint16_t *mask;
+    uint32_t *start;
+    uint32_t *count;
+    int64_t *view_first;
+    int64_t *total;
+    int64_t capacity;
+} gs_coarse_lists;
 
 /* --------------------------------------------------------------- layout */
 
@@ -183,8 +215,9 @@ gs_status gs_project(const gs_params *params /* host */, const gs_camera *cams, 
 /* ------------------------------------------------------ binning and sort */
 
 /* Scratch bytes gs_bin_sort needs for n Gaussians x n_views views over
- * total_tiles tiles and pair_capacity pairs (12 bytes per pair of capacity:
- * the entries listed by super-tile of 4 x 4 tiles, at most one per pair). */
+ * total_tiles tiles and pair_capacity pairs (about 6 bytes per pair of
+ * capacity: the entries listed by super-tile of 4 x 4 tiles, at most one per
+ * pair, as a Gaussian index and a mask of covered tiles). */
 size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capacity, int64_t total_tiles);
 
 /* Tile binning + depth order ("depth-sorted Gaussians overlapping a pixel",
@@ -207,6 +240,24 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
                       void *workspace, size_t workspace_bytes, uint64_t *keys, uint32_t *vals,
                       int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count,
                       int32_t *dev_status, cudaStream_t stream);
+
+/* The super-tile form of gs_bin_sort: the same depth order and tile
+ * rectangles, written as the super-tile lists of `lists` (gs_coarse_lists, a
+ * host struct of device pointers) instead of per-tile lists; the pairs are
+ * counted but not placed.  ranges[tile] = the [start, end) that gs_bin_sort
+ * writes (where the tile's pairs would lie in its vals; the *_coarse
+ * compositing calls take their checkpoint slots from them, gs_tile_order its
+ * order).  *dev_pair_count as gs_bin_sort; more pairs than pair_capacity, or
+ * more list entries than lists->capacity (at most one per pair):
+ * GS_ERR_CAPACITY in dev_status, ranges left empty.  workspace: at least
+ * gs_bin_sort_coarse_workspace_size(n, n_views, total_tiles) bytes, 256-byte
+ * aligned.  Other arguments and errors as gs_bin_sort. */
+size_t gs_bin_sort_coarse_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles);
+gs_status gs_bin_sort_coarse(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n,
+                             int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg /* host */,
+                             void *workspace, size_t workspace_bytes, const gs_coarse_lists *lists /* host */,
+                             int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status,
+                             cudaStream_t stream);
 
 /* gs_bin_sort without a caller-provided workspace, for callers that cannot
  * allocate device memory: work issued while a CUDA graph is being captured
@@ -253,6 +304,17 @@ gs_status gs_tile_order(const uint32_t *ranges, int64_t total_tiles, uint32_t *t
 gs_status gs_render_fwd(const gs_projected *proj /* host */, int64_t n, const uint32_t *vals,
                         const uint32_t *ranges, const gs_camera *cams, int32_t n_views,
                         int64_t total_tiles, const gs_raster_config *cfg /* host */, float *image, gs_fwd_saved saved, int32_t *dev_status, cudaStream_t stream);
+
+/* gs_render_fwd reading the super-tile lists of gs_bin_sort_coarse (lists:
+ * host struct, device buffers; ranges from the same call) instead of tile
+ * lists: every output bit for bit as gs_render_fwd on gs_bin_sort's lists of
+ * the same projection (the same Gaussians in the same order per tile), and
+ * saved.batch_pos (required) receives, per processed batch, the list position
+ * of its first Gaussian for the *_coarse adjoints. */
+gs_status gs_render_fwd_coarse(const gs_projected *proj /* host */, int64_t n, const gs_coarse_lists *lists /* host */,
+                               const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                               const gs_raster_config *cfg /* host */, float *image, gs_fwd_saved saved,
+                               int32_t *dev_status, cudaStream_t stream);
 
 /* ------------------------------------------------------------------ loss */
 
@@ -324,6 +386,21 @@ gs_status gs_project_bwd(const gs_params *params /* host */, const gs_camera *ca
                          const gs_raster_config *cfg /* host */, const float *g2d, const uint8_t *view_gate,
                          gs_grads grads, int32_t accumulate, int32_t *dev_status, cudaStream_t stream);
 
+/* gs_render_bwd and gs_raster_bwd over the super-tile lists (lists and
+ * ranges of gs_bin_sort_coarse, saved from gs_render_fwd_coarse, whose
+ * batch_pos they read): the same gradients up to the order of float atomics. */
+gs_status gs_render_bwd_coarse(const gs_params *params /* host */, const gs_projected *proj /* host */,
+                               const gs_coarse_lists *lists /* host */, const uint32_t *ranges, const gs_camera *cams,
+                               int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg /* host */,
+                               gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate, gs_grads grads,
+                               int32_t accumulate, void *workspace, size_t workspace_bytes, int32_t *dev_status,
+                               cudaStream_t stream);
+gs_status gs_raster_bwd_coarse(const gs_projected *proj /* host */, int64_t n, const gs_coarse_lists *lists /* host */,
+                               const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                               const gs_raster_config *cfg /* host */, gs_fwd_saved saved, const float *dL_dimage,
+                               const uint8_t *view_gate, float *g2d, size_t g2d_bytes, int32_t *dev_status,
+                               cudaStream_t stream);
+
 /* ----------------------------------------------------------------- Adam */
 /* (gs_adam_config and gs_adam_step below; gs_render_bwd_adam after them.) */
 
@@ -373,6 +450,16 @@ gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, 
                              const uint8_t *view_gate, const gs_adam_config *adam /* host */,
                              const int32_t *dev_do_step, int64_t *dev_step, double *norms2, void *workspace,
                              size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream);
+
+/* gs_render_bwd_adam over the super-tile lists (as gs_render_bwd_coarse). */
+gs_status gs_render_bwd_adam_coarse(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                                    const gs_projected *proj /* host */, const gs_coarse_lists *lists /* host */,
+                                    const uint32_t *ranges, const gs_camera *cams, int32_t n_views,
+                                    int64_t total_tiles, const gs_raster_config *cfg /* host */, gs_fwd_saved saved,
+                                    const float *dL_dimage, const uint8_t *view_gate,
+                                    const gs_adam_config *adam /* host */, const int32_t *dev_do_step,
+                                    int64_t *dev_step, double *norms2, void *workspace, size_t workspace_bytes,
+                                    int32_t *dev_status, cudaStream_t stream);
 
 /* The second half of gs_render_bwd_adam on its own: the projection adjoint of
  * the 2D gradients that gs_raster_bwd left in g2d (device, layout and

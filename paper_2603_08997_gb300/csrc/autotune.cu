@@ -169,13 +169,13 @@ extern "C" gs_status gs_autotune(const gs_params *params, const gs_camera *cams_
             result = GS_ERR_CUDA;
             break;
         }
-        gs_projected proj;
+        gs_projected proj{};
         proj.rec = b.rec;
         proj.rect = b.rect;
         proj.tiles_touched = b.touched;
         proj.depth_key = b.depth_key;
         proj.rect16 = b.rect16;
-        gs_fwd_saved saved;
+        gs_fwd_saved saved{};
         saved.T_final = b.T_final;
         saved.n_last = b.n_last;
         saved.ckpt = b.ckpt;
@@ -183,7 +183,7 @@ extern "C" gs_status gs_autotune(const gs_params *params, const gs_camera *cams_
         saved.tile_order = b.tile_order;
         int64_t o[6];
         param_offsets(n, params->sh_degree, o);
-        gs_grads gr;
+        gs_grads gr{};
         gr.means = b.grads + o[0];
         gr.log_scales = b.grads + o[1];
         gr.quats = b.grads + o[2];

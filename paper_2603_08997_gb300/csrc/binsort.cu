@@ -301,6 +301,24 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 constexpr int BIN_GROUP = 16;
 constexpr int COUNT_THREADS = 1024;
 
+constexpr int SUP = kSup;         // tiles per super-tile side
+constexpr int SUP_T = SUP * SUP;  // tiles per super-tile: one mask bit each
+
+// Bits k = 4 row + column of the super-tile's tiles (its first tile at
+// (x0, y0)) that the clipped tile rectangle r covers.
+__device__ __forceinline__ uint32_t cover_mask(ushort4 r, int x0, int y0) {
+    if (r.z == 0) return 0u;
+    const int c0 = max((int)r.x - x0, 0), c1 = min((int)r.x + (int)r.z - x0, SUP);
+    const int r0 = max((int)r.y - y0, 0), r1 = min((int)r.y + (int)r.w - y0, SUP);
+    if (c0 >= c1 || r0 >= r1) return 0u;
+    const uint32_t cols = ((1u << c1) - 1u) & ~((1u << c0) - 1u);
+    uint32_t m = 0;
+#pragma unroll
+    for (int y = 0; y < SUP; ++y)
+        if (y >= r0 && y < r1) m |= cols << (SUP * y);
+    return m;
+}
+
 struct BinGeom {
     int64_t n;       // entries per view
     int64_t chunk;   // entries per chunk
@@ -599,16 +617,17 @@ struct PairWalk {
     }
 };
 
-// Places each pair's Gaussian index into vals and the entry's tile
-// rectangle (in tiles, packed as (x0 | y0 << 16, width | height << 16)) into
-// recs: on the super-tile grid, the records the tile placement reads.
+// Places each pair's Gaussian index into vals and, on the super-tile grid,
+// the mask of the super-tile's tiles that the entry's tile rectangle covers
+// into masks (cover_mask): the records the tile placement and the
+// compositing kernels' super-tile form read.
 template <typename W, int NW>  // W: 32-bit mask words
 __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
                                                           const uint32_t *__restrict__ order,
                                                           const gs_camera *__restrict__ cams, BinGeom g,
                                                           const uint32_t *__restrict__ M,
                                                           const int64_t *sort_count, uint32_t *__restrict__ vals,
-                                                          uint2 *__restrict__ recs) {
+                                                          uint16_t *__restrict__ masks) {
     using SM = ScatterMask<W, NW>;
     constexpr int WB = SM::WB, WIN = SM::WIN;
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -616,7 +635,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
     uint32_t *s_off = reinterpret_cast<uint32_t *>(s_mask + (size_t)g.max_vt * NW);  // [max_vt]
     __shared__ ushort4 s_er[WIN];    // the window's rectangles (in the geometry's grid)
     __shared__ uint32_t s_eg[WIN];   // Gaussian indices
-    __shared__ uint2 s_fr[WIN];      // the window's tile rectangles, packed
+    __shared__ ushort4 s_fr[WIN];    // the window's tile rectangles
     __shared__ int s_pre[WIN + 1];   // first pair of each entry
     __shared__ uint32_t s_tj[SC_THREADS * SC_Q];  // first sub-window: (tile << 9 | entry) per pair
     __shared__ uint32_t s_warp[32];
@@ -646,8 +665,7 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
             }
             s_er[threadIdx.x] = r;
             s_eg[threadIdx.x] = gi;
-            s_fr[threadIdx.x] = make_uint2((uint32_t)fr.x | ((uint32_t)fr.y << 16),
-                                                    (uint32_t)fr.z | ((uint32_t)fr.w << 16));
+            s_fr[threadIdx.x] = fr;
             area = (int)r.z * r.w;
         }
         // the window's pair prefix: a warp scan in the WIN / 32 warps holding
@@ -742,7 +760,8 @@ __global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restr
                         if (wd == jw) below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
                     }
                     vals[s_off[t] + below] = s_eg[jj];
-                    recs[s_off[t] + below] = s_fr[jj];
+                    masks[s_off[t] + below] =
+                        (uint16_t)cover_mask(s_fr[jj], (t % vt.tx) * SUP, (t / vt.tx) * SUP);
                     if (below + 1 == all) {  // the tile's last pair of the window
                         last_t[k] = t;
                         last_n[k] = all;
@@ -780,16 +799,14 @@ bool coarse_scatter_wide(int64_t max_vt) {
 // with entry positions as values, gives every super-tile the depth-ordered
 // list of the entries whose rectangle meets it (its "coarse list").  A coarse
 // list is cut into work items of WI entries, one warp each.  The warp takes
-// its entries 32 at a time; each lane turns its entry's rectangle into a
-// 16-bit mask of the super-tile's tiles it covers, and one ballot per tile
-// gives each covering lane its rank among the group's covering lanes: the
+// its entries 32 at a time; each lane reads its entry's 16-bit mask of the
+// super-tile's tiles it covers (written by the scatter), and one ballot per
+// tile gives each covering lane its rank among the group's covering lanes: the
 // tile's pairs from the item, in depth order, go to consecutive slots.  A
 // count pass gives each (item, tile) its pair count, a scan per super-tile
 // over its items (after the tile's start) the first slots, and the place pass
 // writes.  Every pair is written once, each tile's run contiguously, and no
 // warp waits on another.
-constexpr int SUP = 4;            // tiles per super-tile side
-constexpr int SUP_T = SUP * SUP;  // tiles per super-tile: one mask bit each
 constexpr int WI = 512;           // coarse-list entries per work item (one warp)
 constexpr int FP_THREADS = 256;   // threads of the placement blocks (8 warps)
 
@@ -838,21 +855,6 @@ __global__ void seg_fill(int64_t tiles, const uint32_t *__restrict__ seg_base, u
     for (uint32_t it = seg_base[ct]; it < seg_base[ct + 1]; ++it) item_ct[it] = (uint32_t)ct;
 }
 
-// Bits k = 4 row + column of the super-tile's tiles (its first tile at
-// (x0, y0)) that the clipped tile rectangle r covers.
-__device__ __forceinline__ uint32_t cover_mask(ushort4 r, int x0, int y0) {
-    if (r.z == 0) return 0u;
-    const int c0 = max((int)r.x - x0, 0), c1 = min((int)r.x + (int)r.z - x0, SUP);
-    const int r0 = max((int)r.y - y0, 0), r1 = min((int)r.y + (int)r.w - y0, SUP);
-    if (c0 >= c1 || r0 >= r1) return 0u;
-    const uint32_t cols = ((1u << c1) - 1u) & ~((1u << c0) - 1u);
-    uint32_t m = 0;
-#pragma unroll
-    for (int y = 0; y < SUP; ++y)
-        if (y >= r0 && y < r1) m |= cols << (SUP * y);
-    return m;
-}
-
 // Geometry of work item `item`: its super-tile's first tile, view, entries.
 struct ItemGeom {
     int v, x0, y0, cnt;
@@ -886,7 +888,7 @@ __device__ __forceinline__ ItemGeom item_geom(uint32_t item, const BinGeom &gc, 
 // take items in a grid-stride loop (the item count is on the device); the
 // item's records are read in order (coalesced).
 template <bool PLACE>
-__global__ void __launch_bounds__(FP_THREADS) fine_pass(const uint2 *__restrict__ crect,
+__global__ void __launch_bounds__(FP_THREADS) fine_pass(const uint16_t *__restrict__ cmask,
                                                         const uint32_t *__restrict__ cgid,
                                                         const gs_camera *__restrict__ cams, int n_views, BinGeom gc,
                                                         const uint32_t *__restrict__ cstart,
@@ -910,10 +912,7 @@ __global__ void __launch_bounds__(FP_THREADS) fine_pass(const uint2 *__restrict_
                 const int j = g0 + lane;
                 uint32_t m = 0, gid = 0;
                 if (j < ig.cnt) {
-                    const uint2 q = crect[ig.b0 + j];
-                    const ushort4 r = make_ushort4((unsigned short)(q.x & 0xffffu), (unsigned short)(q.x >> 16),
-                                                   (unsigned short)(q.y & 0xffffu), (unsigned short)(q.y >> 16));
-                    m = cover_mask(r, ig.x0, ig.y0);
+                    m = cmask[ig.b0 + j];
                     if (PLACE) gid = cgid[ig.b0 + j];
                 }
 #pragma unroll
@@ -1077,7 +1076,7 @@ struct BinWorkspace {
     uint32_t *Mc;              // [n_c' * Tc] chunk x super-tile counts, then first slots
     uint32_t *G1c;             // [n_g' * Tc]
     uint32_t *ctotal, *cstart; // [Tc]
-    uint2 *crect;              // [pair_capacity] tile rectangles by super-tile, in depth order
+    uint16_t *cmask;           // [pair_capacity] covered-tile masks by super-tile, in depth order
     uint32_t *cgid;            // [pair_capacity] their Gaussian indices
     int64_t *c_count;          // [2] super-tile pair count, its sort count
     // placement work items
@@ -1088,12 +1087,15 @@ struct BinWorkspace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// coarse_only: the super-tile form (gs_bin_sort_coarse), whose lists live in
+// the caller's buffers and which has no placement pass.
 size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pair_capacity, BinWorkspace *w,
-                     char *base) {
+                     char *base, bool coarse_only = false) {
     const int64_t total = n * n_views;
     const BinGeom g = bin_geom(n, total_tiles, 16, 0);
     const BinGeom gc = coarse_geom(n, total_tiles, n_views, 16, 0, nullptr);
-    const int64_t items = fine_items_cap(pair_capacity, gc.tiles);
+    if (coarse_only) pair_capacity = 0;
+    const int64_t items = coarse_only ? 0 : fine_items_cap(pair_capacity, gc.tiles);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char *p = base ? base + off : nullptr;
@@ -1116,7 +1118,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
     char *G1c = take(sizeof(uint32_t) * (size_t)(gc.n_g * gc.tiles));
     char *ct = take(sizeof(uint32_t) * (size_t)gc.tiles);
     char *cs = take(sizeof(uint32_t) * (size_t)gc.tiles);
-    char *cl = take(sizeof(uint2) * (size_t)pair_capacity);
+    char *cl = take(sizeof(uint16_t) * (size_t)pair_capacity);
     char *cg = take(sizeof(uint32_t) * (size_t)pair_capacity);
     char *cc = take(sizeof(int64_t) * 2);
     char *sb = take(sizeof(uint32_t) * (size_t)(gc.tiles + 1));
@@ -1134,7 +1136,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
         w->G1c = (uint32_t *)G1c;
         w->ctotal = (uint32_t *)ct;
         w->cstart = (uint32_t *)cs;
-        w->crect = (uint2 *)cl;
+        w->cmask = (uint16_t *)cl;
         w->cgid = (uint32_t *)cg;
         w->c_count = (int64_t *)cc;
         w->seg_base = (uint32_t *)sb;
@@ -1142,6 +1144,19 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
         w->run_of = (uint32_t *)ro;
     }
     return off;
+}
+
+// The super-tile form's tile ranges: where each tile's pairs would lie in
+// gs_bin_sort's vals (the checkpoint slots and the tile order use them).
+// Written only when both the pairs and the super-tile lists fit.
+__global__ void tile_ranges(int64_t tiles, const uint32_t *__restrict__ tile_start,
+                            const uint32_t *__restrict__ tile_total, const int64_t *sort_count,
+                            const int64_t *coarse_sort_count, uint2 *__restrict__ ranges) {
+    if (*sort_count == 0 || *coarse_sort_count == 0) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const uint32_t tot = tile_total[t];
+    ranges[t] = tot ? make_uint2(tile_start[t], tile_start[t] + tot) : make_uint2(0u, 0u);
 }
 
 // Tables of up to this many tiles per view fit the shared memory of the
@@ -1176,11 +1191,23 @@ size_t gs_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t pair_capac
     return bin_ws_layout(n, n_views, total_tiles, pair_capacity, nullptr, nullptr);
 }
 
-gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
-                      int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg, void *workspace,
-                      size_t workspace_bytes, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
-                      uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
-    if (!proj || !cams || !cfg || n_views <= 0 || n < 0 || total_tiles <= 0 || !vals || !ranges || !dev_pair_count)
+}  // extern "C"
+
+namespace {
+
+// gs_bin_sort (coarse == nullptr) and gs_bin_sort_coarse (the super-tile
+// lists into the caller's buffers, without the placement of the pairs).
+gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
+                        int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg, void *workspace,
+                        size_t workspace_bytes, uint64_t *keys, uint32_t *vals, const gs_coarse_lists *coarse,
+                        int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status,
+                        cudaStream_t stream) {
+    if (!proj || !cams || !cfg || n_views <= 0 || n < 0 || total_tiles <= 0 || !ranges || !dev_pair_count)
+        return GS_ERR_INVALID_ARG;
+    if (!coarse && !vals) return GS_ERR_INVALID_ARG;
+    if (coarse && (!coarse->gid || !coarse->mask || !coarse->start || !coarse->count || !coarse->view_first ||
+                   !coarse->total || coarse->capacity < 0 || coarse->capacity > ((int64_t)1 << 32) - 65536 ||
+                   ((uintptr_t)coarse->mask & 15)))
         return GS_ERR_INVALID_ARG;
     if (cfg->tile != 8 && cfg->tile != 16 && cfg->tile != 32) return GS_ERR_INVALID_ARG;
     if (pair_capacity < 0 || pair_capacity >= ((int64_t)1 << 32) - 1) return GS_ERR_INVALID_ARG;
@@ -1190,15 +1217,35 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     const int64_t total = n * n_views;
     if (total >= ((int64_t)1 << 32) - 1) return GS_ERR_INVALID_ARG;
     if (total > 0 && (!proj->rec || !proj->rect || !proj->tiles_touched)) return GS_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < bin_ws_layout(n, n_views, total_tiles, pair_capacity, nullptr, nullptr))
+    const bool co = coarse != nullptr;
+    if (!workspace ||
+        workspace_bytes < bin_ws_layout(n, n_views, total_tiles, pair_capacity, nullptr, nullptr, co))
         return GS_ERR_WORKSPACE;
     if ((uintptr_t)workspace & 255) return GS_ERR_WORKSPACE;
     BinWorkspace w;
-    bin_ws_layout(n, n_views, total_tiles, pair_capacity, &w, (char *)workspace);
+    bin_ws_layout(n, n_views, total_tiles, pair_capacity, &w, (char *)workspace, co);
+    int64_t coarse_capacity = pair_capacity;  // at most one super-tile entry per pair
+    int64_t *coarse_total = w.c_count;
+    if (co) {  // the lists go to the caller's buffers
+        w.cgid = coarse->gid;
+        w.cmask = coarse->mask;
+        w.cstart = coarse->start;
+        w.ctotal = coarse->count;
+        w.coff = coarse->view_first;
+        coarse_capacity = coarse->capacity;
+        coarse_total = coarse->total;
+    }
 
     GS_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)total_tiles, stream));
     if (total == 0) {
         GS_TRY(cudaMemsetAsync(dev_pair_count, 0, sizeof(int64_t), stream));
+        if (co) {
+            GS_TRY(cudaMemsetAsync(coarse->total, 0, sizeof(int64_t), stream));
+            const BinGeom gc0 = coarse_geom(n, total_tiles, n_views, cfg->tile, (int)mvt, nullptr);
+            GS_TRY(cudaMemsetAsync(coarse->count, 0, sizeof(uint32_t) * (size_t)gc0.tiles, stream));
+            coarse_offsets<<<1, 32, 0, stream>>>(cams, n_views, cfg->tile, coarse->view_first);
+            GS_TRY_LAUNCH();
+        }
         return GS_OK;
     }
     const BinGeom g = bin_geom(n, total_tiles, cfg->tile, (int)mvt);
@@ -1260,19 +1307,25 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     GS_TRY_LAUNCH();
     // at most as many entry x super-tile pairs as pairs: within the capacity
     // whenever the pairs are
-    bin_starts<<<1, SCAN_THREADS, 0, stream>>>(gc, w.ctotal, w.cstart, pair_capacity, w.c_count, w.c_count + 1,
-                                               dev_status);
+    bin_starts<<<1, SCAN_THREADS, 0, stream>>>(gc, w.ctotal, w.cstart, coarse_capacity, coarse_total,
+                                               w.c_count + 1, dev_status);
     GS_TRY_LAUNCH();
     bin_offsets<<<(unsigned)ceil_div(gc.n_g * gc.tiles, (int64_t)256), 256, 0, stream>>>(
         gc, cams, n_views, w.G1c, w.cstart, w.ctotal, w.c_count + 1, w.Mc, nullptr);
     GS_TRY_LAUNCH();
     if (coarse_scatter_wide(gc.max_vt))
         bin_scatter<uint32_t, 16><<<n_cchunks, SC_THREADS, ScatterMask<uint32_t, 16>::bytes_per_tile * gc.max_vt,
-                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.crect);
+                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.cmask);
     else
         bin_scatter<uint32_t, 4><<<n_cchunks, SC_THREADS, ScatterMask<uint32_t, 4>::bytes_per_tile * gc.max_vt,
-                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.crect);
+                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.cmask);
     GS_TRY_LAUNCH();
+    if (co) {
+        tile_ranges<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(
+            total_tiles, w.tile_start, w.tile_total, w.sort_count, w.c_count + 1, reinterpret_cast<uint2 *>(ranges));
+        GS_TRY_LAUNCH();
+        return GS_OK;
+    }
     // placement work items (segments of the super-tiles' lists)
     seg_layout<<<1, SCAN_THREADS, 0, stream>>>(gc.tiles, w.ctotal, w.sort_count, w.seg_base);
     GS_TRY_LAUNCH();
@@ -1282,7 +1335,7 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
     const int64_t resident = (int64_t)device_sm_count() * 8;  // blocks of 8 warps
     const int64_t want = ceil_div(items_cap, (int64_t)(FP_THREADS / 32));
     const unsigned fp_blocks = (unsigned)(want < resident ? (want > 0 ? want : 1) : resident);
-    fine_pass<false><<<fp_blocks, FP_THREADS, 0, stream>>>(w.crect, w.cgid, cams, n_views, gc, w.cstart, w.ctotal,
+    fine_pass<false><<<fp_blocks, FP_THREADS, 0, stream>>>(w.cmask, w.cgid, cams, n_views, gc, w.cstart, w.ctotal,
                                                            w.seg_base, w.item_ct, w.run_of, vals, total_tiles,
                                                            (int)mvt, pair_capacity);
     GS_TRY_LAUNCH();
@@ -1290,7 +1343,7 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
         cams, n_views, gc, total_tiles, (int)mvt, w.tile_start, w.tile_total, w.seg_base, w.sort_count, w.run_of,
         reinterpret_cast<uint2 *>(ranges));
     GS_TRY_LAUNCH();
-    fine_pass<true><<<fp_blocks, FP_THREADS, 0, stream>>>(w.crect, w.cgid, cams, n_views, gc, w.cstart, w.ctotal,
+    fine_pass<true><<<fp_blocks, FP_THREADS, 0, stream>>>(w.cmask, w.cgid, cams, n_views, gc, w.cstart, w.ctotal,
                                                           w.seg_base, w.item_ct, w.run_of, vals, total_tiles,
                                                           (int)mvt, pair_capacity);
     GS_TRY_LAUNCH();
@@ -1300,6 +1353,34 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
         GS_TRY_LAUNCH();
     }
     return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
+                      int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg, void *workspace,
+                      size_t workspace_bytes, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
+                      uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
+    if (!vals) return GS_ERR_INVALID_ARG;
+    return bin_sort_impl(proj, cams, n_views, n, total_tiles, max_view_tiles, cfg, workspace, workspace_bytes, keys,
+                         vals, nullptr, pair_capacity, ranges, dev_pair_count, dev_status, stream);
+}
+
+size_t gs_bin_sort_coarse_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles) {
+    if (n < 0 || n_views <= 0 || total_tiles <= 0) return 0;
+    return bin_ws_layout(n, n_views, total_tiles, 0, nullptr, nullptr, true);
+}
+
+gs_status gs_bin_sort_coarse(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
+                             int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg,
+                             void *workspace, size_t workspace_bytes, const gs_coarse_lists *lists,
+                             int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status,
+                             cudaStream_t stream) {
+    if (!lists) return GS_ERR_INVALID_ARG;
+    return bin_sort_impl(proj, cams, n_views, n, total_tiles, max_view_tiles, cfg, workspace, workspace_bytes,
+                         nullptr, nullptr, lists, pair_capacity, ranges, dev_pair_count, dev_status, stream);
 }
 
 }  // extern "C"

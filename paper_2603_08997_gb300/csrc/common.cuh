@@ -132,6 +132,143 @@ __device__ __forceinline__ uint32_t next_item(uint32_t *queue, uint32_t *s_item)
     return *s_item;
 }
 
+// Where the compositing kernels find a tile's depth-ordered Gaussians.  Tile
+// lists: vals[ranges[tile]].  Super-tile lists (coarse != 0): the binning
+// lists each (view, Gaussian) entry once per super-tile of kSup x kSup tiles
+// its rectangle meets, in depth order, as its Gaussian index and a 16-bit
+// mask of the super-tile's tiles it covers (bit kSup * row + column); a
+// tile's list is the subsequence of its super-tile's list with the tile's
+// bit set, filtered while the kernels stage it (coarse_gather).
+constexpr int kSup = 4;
+struct ListSrc {
+    const uint32_t *vals;      // tile lists
+    const uint32_t *cgid;      // super-tile lists: Gaussian index per entry
+    const uint16_t *cmask;     //   covered tiles per entry
+    const uint32_t *cstart;    //   first entry of each super-tile
+    const uint32_t *ccount;    //   entries of each super-tile
+    const int64_t *cview;      //   first super-tile of each view
+    uint32_t *batch_pos;       //   per checkpoint slot: list position of the batch's first entry
+};
+
+// The ListSrc of a call on super-tile lists (GS_ERR_INVALID_ARG when a buffer is missing).
+inline gs_status coarse_src(const gs_coarse_lists *l, const gs_fwd_saved &s, ListSrc &out) {
+    if (!l || !l->gid || !l->mask || !l->start || !l->count || !l->view_first || !s.batch_pos)
+        return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)l->mask & 15) return GS_ERR_INVALID_ARG;  // read with vector loads
+    out = ListSrc{};
+    out.cgid = l->gid;
+    out.cmask = l->mask;
+    out.cstart = l->start;
+    out.ccount = l->count;
+    out.cview = l->view_first;
+    out.batch_pos = s.batch_pos;
+    return GS_OK;
+}
+
+// The super-tile of tile (tx, ty) of view v (tiles_x tiles per row) and the
+// tile's bit in its masks.
+__device__ __forceinline__ int64_t super_tile_of(const ListSrc &ls, int v, int tiles_x, int tx, int ty,
+                                                 uint32_t &bit) {
+    const int stx = (tiles_x + kSup - 1) / kSup;
+    bit = (uint32_t)((ty % kSup) * kSup + tx % kSup);
+    return ls.cview[v] + (int64_t)(ty / kSup) * stx + tx / kSup;
+}
+
+// Copies the Gaussian indices of the next `want` (or fewer, at the list's
+// end) entries with mask bit `bit` from positions [pos, end) of a super-tile
+// list to out[0..), in list order, and returns how many; pos moves past the
+// last entry taken.  Per round the block's NTH threads test EPT consecutive
+// entries each, from pos rounded down to a multiple of EPT (one vector load
+// of masks per thread; entries before pos or from end on are not taken); a
+// warp scan and the warps' totals in s_wsum[NTH / 32] rank the covered ones.
+// Called by every thread with block-uniform pos, end and want (two barriers
+// per round; the last one also publishes out).  mask must be 16-byte aligned.
+template <int NTH, int EPT>
+__device__ __forceinline__ int coarse_gather(const ListSrc &ls, uint32_t bit, uint32_t &pos, uint32_t end, int want,
+                                             uint32_t *out, uint32_t *s_wsum, uint32_t *s_next) {
+    static_assert(EPT == 1 || EPT == 2 || EPT == 4 || EPT == 8 || EPT == 16, "masks per thread");
+    constexpr int NW = NTH / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int got = 0;
+    while (got < want && pos < end) {
+        const uint32_t a0 = pos & ~(uint32_t)(EPT - 1);
+        const uint32_t base = a0 + (uint32_t)threadIdx.x * EPT;
+        uint16_t mk[EPT];
+        if (base + EPT <= end) {  // whole vector inside the list
+            if constexpr (EPT >= 8) {
+#pragma unroll
+                for (int q = 0; q < EPT / 8; ++q) {
+                    const uint4 x = reinterpret_cast<const uint4 *>(ls.cmask + base)[q];
+                    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        mk[8 * q + 2 * e] = (uint16_t)(w[e] & 0xffffu);
+                        mk[8 * q + 2 * e + 1] = (uint16_t)(w[e] >> 16);
+                    }
+                }
+            } else if constexpr (EPT == 4) {
+                const uint2 x = *reinterpret_cast<const uint2 *>(ls.cmask + base);
+                mk[0] = (uint16_t)(x.x & 0xffffu);
+                mk[1] = (uint16_t)(x.x >> 16);
+                mk[2] = (uint16_t)(x.y & 0xffffu);
+                mk[3] = (uint16_t)(x.y >> 16);
+            } else if constexpr (EPT == 2) {
+                const uint32_t x = *reinterpret_cast<const uint32_t *>(ls.cmask + base);
+                mk[0] = (uint16_t)(x & 0xffffu);
+                mk[1] = (uint16_t)(x >> 16);
+            } else {
+                mk[0] = ls.cmask[base];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) mk[e] = base + e < end ? ls.cmask[base + e] : (uint16_t)0;
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e)
+            if (base + e >= pos && ((mk[e] >> bit) & 1u)) mine |= 1u << e;
+        const int c = __popc(mine);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_wsum[warp] = (uint32_t)inc;
+        __syncthreads();
+        int before = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int x = (int)s_wsum[w];
+            before += w < warp ? x : 0;
+            tot += x;
+        }
+        int r = got + before + inc - c;  // rank of this thread's first covered entry
+        while (mine) {
+            const int e = __ffs(mine) - 1;
+            mine &= mine - 1;
+            if (r < want) {
+                out[r] = ls.cgid[base + e];
+                if (r == want - 1) *s_next = base + e + 1;
+            }
+            ++r;
+        }
+        const bool filled = got + tot >= want;
+        got = filled ? want : got + tot;
+        __syncthreads();
+        const uint32_t step = (uint32_t)NTH * EPT;
+        pos = filled ? *s_next : (end - a0 > step ? a0 + step : end);
+    }
+    return got;
+}
+
+// Masks each thread tests per gathering round: about 1024 list entries per
+// round for a block of NTH threads.
+template <int NTH>
+__host__ __device__ constexpr int gather_ept() {
+    return NTH >= 1024 ? 1 : (NTH >= 512 ? 2 : (NTH >= 256 ? 4 : (NTH >= 128 ? 8 : 16)));
+}
+
 // Eq. (alpha) at one pixel, evaluated through the conic's Cholesky factor U
 // (Q = U^T U): dp^T Q dp = |U dp|^2 with z0 = u00 dx + u01 dy, z1 = u11 dy.
 // A sum of squares keeps the float32 rounding error near eps * sqrt(cond(Q)).

@@ -67,9 +67,9 @@ __device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane, int
     return d;
 }
 
-template <int TILE, int BATCH, int PPT>
+template <int TILE, int BATCH, int PPT, bool COARSE>
 __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
-    const float4 *__restrict__ rec, int64_t n, const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges,
+    const float4 *__restrict__ rec, int64_t n, const ListSrc ls, const uint2 *__restrict__ ranges,
     const gs_camera *__restrict__ cams, int n_views, gs_raster_config cfg, const float *__restrict__ T_final,
     const int32_t *__restrict__ n_last, const float *__restrict__ ckpt, int64_t ckpt_slots,
     const float *__restrict__ dL_dimage, const uint8_t *__restrict__ view_gate, float4 *__restrict__ g2d,
@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     constexpr int NT = TILE * TILE;
     constexpr int NTH = TILE * TILE / PPT;
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
+    constexpr int EPT = gather_ept<NTH>();  // super-tile list entries tested per thread and round
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
     __shared__ float4 s_c[BATCH];
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     __shared__ float s_acc[BATCH][9];
     __shared__ int s_max;
     __shared__ uint32_t s_item;
+    __shared__ uint32_t s_wsum[NW], s_next;
     for (uint32_t item = first_item(queue, &s_item); item < (uint64_t)total_tiles; item = next_item(queue, &s_item)) {
     const int64_t tile = tile_order ? (int64_t)tile_order[item] : (int64_t)item;
     const int v = view_of_tile(cams, n_views, tile);
@@ -98,6 +100,13 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     const int64_t slot0 = (int64_t)(rg.x / BATCH) + tile;
     const float4 *recv = rec + (int64_t)v * n * 3;
     const float amax = cfg.alpha_max, amin = cfg.alpha_min;
+    uint32_t cbit = 0, cend = 0;  // the super-tile list: this tile's bit, the list's end
+    if constexpr (COARSE) {
+        if (rg.y > rg.x) {
+            const int64_t ct = super_tile_of(ls, v, tiles_x, tx, ty, cbit);
+            cend = ls.cstart[ct] + ls.ccount[ct];
+        }
+    }
 
     int lp[PPT], my_last[PPT];
     float px[PPT], py[PPT], dC0[PPT], dC1[PPT], dC2[PPT], T_end[PPT];
@@ -141,11 +150,16 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
         __syncthreads();
         const int64_t b0 = (int64_t)rg.x + (int64_t)b * BATCH;
         const int cnt = (int)min((int64_t)BATCH, (int64_t)rg.y - b0);
+        if constexpr (COARSE) {  // the batch's indices from the list, from where the forward pass began it
+            const int64_t slot = slot0 + b;
+            uint32_t pos = slot < ckpt_slots ? ls.batch_pos[slot] : cend;
+            coarse_gather<NTH, EPT>(ls, cbit, pos, cend, cnt, s_g, s_wsum, &s_next);
+        }
         for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
             const bool valid = kk < cnt;
             float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
             if (valid) {
-                const uint32_t g = vals[b0 + kk];
+                const uint32_t g = COARSE ? s_g[kk] : ls.vals[b0 + kk];
                 const float4 *r = recv + (int64_t)g * 3;
                 ra = r[0];
                 rc = r[2];
@@ -610,10 +624,25 @@ __global__ void __launch_bounds__(PB) proj_bwd_kernel(gs_params prm, const gs_ca
     }
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool CO>
+using BwdKernel = decltype(&render_bwd_kernel<TILE, 64, PPT, CO>);
+
+template <int TILE, int PPT, bool CO>
+BwdKernel<TILE, PPT, CO> bwd_kernel(int batch) {
+    switch (batch) {
+        case 64: return render_bwd_kernel<TILE, 64, PPT, CO>;
+        case 128: return render_bwd_kernel<TILE, 128, PPT, CO>;
+        case 256: return render_bwd_kernel<TILE, 256, PPT, CO>;
+        default: return nullptr;
+    }
+}
+
+template <int TILE, int PPT, bool CO>
 gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
-                     const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                     const ListSrc &ls, const uint2 *ranges, const gs_camera *cams, int n_views,
                      const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate, float4 *g2d) {
+    const auto kernel = bwd_kernel<TILE, PPT, CO>(batch);
+    if (!kernel) return GS_ERR_UNSUPPORTED;
     dim3 grid((unsigned)total_tiles);
     constexpr int NTH = TILE * TILE / PPT;
     if (s.queue) {  // persistent: the resident blocks (cached per device and staging batch size)
@@ -623,46 +652,27 @@ gs_status launch_bwd(int batch, int64_t total_tiles, cudaStream_t stream, const 
         if (dev < 0) return GS_ERR_UNSUPPORTED;
         if (resident[bi][dev] <= 0) {
             int per_sm = 0;
-            if (batch == 64)
-                GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TILE, 64, PPT>, NTH, 0));
-            else if (batch == 128)
-                GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TILE, 128, PPT>, NTH, 0));
-            else
-                GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TILE, 256, PPT>, NTH, 0));
+            GS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NTH, 0));
             resident[bi][dev] = (per_sm > 0 ? per_sm : 1) * device_sm_count();
         }
         if ((int64_t)resident[bi][dev] < total_tiles) grid = dim3((unsigned)resident[bi][dev]);
         GS_TRY(cudaMemsetAsync(s.queue, 0, sizeof(uint32_t), stream));
     }
-    switch (batch) {
-        case 64:
-            render_bwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                      s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order, s.queue, total_tiles);
-            break;
-        case 128:
-            render_bwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order, s.queue, total_tiles);
-            break;
-        case 256:
-            render_bwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, s.T_final,
-                                                                       s.n_last, s.ckpt, s.ckpt_slots, dL, gate, g2d, s.tile_order, s.queue, total_tiles);
-            break;
-        default:
-            return GS_ERR_UNSUPPORTED;
-    }
+    kernel<<<grid, NTH, 0, stream>>>(rec, n, ls, ranges, cams, n_views, cfg, s.T_final, s.n_last, s.ckpt, s.ckpt_slots,
+                                     dL, gate, g2d, s.tile_order, s.queue, total_tiles);
     GS_TRY_LAUNCH();
     return GS_OK;
 }
 
-template <int TILE>
+template <int TILE, bool CO>
 gs_status launch_bwd_ppt(int ppt, int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
-                         const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                         const ListSrc &ls, const uint2 *ranges, const gs_camera *cams, int n_views,
                          const gs_raster_config &cfg, gs_fwd_saved s, const float *dL, const uint8_t *gate,
                          float4 *g2d) {
     if constexpr (TILE >= 16)
-        if (ppt == 4) return launch_bwd<TILE, 4>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
-    if (ppt == 2) return launch_bwd<TILE, 2>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
-    return launch_bwd<TILE, 1>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, s, dL, gate, g2d);
+        if (ppt == 4) return launch_bwd<TILE, 4, CO>(batch, total_tiles, stream, rec, n, ls, ranges, cams, n_views, cfg, s, dL, gate, g2d);
+    if (ppt == 2) return launch_bwd<TILE, 2, CO>(batch, total_tiles, stream, rec, n, ls, ranges, cams, n_views, cfg, s, dL, gate, g2d);
+    return launch_bwd<TILE, 1, CO>(batch, total_tiles, stream, rec, n, ls, ranges, cams, n_views, cfg, s, dL, gate, g2d);
 }
 
 template <int DEG, int MODE>
@@ -703,21 +713,27 @@ bool proj_params_aligned(const gs_params &p) {
               (uintptr_t)p.sh) & 15);
 }
 
-// Raster adjoint: zero the per-view 2D gradient buffer, then one CTA per tile.
-gs_status raster_bwd_impl(int64_t n, const gs_projected *proj, const uint32_t *vals, const uint32_t *ranges,
-                          const gs_camera *cams, int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg,
-                          gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate, float4 *g2d,
-                          cudaStream_t stream) {
+// Raster adjoint: zero the per-view 2D gradient buffer, then one CTA per tile
+// (tile lists, or super-tile lists when coarse).
+gs_status raster_bwd_impl(int64_t n, const gs_projected *proj, const ListSrc &ls, bool coarse,
+                          const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                          const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                          const uint8_t *view_gate, float4 *g2d, cudaStream_t stream) {
+    const int ppt = cfg->pixels_per_thread, b = cfg->batch;
+    if (ppt != 1 && ppt != 2 && ppt != 4) return GS_ERR_INVALID_ARG;
+    if (ppt == 4 && cfg->tile < 16) return GS_ERR_INVALID_ARG;  // a warp needs 8 x 16 pixels
+    if (b != 64 && b != 128 && b != 256) return GS_ERR_UNSUPPORTED;
+    if (cfg->tile != 8 && cfg->tile != 16 && cfg->tile != 32) return GS_ERR_INVALID_ARG;
     GS_TRY(cudaMemsetAsync(g2d, 0, sizeof(float) * kG2d * (size_t)n * n_views, stream));
     const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
     const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2 && cfg->pixels_per_thread != 4) return GS_ERR_INVALID_ARG;
-    if (cfg->pixels_per_thread == 4 && cfg->tile < 16) return GS_ERR_INVALID_ARG;  // a warp needs 8 x 16 pixels
-    switch (cfg->tile) {
-        case 8: return launch_bwd_ppt<8>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
-        case 16: return launch_bwd_ppt<16>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
-        case 32: return launch_bwd_ppt<32>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
-        default: return GS_ERR_INVALID_ARG;
+    switch (cfg->tile * 2 + (coarse ? 1 : 0)) {
+        case 16: return launch_bwd_ppt<8, false>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 17: return launch_bwd_ppt<8, true>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 32: return launch_bwd_ppt<16, false>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 33: return launch_bwd_ppt<16, true>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        case 64: return launch_bwd_ppt<32, false>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
+        default: return launch_bwd_ppt<32, true>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, saved, dL_dimage, view_gate, g2d);
     }
 }
 
@@ -745,14 +761,14 @@ gs_status project_bwd_impl(const gs_params *params, const gs_camera *cams, int32
 }
 
 template <bool FUSED>
-gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
+gs_status render_bwd_impl(const gs_params *params, const gs_projected *proj, const ListSrc &ls, bool coarse,
                           const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
                           const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
                           const uint8_t *view_gate, gs_grads grads, int32_t accumulate, const AdamFuse &af,
                           void *workspace, cudaStream_t stream) {
     float4 *g2d = reinterpret_cast<float4 *>(workspace);
-    gs_status st = raster_bwd_impl(params->n, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
-                                   view_gate, g2d, stream);
+    gs_status st = raster_bwd_impl(params->n, proj, ls, coarse, ranges, cams, n_views, total_tiles, cfg, saved,
+                                   dL_dimage, view_gate, g2d, stream);
     if (st != GS_OK) return st;
     return project_bwd_impl<FUSED>(params, cams, n_views, cfg, g2d, view_gate, grads, accumulate, af, stream);
 }
@@ -766,13 +782,16 @@ size_t gs_render_bwd_workspace_size(int64_t n, int32_t n_views) {
     return sizeof(float) * kG2d * (size_t)(n > 0 ? n : 1) * (size_t)n_views;
 }
 
-gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
-                        const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
-                        const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
-                        const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
-                        size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
-    (void)dev_status;
-    if (!params || !proj || !cfg || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0)
+}  // extern "C"
+
+namespace {
+
+gs_status render_bwd_entry(const gs_params *params, const gs_projected *proj, const ListSrc &ls, bool coarse,
+                           const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                           const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                           const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
+                           size_t workspace_bytes, cudaStream_t stream) {
+    if (!params || !proj || !cfg || !cams || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0)
         return GS_ERR_INVALID_ARG;
     if (params->n < 0 || params->n >= ((int64_t)1 << 31) || params->sh_degree < 0 || params->sh_degree > 3 ||
         cfg->sh_degree != params->sh_degree)
@@ -785,8 +804,53 @@ gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const
     if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
     if (n == 0) return GS_OK;
     AdamFuse af{};
-    return render_bwd_impl<false>(params, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
-                                  view_gate, grads, accumulate, af, workspace, stream);
+    return render_bwd_impl<false>(params, proj, ls, coarse, ranges, cams, n_views, total_tiles, cfg, saved,
+                                  dL_dimage, view_gate, grads, accumulate, af, workspace, stream);
+}
+
+gs_status raster_bwd_entry(const gs_projected *proj, int64_t n, const ListSrc &ls, bool coarse,
+                           const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                           const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                           const uint8_t *view_gate, float *g2d, size_t g2d_bytes, cudaStream_t stream) {
+    if (!proj || !cfg || !cams || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0 || n < 0 ||
+        n >= ((int64_t)1 << 31))
+        return GS_ERR_INVALID_ARG;
+    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
+    if (!g2d || g2d_bytes < gs_render_bwd_workspace_size(n, n_views) || ((uintptr_t)g2d & 15)) return GS_ERR_WORKSPACE;
+    if (n == 0) return GS_OK;
+    return raster_bwd_impl(n, proj, ls, coarse, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage, view_gate,
+                           reinterpret_cast<float4 *>(g2d), stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_render_bwd(const gs_params *params, const gs_projected *proj, const uint32_t *vals,
+                        const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                        const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                        const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
+                        size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    if (!vals) return GS_ERR_INVALID_ARG;
+    ListSrc ls{};
+    ls.vals = vals;
+    return render_bwd_entry(params, proj, ls, false, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
+                            view_gate, grads, accumulate, workspace, workspace_bytes, stream);
+}
+
+gs_status gs_render_bwd_coarse(const gs_params *params, const gs_projected *proj, const gs_coarse_lists *lists,
+                               const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                               const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                               const uint8_t *view_gate, gs_grads grads, int32_t accumulate, void *workspace,
+                               size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    ListSrc ls{};
+    const gs_status st = coarse_src(lists, saved, ls);
+    if (st != GS_OK) return st;
+    return render_bwd_entry(params, proj, ls, true, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
+                            view_gate, grads, accumulate, workspace, workspace_bytes, stream);
 }
 
 gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, const uint32_t *vals, const uint32_t *ranges,
@@ -794,15 +858,24 @@ gs_status gs_raster_bwd(const gs_projected *proj, int64_t n, const uint32_t *val
                         gs_fwd_saved saved, const float *dL_dimage, const uint8_t *view_gate, float *g2d,
                         size_t g2d_bytes, int32_t *dev_status, cudaStream_t stream) {
     (void)dev_status;
-    if (!proj || !cfg || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0 || n < 0 ||
-        n >= ((int64_t)1 << 31))
-        return GS_ERR_INVALID_ARG;
-    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
-    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
-    if (!g2d || g2d_bytes < gs_render_bwd_workspace_size(n, n_views) || ((uintptr_t)g2d & 15)) return GS_ERR_WORKSPACE;
-    if (n == 0) return GS_OK;
-    return raster_bwd_impl(n, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage, view_gate,
-                           reinterpret_cast<float4 *>(g2d), stream);
+    if (!vals) return GS_ERR_INVALID_ARG;
+    ListSrc ls{};
+    ls.vals = vals;
+    return raster_bwd_entry(proj, n, ls, false, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage, view_gate,
+                            g2d, g2d_bytes, stream);
+}
+
+gs_status gs_raster_bwd_coarse(const gs_projected *proj, int64_t n, const gs_coarse_lists *lists,
+                               const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                               const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                               const uint8_t *view_gate, float *g2d, size_t g2d_bytes, int32_t *dev_status,
+                               cudaStream_t stream) {
+    (void)dev_status;
+    ListSrc ls{};
+    const gs_status st = coarse_src(lists, saved, ls);
+    if (st != GS_OK) return st;
+    return raster_bwd_entry(proj, n, ls, true, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage, view_gate,
+                            g2d, g2d_bytes, stream);
 }
 
 gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views, const gs_raster_config *cfg,
@@ -851,6 +924,32 @@ static gs_status fused_args(float *flat_params, float *m, float *v, int64_t n, i
     return GS_OK;
 }
 
+}  // extern "C"
+
+static gs_status render_bwd_adam_entry(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                                       const gs_projected *proj, const ListSrc &ls, bool coarse,
+                                       const uint32_t *ranges, const gs_camera *cams, int32_t n_views,
+                                       int64_t total_tiles, const gs_raster_config *cfg, gs_fwd_saved saved,
+                                       const float *dL_dimage, const uint8_t *view_gate, const gs_adam_config *adam,
+                                       const int32_t *dev_do_step, int64_t *dev_step, double *norms2,
+                                       void *workspace, size_t workspace_bytes, cudaStream_t stream) {
+    gs_params prm;
+    AdamFuse af;
+    gs_status st = fused_args(flat_params, m, v, n, sh_degree, cfg, adam, dev_do_step, dev_step, norms2, &prm, &af);
+    if (st != GS_OK) return st;
+    if (!proj || !cams || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0) return GS_ERR_INVALID_ARG;
+    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
+    if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
+    if (n == 0) return GS_OK;
+    gs_grads none{};
+    return render_bwd_impl<true>(&prm, proj, ls, coarse, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
+                                 view_gate, none, 0, af, workspace, stream);
+}
+
+extern "C" {
+
 gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
                              const gs_projected *proj, const uint32_t *vals, const uint32_t *ranges,
                              const gs_camera *cams, int32_t n_views, int64_t total_tiles, const gs_raster_config *cfg,
@@ -859,19 +958,28 @@ gs_status gs_render_bwd_adam(float *flat_params, float *m, float *v, int64_t n, 
                              double *norms2, void *workspace, size_t workspace_bytes, int32_t *dev_status,
                              cudaStream_t stream) {
     (void)dev_status;
-    gs_params prm;
-    AdamFuse af;
-    gs_status st = fused_args(flat_params, m, v, n, sh_degree, cfg, adam, dev_do_step, dev_step, norms2, &prm, &af);
+    if (!vals) return GS_ERR_INVALID_ARG;
+    ListSrc ls{};
+    ls.vals = vals;
+    return render_bwd_adam_entry(flat_params, m, v, n, sh_degree, proj, ls, false, ranges, cams, n_views, total_tiles,
+                                 cfg, saved, dL_dimage, view_gate, adam, dev_do_step, dev_step, norms2, workspace,
+                                 workspace_bytes, stream);
+}
+
+gs_status gs_render_bwd_adam_coarse(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,
+                                    const gs_projected *proj, const gs_coarse_lists *lists, const uint32_t *ranges,
+                                    const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                                    const gs_raster_config *cfg, gs_fwd_saved saved, const float *dL_dimage,
+                                    const uint8_t *view_gate, const gs_adam_config *adam,
+                                    const int32_t *dev_do_step, int64_t *dev_step, double *norms2, void *workspace,
+                                    size_t workspace_bytes, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    ListSrc ls{};
+    const gs_status st = coarse_src(lists, saved, ls);
     if (st != GS_OK) return st;
-    if (!proj || !cams || !vals || !ranges || !dL_dimage || n_views <= 0 || total_tiles <= 0) return GS_ERR_INVALID_ARG;
-    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
-    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < gs_render_bwd_workspace_size(n, n_views)) return GS_ERR_WORKSPACE;
-    if ((uintptr_t)workspace & 15) return GS_ERR_WORKSPACE;
-    if (n == 0) return GS_OK;
-    gs_grads none{};
-    return render_bwd_impl<true>(&prm, proj, vals, ranges, cams, n_views, total_tiles, cfg, saved, dL_dimage,
-                                 view_gate, none, 0, af, workspace, stream);
+    return render_bwd_adam_entry(flat_params, m, v, n, sh_degree, proj, ls, true, ranges, cams, n_views, total_tiles,
+                                 cfg, saved, dL_dimage, view_gate, adam, dev_do_step, dev_step, norms2, workspace,
+                                 workspace_bytes, stream);
 }
 
 gs_status gs_project_bwd_adam(float *flat_params, float *m, float *v, int64_t n, int32_t sh_degree,

@@ -12,15 +12,22 @@
 //   slot(tile, b) = floor(range_start / BATCH) + tile + b
 // (TILE * TILE floats, row-major over the tile's pixels), which the backward pass uses to rebuild T without dividing across batches.
 // The CTA stops as soon as every pixel has hit the transmittance floor.
+//
+// Super-tile form (COARSE): the tile's Gaussian indices come from its
+// super-tile's depth-ordered list, filtered by the tile's mask bit while the
+// batches are gathered (coarse_gather, one batch ahead of the record copies);
+// the batches, and so every output, are the same as with the tile's own list.
+// The list position of each batch's first entry goes to batch_pos at the
+// batch's checkpoint slot, for the adjoint.
 #include "common.cuh"
 
 using namespace gsr;
 
 namespace {
 
-template <int TILE, int BATCH, int PPT>
+template <int TILE, int BATCH, int PPT, bool COARSE>
 __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const float4 *__restrict__ rec, int64_t n,
-                                                                       const uint32_t *__restrict__ vals,
+                                                                       const ListSrc ls,
                                                                        const uint2 *__restrict__ ranges,
                                                                        const gs_camera *__restrict__ cams, int n_views,
                                                                        gs_raster_config cfg, float *__restrict__ image,
@@ -33,11 +40,14 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
     constexpr int NTH = TILE * TILE / PPT; // threads
     constexpr int NW = NTH / 32, NWORD = BATCH / 32;
     constexpr int R = (BATCH + NTH - 1) / NTH;  // batch slots per thread
+    constexpr int EPT = gather_ept<NTH>();  // super-tile list entries tested per thread and round
     __shared__ float4 s_a[2][BATCH];  // double buffer: batch b + 1 arrives while batch b is composited
     __shared__ float4 s_b[2][BATCH];
     __shared__ float4 s_c[2][BATCH];
     __shared__ uint32_t s_ov[NW][NWORD];  // per warp: records of the batch that reach its pixel block
     __shared__ uint32_t s_item;
+    __shared__ uint32_t s_idx[COARSE ? BATCH : 1];  // a gathered batch's Gaussian indices
+    __shared__ uint32_t s_wsum[NW], s_next;
     for (uint32_t item = first_item(queue, &s_item); item < (uint64_t)total_tiles; item = next_item(queue, &s_item)) {
     const int64_t tile = tile_order ? (int64_t)tile_order[item] : (int64_t)item;
     const int v = view_of_tile(cams, n_views, tile);
@@ -74,13 +84,37 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
     for (int k = 0; k < PPT; ++k) {
         T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0; done[k] = !inside[k];
     }
-    // Gaussian indices of this thread's slots of batch bb (0xffffffff past the list)
+    // the super-tile list: this tile's bit and the list's unread part
+    uint32_t cbit = 0, cpos = 0, cend = 0;
+    if constexpr (COARSE) {
+        if (len > 0) {
+            const int64_t ct = super_tile_of(ls, v, tiles_x, tx, ty, cbit);
+            cpos = ls.cstart[ct];
+            cend = cpos + ls.ccount[ct];
+        }
+    }
+    // Gaussian indices of this thread's slots of batch bb (0xffffffff past the
+    // list); batches are requested in order 0, 1, 2, ... (the super-tile form
+    // gathers them with the whole block: uniform calls only)
     auto load_index = [&](int64_t bb, uint32_t (&gi)[R]) {
-        const int64_t b0 = (int64_t)rg.x + bb * BATCH;
+        if constexpr (COARSE) {
+            int got = 0;
+            if (bb < nb) {
+                if (threadIdx.x == 0 && slot0 + bb < ckpt_slots) ls.batch_pos[slot0 + bb] = cpos;
+                got = coarse_gather<NTH, EPT>(ls, cbit, cpos, cend, BATCH, s_idx, s_wsum, &s_next);
+            }
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int kk = threadIdx.x + r * NTH;
-            gi[r] = (bb < nb && kk < BATCH && b0 + kk < (int64_t)rg.y) ? vals[b0 + kk] : 0xffffffffu;
+            for (int r = 0; r < R; ++r) {
+                const int kk = threadIdx.x + r * NTH;
+                gi[r] = (kk < got) ? s_idx[kk] : 0xffffffffu;
+            }
+        } else {
+            const int64_t b0 = (int64_t)rg.x + bb * BATCH;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int kk = threadIdx.x + r * NTH;
+                gi[r] = (bb < nb && kk < BATCH && b0 + kk < (int64_t)rg.y) ? ls.vals[b0 + kk] : 0xffffffffu;
+            }
         }
     };
     // start the copies of this thread's records of a batch into buffer buf
@@ -97,10 +131,14 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
         }
         cp_async_commit();
     };
+    // Tile lists: the indices of batch b + 2 load while batch b composites,
+    // the records of batch b + 1 copy meanwhile.  Super-tile lists: batch b + 1
+    // is gathered (a block-wide step) and its copies issued at the start of
+    // batch b, so no batch past the one that finishes the tile is gathered.
     uint32_t gi[R];
     load_index(0, gi);
     issue(gi, 0);
-    load_index(1, gi);  // indices of the next batch, one batch ahead of its copies
+    if constexpr (!COARSE) load_index(1, gi);  // indices of the next batch, one batch ahead of its copies
     for (int64_t b = 0; b < nb; ++b) {
         bool all_done = true;
 #pragma unroll
@@ -113,8 +151,13 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
         }
         const int buf = (int)(b & 1);
         if (b + 1 < nb) {
-            issue(gi, buf ^ 1);
-            load_index(b + 2, gi);
+            if constexpr (COARSE) {
+                load_index(b + 1, gi);
+                issue(gi, buf ^ 1);
+            } else {
+                issue(gi, buf ^ 1);
+                load_index(b + 2, gi);
+            }
             cp_async_wait<1>();  // this thread's copies of batch b have landed
         } else {
             cp_async_wait<0>();
@@ -196,50 +239,73 @@ gs_status item_grid(K kernel, int threads, int64_t total_tiles, bool persistent,
     return GS_OK;
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool CO>
+using FwdKernel = decltype(&render_fwd_kernel<TILE, 64, PPT, CO>);
+
+template <int TILE, int PPT, bool CO>
+FwdKernel<TILE, PPT, CO> fwd_kernel(int batch) {
+    switch (batch) {
+        case 64: return render_fwd_kernel<TILE, 64, PPT, CO>;
+        case 128: return render_fwd_kernel<TILE, 128, PPT, CO>;
+        case 256: return render_fwd_kernel<TILE, 256, PPT, CO>;
+        default: return nullptr;
+    }
+}
+
+template <int TILE, int PPT, bool CO>
 gs_status launch_fwd(int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
-                     const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                     const ListSrc &ls, const uint2 *ranges, const gs_camera *cams, int n_views,
                      const gs_raster_config &cfg, float *image, gs_fwd_saved s) {
-    dim3 grid;
+    const auto kernel = fwd_kernel<TILE, PPT, CO>(batch);
+    if (!kernel) return GS_ERR_UNSUPPORTED;
     constexpr int NTH = TILE * TILE / PPT;
     static int resident[3][kMaxDevices] = {};  // per staging batch size
-    {
-        const int bi = batch == 64 ? 0 : (batch == 128 ? 1 : 2);
-        gs_status st = GS_OK;
-        if (batch == 64) st = item_grid(render_fwd_kernel<TILE, 64, PPT>, NTH, total_tiles, s.queue, resident[bi], grid);
-        else if (batch == 128) st = item_grid(render_fwd_kernel<TILE, 128, PPT>, NTH, total_tiles, s.queue, resident[bi], grid);
-        else st = item_grid(render_fwd_kernel<TILE, 256, PPT>, NTH, total_tiles, s.queue, resident[bi], grid);
-        if (st != GS_OK) return st;
-    }
+    const int bi = batch == 64 ? 0 : (batch == 128 ? 1 : 2);
+    dim3 grid;
+    const gs_status st = item_grid(kernel, NTH, total_tiles, s.queue, resident[bi], grid);
+    if (st != GS_OK) return st;
     if (s.queue) GS_TRY(cudaMemsetAsync(s.queue, 0, sizeof(uint32_t), stream));
-    switch (batch) {
-        case 64:
-            render_fwd_kernel<TILE, 64, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                      s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order, s.queue, total_tiles);
-            break;
-        case 128:
-            render_fwd_kernel<TILE, 128, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order, s.queue, total_tiles);
-            break;
-        case 256:
-            render_fwd_kernel<TILE, 256, PPT><<<grid, NTH, 0, stream>>>(rec, n, vals, ranges, cams, n_views, cfg, image,
-                                                                       s.T_final, s.n_last, s.ckpt, s.ckpt_slots, s.tile_order, s.queue, total_tiles);
-            break;
-        default:
-            return GS_ERR_UNSUPPORTED;
-    }
+    kernel<<<grid, NTH, 0, stream>>>(rec, n, ls, ranges, cams, n_views, cfg, image, s.T_final, s.n_last, s.ckpt,
+                                     s.ckpt_slots, s.tile_order, s.queue, total_tiles);
     GS_TRY_LAUNCH();
     return GS_OK;
 }
 
-template <int TILE>
+template <int TILE, bool CO>
 gs_status launch_fwd_ppt(int ppt, int batch, int64_t total_tiles, cudaStream_t stream, const float4 *rec, int64_t n,
-                         const uint32_t *vals, const uint2 *ranges, const gs_camera *cams, int n_views,
+                         const ListSrc &ls, const uint2 *ranges, const gs_camera *cams, int n_views,
                          const gs_raster_config &cfg, float *image, gs_fwd_saved s) {
     if constexpr (TILE >= 16)
-        if (ppt == 4) return launch_fwd<TILE, 4>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
-    if (ppt == 2) return launch_fwd<TILE, 2>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
-    return launch_fwd<TILE, 1>(batch, total_tiles, stream, rec, n, vals, ranges, cams, n_views, cfg, image, s);
+        if (ppt == 4) return launch_fwd<TILE, 4, CO>(batch, total_tiles, stream, rec, n, ls, ranges, cams, n_views, cfg, image, s);
+    if (ppt == 2) return launch_fwd<TILE, 2, CO>(batch, total_tiles, stream, rec, n, ls, ranges, cams, n_views, cfg, image, s);
+    return launch_fwd<TILE, 1, CO>(batch, total_tiles, stream, rec, n, ls, ranges, cams, n_views, cfg, image, s);
+}
+
+gs_status render_fwd_impl(const gs_projected *proj, int64_t n, const ListSrc &ls, bool coarse,
+                          const uint32_t *ranges, const gs_camera *cams, int32_t n_views, int64_t total_tiles,
+                          const gs_raster_config *cfg, float *image, gs_fwd_saved saved, cudaStream_t stream) {
+    if (!proj || !cfg || !cams || !ranges || !image || n_views <= 0 || n < 0 || total_tiles <= 0)
+        return GS_ERR_INVALID_ARG;
+    if (total_tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
+    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
+    if (n > 0 && !proj->rec) return GS_ERR_INVALID_ARG;
+    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
+    const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
+    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+    const int ppt = cfg->pixels_per_thread;
+    if (ppt != 1 && ppt != 2 && ppt != 4) return GS_ERR_INVALID_ARG;
+    if (ppt == 4 && cfg->tile < 16) return GS_ERR_INVALID_ARG;  // a warp needs 8 x 16 pixels
+    if (cfg->batch != 64 && cfg->batch != 128 && cfg->batch != 256) return GS_ERR_UNSUPPORTED;
+    const int b = cfg->batch;
+    switch (cfg->tile * 2 + (coarse ? 1 : 0)) {
+        case 16: return launch_fwd_ppt<8, false>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, image, saved);
+        case 17: return launch_fwd_ppt<8, true>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, image, saved);
+        case 32: return launch_fwd_ppt<16, false>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, image, saved);
+        case 33: return launch_fwd_ppt<16, true>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, image, saved);
+        case 64: return launch_fwd_ppt<32, false>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, image, saved);
+        case 65: return launch_fwd_ppt<32, true>(ppt, b, total_tiles, stream, rec, n, ls, rg, cams, n_views, *cfg, image, saved);
+        default: return GS_ERR_INVALID_ARG;
+    }
 }
 
 }  // namespace
@@ -249,20 +315,19 @@ extern "C" gs_status gs_render_fwd(const gs_projected *proj, int64_t n, const ui
                                    const gs_raster_config *cfg, float *image, gs_fwd_saved saved,
                                    int32_t *dev_status, cudaStream_t stream) {
     (void)dev_status;
-    if (!proj || !cfg || !cams || !vals || !ranges || !image || n_views <= 0 || n < 0 || total_tiles <= 0)
-        return GS_ERR_INVALID_ARG;
-    if (total_tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
-    if (!saved.T_final || !saved.n_last || !saved.ckpt || saved.ckpt_slots <= 0) return GS_ERR_INVALID_ARG;
-    if (n > 0 && !proj->rec) return GS_ERR_INVALID_ARG;
-    if ((uintptr_t)proj->rec & 15) return GS_ERR_INVALID_ARG;
-    const float4 *rec = reinterpret_cast<const float4 *>(proj->rec);
-    const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-    if (cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2 && cfg->pixels_per_thread != 4) return GS_ERR_INVALID_ARG;
-    if (cfg->pixels_per_thread == 4 && cfg->tile < 16) return GS_ERR_INVALID_ARG;  // a warp needs 8 x 16 pixels
-    switch (cfg->tile) {
-        case 8: return launch_fwd_ppt<8>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
-        case 16: return launch_fwd_ppt<16>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
-        case 32: return launch_fwd_ppt<32>(cfg->pixels_per_thread, cfg->batch, total_tiles, stream, rec, n, vals, rg, cams, n_views, *cfg, image, saved);
-        default: return GS_ERR_INVALID_ARG;
-    }
+    if (!vals) return GS_ERR_INVALID_ARG;
+    ListSrc ls{};
+    ls.vals = vals;
+    return render_fwd_impl(proj, n, ls, false, ranges, cams, n_views, total_tiles, cfg, image, saved, stream);
+}
+
+extern "C" gs_status gs_render_fwd_coarse(const gs_projected *proj, int64_t n, const gs_coarse_lists *lists,
+                                          const uint32_t *ranges, const gs_camera *cams, int32_t n_views,
+                                          int64_t total_tiles, const gs_raster_config *cfg, float *image,
+                                          gs_fwd_saved saved, int32_t *dev_status, cudaStream_t stream) {
+    (void)dev_status;
+    ListSrc ls{};
+    const gs_status st = coarse_src(lists, saved, ls);
+    if (st != GS_OK) return st;
+    return render_fwd_impl(proj, n, ls, true, ranges, cams, n_views, total_tiles, cfg, image, saved, stream);
 }

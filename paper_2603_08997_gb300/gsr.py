@@ -52,7 +52,12 @@ class gs_projected(C.Structure):
 
 class gs_fwd_saved(C.Structure):
     _fields_ = [("T_final", C.c_void_p), ("n_last", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_slots", C.c_int64),
-                ("tile_order", C.c_void_p), ("queue", C.c_void_p)]
+                ("tile_order", C.c_void_p), ("queue", C.c_void_p), ("batch_pos", C.c_void_p)]
+
+
+class gs_coarse_lists(C.Structure):
+    _fields_ = [("gid", C.c_void_p), ("mask", C.c_void_p), ("start", C.c_void_p), ("count", C.c_void_p),
+                ("view_first", C.c_void_p), ("total", C.c_void_p), ("capacity", C.c_int64)]
 
 
 class gs_adam_config(C.Structure):
@@ -95,7 +100,21 @@ _PROTOS = {
                               _P, _P, _I64, _P, _P, _P, _S]),
     "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config),
                                       _P, _P, _I64, _P, _P, _P, _S]),
+    "gs_bin_sort_coarse_workspace_size": (C.c_size_t, [_I64, _I32, _I64]),
+    "gs_bin_sort_coarse": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config),
+                                     _P, _SZ, C.POINTER(gs_coarse_lists), _I64, _P, _P, _P, _S]),
     "gs_tile_order": (C.c_int, [_P, _I64, _P, _S]),
+    "gs_render_fwd_coarse": (C.c_int, [C.POINTER(gs_projected), _I64, C.POINTER(gs_coarse_lists), _P, _P, _I32, _I64,
+                                       C.POINTER(gs_raster_config), _P, gs_fwd_saved, _P, _S]),
+    "gs_render_bwd_coarse": (C.c_int, [C.POINTER(gs_params), C.POINTER(gs_projected), C.POINTER(gs_coarse_lists), _P,
+                                       _P, _I32, _I64, C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, gs_grads,
+                                       _I32, _P, _SZ, _P, _S]),
+    "gs_raster_bwd_coarse": (C.c_int, [C.POINTER(gs_projected), _I64, C.POINTER(gs_coarse_lists), _P, _P, _I32, _I64,
+                                       C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P, _P, _SZ, _P, _S]),
+    "gs_render_bwd_adam_coarse": (C.c_int, [_P, _P, _P, _I64, _I32, C.POINTER(gs_projected),
+                                            C.POINTER(gs_coarse_lists), _P, _P, _I32, _I64,
+                                            C.POINTER(gs_raster_config), gs_fwd_saved, _P, _P,
+                                            C.POINTER(gs_adam_config), _P, _P, _P, _P, _SZ, _P, _S]),
     "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), _I64, _P, _P, _P, _I32, _I64, C.POINTER(gs_raster_config),
                                 _P, gs_fwd_saved, _P, _S]),
     "gs_loss_workspace_size": (C.c_size_t, [C.POINTER(gs_camera), _I32]),

@@ -33,6 +33,9 @@ class RasterSettings:
     pixels_per_thread_fwd: int = 1  # forward compositing
     longest_tiles_first: bool = True  # launch tiles by descending list length (gs_tile_order)
     persistent: bool = False  # compositing kernels as a persistent grid taking tiles from a device queue
+    # the binning writes super-tile lists (gs_bin_sort_coarse) and the compositing
+    # kernels filter each tile's entries from them (the *_coarse calls)
+    coarse_lists: bool = False
 
     def struct(self, sh_degree: int) -> gsr.gs_raster_config:
         c = gsr.gs_raster_config()
@@ -131,7 +134,8 @@ class Renderer:
     """All per-view buffers of one rasterization pipeline over `views`."""
 
     def __init__(self, n: int, sh_degree: int, views: Views, settings: RasterSettings | None = None,
-                 pair_capacity: int | None = None, device="cuda", keep_keys: bool = False):
+                 pair_capacity: int | None = None, device="cuda", keep_keys: bool = False,
+                 coarse_capacity: int | None = None):
         self.s = settings or RasterSettings()
         self.n, self.sh_degree, self.views = int(n), int(sh_degree), views
         # True when the device cameras are chosen on the device (slots filled by
@@ -153,7 +157,22 @@ class Renderer:
         self.depth_key = torch.empty(V * n, dtype=torch.int32, device=dev)
         self.rect16 = torch.empty(V * n * 4, dtype=torch.int16, device=dev)
         self.aux_valid = False
-        self.vals = torch.empty(max(self.cap, 1), dtype=torch.int32, device=dev)
+        self.coarse = bool(self.s.coarse_lists)
+        if self.coarse:  # super-tile lists (at most one entry per pair)
+            self.ccap = int(coarse_capacity) if coarse_capacity is not None else self.cap
+            n_st = T // 4 + V
+            self.c_gid = torch.empty(max(self.ccap, 1), dtype=torch.int32, device=dev)
+            self.c_mask = torch.empty(max(self.ccap, 1), dtype=torch.int16, device=dev)
+            self.c_start = torch.empty(n_st, dtype=torch.int32, device=dev)
+            self.c_count = torch.zeros(n_st, dtype=torch.int32, device=dev)
+            self.c_view_first = torch.empty(V + 1, dtype=torch.int64, device=dev)
+            self.c_total = torch.zeros(1, dtype=torch.int64, device=dev)
+            self.lists = gsr.gs_coarse_lists(self.c_gid.data_ptr(), self.c_mask.data_ptr(), self.c_start.data_ptr(),
+                                             self.c_count.data_ptr(), self.c_view_first.data_ptr(),
+                                             self.c_total.data_ptr(), self.ccap)
+            self.vals = None
+        else:
+            self.vals = torch.empty(max(self.cap, 1), dtype=torch.int32, device=dev)
         self.keys = torch.empty(max(self.cap, 1), dtype=torch.int64, device=dev) if keep_keys else None
         self.ranges = torch.empty(2 * T, dtype=torch.int32, device=dev)
         self.tile_order = torch.empty(T, dtype=torch.int32, device=dev) if self.s.longest_tiles_first else None
@@ -165,8 +184,12 @@ class Renderer:
         self.n_last = torch.empty(P, dtype=torch.int32, device=dev)
         self.ckpt_slots = int(gsr.lib().gs_ckpt_slots(self.cap, T, self.s.batch))
         self.ckpt = torch.empty(self.ckpt_slots * self.s.tile * self.s.tile, dtype=torch.float32, device=dev)
+        self.batch_pos = torch.empty(self.ckpt_slots, dtype=torch.int32, device=dev) if self.coarse else None
         L = gsr.lib()
-        self.bin_ws_bytes = int(L.gs_bin_sort_workspace_size(n, V, self.cap, T))
+        if self.coarse:
+            self.bin_ws_bytes = int(L.gs_bin_sort_coarse_workspace_size(n, V, T))
+        else:
+            self.bin_ws_bytes = int(L.gs_bin_sort_workspace_size(n, V, self.cap, T))
         self.bin_ws = torch.empty(self.bin_ws_bytes, dtype=torch.uint8, device=dev)
         self.loss_ws_bytes = int(L.gs_loss_workspace_size(views.host, V))
         self.loss_ws = torch.empty(self.loss_ws_bytes, dtype=torch.uint8, device=dev)
@@ -189,6 +212,7 @@ class Renderer:
                                                      self.ckpt.data_ptr(), self.ckpt_slots)
         s.tile_order = self.tile_order.data_ptr() if self.tile_order is not None else None
         s.queue = self.queue.data_ptr() if self.queue is not None else None
+        s.batch_pos = self.batch_pos.data_ptr() if self.batch_pos is not None else None
         return s
 
     # --- pipeline steps (each one C-ABI call)
@@ -199,19 +223,32 @@ class Renderer:
 
     def bin_sort(self, stream=None) -> None:
         proj = self.c_proj()
-        gsr.call("gs_bin_sort", C.byref(proj), gsr.ptr(self.views.dev), self.views.n, self.n,
-                 self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws), self.bin_ws_bytes,
-                 gsr.ptr(self.keys), gsr.ptr(self.vals), self.cap, gsr.ptr(self.ranges), gsr.ptr(self.pair_count),
-                 gsr.ptr(self.status), gsr.stream_handle(stream))
+        if self.coarse:
+            gsr.call("gs_bin_sort_coarse", C.byref(proj), gsr.ptr(self.views.dev), self.views.n, self.n,
+                     self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws),
+                     self.bin_ws_bytes, C.byref(self.lists), self.cap, gsr.ptr(self.ranges),
+                     gsr.ptr(self.pair_count), gsr.ptr(self.status), gsr.stream_handle(stream))
+        else:
+            gsr.call("gs_bin_sort", C.byref(proj), gsr.ptr(self.views.dev), self.views.n, self.n,
+                     self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws),
+                     self.bin_ws_bytes, gsr.ptr(self.keys), gsr.ptr(self.vals), self.cap, gsr.ptr(self.ranges),
+                     gsr.ptr(self.pair_count), gsr.ptr(self.status), gsr.stream_handle(stream))
         if self.tile_order is not None:
             gsr.call("gs_tile_order", gsr.ptr(self.ranges), self.views.total_tiles, gsr.ptr(self.tile_order),
                      gsr.stream_handle(stream))
 
     def render_fwd(self, stream=None) -> None:
         proj = self.c_proj()
-        gsr.call("gs_render_fwd", C.byref(proj), self.n, gsr.ptr(self.vals), gsr.ptr(self.ranges),
+        name, lists = self._lists("gs_render_fwd")
+        gsr.call(name, C.byref(proj), self.n, lists, gsr.ptr(self.ranges),
                  gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg_fwd),
                  gsr.ptr(self.image), self.c_saved(), gsr.ptr(self.status), gsr.stream_handle(stream))
+
+    def _lists(self, name: str):
+        """The call for this renderer's list form and its list argument."""
+        if self.coarse:
+            return name + "_coarse", C.byref(self.lists)
+        return name, gsr.ptr(self.vals)
 
     def forward(self, params: gsr.gs_params, stream=None) -> torch.Tensor:
         self.project(params, stream)
@@ -240,7 +277,8 @@ class Renderer:
                  view_gate: torch.Tensor | None = None, accumulate: bool = False, stream=None) -> None:
         proj = self.c_proj()
         dl = self.dL_dimage if dL_dimage is None else dL_dimage
-        gsr.call("gs_render_bwd", C.byref(params), C.byref(proj), gsr.ptr(self.vals), gsr.ptr(self.ranges),
+        name, lists = self._lists("gs_render_bwd")
+        gsr.call(name, C.byref(params), C.byref(proj), lists, gsr.ptr(self.ranges),
                  gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg),
                  self.c_saved(), gsr.ptr(dl), gsr.ptr(view_gate), grads, int(bool(accumulate)),
                  gsr.ptr(self.bwd_ws), self.bwd_ws_bytes, gsr.ptr(self.status), gsr.stream_handle(stream))
@@ -250,7 +288,8 @@ class Renderer:
         """Raster adjoint only: per-view 2D gradients into self.bwd_ws ([V][N][12] floats)."""
         proj = self.c_proj()
         dl = self.dL_dimage if dL_dimage is None else dL_dimage
-        gsr.call("gs_raster_bwd", C.byref(proj), self.n, gsr.ptr(self.vals), gsr.ptr(self.ranges),
+        name, lists = self._lists("gs_raster_bwd")
+        gsr.call(name, C.byref(proj), self.n, lists, gsr.ptr(self.ranges),
                  gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg), self.c_saved(),
                  gsr.ptr(dl), gsr.ptr(view_gate), gsr.ptr(self.bwd_ws), self.bwd_ws_bytes, gsr.ptr(self.status),
                  gsr.stream_handle(stream))
@@ -270,8 +309,9 @@ class Renderer:
         (2 float64, optional) receives the sums of g^2 and of the squared update."""
         proj = self.c_proj()
         dl = self.dL_dimage if dL_dimage is None else dL_dimage
-        gsr.call("gs_render_bwd_adam", gsr.ptr(model.flat), gsr.ptr(adam.m), gsr.ptr(adam.v), model.n,
-                 model.sh_degree, C.byref(proj), gsr.ptr(self.vals), gsr.ptr(self.ranges), gsr.ptr(self.views.dev),
+        name, lists = self._lists("gs_render_bwd_adam")
+        gsr.call(name, gsr.ptr(model.flat), gsr.ptr(adam.m), gsr.ptr(adam.v), model.n,
+                 model.sh_degree, C.byref(proj), lists, gsr.ptr(self.ranges), gsr.ptr(self.views.dev),
                  self.views.n, self.views.total_tiles, C.byref(self.cfg), self.c_saved(), gsr.ptr(dl),
                  gsr.ptr(view_gate), C.byref(adam.cfg), gsr.ptr(do_step), gsr.ptr(adam.step_count), gsr.ptr(norms2),
                  gsr.ptr(self.bwd_ws), self.bwd_ws_bytes, gsr.ptr(self.status), gsr.stream_handle(stream))
@@ -292,7 +332,18 @@ class Renderer:
         Gaussian) pairs with a contributor, staged list entries."""
         counts = torch.zeros(5, dtype=torch.int64, device=self.image.device)
         proj = self.c_proj()
-        gsr.call("gs_raster_census", C.byref(proj), self.n, gsr.ptr(self.vals), gsr.ptr(self.ranges),
+        vals = self.vals
+        if self.coarse:  # the census walks tile lists: bin the same projection into them once
+            dev = self.image.device
+            vals = torch.empty(max(self.cap, 1), dtype=torch.int32, device=dev)
+            ranges = torch.empty_like(self.ranges)
+            ws_bytes = int(gsr.lib().gs_bin_sort_workspace_size(self.n, self.views.n, self.cap, self.views.total_tiles))
+            ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+            gsr.call("gs_bin_sort", C.byref(proj), gsr.ptr(self.views.dev), self.views.n, self.n,
+                     self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(ws), ws_bytes, None,
+                     gsr.ptr(vals), self.cap, gsr.ptr(ranges), gsr.ptr(self.pair_count), gsr.ptr(self.status),
+                     gsr.stream_handle(stream))
+        gsr.call("gs_raster_census", C.byref(proj), self.n, gsr.ptr(vals), gsr.ptr(self.ranges),
                  gsr.ptr(self.views.dev), self.views.n, self.views.total_tiles, C.byref(self.cfg),
                  gsr.ptr(self.n_last), gsr.ptr(counts), gsr.stream_handle(stream))
         torch.cuda.synchronize()  # the census ran on `stream`, not necessarily the current one
