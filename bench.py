@@ -122,7 +122,7 @@ def run_c4(args) -> None:
     # blocks take (view, tile) items longest-first from a device queue, each
     # view with its own tile grid
     import dataclasses
-    st = dataclasses.replace(st, persistent=not args.c4_slots)
+    st = dataclasses.replace(st, persistent=not args.c4_slots, coarse_lists=args.lists == "coarse")
     pre = RefinementLoop(model, cams, targets, synth.pre_sequence(pre_iters * B, args.views), st, gated=False,
                          pair_capacity=cap, views_per_step=B)
     pre.capture()

@@ -247,9 +247,10 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
  * counted but not placed.  ranges[tile] = the [start, end) that gs_bin_sort
  * writes (where the tile's pairs would lie in its vals; the *_coarse
  * compositing calls take their checkpoint slots from them, gs_tile_order its
- * order).  *dev_pair_count as gs_bin_sort; more pairs than pair_capacity, or
- * more list entries than lists->capacity (at most one per pair):
- * GS_ERR_CAPACITY in dev_status, ranges left empty.  workspace: at least
+ * order).  *dev_pair_count as gs_bin_sort (the pairs are counted from the
+ * lists' masks; 0 when the lists did not fit); more pairs than
+ * pair_capacity, or more list entries than lists->capacity (at most one per
+ * pair): GS_ERR_CAPACITY in dev_status, ranges left empty.  workspace: at least
  * gs_bin_sort_coarse_workspace_size(n, n_views, total_tiles) bytes, 256-byte
  * aligned.  Other arguments and errors as gs_bin_sort. */
 size_t gs_bin_sort_coarse_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles);

@@ -1146,6 +1146,94 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
     return off;
 }
 
+// The super-tile form's tile totals: TT_SPLIT blocks per super-tile count,
+// per tile of it, the list entries whose mask has the tile's bit (the pairs
+// the tile lists would hold), each over a contiguous part of the list read
+// eight masks at a time, and add them to tile_total (zero at launch).  A view
+// whose tile grid is larger than the tables hold gets GS_ERR_INVALID_ARG and
+// no pairs, as on the tile grid; nothing is counted when the lists did not
+// fit.  The masks are 16-byte aligned.
+constexpr int TT_THREADS = 256;
+constexpr int TT_SPLIT = 8;
+__global__ void __launch_bounds__(TT_THREADS) coarse_tile_totals(
+    const gs_camera *__restrict__ cams, int n_views, BinGeom gc, int64_t fine_tiles, int fine_max_vt,
+    const uint32_t *__restrict__ cstart, const uint32_t *__restrict__ ctotal, const uint16_t *__restrict__ cmask,
+    const int64_t *coarse_sort_count, uint32_t *__restrict__ tile_total, int32_t *dev_status) {
+    __shared__ uint32_t s_c[TT_THREADS / 32][SUP_T];
+    const int64_t ct = blockIdx.x / TT_SPLIT;
+    const int part = (int)(blockIdx.x % TT_SPLIT);
+    if (ct >= gc.coff[n_views]) return;  // whole block
+    const int v = view_of_grid_tile(gc, cams, n_views, ct);
+    const ViewTiles ft = view_tiles(cams[v], gc.tile);
+    if (!view_fits(ft, fine_tiles, fine_max_vt)) {
+        if (threadIdx.x == 0 && part == 0) set_status(dev_status, GS_ERR_INVALID_ARG);
+        return;
+    }
+    if (*coarse_sort_count == 0) return;
+    const uint32_t len = ctotal[ct];
+    const uint32_t lo = cstart[ct] + (uint32_t)(((uint64_t)len * part) / TT_SPLIT);
+    const uint32_t hi = cstart[ct] + (uint32_t)(((uint64_t)len * (part + 1)) / TT_SPLIT);
+    uint32_t c[SUP_T];
+#pragma unroll
+    for (int k = 0; k < SUP_T; ++k) c[k] = 0;
+    for (uint32_t p = (lo & ~7u) + 8u * threadIdx.x; p < hi; p += 8u * TT_THREADS) {
+        uint32_t w[4];
+        if (p + 8 <= hi) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(cmask + p);
+            w[0] = x.x;
+            w[1] = x.y;
+            w[2] = x.z;
+            w[3] = x.w;
+        } else {  // the part's last vector: plain loads inside it
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t a = p + 2 * e < hi ? cmask[p + 2 * e] : 0u;
+                const uint32_t b = p + 2 * e + 1 < hi ? cmask[p + 2 * e + 1] : 0u;
+                w[e] = a | (b << 16);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {  // masks before lo (the aligned head) are not this part's
+            if (p + 2 * e < lo) w[e] &= 0xffff0000u;
+            if (p + 2 * e + 1 < lo) w[e] &= 0x0000ffffu;
+        }
+        // four-bit counters: nibble n of acc[j] counts bit 4 (n % 4) + j of
+        // the masks (each word holds two), at most 4 per nibble here
+        uint32_t acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] += (w[e] >> j) & 0x11111111u;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int nb = 0; nb < 8; ++nb) c[4 * (nb % 4) + j] += (acc[j] >> (4 * nb)) & 15u;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < SUP_T; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < SUP_T; ++k) s_c[warp][k] = c[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < SUP_T) {
+        const int k = threadIdx.x;
+        const int ctx = (ft.tx + SUP - 1) / SUP;
+        const int64_t lct = ct - gc.coff[v];
+        const int x = (int)(lct % ctx) * SUP + k % SUP, y = (int)(lct / ctx) * SUP + k / SUP;
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < TT_THREADS / 32; ++w) t += s_c[w][k];
+        if (x < ft.tx && y < ft.ty && t) atomicAdd(&tile_total[ft.off + (int64_t)y * ft.tx + x], t);
+    }
+}
+
 // The super-tile form's tile ranges: where each tile's pairs would lie in
 // gs_bin_sort's vals (the checkpoint slots and the tile order use them).
 // Written only when both the pairs and the super-tile lists fit.
@@ -1285,15 +1373,19 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
         bin_rects<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(rect, proj->tiles_touched, order, cams, g,
                                                                      total, w.srect);
     GS_TRY_LAUNCH();
-    GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
-    const unsigned n_chunks = (unsigned)(g.n_c * n_views);
-    bin_count<<<n_chunks, COUNT_THREADS, 2 * smem + 8, stream>>>(w.srect, cams, g, nullptr, w.G1, dev_status);
-    GS_TRY_LAUNCH();
-    bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
-    GS_TRY_LAUNCH();
-    bin_starts<<<1, SCAN_THREADS, 0, stream>>>(g, w.tile_total, w.tile_start, pair_capacity, dev_pair_count,
-                                               w.sort_count, dev_status);
-    GS_TRY_LAUNCH();
+    if (co) {  // the tile totals come from the lists' masks, after the scatter
+        GS_TRY(cudaMemsetAsync(w.tile_total, 0, sizeof(uint32_t) * (size_t)total_tiles, stream));
+    } else {
+        GS_TRY(cudaMemsetAsync(w.G1, 0, sizeof(uint32_t) * (size_t)(g.n_g * total_tiles), stream));
+        const unsigned n_chunks = (unsigned)(g.n_c * n_views);
+        bin_count<<<n_chunks, COUNT_THREADS, 2 * smem + 8, stream>>>(w.srect, cams, g, nullptr, w.G1, dev_status);
+        GS_TRY_LAUNCH();
+        bin_groups<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(g, w.G1, w.tile_total);
+        GS_TRY_LAUNCH();
+        bin_starts<<<1, SCAN_THREADS, 0, stream>>>(g, w.tile_total, w.tile_start, pair_capacity, dev_pair_count,
+                                                   w.sort_count, dev_status);
+        GS_TRY_LAUNCH();
+    }
     // the super-tile grid
     coarse_offsets<<<1, 32, 0, stream>>>(cams, n_views, cfg->tile, w.coff);
     GS_TRY_LAUNCH();
@@ -1321,6 +1413,13 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
                                          stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.cmask);
     GS_TRY_LAUNCH();
     if (co) {
+        coarse_tile_totals<<<(unsigned)(gc.tiles * TT_SPLIT), TT_THREADS, 0, stream>>>(cams, n_views, gc, total_tiles, (int)mvt,
+                                                                           w.cstart, w.ctotal, w.cmask,
+                                                                           w.c_count + 1, w.tile_total, dev_status);
+        GS_TRY_LAUNCH();
+        bin_starts<<<1, SCAN_THREADS, 0, stream>>>(g, w.tile_total, w.tile_start, pair_capacity, dev_pair_count,
+                                                   w.sort_count, dev_status);
+        GS_TRY_LAUNCH();
         tile_ranges<<<(unsigned)ceil_div(total_tiles, (int64_t)256), 256, 0, stream>>>(
             total_tiles, w.tile_start, w.tile_total, w.sort_count, w.c_count + 1, reinterpret_cast<uint2 *>(ranges));
         GS_TRY_LAUNCH();

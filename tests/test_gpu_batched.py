@@ -160,10 +160,13 @@ def test_batched_loop_runs_and_gates():
     assert gpu_util.rel_err(one[1], one[0]) < 1e-6
 
 
-def test_batched_loop_compact_persistent_equals_default():
+@pytest.mark.parametrize("coarse", [False, True])
+def test_batched_loop_compact_persistent_equals_default(coarse):
     """The batched loop with per-view packed tile grids and persistent
-    compositing takes the same decisions and steps as with largest-view slots
-    and a block per tile (parameters equal up to the order of float atomics)."""
+    compositing (with tile lists, and with super-tile lists over the packed
+    grids) takes the same decisions and steps as with largest-view slots,
+    tile lists and a block per tile (parameters equal up to the order of
+    float atomics)."""
     gpu_util.lib()
     scene, _, _ = synth.case_c1(n=1500)
     cams = _cams()
@@ -173,7 +176,7 @@ def test_batched_loop_compact_persistent_equals_default():
     out = []
     for compact in (False, True):
         model = raster.GaussianModel.from_scene(scene)
-        st = raster.RasterSettings(persistent=compact)
+        st = raster.RasterSettings(persistent=compact, coarse_lists=compact and coarse)
         loop = RefinementLoop(model, cams, targets, seq, st, gated=True, W=4, views_per_step=3, log_capacity=16,
                               compact_tiles=compact, batch_lr_scale=True)
         for _ in range(12):

@@ -17,12 +17,12 @@ pytestmark = pytest.mark.gpu
 GROUPS = ("means", "log_scales", "quats", "opacity_logit", "sh")
 
 
-def _setup(scene, cam, tile=16, batch=256, ppt=2):
+def _setup(scene, cam, tile=16, batch=256, ppt=2, coarse=False):
     gpu_util.lib()
     views = raster.Views([cam], tile)
     r = raster.Renderer(scene.n, scene.sh_degree, views,
                         raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt,
-                                              pixels_per_thread_fwd=ppt))
+                                              pixels_per_thread_fwd=ppt, coarse_lists=coarse))
     model = raster.GaussianModel.from_scene(scene)
     return r, model
 
@@ -89,15 +89,16 @@ def test_backward_full_loss_c1(tile, batch, ppt):
     _check_grads(gpu_util.gpu_grads(model, adam.grad), og)
 
 
-def test_backward_c2():
-    """The full C2 scene (200,000 Gaussians SH3, 980x545) through the loss.
-    dL/dimage is zeroed on both sides where the L1 sign is a float32 tie
-    (gpu_util.l1_tie_mask, from the oracle's image); everywhere else each side
-    uses its own loss gradient."""
+@pytest.mark.parametrize("coarse", [False, True])
+def test_backward_c2(coarse):
+    """The full C2 scene (200,000 Gaussians SH3, 980x545) through the loss,
+    with tile lists and with super-tile lists.  dL/dimage is zeroed on both
+    sides where the L1 sign is a float32 tie (gpu_util.l1_tie_mask, from the
+    oracle's image); everywhere else each side uses its own loss gradient."""
     scene, tscene, cam, noise = synth.case_c2()
     rc = oracle.RasterConfig()
     target = (oracle.forward(tscene, cam, rc)["image"] + noise).astype(np.float32)
-    r, model = _setup(scene, cam)
+    r, model = _setup(scene, cam, coarse=coarse)
     adam = raster.AdamState(model)
     r.forward(model.c_params())
     r.compute_loss(torch.from_numpy(target.ravel()).cuda(), with_grad=True)

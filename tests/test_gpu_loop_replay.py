@@ -3,7 +3,8 @@ views at 1297x840), run as the captured CUDA graph: the per-iteration log of
 losses and gate decisions, replayed through the Algorithm 1 oracle, gives
 the same decisions bit for bit; the logged gradient and update norms are
 zero exactly on the skipped iterations.  A batched run (2 views per
-iteration) is replayed the same way under reading (vii)."""
+iteration) is replayed the same way under reading (vii).  The bench's list
+form (super-tile lists) and the tile lists both."""
 import numpy as np
 import pytest
 import torch
@@ -41,8 +42,8 @@ def _replay(seq, log, B, W):
     return want
 
 
-@pytest.mark.parametrize("B", [1, 2])
-def test_loop_decisions_replay_bit_exact(B):
+@pytest.mark.parametrize("B,coarse", [(1, True), (1, False), (2, True)])
+def test_loop_decisions_replay_bit_exact(B, coarse):
     from paper_2603_08997_gb300 import raster
     from paper_2603_08997_gb300.refine import RefinementLoop
     gpu_util.lib()
@@ -51,8 +52,8 @@ def test_loop_decisions_replay_bit_exact(B):
     targets = _targets(gt, cams, raster, dev)
     model = raster.GaussianModel.from_scene(start, dev)
     W = 500 if B == 1 else 300
-    loop = RefinementLoop(model, cams, targets, seq, gated=True, W=W, views_per_step=B, pair_capacity=24 * gt.n * B,
-                          log_capacity=ITERS)
+    loop = RefinementLoop(model, cams, targets, seq, raster.RasterSettings(coarse_lists=coarse), gated=True, W=W,
+                          views_per_step=B, pair_capacity=24 * gt.n * B, log_capacity=ITERS)
     loop.capture()
     for _ in range(ITERS):
         loop.step_graph()

@@ -17,6 +17,8 @@ stress cases of the adjoint's transmittance rebuild.
   Every other parameter must agree within 2e-6 relative (normwise per group,
   and per element against 2e-6 of the group's RMS); the moments within the
   gradient bar (m 1e-4, v 2e-4 normwise).
+  Both list forms (tile lists; super-tile lists filtered by the kernels, the
+  bench's form) at C1 and at the full C2 size.
 * The raster adjoint on near-opaque stacks: 600 Gaussians over a 32x32 image,
   alpha' reaching the 0.99 clamp at positions 40 and 230; with both, every
   pixel has 230 contributors inside the first 256-record batch and stops
@@ -57,8 +59,9 @@ def _grad_vec(g: dict) -> dict:
     return {k: np.asarray(g[k], np.float64).ravel() for k in GROUPS}
 
 
-@pytest.mark.parametrize("case,steps", [("c1", 1), ("c1", 3), ("c2", 1), ("c2", 3)])
-def test_fused_backward_adam_against_oracle(case, steps):
+@pytest.mark.parametrize("case,steps,coarse", [("c1", 1, False), ("c1", 3, False), ("c2", 1, False),
+                                               ("c2", 3, False), ("c1", 3, True), ("c2", 3, True)])
+def test_fused_backward_adam_against_oracle(case, steps, coarse):
     gpu_util.lib()
     rc = oracle.RasterConfig()
     if case == "c1":
@@ -68,7 +71,7 @@ def test_fused_backward_adam_against_oracle(case, steps):
         target = (oracle.forward(tscene, cam, rc)["image"] + noise).astype(np.float32)
     cfg = AdamConfig()
     views = raster.Views([cam], 16)
-    r = raster.Renderer(scene.n, scene.sh_degree, views, raster.RasterSettings())
+    r = raster.Renderer(scene.n, scene.sh_degree, views, raster.RasterSettings(coarse_lists=coarse))
     model = raster.GaussianModel.from_scene(scene)
     adam = raster.AdamState(model, lr=cfg.lrs(), beta1=cfg.beta1, beta2=cfg.beta2, eps=cfg.eps)
     grad = torch.zeros_like(model.flat)
@@ -141,13 +144,13 @@ def test_fused_backward_adam_against_oracle(case, steps):
             assert gpu_util.rel_err(got_v[k][ok], v[k][ok]) <= 2e-4, (k, gpu_util.rel_err(got_v[k][ok], v[k][ok]))
 
 
-def _stack_case(clamp_at, tile=16, batch=256, ppt=2):
+def _stack_case(clamp_at, tile=16, batch=256, ppt=2, coarse=False):
     gpu_util.lib()
     cam = synth.camera_pinhole(50, 50, 16, 16, 32, 32)
     rec = synth.opaque_stack_records(600, 32, 32, clamp_at=clamp_at, seed=3)
     views = raster.Views([cam], tile)
     r = raster.Renderer(600, 0, views, raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt,
-                                                              pixels_per_thread_fwd=ppt))
+                                                              pixels_per_thread_fwd=ppt, coarse_lists=coarse))
     dev, orc = gpu_util.records([rec], [cam], tile)
     gpu_util.set_projected(r, dev)
     r.bin_sort()
@@ -156,9 +159,10 @@ def _stack_case(clamp_at, tile=16, batch=256, ppt=2):
 
 
 @pytest.mark.parametrize("clamp_at", [(40, 230), (40,)])
-@pytest.mark.parametrize("tile,batch,ppt", [(16, 256, 2), (16, 128, 1), (8, 256, 2), (32, 256, 2)])
-def test_raster_bwd_near_opaque_stack(clamp_at, tile, batch, ppt):
-    cam, r, orc = _stack_case(clamp_at, tile, batch, ppt)
+@pytest.mark.parametrize("tile,batch,ppt,coarse", [(16, 256, 2, False), (16, 128, 1, False), (8, 256, 2, False),
+                                                   (32, 256, 2, False), (16, 256, 2, True), (8, 128, 1, True)])
+def test_raster_bwd_near_opaque_stack(clamp_at, tile, batch, ppt, coarse):
+    cam, r, orc = _stack_case(clamp_at, tile, batch, ppt, coarse)
     dl = synth.dl_dimage(cam.width, cam.height, seed=9)
     g2d = r.raster_bwd(dL_dimage=torch.from_numpy(dl.ravel()).cuda()).double().cpu().numpy()[0]
     torch.cuda.synchronize()

@@ -17,11 +17,12 @@ from tests import gpu_util
 pytestmark = pytest.mark.gpu
 
 
-def _renderer(cams, n, sh_degree=0, tile=16, batch=256, cap=None, keys=True, ppt=2):
+def _renderer(cams, n, sh_degree=0, tile=16, batch=256, cap=None, keys=True, ppt=2, coarse=False):
     gpu_util.lib()
     views = raster.Views(cams, tile)
-    st = raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt, pixels_per_thread_fwd=ppt)
-    return raster.Renderer(n, sh_degree, views, st, pair_capacity=cap, keep_keys=keys)
+    st = raster.RasterSettings(tile=tile, batch=batch, pixels_per_thread=ppt, pixels_per_thread_fwd=ppt,
+                               coarse_lists=coarse)
+    return raster.Renderer(n, sh_degree, views, st, pair_capacity=cap, keep_keys=keys and not coarse)
 
 
 def _sorted_pairs(r):
@@ -213,12 +214,14 @@ def test_projection_c2():
     assert ((gr[:, 0] <= exv[:, 0]) & (gr[:, 1] <= exv[:, 1]) & (gr[:, 2] >= exv[:, 2]) & (gr[:, 3] >= exv[:, 3])).all()
 
 
-def test_render_end_to_end_c2():
-    """The full C2 scene rendered end to end; flagged pixels (within 1e-4 of a
-    cut-off, the projection's float32 reach) below 1% of the image, pixels
-    beyond 1e-5 of the peak at most 0.01% (each within 1e-4)."""
+@pytest.mark.parametrize("coarse", [False, True])
+def test_render_end_to_end_c2(coarse):
+    """The full C2 scene rendered end to end (tile lists and super-tile lists);
+    flagged pixels (within 1e-4 of a cut-off, the projection's float32 reach)
+    below 1% of the image, pixels beyond 1e-5 of the peak at most 0.01% (each
+    within 1e-4)."""
     scene, _, cam, _ = synth.case_c2()
-    r = _renderer([cam], scene.n, sh_degree=3, cap=24 * scene.n)
+    r = _renderer([cam], scene.n, sh_degree=3, cap=24 * scene.n, coarse=coarse)
     model = raster.GaussianModel.from_scene(scene)
     r.forward(model.c_params())
     torch.cuda.synchronize()
