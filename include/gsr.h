@@ -247,7 +247,12 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
  * counted but not placed.  ranges[tile] = the [start, end) that gs_bin_sort
  * writes (where the tile's pairs would lie in its vals; the *_coarse
  * compositing calls take their checkpoint slots from them, gs_tile_order its
- * order).  *dev_pair_count as gs_bin_sort (the pairs are counted from the
+ * order).  max_view_super_tiles: the largest super-tile count of one view,
+ * ceil(tiles_x / 4) * ceil(tiles_y / 4), or 0 to bound it by
+ * max_view_tiles / 4 + 1 (the bound of the skinniest grid); a tighter bound
+ * lets more of the placement's warps share an SM; a view with more super-tiles
+ * than it sets GS_ERR_INVALID_ARG in dev_status and emits nothing.
+ * *dev_pair_count as gs_bin_sort (the pairs are counted from the
  * lists' masks; 0 when the lists did not fit); more pairs than
  * pair_capacity, or more list entries than lists->capacity (at most one per
  * pair): GS_ERR_CAPACITY in dev_status, ranges left empty.  workspace: at least
@@ -255,7 +260,8 @@ gs_status gs_bin_sort(const gs_projected *proj /* host */, const gs_camera *cams
  * aligned.  Other arguments and errors as gs_bin_sort. */
 size_t gs_bin_sort_coarse_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles);
 gs_status gs_bin_sort_coarse(const gs_projected *proj /* host */, const gs_camera *cams, int32_t n_views, int64_t n,
-                             int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg /* host */,
+                             int64_t total_tiles, int32_t max_view_tiles, int32_t max_view_super_tiles,
+                             const gs_raster_config *cfg /* host */,
                              void *workspace, size_t workspace_bytes, const gs_coarse_lists *lists /* host */,
                              int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status,
                              cudaStream_t stream);

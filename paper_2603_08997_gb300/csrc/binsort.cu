@@ -8,7 +8,7 @@
 //   1. sort the V*N (view, Gaussian) entries by depth bits (stable, so equal
 //      depths keep ascending index), then stably by view;
 //   2. place every pair by a counting sort over tiles that walks the entries
-//      in that order (see bin_count .. bin_scatter below).
+//      in that order (see bin_count .. coarse_place below).
 // A stable sort by tile of a depth-ordered list is ordered by
 // (tile, depth, index), i.e. exactly the 64-bit key order.  Stage 2 runs in
 // two levels: a chunked counting sort of the entries by 4 x 4-tile
@@ -53,16 +53,86 @@ __device__ __forceinline__ void block_range(int64_t count, int G, int b, int64_t
     if (end > count) end = count;
 }
 
+// Depth-key range.  Keys are float32 bits of positive depths, 0xffffffff for
+// culled entries.  Sorting k - min over the visible keys (culled ones mapped
+// to the largest value: they emit no pairs, so where they land is
+// irrelevant) gives the same order of the visible entries, ties included;
+// passes whose digit lies above the range's bit length are then no-ops of
+// the stable sort and are replaced by a copy.  krange = {min, max} over the
+// visible keys (start {0xffffffff, 0}); one pair of atomics per block.
+__global__ void key_range_kernel(const uint32_t *__restrict__ keys, int64_t count, uint32_t *__restrict__ krange) {
+    __shared__ uint32_t s_lo[32], s_hi[32];
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += 4 * stride) {
+        uint32_t k[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[j] = i + j * stride < count ? keys[i + j * stride] : 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (k[j] != 0xffffffffu) {
+                lo = min(lo, k[j]);
+                hi = max(hi, k[j]);
+            }
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nwarps = blockDim.x >> 5;
+        lo = threadIdx.x < nwarps ? s_lo[threadIdx.x] : 0xffffffffu;
+        hi = threadIdx.x < nwarps ? s_hi[threadIdx.x] : 0u;
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (threadIdx.x == 0) {
+            atomicMin(&krange[0], lo);
+            atomicMax(&krange[1], hi);
+        }
+    }
+}
+
+// Bits of the range (0: at most one distinct visible key).
+__device__ __forceinline__ int range_bits(const uint32_t *krange) {
+    const uint32_t lo = krange[0], hi = krange[1];
+    return hi > lo ? 32 - __clz(hi - lo) : 0;
+}
+
+// The range as read once per thread: keys map to k - lo, culled ones to
+// hi - lo, everything to 0 when no key is visible.
+struct KeyRange {
+    uint32_t lo, hi;
+    bool on;
+    __device__ __forceinline__ KeyRange(const uint32_t *krange, bool first) {
+        on = first && krange;
+        lo = on ? krange[0] : 0u;
+        hi = on ? krange[1] : 0u;
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+        if (!on) return k;
+        if (hi < lo) return 0u;
+        return k == 0xffffffffu ? hi - lo : k - lo;
+    }
+};
+
+template <bool FIRST>
 __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t *__restrict__ keys, const int64_t *d_count,
                                                          int64_t cap, int shift, uint32_t mask,
-                                                         uint32_t *__restrict__ counts) {
+                                                         uint32_t *__restrict__ counts,
+                                                         const uint32_t *__restrict__ krange) {
     __shared__ uint32_t hist[RADIX];
+    if (krange && shift >= range_bits(krange)) return;  // a no-op pass (copied by the downsweep)
     for (int i = threadIdx.x; i < RADIX; i += RS_THREADS) hist[i] = 0;
     __syncthreads();
     const int64_t count = effective_count(d_count, cap);
     int64_t begin, end;
     block_range(count, gridDim.x, blockIdx.x, begin, end);
-    for (int64_t i = begin + threadIdx.x; i < end; i += RS_THREADS) atomicAdd(&hist[(keys[i] >> shift) & mask], 1u);
+    const KeyRange kr(krange, FIRST);
+    for (int64_t i = begin + threadIdx.x; i < end; i += RS_THREADS) atomicAdd(&hist[(kr(keys[i]) >> shift) & mask], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) counts[(int64_t)d * gridDim.x + blockIdx.x] = hist[d];
 }
@@ -99,8 +169,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
 // Digit offsets, part 1: block d scans row d of the digit-major counts
 // [RADIX][G] (exclusive, in place) and writes the row total.  The downsweep
 // adds each digit's base (exclusive scan of the totals) itself.
-__global__ void __launch_bounds__(RS_THREADS) rs_scan(uint32_t *a, int G, uint32_t *totals) {
+__global__ void __launch_bounds__(RS_THREADS) rs_scan(uint32_t *a, int G, uint32_t *totals, int shift,
+                                                      const uint32_t *__restrict__ krange) {
     __shared__ uint32_t warp_sums[32];
+    if (krange && shift >= range_bits(krange)) return;
     uint32_t *row = a + (int64_t)blockIdx.x * G;
     const int per = (G + RS_THREADS - 1) / RS_THREADS;
     const int lo = min(G, (int)threadIdx.x * per), hi = min(G, lo + per);
@@ -117,13 +189,15 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scan(uint32_t *a, int G, uint32
     if (threadIdx.x == 0) totals[blockIdx.x] = total;
 }
 
+template <bool FIRST>
 __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__restrict__ keys_in,
                                                            const uint32_t *__restrict__ vals_in,
                                                            uint32_t *__restrict__ keys_out,
                                                            uint32_t *__restrict__ vals_out, const int64_t *d_count,
                                                            int64_t cap, int shift, uint32_t mask,
                                                            const uint32_t *__restrict__ offsets,
-                                                           const uint32_t *__restrict__ totals) {
+                                                           const uint32_t *__restrict__ totals,
+                                                           const uint32_t *__restrict__ krange) {
     __shared__ uint32_t s_run[RADIX];   // global start of this block's next run per digit
     __shared__ uint32_t s_tot[RADIX];   // tile count per digit
     __shared__ uint32_t s_loc[RADIX];   // tile-local start per digit
@@ -133,6 +207,17 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     __shared__ uint32_t s_warp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    const KeyRange kr(krange, FIRST);
+    if (krange && shift >= range_bits(krange)) {  // every key's digit is 0: the stable pass keeps the order
+        const int64_t count = effective_count(d_count, cap);
+        int64_t begin, end;
+        block_range(count, gridDim.x, blockIdx.x, begin, end);
+        for (int64_t i = begin + threadIdx.x; i < end; i += RS_THREADS) {
+            keys_out[i] = kr(keys_in[i]);
+            vals_out[i] = vals_in ? vals_in[i] : (uint32_t)i;
+        }
+        return;
+    }
     {
         // digit base = exclusive scan of the digit totals (thread d owns digit d)
         uint32_t all;
@@ -156,6 +241,10 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             const bool valid = li < n_tile;
             k[r] = valid ? keys_in[base + li] : 0u;
             v[r] = valid ? (vals_in ? vals_in[base + li] : (uint32_t)(base + li)) : 0u;  // no values: the index
+        }
+        if constexpr (FIRST) {  // into the range, after every load is in flight
+#pragma unroll
+            for (int r = 0; r < RS_ITEMS; ++r) k[r] = kr(k[r]);
         }
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
@@ -233,8 +322,12 @@ int rs_blocks(int64_t cap) {
 // (ka, va), 1 when it is in (kb, vb).
 // If k0 is given, the first pass reads its keys from k0 (left unchanged) with
 // each key's index as its value, instead of from (ka, va).
+// krange (device, nullable): the depth-key range of key_range_kernel; the
+// first pass then sorts keys relative to it and passes above its bit length
+// copy (see key_range_kernel).
 int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int64_t *d_count, int64_t cap,
-               int bits, uint32_t *counts, cudaStream_t stream, const uint32_t *k0 = nullptr) {
+               int bits, uint32_t *counts, cudaStream_t stream, const uint32_t *k0 = nullptr,
+               const uint32_t *krange = nullptr) {
     const int G = rs_blocks(cap);
     int cur = 0;
     for (int shift = 0; shift < bits; shift += RADIX_BITS) {
@@ -248,9 +341,17 @@ int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int
         }
         uint32_t *ko = cur ? ka : kb, *vo = cur ? va : vb;
         uint32_t *totals = counts + (size_t)RADIX * RS_MAX_BLOCKS;
-        rs_upsweep<<<G, RS_THREADS, 0, stream>>>(ki, d_count, cap, shift, mask, counts);
-        rs_scan<<<RADIX, RS_THREADS, 0, stream>>>(counts, G, totals);
-        rs_downsweep<<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts, totals);
+        if (shift == 0 && krange)  // the first pass maps the keys into the range
+            rs_upsweep<true><<<G, RS_THREADS, 0, stream>>>(ki, d_count, cap, shift, mask, counts, krange);
+        else
+            rs_upsweep<false><<<G, RS_THREADS, 0, stream>>>(ki, d_count, cap, shift, mask, counts, krange);
+        rs_scan<<<RADIX, RS_THREADS, 0, stream>>>(counts, G, totals, shift, krange);
+        if (shift == 0 && krange)
+            rs_downsweep<true><<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts, totals,
+                                                             krange);
+        else
+            rs_downsweep<false><<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts,
+                                                              totals, krange);
         cur ^= 1;
     }
     return cur;
@@ -293,11 +394,12 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 //                capacity check;
 //   bin_offsets: per (group, tile), the count matrix becomes the chunks' first
 //                slots, and group 0 writes the tile's range;
-//   bin_scatter: one block per chunk places the chunk's pairs (below).
+//   coarse_place: one block per chunk places the chunk's pairs (below).
 // On the tile grid only the tile totals are used (bin_count, bin_groups,
 // bin_starts: each tile's start and range); the placement runs on the grid of
-// super-tiles (BinGeom.sup), where bin_scatter places entry positions, and
-// stage 2b fills the tiles.
+// super-tiles (BinGeom.sup), where coarse_place writes the super-tile lists,
+// and stage 2b fills the tiles (or, in the super-tile form, the compositing
+// kernels filter them).
 constexpr int BIN_GROUP = 16;
 constexpr int COUNT_THREADS = 1024;
 
@@ -478,10 +580,15 @@ __global__ void bin_groups(BinGeom g, uint32_t *__restrict__ G1, uint32_t *__res
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gt >= g.tiles) return;
     uint32_t run = 0;
-    for (int64_t k = 0; k < g.n_g; ++k) {
-        const uint32_t x = G1[k * g.tiles + gt];
-        G1[k * g.tiles + gt] = run;
-        run += x;
+    for (int64_t k0 = 0; k0 < g.n_g; k0 += 16) {  // 16 independent loads in flight, then their prefix
+        uint32_t x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = k0 + j < g.n_g ? G1[(k0 + j) * g.tiles + gt] : 0u;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (k0 + j < g.n_g) G1[(k0 + j) * g.tiles + gt] = run;
+            run += x[j];
+        }
     }
     tile_total[gt] = run;
 }
@@ -558,238 +665,199 @@ __global__ void bin_offsets(BinGeom g, const gs_camera *__restrict__ cams, int n
     }
 }
 
-// One block per chunk.  The chunk's first slot per tile is held in shared
-// memory (s_off).  The block takes its entries WIN at a time (a window, WIN =
-// the bits of one tile's entry mask); the window's pairs, in order (entry,
-// then tile row-major), are expanded with each thread taking an equal
-// contiguous run, so one large rectangle does not stall the block.
-//   pass A: every pair sets bit j (its entry within the window) in its tile's
-//           mask (shared atomicOr, order-free);
-//   pass B: a pair's rank among the window's pairs of its tile is the number
-//           of mask bits below j; it goes to s_off[tile] + rank.  The pair
-//           with the highest bit then advances s_off[tile] by the mask's
-//           population and clears the mask.
-// Pass B runs in sub-windows of SC_THREADS * SC_Q pairs; a tile's last pair is
-// never in an earlier sub-window than its other pairs, so each sub-window's
-// advances can follow it directly.
-constexpr int SC_THREADS = 512;
-constexpr int SC_Q = 4;  // pairs per thread per sub-window
+// The super-tile lists, placed by warps.  One block per chunk of a view's
+// depth-ordered entries (the chunks of the count matrix M, whose row for the
+// chunk holds each super-tile's first slot); each of its warps takes a
+// contiguous part of the chunk.  Phase 1: every warp counts its pairs per
+// super-tile (shared atomics into its own row).  Phase 2: per super-tile, the
+// warps' first slots follow from the chunk's first slot and the counts of
+// the warps before.  Phase 3, per window of 32 entries: lane j sets bit j of
+// the window's word of every super-tile of its rectangle (shared atomicOr),
+// so a pair's rank among the window's pairs of its super-tile is the
+// popcount of the bits below j; the window's pairs, spread evenly over the
+// lanes (a warp scan of the entries' pair counts; lane l takes pairs
+// p0 + l for p0 = 0, 32, ...), are written there (Gaussian index and the
+// super-tile's covered-tile mask), and the pair of each word's lowest entry
+// advances the warp's slot and clears the word.  Warps never wait on one
+// another (only __syncwarp inside a warp); the order is the stable one the
+// count matrix implies.  Shared memory: two rows of max_vt words per warp.
+constexpr int CP_MAX_WARPS = 16;
 
-template <typename W, int NW>
-struct ScatterMask {
-    static constexpr int WB = 8 * (int)sizeof(W);
-    static constexpr int WIN = WB * NW;  // entries per window
-    static constexpr size_t bytes_per_tile = sizeof(W) * NW + sizeof(uint32_t);
-};
-
-// Walks the pairs [p0, p1) of a window in list order.
-struct PairWalk {
-    int jj, dx, t, w, nxt;
-    __device__ __forceinline__ void start(int p0, const int *s_pre, const ushort4 *s_er, int win, int tx) {
-        int lo = 0, hi = win - 1;  // the last j with s_pre[j] <= p0 (so empty entries are skipped)
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_pre[mid] <= p0) lo = mid; else hi = mid - 1;
+// Window of 32 entries of a warp: lane j holds entry j's rectangle (in the
+// super-tile grid) and the inclusive prefix of the pair counts.
+struct PairWindow {
+    ushort4 r;
+    int incl, total;
+    // pair p of the window -> its entry j and super-tile (cx, cy)
+    __device__ __forceinline__ void pair(int p, int &j, int &cx, int &cy) const {
+        int lo = 0;  // the first lane whose inclusive prefix exceeds p
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+            if (probe <= p) lo += step;
         }
-        jj = lo;
-        const ushort4 er = s_er[jj];
-        w = er.z;
-        const int k = p0 - s_pre[jj], dy = k / w;
-        dx = k - dy * w;
-        t = (er.y + dy) * tx + er.x + dx;
-        nxt = s_pre[jj + 1];
-    }
-    // step from pair p to pair p + 1 (p + 1 < end of the window)
-    __device__ __forceinline__ void next(int p, const int *s_pre, const ushort4 *s_er, int tx) {
-        if (p + 1 == nxt) {
-            do { ++jj; } while (s_pre[jj + 1] <= p + 1);
-            const ushort4 er = s_er[jj];
-            w = er.z;
-            dx = 0;
-            t = er.y * tx + er.x;
-            nxt = s_pre[jj + 1];
-        } else if (++dx == w) {
-            dx = 0;
-            t += tx - (w - 1);
+        j = lo;
+        const uint32_t xy = __shfl_sync(0xffffffffu, (uint32_t)r.x | ((uint32_t)r.y << 16), j);
+        const int w = __shfl_sync(0xffffffffu, (int)r.z, j);
+        const int before = __shfl_sync(0xffffffffu, incl - (int)r.z * r.w, j);
+        const int k = p - before;
+        int dy = 0;
+        if (w > 1) {  // k / w from the float reciprocal, corrected by one step (k, w < 2^16)
+            dy = __float2int_rz((float)k * __frcp_rn((float)w));
+            if (dy * w > k) --dy;
+            else if ((dy + 1) * w <= k) ++dy;
         } else {
-            ++t;
+            dy = k;
         }
+        cx = (int)(xy & 0xffffu) + (k - dy * w);
+        cy = (int)(xy >> 16) + dy;
     }
 };
 
-// Places each pair's Gaussian index into vals and, on the super-tile grid,
-// the mask of the super-tile's tiles that the entry's tile rectangle covers
-// into masks (cover_mask): the records the tile placement and the
-// compositing kernels' super-tile form read.
-template <typename W, int NW>  // W: 32-bit mask words
-__global__ void __launch_bounds__(SC_THREADS) bin_scatter(const ushort4 *__restrict__ srect,
-                                                          const uint32_t *__restrict__ order,
-                                                          const gs_camera *__restrict__ cams, BinGeom g,
-                                                          const uint32_t *__restrict__ M,
-                                                          const int64_t *sort_count, uint32_t *__restrict__ vals,
-                                                          uint16_t *__restrict__ masks) {
-    using SM = ScatterMask<W, NW>;
-    constexpr int WB = SM::WB, WIN = SM::WIN;
-    extern __shared__ __align__(16) unsigned char s_raw[];
-    W *s_mask = reinterpret_cast<W *>(s_raw);                                     // [max_vt][NW]
-    uint32_t *s_off = reinterpret_cast<uint32_t *>(s_mask + (size_t)g.max_vt * NW);  // [max_vt]
-    __shared__ ushort4 s_er[WIN];    // the window's rectangles (in the geometry's grid)
-    __shared__ uint32_t s_eg[WIN];   // Gaussian indices
-    __shared__ ushort4 s_fr[WIN];    // the window's tile rectangles
-    __shared__ int s_pre[WIN + 1];   // first pair of each entry
-    __shared__ uint32_t s_tj[SC_THREADS * SC_Q];  // first sub-window: (tile << 9 | entry) per pair
-    __shared__ uint32_t s_warp[32];
+__device__ __forceinline__ PairWindow pair_window(ushort4 r, int lane) {
+    PairWindow pw;
+    pw.r = r;
+    int inc = (int)r.z * r.w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    pw.incl = inc;
+    pw.total = __shfl_sync(0xffffffffu, inc, 31);
+    return pw;
+}
+
+__global__ void __launch_bounds__(CP_MAX_WARPS * 32) coarse_place(const ushort4 *__restrict__ srect,
+                                                                  const uint32_t *__restrict__ order,
+                                                                  const gs_camera *__restrict__ cams, BinGeom g,
+                                                                  const uint32_t *__restrict__ M,
+                                                                  const int64_t *sort_count,
+                                                                  uint32_t *__restrict__ gid_out,
+                                                                  uint16_t *__restrict__ mask_out) {
+    extern __shared__ uint32_t s_tab[];  // [warps][max_vt] counts, then slots; [warps][max_vt] window bits
     if (*sort_count == 0) return;
     const int64_t v = blockIdx.x / g.n_c, c = blockIdx.x % g.n_c;
     const ViewTiles vt = view_grid(g, cams, v);
     if (!view_fits(vt, g.tiles, g.max_vt)) return;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const int T = vt.tx * vt.ty;
-    const uint32_t *row = M + g.n_c * vt.off + c * T;
-    for (int t = threadIdx.x; t < T; t += SC_THREADS) {
-        s_off[t] = row[t];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) s_mask[t * NW + k] = 0;
+    uint32_t *slot = s_tab + (size_t)warp * g.max_vt;
+    uint32_t *bits = s_tab + (size_t)(nw + warp) * g.max_vt;
+    for (int t = threadIdx.x; t < nw * T; t += blockDim.x) {
+        s_tab[(size_t)(t / T) * g.max_vt + t % T] = 0u;
+        s_tab[(size_t)(nw + t / T) * g.max_vt + t % T] = 0u;
     }
+    __syncthreads();
     const int64_t e0 = v * g.n + c * g.chunk, e1 = v * g.n + min((c + 1) * g.chunk, g.n);
-    for (int64_t base = e0; base < e1; base += WIN) {
-        int area = 0;
-        if (threadIdx.x < WIN) {
-            const int64_t i = base + threadIdx.x;
-            ushort4 r = make_ushort4(0, 0, 0, 0);
-            uint32_t gi = 0;
-            ushort4 fr = make_ushort4(0, 0, 0, 0);
-            if (i < e1) {
-                fr = srect[i];
-                r = grid_rect(g, fr);
-                gi = (uint32_t)((int64_t)order[i] - v * g.n);
+    const int64_t per = ((e1 - e0 + nw - 1) / nw + 31) / 32 * 32;  // whole windows per warp
+    const int64_t w0 = min(e1, e0 + warp * per), w1 = min(e1, w0 + per);
+    // phase 1: the warp's pairs per super-tile (each lane its own entry's, row by row)
+    for (int64_t base = w0; base < w1; base += 32) {
+        const int64_t i = base + lane;
+        const ushort4 r = i < w1 ? grid_rect(g, srect[i]) : make_ushort4(0, 0, 0, 0);
+        const int area = (int)r.z * r.w;
+        int t = r.y * vt.tx + r.x, x = 0;
+        for (int k = 0; k < area; ++k) {
+            atomicAdd(&slot[t], 1u);
+            if (++x == r.z) {
+                x = 0;
+                t += vt.tx - (r.z - 1);
+            } else {
+                ++t;
             }
-            s_er[threadIdx.x] = r;
-            s_eg[threadIdx.x] = gi;
-            s_fr[threadIdx.x] = fr;
-            area = (int)r.z * r.w;
         }
-        // the window's pair prefix: a warp scan in the WIN / 32 warps holding
-        // entries, their totals through shared memory (one barrier).  The
-        // barrier also orders the previous window's mask clearing and slot
-        // advances before this window's pass A.
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        int inc = area;
-        if (threadIdx.x < WIN) {  // whole warps
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, inc, off);
-                if (lane >= off) inc += y;
-            }
-            if (lane == 31) s_warp[warp] = (uint32_t)inc;
+    }
+    __syncthreads();
+    // phase 2: the warps' first slots per super-tile
+    const uint32_t *row = M + g.n_c * vt.off + c * T;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        uint32_t run = row[t];
+        for (int w = 0; w < nw; ++w) {
+            uint32_t *x = s_tab + (size_t)w * g.max_vt + t;
+            const uint32_t cnt = *x;
+            *x = run;
+            run += cnt;
         }
-        __syncthreads();
-        int before = 0, tot = 0;
-#pragma unroll
-        for (int w = 0; w < WIN / 32; ++w) {
-            const int x = (int)s_warp[w];
-            before += w < warp ? x : 0;
-            tot += x;
+    }
+    __syncthreads();
+    // phase 3: place (the next window's entries load while this one is placed)
+    ushort4 fr_next = make_ushort4(0, 0, 0, 0);
+    uint32_t g_next = 0;
+    if (w0 + lane < w1) {
+        fr_next = srect[w0 + lane];
+        g_next = (uint32_t)((int64_t)order[w0 + lane] - v * g.n);
+    }
+    for (int64_t base = w0; base < w1; base += 32) {
+        const ushort4 fr = fr_next;  // lane j: entry j's tile rectangle and Gaussian index
+        const uint32_t gi = g_next;
+        const int64_t nx = base + 32 + lane;
+        if (nx < w1) {
+            fr_next = srect[nx];
+            g_next = (uint32_t)((int64_t)order[nx] - v * g.n);
         }
-        if (threadIdx.x < WIN) s_pre[threadIdx.x] = before + inc - area;
-        if (threadIdx.x == 0) s_pre[WIN] = tot;
-        __syncthreads();
-        // pass A: entry masks per tile (the first sub-window's pairs are also
-        // recorded for pass B)
-        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
-            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
-            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
-            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
-            if (p0 < p1) {
-                PairWalk it;
-                it.start(p0, s_pre, s_er, WIN, vt.tx);
-                for (int p = p0;; ++p) {
-                    atomicOr(&s_mask[it.t * NW + it.jj / WB], (W)1 << (it.jj % WB));
-                    if (sw == 0) s_tj[p] = ((uint32_t)it.t << 9) | (uint32_t)it.jj;  // for pass B
-                    if (p + 1 >= p1) break;
-                    it.next(p, s_pre, s_er, vt.tx);
+        const ushort4 r = base + lane < w1 ? grid_rect(g, fr) : make_ushort4(0, 0, 0, 0);
+        const int area = (int)r.z * r.w;
+        const int t0 = r.y * vt.tx + r.x;
+        {  // pass A: the lane's own pairs, row by row
+            int t = t0, x = 0;
+            for (int k = 0; k < area; ++k) {
+                atomicOr(&bits[t], 1u << lane);
+                if (++x == r.z) {
+                    x = 0;
+                    t += vt.tx - (r.z - 1);
+                } else {
+                    ++t;
                 }
             }
         }
-        __syncthreads();
-        // pass B: place, then advance the tiles whose last pair is in this sub-window
-        for (int sw = 0; sw < tot; sw += SC_THREADS * SC_Q) {
-            const int cnt = min(SC_THREADS * SC_Q, tot - sw);
-            const int q = (cnt + SC_THREADS - 1) / SC_THREADS;
-            const int p0 = sw + min(cnt, (int)threadIdx.x * q), p1 = sw + min(cnt, ((int)threadIdx.x + 1) * q);
-            int last_t[SC_Q];
-            uint32_t last_n[SC_Q];
-#pragma unroll
-            for (int k = 0; k < SC_Q; ++k) last_t[k] = -1;
-            if (p0 < p1) {
-                PairWalk it;
-                if (sw != 0) it.start(p0, s_pre, s_er, WIN, vt.tx);
-#pragma unroll
-                for (int k = 0; k < SC_Q; ++k) {
-                    const int p = p0 + k;
-                    if (p >= p1) break;
-                    int t, jj;
-                    if (sw == 0) {  // the first sub-window's pairs were recorded by pass A
-                        const uint32_t tj = s_tj[p];
-                        t = (int)(tj >> 9);
-                        jj = (int)(tj & 0x1ffu);
-                    } else {
-                        if (k > 0) it.next(p - 1, s_pre, s_er, vt.tx);
-                        t = it.t;
-                        jj = it.jj;
-                    }
-                    const int jw = jj / WB, jb = jj % WB;
-                    W mw[NW];
-                    if constexpr (NW == 4) {  // the tile's four words in one 16-byte load
-                        static_assert(sizeof(W) == 4, "four 32-bit mask words");
-                        const uint4 q4 = *reinterpret_cast<const uint4 *>(s_mask + t * NW);
-                        mw[0] = q4.x;
-                        mw[1] = q4.y;
-                        mw[2] = q4.z;
-                        mw[3] = q4.w;
-                    } else {
-#pragma unroll
-                        for (int wd = 0; wd < NW; ++wd) mw[wd] = s_mask[t * NW + wd];
-                    }
-                    uint32_t below = 0, all = 0;
-#pragma unroll
-                    for (int wd = 0; wd < NW; ++wd) {
-                        const W m = mw[wd];
-                        const uint32_t pc = (uint32_t)__popc((uint32_t)m);
-                        all += pc;
-                        if (wd < jw) below += pc;
-                        if (wd == jw) below += (uint32_t)__popc((uint32_t)(m & (((W)1 << jb) - 1)));
-                    }
-                    vals[s_off[t] + below] = s_eg[jj];
-                    masks[s_off[t] + below] =
-                        (uint16_t)cover_mask(s_fr[jj], (t % vt.tx) * SUP, (t / vt.tx) * SUP);
-                    if (below + 1 == all) {  // the tile's last pair of the window
-                        last_t[k] = t;
-                        last_n[k] = all;
-                    }
-                }
+        __syncwarp();
+        // pass B: the window's pairs spread evenly over the lanes
+        const PairWindow pw = pair_window(r, lane);
+        const uint32_t fxy = (uint32_t)fr.x | ((uint32_t)fr.y << 16), fwh = (uint32_t)fr.z | ((uint32_t)fr.w << 16);
+        for (int p0 = 0; p0 < pw.total; p0 += 32) {
+            int j = 0, cx = 0, cy = 0;
+            pw.pair(p0 + lane, j, cx, cy);
+            const uint32_t jxy = __shfl_sync(0xffffffffu, fxy, j);
+            const uint32_t jwh = __shfl_sync(0xffffffffu, fwh, j);
+            const uint32_t gj = __shfl_sync(0xffffffffu, gi, j);
+            if (p0 + lane < pw.total) {
+                const int t = cy * vt.tx + cx;
+                const uint32_t d = slot[t] + (uint32_t)__popc(bits[t] & ((1u << j) - 1u));
+                const ushort4 frj = make_ushort4((unsigned short)(jxy & 0xffffu), (unsigned short)(jxy >> 16),
+                                                 (unsigned short)(jwh & 0xffffu), (unsigned short)(jwh >> 16));
+                gid_out[d] = gj;
+                mask_out[d] = (uint16_t)cover_mask(frj, cx * SUP, cy * SUP);
             }
-            __syncthreads();
-            // No barrier after the advances: a tile advanced here has no pair in
-            // a later sub-window of this window, and the next window's first
-            // barrier orders them before its pass A.
-#pragma unroll
-            for (int k = 0; k < SC_Q; ++k) {
-                if (last_t[k] >= 0) {
-                    s_off[last_t[k]] += last_n[k];
-#pragma unroll
-                    for (int wd = 0; wd < NW; ++wd) s_mask[last_t[k] * NW + wd] = 0;
+        }
+        __syncwarp();
+        {  // pass C: the lane's own pairs again
+            int t = t0, x = 0;
+            for (int k = 0; k < area; ++k) {
+                const uint32_t b = bits[t];
+                if (b != 0u && (b & lt) == 0u) {  // the word's lowest entry (others see it or 0)
+                    slot[t] += (uint32_t)__popc(b);
+                    bits[t] = 0u;
+                }
+                if (++x == r.z) {
+                    x = 0;
+                    t += vt.tx - (r.z - 1);
+                } else {
+                    ++t;
                 }
             }
         }
+        __syncwarp();
     }
 }
 
-// Window width of the super-tile scatter: 512 entries (sixteen 32-bit masks
-// per super-tile) where the table stays small enough for two blocks per SM,
-// else 128.  The masks are 32-bit words because shared-memory atomicOr is
-// native at that width.
-bool coarse_scatter_wide(int64_t max_vt) {
-    return (size_t)max_vt * ScatterMask<uint32_t, 16>::bytes_per_tile <= (size_t)96 * 1024;
+// Warps per block of coarse_place: the most (up to CP_MAX_WARPS, a power of
+// two) whose tables fit 200 KB of shared memory.
+int coarse_place_warps(int64_t max_vt) {
+    int w = CP_MAX_WARPS;
+    while (w > 1 && (size_t)2 * w * max_vt * sizeof(uint32_t) > (size_t)200 * 1024) w >>= 1;
+    return w;
 }
 
 // ----------------------------------------------------------------------------
@@ -1045,7 +1113,10 @@ BinGeom bin_geom(int64_t n, int64_t total_tiles, int tile, int max_vt) {
 // + 1 super-tiles (tx + ty <= T + 1), so all views together at most
 // total_tiles / 4 + n_views.  Smaller tables allow shorter chunks (about four
 // per SM).
-BinGeom coarse_geom(int64_t n, int64_t total_tiles, int64_t n_views, int tile, int max_vt, const int64_t *coff) {
+// max_super > 0: the caller's bound on one view's super-tiles (at most the
+// above), which sizes the shared-memory tables of the placement.
+BinGeom coarse_geom(int64_t n, int64_t total_tiles, int64_t n_views, int tile, int max_vt, const int64_t *coff,
+                    int max_super = 0) {
     BinGeom g;
     g.n = n;
     g.chunk = bin_chunk(n, 608);
@@ -1054,6 +1125,7 @@ BinGeom coarse_geom(int64_t n, int64_t total_tiles, int64_t n_views, int tile, i
     g.tiles = total_tiles / 4 + n_views;
     g.tile = tile;
     g.max_vt = max_vt / 4 + 1;
+    if (max_super > 0 && max_super < g.max_vt) g.max_vt = max_super;
     g.sup = SUP;
     g.coff = coff;
     return g;
@@ -1107,7 +1179,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
         char *b = take(sizeof(uint32_t) * (size_t)(total > 0 ? total : 1));
         if (w) { w->dk[i] = (uint32_t *)a; w->dv[i] = (uint32_t *)b; }
     }
-    char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1));
+    char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1) + 2 * sizeof(uint32_t));
     char *G1 = take(sizeof(uint32_t) * (size_t)(g.n_g * total_tiles));
     char *tt = take(sizeof(uint32_t) * (size_t)total_tiles);
     char *ts = take(sizeof(uint32_t) * (size_t)total_tiles);
@@ -1260,12 +1332,8 @@ gs_status bin_smem_attributes() {
     if (done[dev]) return GS_OK;
     const int bytes = (int)(sizeof(uint32_t) * kMaxViewTiles);
     GS_TRY(cudaFuncSetAttribute(bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bytes + 8));
-    // the super-tile scatter: tables of at most kMaxViewTiles / 4 + 1 super-tiles
-    const int coarse_vt = kMaxViewTiles / 4 + 1;
-    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(96 * 1024)));
-    GS_TRY(cudaFuncSetAttribute(bin_scatter<uint32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(ScatterMask<uint32_t, 4>::bytes_per_tile * coarse_vt)));
+    // the super-tile placement: its warps' tables within 200 KB (coarse_place_warps)
+    GS_TRY(cudaFuncSetAttribute(coarse_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
     done[dev] = true;
     return GS_OK;
 }
@@ -1286,7 +1354,8 @@ namespace {
 // gs_bin_sort (coarse == nullptr) and gs_bin_sort_coarse (the super-tile
 // lists into the caller's buffers, without the placement of the pairs).
 gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
-                        int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg, void *workspace,
+                        int64_t total_tiles, int32_t max_view_tiles, int32_t max_super, const gs_raster_config *cfg,
+                        void *workspace,
                         size_t workspace_bytes, uint64_t *keys, uint32_t *vals, const gs_coarse_lists *coarse,
                         int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status,
                         cudaStream_t stream) {
@@ -1339,13 +1408,22 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
     const BinGeom g = bin_geom(n, total_tiles, cfg->tile, (int)mvt);
     // 1. depth order of all (view, Gaussian) entries, then grouped by view
     int sel;
+    uint32_t *krange = w.counts + (size_t)RADIX * (RS_MAX_BLOCKS + 1);
+    GS_TRY(cudaMemsetAsync(krange, 0xff, sizeof(uint32_t), stream));
+    GS_TRY(cudaMemsetAsync(krange + 1, 0, sizeof(uint32_t), stream));
+    const unsigned kr_blocks = (unsigned)min((int64_t)device_sm_count() * 4, ceil_div(total, (int64_t)256));
     if (proj->depth_key) {  // written by gs_project
-        sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream, proj->depth_key);
+        key_range_kernel<<<kr_blocks, 256, 0, stream>>>(proj->depth_key, total, krange);
+        GS_TRY_LAUNCH();
+        sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream, proj->depth_key,
+                         krange);
     } else {
         depth_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(proj->rec, proj->tiles_touched, total,
                                                                              w.dk[0], w.dv[0]);
         GS_TRY_LAUNCH();
-        sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream);
+        key_range_kernel<<<kr_blocks, 256, 0, stream>>>(w.dk[0], total, krange);
+        GS_TRY_LAUNCH();
+        sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream, nullptr, krange);
     }
     GS_TRY_LAUNCH();
     if (n_views > 1) {
@@ -1389,7 +1467,8 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
     // the super-tile grid
     coarse_offsets<<<1, 32, 0, stream>>>(cams, n_views, cfg->tile, w.coff);
     GS_TRY_LAUNCH();
-    const BinGeom gc = coarse_geom(n, total_tiles, n_views, cfg->tile, (int)mvt, w.coff);
+    if (max_super < 0) return GS_ERR_INVALID_ARG;
+    const BinGeom gc = coarse_geom(n, total_tiles, n_views, cfg->tile, (int)mvt, w.coff, max_super);
     const size_t csmem = sizeof(uint32_t) * (size_t)gc.max_vt;
     GS_TRY(cudaMemsetAsync(w.G1c, 0, sizeof(uint32_t) * (size_t)(gc.n_g * gc.tiles), stream));
     const unsigned n_cchunks = (unsigned)(gc.n_c * n_views);
@@ -1405,12 +1484,12 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
     bin_offsets<<<(unsigned)ceil_div(gc.n_g * gc.tiles, (int64_t)256), 256, 0, stream>>>(
         gc, cams, n_views, w.G1c, w.cstart, w.ctotal, w.c_count + 1, w.Mc, nullptr);
     GS_TRY_LAUNCH();
-    if (coarse_scatter_wide(gc.max_vt))
-        bin_scatter<uint32_t, 16><<<n_cchunks, SC_THREADS, ScatterMask<uint32_t, 16>::bytes_per_tile * gc.max_vt,
-                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.cmask);
-    else
-        bin_scatter<uint32_t, 4><<<n_cchunks, SC_THREADS, ScatterMask<uint32_t, 4>::bytes_per_tile * gc.max_vt,
-                                         stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid, w.cmask);
+    {
+        const int cw = coarse_place_warps(gc.max_vt);
+        const size_t cp_smem = (size_t)2 * cw * gc.max_vt * sizeof(uint32_t);
+        coarse_place<<<n_cchunks, cw * 32, cp_smem, stream>>>(w.srect, order, cams, gc, w.Mc, w.c_count + 1, w.cgid,
+                                                             w.cmask);
+    }
     GS_TRY_LAUNCH();
     if (co) {
         coarse_tile_totals<<<(unsigned)(gc.tiles * TT_SPLIT), TT_THREADS, 0, stream>>>(cams, n_views, gc, total_tiles, (int)mvt,
@@ -1463,8 +1542,8 @@ gs_status gs_bin_sort(const gs_projected *proj, const gs_camera *cams, int32_t n
                       size_t workspace_bytes, uint64_t *keys, uint32_t *vals, int64_t pair_capacity,
                       uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
     if (!vals) return GS_ERR_INVALID_ARG;
-    return bin_sort_impl(proj, cams, n_views, n, total_tiles, max_view_tiles, cfg, workspace, workspace_bytes, keys,
-                         vals, nullptr, pair_capacity, ranges, dev_pair_count, dev_status, stream);
+    return bin_sort_impl(proj, cams, n_views, n, total_tiles, max_view_tiles, 0, cfg, workspace, workspace_bytes,
+                         keys, vals, nullptr, pair_capacity, ranges, dev_pair_count, dev_status, stream);
 }
 
 size_t gs_bin_sort_coarse_workspace_size(int64_t n, int32_t n_views, int64_t total_tiles) {
@@ -1473,13 +1552,14 @@ size_t gs_bin_sort_coarse_workspace_size(int64_t n, int32_t n_views, int64_t tot
 }
 
 gs_status gs_bin_sort_coarse(const gs_projected *proj, const gs_camera *cams, int32_t n_views, int64_t n,
-                             int64_t total_tiles, int32_t max_view_tiles, const gs_raster_config *cfg,
-                             void *workspace, size_t workspace_bytes, const gs_coarse_lists *lists,
-                             int64_t pair_capacity, uint32_t *ranges, int64_t *dev_pair_count, int32_t *dev_status,
-                             cudaStream_t stream) {
+                             int64_t total_tiles, int32_t max_view_tiles, int32_t max_view_super_tiles,
+                             const gs_raster_config *cfg, void *workspace, size_t workspace_bytes,
+                             const gs_coarse_lists *lists, int64_t pair_capacity, uint32_t *ranges,
+                             int64_t *dev_pair_count, int32_t *dev_status, cudaStream_t stream) {
     if (!lists) return GS_ERR_INVALID_ARG;
-    return bin_sort_impl(proj, cams, n_views, n, total_tiles, max_view_tiles, cfg, workspace, workspace_bytes,
-                         nullptr, nullptr, lists, pair_capacity, ranges, dev_pair_count, dev_status, stream);
+    return bin_sort_impl(proj, cams, n_views, n, total_tiles, max_view_tiles, max_view_super_tiles, cfg, workspace,
+                         workspace_bytes, nullptr, nullptr, lists, pair_capacity, ranges, dev_pair_count, dev_status,
+                         stream);
 }
 
 }  // extern "C"

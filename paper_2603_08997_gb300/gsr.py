@@ -101,7 +101,8 @@ _PROTOS = {
     "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config),
                                       _P, _P, _I64, _P, _P, _P, _S]),
     "gs_bin_sort_coarse_workspace_size": (C.c_size_t, [_I64, _I32, _I64]),
-    "gs_bin_sort_coarse": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, C.POINTER(gs_raster_config),
+    "gs_bin_sort_coarse": (C.c_int, [C.POINTER(gs_projected), _P, _I32, _I64, _I64, _I32, _I32,
+                                     C.POINTER(gs_raster_config),
                                      _P, _SZ, C.POINTER(gs_coarse_lists), _I64, _P, _P, _P, _S]),
     "gs_tile_order": (C.c_int, [_P, _I64, _P, _S]),
     "gs_render_fwd_coarse": (C.c_int, [C.POINTER(gs_projected), _I64, C.POINTER(gs_coarse_lists), _P, _P, _I32, _I64,

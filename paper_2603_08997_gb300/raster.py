@@ -122,6 +122,8 @@ class Views:
         self.dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
         self.sizes = [(int(c.width), int(c.height)) for c in cams]
         self.max_view_tiles = max(-(-w // tile) * -(-h // tile) for w, h in self.sizes)
+        # super-tiles of 4 x 4 tiles per view (the super-tile lists' tables)
+        self.max_view_super_tiles = max(-(-(-(-w // tile)) // 4) * -(-(-(-h // tile)) // 4) for w, h in self.sizes)
         self.pix_offsets = [int(self.host[v].pix_offset) for v in range(self.n)]
 
     def image_view(self, flat: torch.Tensor, v: int) -> torch.Tensor:
@@ -225,7 +227,8 @@ class Renderer:
         proj = self.c_proj()
         if self.coarse:
             gsr.call("gs_bin_sort_coarse", C.byref(proj), gsr.ptr(self.views.dev), self.views.n, self.n,
-                     self.views.total_tiles, self.views.max_view_tiles, C.byref(self.cfg), gsr.ptr(self.bin_ws),
+                     self.views.total_tiles, self.views.max_view_tiles, self.views.max_view_super_tiles,
+                     C.byref(self.cfg), gsr.ptr(self.bin_ws),
                      self.bin_ws_bytes, C.byref(self.lists), self.cap, gsr.ptr(self.ranges),
                      gsr.ptr(self.pair_count), gsr.ptr(self.status), gsr.stream_handle(stream))
         else:

@@ -256,3 +256,27 @@ def test_loop_equals_tile_lists():
         loop.close()
     np.testing.assert_allclose(logs[1]["loss"], logs[0]["loss"], rtol=1e-5)
     assert np.array_equal(logs[0]["g"], logs[1]["g"])
+
+
+def test_super_tile_bound_too_small_is_an_error():
+    """A view with more super-tiles than max_view_super_tiles: GS_ERR_INVALID_ARG
+    in the status word and no entries or ranges for it; the exact bound works."""
+    import ctypes as C
+    sizes, cams, dev, _ = _case(1, 2000, 501, 16)
+    r = _renderer(cams, 2000, True)
+    gpu_util.set_projected(r, dev)
+    exact = r.views.max_view_super_tiles
+    for bound, want in ((exact, 0), (exact - 1, gsr.GS_ERR_INVALID_ARG)):
+        r.status.zero_()
+        r.ranges.fill_(7)
+        proj = r.c_proj()
+        gsr.call("gs_bin_sort_coarse", C.byref(proj), gsr.ptr(r.views.dev), r.views.n, r.n, r.views.total_tiles,
+                 r.views.max_view_tiles, bound, C.byref(r.cfg), gsr.ptr(r.bin_ws), r.bin_ws_bytes,
+                 C.byref(r.lists), r.cap, gsr.ptr(r.ranges), gsr.ptr(r.pair_count), gsr.ptr(r.status),
+                 gsr.stream_handle())
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == want
+        if want:
+            assert int(r.ranges.abs().sum().item()) == 0 and int(r.c_total.item()) == 0
+        else:
+            assert int(r.c_total.item()) > 0 and int(r.ranges.abs().sum().item()) > 0
