@@ -74,9 +74,10 @@ def parse():
                     help="NEXT-4: opacity prune + compaction at eps_alpha in (0.005, 0.05, 0.2), then SkipGS")
     ap.add_argument("--c2", action="store_true", help="C2: 200k-Gaussian fwd+bwd+Adam iteration timing")
     ap.add_argument("--c5", action="store_true", help="C5: 6M Gaussians, 4x1080p fwd+bwd batch timing and memory")
-    ap.add_argument("--lists", default="coarse", choices=["coarse", "tile"],
+    ap.add_argument("--lists", default="coarse", choices=["coarse", "tile", "auto"],
                     help="coarse: the binning writes super-tile lists and the compositing kernels filter each "
-                         "tile's entries from them; tile: per-tile lists (gs_bin_sort)")
+                         "tile's entries from them; tile: per-tile lists (gs_bin_sort); auto (the --c2 and --c4 "
+                         "modes): the faster of the two on the mode's workload (autotune.choose_list_form)")
     ap.add_argument("--stages-once", action="store_true",
                     help="run two eager iterations of every stage on one view of the workload and exit "
                          "(a small, fixed launch sequence for hardware-counter captures)")
@@ -123,6 +124,9 @@ def run_c4(args) -> None:
     # view with its own tile grid
     import dataclasses
     st = dataclasses.replace(st, persistent=not args.c4_slots, coarse_lists=args.lists == "coarse")
+    form_ms = None
+    if args.lists == "auto":  # the faster list form for this batch shape
+        st, form_ms = autotune.choose_list_form(model, cams[:B], targets[:B], st, pair_capacity=cap)
     pre = RefinementLoop(model, cams, targets, synth.pre_sequence(pre_iters * B, args.views), st, gated=False,
                          pair_capacity=cap, views_per_step=B)
     pre.capture()
@@ -176,7 +180,8 @@ def run_c4(args) -> None:
                   "persistent: resident blocks take (view, tile) items longest-first from a queue; per-view tile grids",
         "autotuned": {"tile": st.tile, "batch": st.batch, "pixels_per_thread_fwd": st.pixels_per_thread_fwd,
                       "pixels_per_thread_bwd": st.pixels_per_thread,
-                      "candidates_ms": {f"{t}/{b}/{pf}/{pb}": v for (t, b, pf, pb), v in tune_ms.items()}},
+                      "candidates_ms": {f"{t}/{b}/{pf}/{pb}": v for (t, b, pf, pb), v in tune_ms.items()},
+                      "lists": "super-tile" if st.coarse_lists else "tile", "list_form_ms": form_ms},
         "device_status": [s_full, s_gated, s_g1, s_fp, s_gp], "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.n // 1000000}M Gaussians SH3, {args.views} ring views at resolutions drawn "
                                "from 640x360/980x545/1297x840/1600x1063, 8 views per iteration",
@@ -441,8 +446,12 @@ def run_c2(args) -> None:
     target = (rt.image.view(1, 3, cam.height, cam.width) + torch.from_numpy(noise).to(dev)).contiguous()
     del mt, rt
     torch.cuda.synchronize()
-    torch.cuda.reset_peak_memory_stats(dev)
     model = raster.GaussianModel.from_scene(scene, dev)
+    form_ms = None
+    if args.lists == "auto":  # the faster list form on this workload
+        from paper_2603_08997_gb300 import autotune
+        st, form_ms = autotune.choose_list_form(model, [cam], [target[0]], st, pair_capacity=48 * scene.n)
+    torch.cuda.reset_peak_memory_stats(dev)
     K = max(args.steps, 1)
     loop = RefinementLoop(model, [cam], target, np.zeros(K + args.warmup, np.int32), st, gated=False,
                           pair_capacity=48 * scene.n)
@@ -463,6 +472,7 @@ def run_c2(args) -> None:
                       "stage_ms": {k: round(v["ms"], 4) for k, v in stages.items()},
                       "pairs": int(loop.renderer.pair_count.item()), "status": int(loop.renderer.status.item()),
                       "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                      "lists": "super-tile" if st.coarse_lists else "tile", "list_form_ms": form_ms,
                       "dtype": "f32", "data": "synthetic"}))
 
 

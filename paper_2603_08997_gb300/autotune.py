@@ -21,7 +21,7 @@ import os
 import torch
 
 from . import gsr
-from .raster import GaussianModel, RasterSettings
+from .raster import GaussianModel, RasterSettings, Renderer, Views
 
 DEFAULT_CANDIDATES = tuple((t, b, pf, pb) for t in (8, 16, 32) for b in (64, 128, 256)
                            for pf, pb in ((1, 2), (1, 1), (2, 2)))
@@ -79,6 +79,57 @@ def time_candidates(model: GaussianModel, cams: list, targets, base: RasterSetti
     gsr.check("gs_autotune", code)
     del ws
     return [float(ms[i]) for i in range(n)]
+
+
+def choose_list_form(model: GaussianModel, cams: list, targets, base: RasterSettings | None = None, reps: int = 5,
+                     pair_capacity: int | None = None):
+    """Which list form is faster for this workload: per-tile lists, or
+    super-tile lists that the compositing kernels filter (RasterSettings.
+    coarse_lists).  The super-tile form skips writing the tile lists and
+    reads only the prefix of each list a tile composites, so it wins where
+    pixels reach the transmittance floor early (dense scenes); where tiles
+    composite their whole lists it pays for the filtering.  Both forms give
+    the same images and the same gradients up to float-atomic order, so the
+    choice is made on time alone: `reps` iterations of binning, forward,
+    loss with its gradient and the raster adjoint over all `cams` in one
+    call (projection once, outside the timing), CUDA events on the current
+    stream.  targets: one [3, H_v, W_v] device tensor per camera.  Returns
+    (settings with the faster form, {"tile": ms, "coarse": ms})."""
+    base = base or RasterSettings()
+    flat = torch.cat([t.contiguous().view(-1) for t in targets]).to(model.flat.device)
+    k = len(cams)
+    cap = int(pair_capacity) if pair_capacity else max(1 << 16, 24 * model.n * k)
+    times = {}
+    for form in ("tile", "coarse"):
+        st = dataclasses.replace(base, coarse_lists=form == "coarse")
+        r = Renderer(model.n, model.sh_degree, Views(cams, st.tile, model.flat.device), st, pair_capacity=cap)
+        p = model.c_params()
+        r.project(p)
+
+        def one():
+            r.bin_sort()
+            r.render_fwd()
+            r.compute_loss(flat, with_grad=True)
+            r.raster_bwd()
+
+        one()
+        torch.cuda.synchronize()
+        if int(r.status.item()) != 0:
+            times[form] = float("inf")  # e.g. more pairs than the capacity
+            continue
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(max(int(reps), 1)):
+            one()
+        e1.record()
+        torch.cuda.synchronize()
+        times[form] = e0.elapsed_time(e1) / max(int(reps), 1)
+        del r
+    torch.cuda.empty_cache()
+    if min(times.values()) == float("inf"):
+        raise RuntimeError("choose_list_form: neither list form runs this workload (capacity)")
+    best = min(times, key=times.get)
+    return dataclasses.replace(base, coarse_lists=best == "coarse"), times
 
 
 def autotune(model: GaussianModel, cams: list, targets, base: RasterSettings | None = None,

@@ -317,3 +317,20 @@ def test_host_targets_feed_equals_device_targets():
         loop.close()
     assert np.array_equal(logs[0]["loss"], logs[1]["loss"])
     assert np.array_equal(logs[0]["g"], logs[1]["g"])
+
+
+def test_choose_list_form_times_both_and_keeps_the_shape():
+    """autotune.choose_list_form times both list forms on the workload and
+    returns the faster one, the launch shape untouched."""
+    from paper_2603_08997_gb300 import autotune
+    gpu_util.lib()
+    scene, _, _ = synth.case_c1(n=1500)
+    cams = _cams()
+    model = raster.GaussianModel.from_scene(scene)
+    rng = np.random.default_rng(11)
+    targets = [torch.from_numpy(rng.uniform(0, 1, (3, h, w)).astype(np.float32)).cuda() for w, h in SIZES]
+    base = raster.RasterSettings(tile=8, batch=128)
+    st, ms = autotune.choose_list_form(model, cams, targets, base, reps=2)
+    assert set(ms) == {"tile", "coarse"} and all(0.0 < v < 1e3 for v in ms.values())
+    assert st.coarse_lists == (ms["coarse"] < ms["tile"])
+    assert (st.tile, st.batch) == (8, 128)
