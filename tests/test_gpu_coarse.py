@@ -280,3 +280,41 @@ def test_super_tile_bound_too_small_is_an_error():
             assert int(r.ranges.abs().sum().item()) == 0 and int(r.c_total.item()) == 0
         else:
             assert int(r.c_total.item()) > 0 and int(r.ranges.abs().sum().item()) > 0
+
+
+@pytest.mark.parametrize("depths", ["equal", "wide", "one_visible"])
+def test_depth_order_across_key_ranges(depths):
+    """The depth sort works on keys relative to the visible keys' range and
+    copies the passes above its bit length: all depths equal (every pass a
+    copy: ties in index order), depths spanning 0.2..1e5 (no pass copied),
+    and a single visible Gaussian.  Tile lists (both forms) bit-exact
+    against the oracle's binning."""
+    sizes = [(150, 97), (64, 40)]
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h) for w, h in sizes]
+    recs = [synth.projected_records(3000, w, h, seed=601 + v) for v, (w, h) in enumerate(sizes)]
+    rng = np.random.default_rng(7)
+    for r in recs:
+        if depths == "equal":
+            r["depth"][:] = np.float32(3.5)
+        elif depths == "wide":
+            r["depth"][:] = np.exp(rng.uniform(np.log(0.2), np.log(1e5), r["depth"].shape)).astype(np.float32)
+        else:
+            r["culled"][:] = True
+            r["culled"][17] = False
+    dev, orc = gpu_util.records(recs, cams, 16)
+    _, ovals, oranges, _ = oracle.bin_sort(orc, cams, 16)
+    for coarse in (False, True):
+        r = _renderer(cams, 3000, coarse)
+        r._orc = orc
+        gpu_util.set_projected(r, dev)
+        r.bin_sort()
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        assert int(r.pair_count.item()) == len(ovals)
+        assert np.array_equal(r.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), oranges)
+        if coarse:
+            for t, g in _host_lists(r, cams, 16).items():
+                assert np.array_equal(g, ovals[oranges[t, 0]:oranges[t, 1]]), t
+        else:
+            P = int(r.pair_count.item())
+            assert np.array_equal(r.vals[:P].cpu().numpy().view(np.uint32), ovals)
