@@ -12,15 +12,18 @@
 // A stable sort by tile of a depth-ordered list is ordered by
 // (tile, depth, index), i.e. exactly the 64-bit key order.  Stage 2 runs in
 // two levels: a chunked counting sort of the entries by 4 x 4-tile
-// super-tile, then, per super-tile, one warp per tile selecting the tile's
-// entries from the super-tile's depth-ordered list (stage 2b below).
+// super-tile (coarse_place), then, per super-tile, warps selecting each
+// tile's entries from the super-tile's depth-ordered list (stage 2b below).
+// gs_bin_sort_coarse stops after the first level: its lists are the output.
 //
 // Every kernel reads the counts it needs from device memory, so the whole
-// call can be captured in a CUDA graph.  The radix sort is a reduce-then-scan LSD
-// sort: an upsweep histogram per block, one exclusive scan over the
+// call can be captured in a CUDA graph.  The radix sort is a reduce-then-scan
+// LSD sort: an upsweep histogram per block, one exclusive scan over the
 // digit-major (digit, block) counts, and a downsweep that ranks each tile of
-// 2048 keys with warp ballots (one per digit bit), reorders the tile by digit in shared
-// memory and writes each digit's run contiguously.
+// 2048 keys with warp ballots (one per digit bit), reorders the tile by digit
+// in shared memory and writes each digit's run contiguously.  Keys are
+// sorted relative to the visible keys' range (key_range_kernel), so passes
+// above the range's bit length are copies.
 #include "common.cuh"
 
 using namespace gsr;
@@ -923,9 +926,9 @@ __global__ void seg_fill(int64_t tiles, const uint32_t *__restrict__ seg_base, u
     for (uint32_t it = seg_base[ct]; it < seg_base[ct + 1]; ++it) item_ct[it] = (uint32_t)ct;
 }
 
-// Geometry of work item `item`: its super-tile's first tile, view, entries.
+// Geometry of work item `item`: its view and its entries of the super-tile's list.
 struct ItemGeom {
-    int v, x0, y0, cnt;
+    int v, cnt;
     uint32_t b0;
     bool fits;
 };
@@ -940,10 +943,6 @@ __device__ __forceinline__ ItemGeom item_geom(uint32_t item, const BinGeom &gc, 
     ig.v = view_of_grid_tile(gc, cams, n_views, ct);
     const ViewTiles ft = view_tiles(cams[ig.v], gc.tile);
     ig.fits = view_fits(ft, fine_tiles, fine_max_vt);
-    const int ctx = (ft.tx + SUP - 1) / SUP;
-    const int64_t lct = (int64_t)ct - gc.coff[ig.v];
-    ig.x0 = (int)(lct % ctx) * SUP;
-    ig.y0 = (int)(lct / ctx) * SUP;
     ig.b0 = cstart[ct] + sg * WI;
     ig.cnt = (int)min((uint32_t)WI, ctotal[ct] - sg * WI);
     return ig;
@@ -1362,6 +1361,7 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
     if (!proj || !cams || !cfg || n_views <= 0 || n < 0 || total_tiles <= 0 || !ranges || !dev_pair_count)
         return GS_ERR_INVALID_ARG;
     if (!coarse && !vals) return GS_ERR_INVALID_ARG;
+    if (max_super < 0) return GS_ERR_INVALID_ARG;
     if (coarse && (!coarse->gid || !coarse->mask || !coarse->start || !coarse->count || !coarse->view_first ||
                    !coarse->total || coarse->capacity < 0 || coarse->capacity > ((int64_t)1 << 32) - 65536 ||
                    ((uintptr_t)coarse->mask & 15)))
@@ -1467,7 +1467,6 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
     // the super-tile grid
     coarse_offsets<<<1, 32, 0, stream>>>(cams, n_views, cfg->tile, w.coff);
     GS_TRY_LAUNCH();
-    if (max_super < 0) return GS_ERR_INVALID_ARG;
     const BinGeom gc = coarse_geom(n, total_tiles, n_views, cfg->tile, (int)mvt, w.coff, max_super);
     const size_t csmem = sizeof(uint32_t) * (size_t)gc.max_vt;
     GS_TRY(cudaMemsetAsync(w.G1c, 0, sizeof(uint32_t) * (size_t)(gc.n_g * gc.tiles), stream));

@@ -130,3 +130,38 @@ def test_autotune_host_checks(lib):
     assert lib.gs_autotune(*args, C.c_void_p(1 << 20), big - 1, ms, C.byref(best), None) == gsr.GS_ERR_WORKSPACE
     rc.sh_degree = 2
     assert lib.gs_autotune(*args, C.c_void_p(1 << 20), big, ms, C.byref(best), None) == gsr.GS_ERR_INVALID_ARG
+
+
+def test_super_tile_form_host_checks(lib):
+    """The super-tile calls reject missing or misaligned list buffers, an
+    oversized list capacity, a negative super-tile bound and a missing
+    batch_pos before any launch; their workspace is smaller than the
+    tile-list form's."""
+    from paper_2603_08997_gb300 import gsr
+    n, V, T = 100000, 2, 4000
+    small = lib.gs_bin_sort_coarse_workspace_size(n, V, T)
+    assert 0 < small < lib.gs_bin_sort_workspace_size(n, V, 24 * n, T)
+    assert lib.gs_bin_sort_coarse_workspace_size(-1, V, T) == 0
+    dev = C.c_void_p(1 << 20)  # a stand-in device address: every call below returns before using it
+    proj = gsr.gs_projected(dev.value, dev.value, dev.value, None, None)
+    cfg = gsr.gs_raster_config()
+    cfg.tile, cfg.batch, cfg.pixels_per_thread = 16, 256, 2
+
+    def lists(mask=1 << 20, cap=1000):
+        return gsr.gs_coarse_lists(dev.value, mask, dev.value, dev.value, dev.value, dev.value, cap)
+
+    def bin_call(lst, bound=0):
+        return lib.gs_bin_sort_coarse(C.byref(proj), dev, V, n, T, 0, bound, C.byref(cfg), dev, 1 << 30,
+                                      C.byref(lst) if lst is not None else None, 24 * n, dev, dev, dev, None)
+    assert bin_call(None) == gsr.GS_ERR_INVALID_ARG
+    assert bin_call(lists(mask=(1 << 20) + 2)) == gsr.GS_ERR_INVALID_ARG       # masks not 16-byte aligned
+    assert bin_call(lists(cap=(1 << 32) - 1)) == gsr.GS_ERR_INVALID_ARG        # capacity above 2^32 - 65536
+    assert bin_call(lists(), bound=-1) == gsr.GS_ERR_INVALID_ARG
+    saved = gsr.gs_fwd_saved(dev.value, dev.value, dev.value, 100, None, None, None)  # no batch_pos
+    assert lib.gs_render_fwd_coarse(C.byref(proj), n, C.byref(lists()), dev, dev, V, T, C.byref(cfg), dev, saved,
+                                    None, None) == gsr.GS_ERR_INVALID_ARG
+    saved.batch_pos = dev.value
+    assert lib.gs_render_fwd_coarse(C.byref(proj), n, None, dev, dev, V, T, C.byref(cfg), dev, saved, None,
+                                    None) == gsr.GS_ERR_INVALID_ARG
+    assert lib.gs_raster_bwd_coarse(C.byref(proj), n, None, dev, dev, V, T, C.byref(cfg), saved, dev, None, dev,
+                                    1 << 30, None, None) == gsr.GS_ERR_INVALID_ARG
