@@ -131,8 +131,10 @@ typedef struct {
  *   n_last  [total pixels]: 1 + position, in its tile's list, of the pixel's
  *            last contributor (0 = none);
  *   ckpt    [ckpt_slots][tile*tile]: transmittance of every pixel at the
- *            start of each staging batch the forward pass processed (per-tile
- *            transmittance checkpoints); gs_ckpt_slots gives ckpt_slots. */
+ *            start of each staging batch the forward pass processed after the
+ *            tile's first (which starts at T = 1; its slot is not written)
+ *            (per-tile transmittance checkpoints); gs_ckpt_slots gives
+ *            ckpt_slots. */
 typedef struct {
     float *T_final;
     int32_t *n_last;

@@ -7,8 +7,8 @@
 // asynchronously one batch ahead into a second buffer) and marks, per warp,
 // the records whose support box reaches the warp's pixel block (one ballot
 // per warp and 32 records); every warp then walks only its marked records,
-// in order.  At the start of every batch each pixel
-// stores its transmittance into the checkpoint slot
+// in order.  At the start of every batch but the tile's first (which starts
+// at T = 1) each pixel stores its transmittance into the checkpoint slot
 //   slot(tile, b) = floor(range_start / BATCH) + tile + b
 // (TILE * TILE floats, row-major over the tile's pixels), which the backward pass uses to rebuild T without dividing across batches.
 // The CTA stops as soon as every pixel has hit the transmittance floor.
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
 #pragma unroll
         for (int k = 0; k < PPT; ++k) all_done &= done[k];
         if (__syncthreads_count(!all_done) == 0) break;  // every warp is also past batch b - 1
-        if (slot0 + b < ckpt_slots) {
+        if (b > 0 && slot0 + b < ckpt_slots) {  // the first batch starts at T = 1: nothing to store
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
                 if (inside[k]) ckpt[(slot0 + b) * NT + lp[k]] = T[k];
