@@ -78,6 +78,8 @@ def parse():
                     help="coarse: the binning writes super-tile lists and the compositing kernels filter each "
                          "tile's entries from them; tile: per-tile lists (gs_bin_sort); auto (the --c2 and --c4 "
                          "modes): the faster of the two on the mode's workload (autotune.choose_list_form)")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="the FP64 oracle's stages timed on C2 on one host core and on all of them")
     ap.add_argument("--stages-once", action="store_true",
                     help="run two eager iterations of every stage on one view of the workload and exit "
                          "(a small, fixed launch sequence for hardware-counter captures)")
@@ -474,6 +476,71 @@ def run_c2(args) -> None:
                       "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
                       "lists": "super-tile" if st.coarse_lists else "tile", "list_form_ms": form_ms,
                       "dtype": "f32", "data": "synthetic"}))
+
+
+def run_oracle_timing(args) -> None:
+    """The FP64 oracle's stages (the baseline the kernels are compared with,
+    not a target) timed on the C2 scene (200k Gaussians SH3, 980x545) on one
+    host core and on all of them: projection, binning, compositing, loss and
+    its gradient, raster adjoint, projection adjoint, the Adam step over
+    every parameter, and the gate's decision and EMA update over 5000 losses.
+    Wall time of each call on this host (CPU work; no GPU is used)."""
+    import time
+
+    import numpy as np
+
+    import oracle
+    import synth
+    from oracle.adam import AdamConfig, adam_step, lr_vector
+    from oracle.gate import Gate, GateConfig
+
+    oracle.core.build()
+    scene, tscene, cam, noise = synth.case_c2()
+    rc = oracle.RasterConfig()
+    target = (oracle.forward(tscene, cam, rc)["image"] + noise).astype(np.float32)
+    all_cores = oracle.num_threads()
+    rows = {}
+    # The first pass only warms the host's allocator (first-touch page faults
+    # are not the oracle's arithmetic); the two after it are reported.
+    for threads in (all_cores, 1, all_cores):
+        oracle.set_num_threads(threads)
+        t = {}
+
+        def timed(name, fn):
+            t0 = time.perf_counter()
+            out = fn()
+            t[name] = (time.perf_counter() - t0) * 1e3
+            return out
+
+        proj = timed("project", lambda: oracle.project(scene, cam, rc))
+        _, vals, ranges, _ = timed("bin_sort", lambda: oracle.bin_sort([proj], [cam], rc.tile))
+        f = timed("render_fwd", lambda: oracle.render(proj, cam, vals, ranges, rc, 0))
+        L, dL = timed("loss", lambda: oracle.loss_and_grad(f["image"], target))
+        g2d = timed("raster_bwd", lambda: oracle.raster_bwd(proj, cam, vals, ranges, rc, dL, 0))
+        grads = timed("project_bwd", lambda: oracle.project_bwd(scene, cam, rc, g2d))
+        cfg = AdamConfig()
+        lr = lr_vector(scene.means.shape[0], scene.sh.shape[1], cfg)
+        flat_p = np.concatenate([np.asarray(getattr(scene, k), np.float64).ravel()
+                                 for k in ("means", "log_scales", "quats", "opacity_logit", "sh")])
+        flat_g = np.concatenate([np.asarray(grads[k], np.float64).ravel()
+                                 for k in ("means", "log_scales", "quats", "opacity_logit", "sh")])
+        zeros = np.zeros_like(flat_p)
+        timed("adam", lambda: adam_step(flat_p, flat_g, zeros, zeros, 0, lr, cfg))
+        rng = np.random.default_rng(0)
+        views, losses = rng.integers(0, 200, 5000), rng.uniform(0.004, 0.006, 5000)
+
+        def gate_run():
+            gt = Gate(GateConfig(W=500, beta=0.95, eps=1e-8, rho_lo=0.5, n_views=200))
+            for v_, l_ in zip(views, losses):
+                gt.decide(int(v_), float(l_))
+                gt.update(int(v_), float(l_))
+        timed("gate_5000_iterations", gate_run)
+        t["iteration_fwd_loss_bwd_adam"] = sum(t[k] for k in ("project", "bin_sort", "render_fwd", "loss",
+                                                               "raster_bwd", "project_bwd", "adam"))
+        rows[f"{threads}_thread{'s' if threads > 1 else ''}"] = {k: round(v, 2) for k, v in t.items()}
+    print(json.dumps({"metric": "FP64 oracle stage times on C2 (200k Gaussians SH3, 980x545), ms",
+                      "host_cores": os.cpu_count(), "threads_all": all_cores, "pairs": int(len(vals)),
+                      "rows": rows, "kind": "oracle", "data": "synthetic"}))
 
 
 def run_c5(args) -> None:
@@ -1077,6 +1144,10 @@ def main():
         return
     if args.stages_once:
         stages_once(args)
+        return
+    if args.oracle_timing:
+        if rank == 0:
+            run_oracle_timing(args)
         return
     if args.c4:
         run_c4(args)
