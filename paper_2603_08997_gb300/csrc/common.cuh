@@ -72,6 +72,36 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// Packed float pairs: two floats in one 64-bit register, operated on by one
+// f32x2 instruction (fma.rn / mul.rn), each lane rounded as the scalar
+// instruction rounds it.  Halves the issued instructions of pairwise
+// arithmetic.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t dup2(float a) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // One Adam update of a scalar (Kingma & Ba, bias-corrected): lr_t = lr / (1 -
 // beta1^t), ibc2 = 1 / sqrt(1 - beta2^t).  Shared by the standalone optimizer
 // kernel and the fused adjoint + optimizer kernel so both round alike.

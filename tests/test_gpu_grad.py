@@ -47,6 +47,32 @@ def test_loss_multi_view():
         assert gpu_util.rel_err(g, dL) < 1e-4
 
 
+def test_loss_full_view():
+    """The 1297 x 840 view: flat regions (SSIM's variances near zero, where the
+    window sums' centre shift matters), smooth ramps and noise, over 41 x 27
+    output tiles with ragged right and bottom edges."""
+    w, h = 1297, 840
+    cam = synth.camera_pinhole(900, 900, w / 2, h / 2, w, h)
+    gpu_util.lib()
+    views = raster.Views([cam], 16)
+    r = raster.Renderer(10, 0, views)
+    rng = np.random.default_rng(5)
+    yy, xx = np.mgrid[0:h, 0:w]
+    img = np.empty((3, h, w), np.float32)
+    img[0] = 0.5 + 0.4 * np.sin(xx / 37.0) * np.cos(yy / 23.0)
+    img[1] = np.where(xx < w // 2, 0.25, 0.75)  # flat halves
+    img[2] = rng.uniform(0, 1, (h, w))
+    tgt = np.clip(img + rng.normal(0, 0.05, img.shape) * (xx % 3 > 0), 0, 1).astype(np.float32)
+    r.image.copy_(torch.from_numpy(img.ravel()))
+    t = torch.from_numpy(tgt.ravel()).cuda()
+    r.compute_loss(t, with_grad=True)
+    torch.cuda.synchronize()
+    L, dL = oracle.loss_and_grad(img, tgt)
+    assert abs(float(r.loss[0].item()) - L) <= 1e-5 * abs(L)
+    g = r.views.image_view(r.dL_dimage, 0).cpu().numpy()
+    assert gpu_util.rel_err(g, dL) < 1e-4
+
+
 def _check_grads(gg, og, tol=1e-4):
     for k in GROUPS:
         a, b = gg[k], og[k]
