@@ -23,7 +23,9 @@
 // 2048 keys with warp ballots (one per digit bit), reorders the tile by digit
 // in shared memory and writes each digit's run contiguously.  Keys are
 // sorted relative to the visible keys' range (key_range_kernel), so passes
-// above the range's bit length are copies.
+// above the range's bit length are copies; for one view in the super-tile
+// form they do nothing at all, the last pass that sorts bits writing the depth
+// order and the entries' rectangles directly (RsFinal).
 #include "common.cuh"
 
 using namespace gsr;
@@ -41,6 +43,39 @@ constexpr int SCAN_THREADS = 1024;
 static_assert(RS_THREADS == RADIX, "the downsweep gives each thread one digit");
 
 static_assert(RS_MAX_BLOCKS <= 4 * RS_THREADS, "rs_scan holds at most four counts per thread");
+
+struct ViewTiles {
+    int64_t off;  // first global tile id
+    int tx, ty;   // tile grid
+};
+
+__device__ __forceinline__ ViewTiles view_tiles(const gs_camera &cam, int tile) {
+    ViewTiles vt;
+    vt.off = cam.tile_offset;
+    vt.tx = (cam.width + tile - 1) / tile;
+    vt.ty = (cam.height + tile - 1) / tile;
+    return vt;
+}
+
+__device__ __forceinline__ bool view_fits(const ViewTiles &vt, int64_t tiles, int max_vt) {
+    const int64_t T = (int64_t)vt.tx * vt.ty;
+    return vt.tx > 0 && vt.ty > 0 && T <= max_vt && vt.off >= 0 && vt.off + T <= tiles;
+}
+
+// The last pass of the depth sort may write, instead of the next ping-pong
+// buffer, the entry ids alone to a buffer of their own (vals_final) and, for a
+// single view, each entry's packed rectangle beside them (dst[pos] =
+// src[entry], zero when the view's tile grid does not fit the tables): the
+// pass after it then has nothing to copy, and the rectangles need no gather
+// of their own.
+struct RsFinal {
+    uint32_t *vals;     // nullptr: every pass ping-pongs
+    const ushort4 *src; // optional: rectangles by entry id
+    ushort4 *dst;       //           and by depth position
+    const gs_camera *cam;
+    int tile, max_vt;
+    int64_t tiles;
+};
 
 __device__ __forceinline__ int64_t effective_count(const int64_t *d_count, int64_t cap) {
     if (!d_count) return cap;
@@ -200,7 +235,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
                                                            int64_t cap, int shift, uint32_t mask,
                                                            const uint32_t *__restrict__ offsets,
                                                            const uint32_t *__restrict__ totals,
-                                                           const uint32_t *__restrict__ krange) {
+                                                           const uint32_t *__restrict__ krange, RsFinal fin) {
     __shared__ uint32_t s_run[RADIX];   // global start of this block's next run per digit
     __shared__ uint32_t s_tot[RADIX];   // tile count per digit
     __shared__ uint32_t s_loc[RADIX];   // tile-local start per digit
@@ -211,13 +246,32 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const KeyRange kr(krange, FIRST);
-    if (krange && shift >= range_bits(krange)) {  // every key's digit is 0: the stable pass keeps the order
+    const int rb = krange ? range_bits(krange) : 32;
+    bool last = false;  // this pass writes fin.vals (and the rectangles)
+    bool rfits = false;
+    if (fin.vals) {  // with krange: the passes after the last one that sorts bits are no-ops
+        const int last_shift = rb > 0 ? ((rb - 1) / RADIX_BITS) * RADIX_BITS : 0;
+        if (shift > last_shift) return;
+        last = shift == last_shift;
+        rfits = last && fin.dst && view_fits(view_tiles(*fin.cam, fin.tile), fin.tiles, fin.max_vt);
+    }
+    // the last pass's outputs for entry id `val` at sorted position `pos`
+    auto put_last = [&](int64_t pos, uint32_t val) {
+        fin.vals[pos] = val;
+        if (fin.dst) fin.dst[pos] = rfits ? fin.src[val] : make_ushort4(0, 0, 0, 0);
+    };
+    if (krange && shift >= rb) {  // every key's digit is 0: the stable pass keeps the order
         const int64_t count = effective_count(d_count, cap);
         int64_t begin, end;
         block_range(count, gridDim.x, blockIdx.x, begin, end);
         for (int64_t i = begin + threadIdx.x; i < end; i += RS_THREADS) {
-            keys_out[i] = kr(keys_in[i]);
-            vals_out[i] = vals_in ? vals_in[i] : (uint32_t)i;
+            const uint32_t val = vals_in ? vals_in[i] : (uint32_t)i;
+            if (last) {
+                put_last(i, val);
+            } else {
+                keys_out[i] = kr(keys_in[i]);
+                vals_out[i] = val;
+            }
         }
         return;
     }
@@ -304,8 +358,12 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
             const uint32_t key = s_k[i];
             const uint32_t d = (key >> shift) & mask;
             const uint32_t pos = s_run[d] + (uint32_t)i - s_loc[d];
-            keys_out[pos] = key;
-            vals_out[pos] = s_v[i];
+            if (last) {
+                put_last(pos, s_v[i]);
+            } else {
+                keys_out[pos] = key;
+                vals_out[pos] = s_v[i];
+            }
         }
         __syncthreads();
         for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) s_run[d] += s_tot[d];
@@ -328,9 +386,12 @@ int rs_blocks(int64_t cap) {
 // krange (device, nullable): the depth-key range of key_range_kernel; the
 // first pass then sorts keys relative to it and passes above its bit length
 // copy (see key_range_kernel).
+// fin.vals (with krange): the last pass that sorts bits writes the entry ids
+// (and the rectangles) there and the passes after it do nothing; the return
+// value is then meaningless.
 int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int64_t *d_count, int64_t cap,
                int bits, uint32_t *counts, cudaStream_t stream, const uint32_t *k0 = nullptr,
-               const uint32_t *krange = nullptr) {
+               const uint32_t *krange = nullptr, RsFinal fin = RsFinal{}) {
     const int G = rs_blocks(cap);
     int cur = 0;
     for (int shift = 0; shift < bits; shift += RADIX_BITS) {
@@ -351,10 +412,10 @@ int radix_sort(uint32_t *ka, uint32_t *va, uint32_t *kb, uint32_t *vb, const int
         rs_scan<<<RADIX, RS_THREADS, 0, stream>>>(counts, G, totals, shift, krange);
         if (shift == 0 && krange)
             rs_downsweep<true><<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts, totals,
-                                                             krange);
+                                                             krange, krange ? fin : RsFinal{});
         else
             rs_downsweep<false><<<G, RS_THREADS, 0, stream>>>(ki, vi, ko, vo, d_count, cap, shift, mask, counts,
-                                                              totals, krange);
+                                                              totals, krange, krange ? fin : RsFinal{});
         cur ^= 1;
     }
     return cur;
@@ -388,7 +449,8 @@ __global__ void view_keys_kernel(const uint32_t *__restrict__ order, int64_t tot
 // with start(t) the exclusive scan of the tile totals over global tile ids.
 // That is the position of the pair in the stable sort by tile of the
 // depth-ordered pair list, so no pair key is ever materialised or sorted.
-//   bin_rects:   the clipped rectangles in depth order (one gather);
+//   bin_rects:   the clipped rectangles in depth order (one gather, or
+//                written by the depth sort's last pass);
 //   bin_count:   one block per chunk: per-tile counts in shared memory, written
 //                as the chunk's row of the count matrix (chunk-major per view)
 //                and added into the per-group sums (BIN_GROUP chunks a group);
@@ -444,19 +506,6 @@ int64_t bin_chunk(int64_t n, int64_t chunks = 304) {
     return c < 1024 ? 1024 : c;
 }
 
-struct ViewTiles {
-    int64_t off;  // first global tile id
-    int tx, ty;   // tile grid
-};
-
-__device__ __forceinline__ ViewTiles view_tiles(const gs_camera &cam, int tile) {
-    ViewTiles vt;
-    vt.off = cam.tile_offset;
-    vt.tx = (cam.width + tile - 1) / tile;
-    vt.ty = (cam.height + tile - 1) / tile;
-    return vt;
-}
-
 // The grid a BinGeom counts and places on: the view's tiles, or its
 // super-tiles (SUP x SUP tiles each; the view's first super-tile id from
 // g.coff).
@@ -489,10 +538,6 @@ __device__ __forceinline__ int view_of_grid_tile(const BinGeom &g, const gs_came
 
 // Does the view's tile table fit the shared-memory tables and the global
 // tile range?  (Tile offsets that disagree with total_tiles would not.)
-__device__ __forceinline__ bool view_fits(const ViewTiles &vt, int64_t tiles, int max_vt) {
-    const int64_t T = (int64_t)vt.tx * vt.ty;
-    return vt.tx > 0 && vt.ty > 0 && T <= max_vt && vt.off >= 0 && vt.off + T <= tiles;
-}
 
 // Rectangle of an entry clipped to its view's tile grid, packed as
 // (x0, y0, width, height) in 16 bits each; width 0 = no pair (culled/empty).
@@ -1136,6 +1181,7 @@ int64_t fine_items_cap(int64_t pair_capacity, int64_t coarse_tiles) {
 
 struct BinWorkspace {
     uint32_t *dk[2], *dv[2];   // depth (then view) keys / entry ids, ping-pong, [V*N]
+    uint32_t *dvf;             // super-tile form: entry ids in depth order from the last radix pass, [V*N]
     uint32_t *counts;          // [RADIX * RS_MAX_BLOCKS] + [RADIX] digit totals
     uint32_t *G1;              // [n_g * total_tiles] group sums of the tile counts
     uint32_t *tile_total;      // [total_tiles]
@@ -1178,6 +1224,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
         char *b = take(sizeof(uint32_t) * (size_t)(total > 0 ? total : 1));
         if (w) { w->dk[i] = (uint32_t *)a; w->dv[i] = (uint32_t *)b; }
     }
+    char *dvf = coarse_only ? take(sizeof(uint32_t) * (size_t)(total > 0 ? total : 1)) : nullptr;
     char *counts = take(sizeof(uint32_t) * RADIX * (RS_MAX_BLOCKS + 1) + 2 * sizeof(uint32_t));
     char *G1 = take(sizeof(uint32_t) * (size_t)(g.n_g * total_tiles));
     char *tt = take(sizeof(uint32_t) * (size_t)total_tiles);
@@ -1196,6 +1243,7 @@ size_t bin_ws_layout(int64_t n, int64_t n_views, int64_t total_tiles, int64_t pa
     char *ic = take(sizeof(uint32_t) * (size_t)items);
     char *ro = take(sizeof(uint32_t) * (size_t)items * SUP_T);
     if (w) {
+        w->dvf = (uint32_t *)dvf;
         w->counts = (uint32_t *)counts;
         w->G1 = (uint32_t *)G1;
         w->tile_total = (uint32_t *)tt;
@@ -1412,11 +1460,18 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
     GS_TRY(cudaMemsetAsync(krange, 0xff, sizeof(uint32_t), stream));
     GS_TRY(cudaMemsetAsync(krange + 1, 0, sizeof(uint32_t), stream));
     const unsigned kr_blocks = (unsigned)min((int64_t)device_sm_count() * 4, ceil_div(total, (int64_t)256));
+    // one view in the super-tile form: the last radix pass writes the depth
+    // order to dvf with the packed rectangles beside it (no bin_rects16)
+    const bool fused = co && n_views == 1 && proj->depth_key && proj->rect16 && w.dvf;
     if (proj->depth_key) {  // written by gs_project
         key_range_kernel<<<kr_blocks, 256, 0, stream>>>(proj->depth_key, total, krange);
         GS_TRY_LAUNCH();
+        RsFinal fin{};
+        if (fused)
+            fin = RsFinal{w.dvf, reinterpret_cast<const ushort4 *>(proj->rect16), w.srect, cams, g.tile, g.max_vt,
+                          g.tiles};
         sel = radix_sort(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, total, 32, w.counts, stream, proj->depth_key,
-                         krange);
+                         krange, fin);
     } else {
         depth_keys_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(proj->rec, proj->tiles_touched, total,
                                                                              w.dk[0], w.dv[0]);
@@ -1433,7 +1488,7 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
                           w.counts, stream);
         GS_TRY_LAUNCH();
     }
-    const uint32_t *order = w.dv[sel];
+    const uint32_t *order = fused ? w.dvf : w.dv[sel];
     const int4 *rect = reinterpret_cast<const int4 *>(proj->rect);
     // 2. the pairs by tile, in depth order: tile totals and starts (chunked
     // counts on the tile grid), then the entries by super-tile (the chunked
@@ -1444,13 +1499,15 @@ gs_status bin_sort_impl(const gs_projected *proj, const gs_camera *cams, int32_t
         const gs_status st = bin_smem_attributes();
         if (st != GS_OK) return st;
     }
-    if (proj->rect16)  // written by gs_project
-        bin_rects16<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(
-            reinterpret_cast<const ushort4 *>(proj->rect16), order, cams, g, total, w.srect);
-    else
-        bin_rects<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(rect, proj->tiles_touched, order, cams, g,
-                                                                     total, w.srect);
-    GS_TRY_LAUNCH();
+    if (!fused) {  // (fused: the rectangles came with the depth order)
+        if (proj->rect16)  // written by gs_project
+            bin_rects16<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(
+                reinterpret_cast<const ushort4 *>(proj->rect16), order, cams, g, total, w.srect);
+        else
+            bin_rects<<<(unsigned)ceil_div(total, 256), 256, 0, stream>>>(rect, proj->tiles_touched, order, cams, g,
+                                                                         total, w.srect);
+        GS_TRY_LAUNCH();
+    }
     if (co) {  // the tile totals come from the lists' masks, after the scatter
         GS_TRY(cudaMemsetAsync(w.tile_total, 0, sizeof(uint32_t) * (size_t)total_tiles, stream));
     } else {

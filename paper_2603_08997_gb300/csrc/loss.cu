@@ -246,38 +246,28 @@ __global__ void __launch_bounds__(LOSS_THREADS, 4) ssim_fwd_kernel(const float *
 
 // Per view: fixed-order sum of the block partials -> loss (n = 3 W H, from
 // the device camera when given).
-constexpr int RED_THREADS = 1024, RED_UNROLL = 4;
-
-__global__ void __launch_bounds__(RED_THREADS) loss_reduce_kernel(const double2 *__restrict__ partials, int nblocks,
-                                                                  double n, const gs_camera *__restrict__ cam_dev,
-                                                                  float lambda, float *__restrict__ loss_out) {
+__global__ void loss_reduce_kernel(const double2 *__restrict__ partials, int nblocks, double n,
+                                   const gs_camera *__restrict__ cam_dev, float lambda, float *__restrict__ loss_out) {
     if (cam_dev) n = 3.0 * (double)cam_dev->width * (double)cam_dev->height;
-    __shared__ double s0[RED_THREADS / 32], s1[RED_THREADS / 32];
+    __shared__ double s0[256], s1[256];
     double a = 0.0, b = 0.0;
-    for (int base = 0; base < nblocks; base += RED_THREADS * RED_UNROLL) {
-        double2 p[RED_UNROLL];
-#pragma unroll
-        for (int k = 0; k < RED_UNROLL; ++k) {  // every load in flight before the sums
-            const int i = base + k * RED_THREADS + (int)threadIdx.x;
-            p[k] = i < nblocks ? partials[i] : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int k = 0; k < RED_UNROLL; ++k) {
-            a += p[k].x;
-            b += p[k].y;
-        }
+    for (int i = threadIdx.x; i < nblocks; i += 256) {
+        const double2 p = partials[i];
+        a += p.x;
+        b += p.y;
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, off);
-        b += __shfl_xor_sync(0xffffffffu, b, off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { s0[warp] = a; s1[warp] = b; }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
     __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s0[threadIdx.x] += s0[threadIdx.x + off];
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double t0 = 0.0, t1 = 0.0;
-        for (int w = 0; w < RED_THREADS / 32; ++w) { t0 += s0[w]; t1 += s1[w]; }
-        const double ssim = t0 / n, l1 = t1 / n;
+        const double ssim = s0[0] / n, l1 = s1[0] / n;
         *loss_out = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
     }
 }
@@ -445,7 +435,7 @@ gs_status gs_loss(const float *image, const float *target, const int64_t *target
                                                           cams_dev ? cams_dev + v : nullptr, win,
                                                           dmaps + 9 * c.pix_offset, partials + boff);
         GS_TRY_LAUNCH();
-        loss_reduce_kernel<<<1, RED_THREADS, 0, stream>>>(partials + boff, (int)(grid.x * grid.y * grid.z),
+        loss_reduce_kernel<<<1, 256, 0, stream>>>(partials + boff, (int)(grid.x * grid.y * grid.z),
                                                   3.0 * (double)c.width * c.height, cams_dev ? cams_dev + v : nullptr,
                                                   lambda_ssim, loss_per_view + v);
         GS_TRY_LAUNCH();

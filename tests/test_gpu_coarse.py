@@ -318,3 +318,41 @@ def test_depth_order_across_key_ranges(depths):
         else:
             P = int(r.pair_count.item())
             assert np.array_equal(r.vals[:P].cpu().numpy().view(np.uint32), ovals)
+
+
+@pytest.mark.parametrize("depths", ["equal", "typical", "wide", "one_visible"])
+def test_projected_single_view_depth_order(depths):
+    """One view through gs_project's depth keys and packed rectangles, where
+    the depth sort's last pass writes the depth order and the rectangles
+    itself: the super-tile lists hold, tile for tile, the tile lists of the
+    same projection (whose binning is bit-exact against the oracle's), and
+    the images are equal, for key ranges of 0 bits (all depths equal), about
+    23 bits (last pass the third), 28 bits (all four passes) and a single
+    visible Gaussian."""
+    depth = {"equal": (3.5, 3.5), "typical": (2.0, 4.0), "wide": (0.3, 1e5), "one_visible": (2.0, 4.0)}[depths]
+    scene, cam = synth.scene_tiny(3000, seed=31, width=160, height=96, sh_degree=0, depth=depth)
+    if depths == "one_visible":
+        scene.means[1:, 2] = -1.0  # behind the camera: culled
+    out = []
+    for coarse in (False, True):
+        gpu_util.lib()
+        r = raster.Renderer(scene.n, 0, raster.Views([cam], 16), raster.RasterSettings(coarse_lists=coarse))
+        r.forward(raster.GaussianModel.from_scene(scene).c_params())
+        torch.cuda.synchronize()
+        assert int(r.status.item()) == 0
+        out.append(r)
+    rt, rc = out
+    P = int(rt.pair_count.item())
+    assert int(rc.pair_count.item()) == P
+    if depths == "one_visible":
+        assert 0 < P <= 4
+    rg = rt.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    assert np.array_equal(rc.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), rg)
+    tv = rt.vals[:P].cpu().numpy().view(np.uint32)
+    rc._orc = [{"rect": rc.rect.cpu().numpy().reshape(-1, 4)}]  # masks checked against the projection's rectangles
+    lists = _host_lists(rc, [cam], 16)
+    assert len(lists) == rt.views.total_tiles
+    for t, g in lists.items():
+        assert np.array_equal(g, tv[rg[t, 0]:rg[t, 1]]), t
+    assert torch.equal(rc.image, rt.image)
+
