@@ -85,6 +85,7 @@ class GaussianModel:
         p.means, p.log_scales, p.quats = v["means"].data_ptr(), v["log_scales"].data_ptr(), v["quats"].data_ptr()
         p.opacity_logit, p.sh = v["opacity_logit"].data_ptr(), v["sh"].data_ptr()
         p.n, p.sh_degree = self.n, self.sh_degree
+        p._owner = (self, v)  # the struct holds raw pointers: keep their storage alive with it
         return p
 
     def c_grads(self, flat: torch.Tensor) -> gsr.gs_grads:
@@ -92,6 +93,7 @@ class GaussianModel:
         g = gsr.gs_grads()
         g.means, g.log_scales, g.quats = v["means"].data_ptr(), v["log_scales"].data_ptr(), v["quats"].data_ptr()
         g.opacity_logit, g.sh = v["opacity_logit"].data_ptr(), v["sh"].data_ptr()
+        g._owner = v
         return g
 
 

@@ -165,3 +165,36 @@ def test_super_tile_form_host_checks(lib):
                                     None) == gsr.GS_ERR_INVALID_ARG
     assert lib.gs_raster_bwd_coarse(C.byref(proj), n, None, dev, dev, V, T, C.byref(cfg), saved, dev, None, dev,
                                     1 << 30, None, None) == gsr.GS_ERR_INVALID_ARG
+
+
+def test_param_structs_keep_their_tensors_alive():
+    """gs_params / gs_grads hold raw device pointers: the structs returned by
+    c_params and c_grads keep the model and the gradient buffer alive, so a
+    temporary model's storage cannot be reused while its struct is passed
+    on (CPU tensors; no kernel runs)."""
+    import gc
+    import weakref
+
+    import torch
+
+    import synth
+    from paper_2603_08997_gb300 import raster
+    scene, _ = synth.scene_tiny(8, seed=1)
+    m = raster.GaussianModel.from_scene(scene, torch.device("cpu"))
+    ref = weakref.ref(m)
+    p = m.c_params()
+    del m
+    gc.collect()
+    assert ref() is not None and p.means == ref().views["means"].data_ptr()
+    del p
+    gc.collect()
+    assert ref() is None
+    flat = torch.zeros(raster.GaussianModel.from_scene(scene, torch.device("cpu")).flat.numel())
+    fref = weakref.ref(flat)
+    g = raster.GaussianModel.from_scene(scene, torch.device("cpu")).c_grads(flat)
+    del flat
+    gc.collect()
+    assert fref() is not None
+    del g
+    gc.collect()
+    assert fref() is None
