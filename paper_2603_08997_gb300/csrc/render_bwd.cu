@@ -6,7 +6,8 @@
 // A_k = sum_{j>k} c_j a_j T_j + T_end bg (the colour behind contributor k),
 // Eq. (blend) gives dC/dc_k = a_k T_k and dC/da_k = c_k T_k - A_k / (1 - a_k).
 // Batches are visited last to first and each pixel walks back from its last
-// contributor, so A_k is a plain suffix sum.  T is rebuilt by
+// contributor, so A_k is a plain suffix sum; a pixel keeps only its product
+// with dL/dC (one scalar instead of three).  T is rebuilt by
 // T_k = T_{k+1} / (1 - a_k), re-anchored at every batch boundary on the
 // transmittance checkpoint the forward pass stored, so division error never
 // spans more than one batch.  The alphas come from the same bit-exact
@@ -138,13 +139,13 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
     if (local_max > 0) atomicMax(&s_max, local_max);
     __syncthreads();
     const int max_last = s_max;
-    float A0[PPT], A1[PPT], A2[PPT];
+    // S = sum_c dL/dC_c A_c (A_c: the colour behind the current contributor),
+    // kept instead of the three A_c: dL/da_k needs no more, and the suffix
+    // step A_c += c_c w adds (dL/dC . c) w to it
+    float S[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        A0[k] = T_end[k] * cfg.bg[0];
-        A1[k] = T_end[k] * cfg.bg[1];
-        A2[k] = T_end[k] * cfg.bg[2];
-    }
+    for (int k = 0; k < PPT; ++k)
+        S[k] = T_end[k] * (dC0[k] * cfg.bg[0] + dC1[k] * cfg.bg[1] + dC2[k] * cfg.bg[2]);
 
     for (int b = (max_last + BATCH - 1) / BATCH - 1; b >= 0; --b) {
         __syncthreads();
@@ -214,25 +215,26 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                 const float inv = rcp_approx(om);  // 1 - alpha >= 0.01
                 const float Tk = T[k] * inv;
                 const float wgt = ae.alpha * Tk;
-                const float c0 = sb.z, c1 = sb.w, c2 = sc.x;
                 gv[6] += dC0[k] * wgt;
                 gv[7] += dC1[k] * wgt;
                 gv[8] += dC2[k] * wgt;
-                const float da = dC0[k] * (c0 * Tk - A0[k] * inv) + dC1[k] * (c1 * Tk - A1[k] * inv) +
-                                 dC2[k] * (c2 * Tk - A2[k] * inv);
-                A0[k] += c0 * wgt;
-                A1[k] += c1 * wgt;
-                A2[k] += c2 * wgt;
+                const float dcc = dC0[k] * sb.z + dC1[k] * sb.w + dC2[k] * sc.x;  // dL/dC . c
+                const float da = dcc * Tk - S[k] * inv;
+                S[k] += dcc * wgt;
                 T[k] = Tk;
                 if (!ae.clamped) {
-                    gv[5] += da * ae.G;                      // dL/d opacity
-                    const float gG = da * sb.y * ae.G;       // G dL/dG
-                    gv[0] += gG * sa.z * ae.z0;              // dL/d mean2D.x = G dG (Q dp)_x
-                    gv[1] += gG * (sa.w * ae.z0 + sb.x * ae.z1);  // dL/d mean2D.y
-                    const float dq = -0.5f * gG;             // dL/d(dp^T Q dp)
-                    gv[2] += dq * ae.dx * ae.dx;
-                    gv[3] += 2.f * dq * ae.dx * ae.dy;
-                    gv[4] += dq * ae.dy * ae.dy;
+                    const float dG = da * ae.G;
+                    gv[5] += dG;                             // dL/d opacity
+                    const float gG = dG * sb.y;              // G dL/dG
+                    const float u = gG * ae.z0;
+                    gv[0] += u * sa.z;                       // dL/d mean2D.x = G dG (Q dp)_x
+                    gv[1] += u * sa.w + gG * sb.x * ae.z1;   // dL/d mean2D.y
+                    // dL/d(dp^T Q dp) = -gG / 2: the conic terms are summed
+                    // without the factors -1/2, -1, -1/2 (applied at the flush)
+                    const float ex = gG * ae.dx, ey = gG * ae.dy;
+                    gv[2] += ex * ae.dx;
+                    gv[3] += ex * ae.dy;
+                    gv[4] += ey * ae.dy;
                 }
             }
             const uint32_t cm = __ballot_sync(FULL, contrib);
@@ -255,8 +257,8 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
             for (int q = 0; q < 9; ++q) nz |= a[q] != 0.f;
             if (!nz) continue;
             float4 *dst = g2d + ((int64_t)v * n + s_g[kk]) * 3;
-            atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
-            atomicAdd(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
+            atomicAdd(dst, make_float4(a[0], a[1], -0.5f * a[2], -a[3]));
+            atomicAdd(dst + 1, make_float4(-0.5f * a[4], a[5], a[6], a[7]));
             atomicAdd(&dst[2].x, a[8]);
         }
     }
