@@ -13,10 +13,13 @@
 // spans more than one batch.  The alphas come from the same bit-exact
 // evaluation as the forward pass, so the contributor set is identical.
 //
-// Per Gaussian the 9 gradients (mean2D 2, conic 3, opacity 1, colour 3) of a
-// thread's pixels are summed, then reduced across the warp with a halving shuffle tree (12 shuffles for 9
-// values), summed per Gaussian in shared memory, and added once per
-// (Gaussian, tile) to a per-view buffer with float4 vector atomics.
+// Per Gaussian 9 sums over a thread's pixels (sum dG z with z = U dp, the
+// three entries of sum dG dp dp^T, dL/d opacity, the 3 colour gradients;
+// dG = dL/d alpha G) are reduced across the warp with a halving shuffle
+// tree (12 shuffles for 9 values), summed per Gaussian in shared memory, and
+// turned into the mean2D and conic gradients (the factors the record fixes:
+// opacity, U^T, -1/2) once per (Gaussian, tile), added to a per-view buffer
+// with float4 vector atomics.
 //
 // Projection adjoint: one lane per Gaussian chains those 2D gradients
 // through Eq. (proj), Eq. (cov), the SH colour and the sigmoid to the
@@ -223,15 +226,15 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
                 S[k] += dcc * wgt;
                 T[k] = Tk;
                 if (!ae.clamped) {
+                    // dG = dL/da G = dL/d opacity; G dL/dG = o dG.  Per record
+                    // the pixels sum dG z (z = U dp) and dG dp dp^T; the flush
+                    // applies o, U^T (dL/d mean2D = o U^T sum dG z) and the
+                    // conic factors -1/2, -1, -1/2 once per (Gaussian, tile)
                     const float dG = da * ae.G;
-                    gv[5] += dG;                             // dL/d opacity
-                    const float gG = dG * sb.y;              // G dL/dG
-                    const float u = gG * ae.z0;
-                    gv[0] += u * sa.z;                       // dL/d mean2D.x = G dG (Q dp)_x
-                    gv[1] += u * sa.w + gG * sb.x * ae.z1;   // dL/d mean2D.y
-                    // dL/d(dp^T Q dp) = -gG / 2: the conic terms are summed
-                    // without the factors -1/2, -1, -1/2 (applied at the flush)
-                    const float ex = gG * ae.dx, ey = gG * ae.dy;
+                    gv[5] += dG;
+                    gv[0] += dG * ae.z0;
+                    gv[1] += dG * ae.z1;
+                    const float ex = dG * ae.dx, ey = dG * ae.dy;
                     gv[2] += ex * ae.dx;
                     gv[3] += ex * ae.dy;
                     gv[4] += ey * ae.dy;
@@ -256,9 +259,13 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
 #pragma unroll
             for (int q = 0; q < 9; ++q) nz |= a[q] != 0.f;
             if (!nz) continue;
+            // dL/d mean2D = o U^T sum dG z (U = [[u00, u01], [0, u11]] in
+            // the record: a.z, a.w, b.x; o = b.y); dL/dQ = -o/2 sum dG dp dp^T
+            const float4 ra = s_a[kk], rb = s_b[kk];
+            const float o = rb.y, ho = -0.5f * o;
             float4 *dst = g2d + ((int64_t)v * n + s_g[kk]) * 3;
-            atomicAdd(dst, make_float4(a[0], a[1], -0.5f * a[2], -a[3]));
-            atomicAdd(dst + 1, make_float4(-0.5f * a[4], a[5], a[6], a[7]));
+            atomicAdd(dst, make_float4(o * (ra.z * a[0]), o * (ra.w * a[0] + rb.x * a[1]), ho * a[2], -o * a[3]));
+            atomicAdd(dst + 1, make_float4(ho * a[4], a[5], a[6], a[7]));
             atomicAdd(&dst[2].x, a[8]);
         }
     }
