@@ -350,21 +350,50 @@ __device__ __forceinline__ bool warp_overlaps(float4 a, float4 c, float wx, floa
     return fabsf(a.x - (wx + 3.5f)) <= c.z + 3.5f && fabsf(a.y - (wy + hy)) <= c.w + hy;
 }
 
+// Lower bound of q(dp) = |U dp|^2 (Q = U^T U, U = [[u00, u01], [0, u11]],
+// u00, u11 > 0) over the offsets [dx0, dx1] x [dy0, dy1]: 0 when they
+// contain dp = 0, else the least of q's minima along the four edges (q is
+// convex with its minimum at 0, so over the rectangle it is least on the
+// boundary); along an edge q is a quadratic in one offset, minimised in closed
+// form and clamped to the edge.
+__device__ __forceinline__ float rect_qmin(float u00, float u01, float u11, float dx0, float dx1, float dy0,
+                                           float dy1) {
+    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
+    const float sv = -u00 * u01 / (u01 * u01 + u11 * u11);  // dy minimising q at dx = 1
+    const float sh = -u01 / u00;                            // dx minimising q at dy = 1
+    auto at = [&](float dx, float dy) {
+        const float z0 = u00 * dx + u01 * dy, z1 = u11 * dy;
+        return z0 * z0 + z1 * z1;
+    };
+    const float qa = at(dx0, fminf(fmaxf(sv * dx0, dy0), dy1)), qb = at(dx1, fminf(fmaxf(sv * dx1, dy0), dy1));
+    const float qc = at(fminf(fmaxf(sh * dy0, dx0), dx1), dy0), qd = at(fminf(fmaxf(sh * dy1, dx0), dx1), dy1);
+    return fminf(fminf(qa, qb), fminf(qc, qd));
+}
+
 // Overlap masks of one staged batch of records: for every warp w of the CTA,
 // bit (j % 32) of word j / 32 of row w is set when record j's support box
-// reaches w's pixel block (the warp_overlaps test).  Called by whole warps for
-// batch slots kk = threadIdx.x, threadIdx.x + NTH, ... < BATCH; a (a.x, a.y =
-// mean2D) and c (c.z, c.w = support half-extents) are the slot's record, valid
-// false past the batch's end.  One ballot per target warp and 32 slots.
+// reaches w's pixel block (the warp_overlaps test) and so does its support
+// ellipse dp^T Q dp <= 2 ln(o / alpha_min): no pixel outside it has
+// alpha' >= alpha_min, so a record whose ellipse misses the block (minimum
+// of dp^T Q dp over the block's pixel centres above the bound, with a margin
+// far beyond float32 rounding) contributes nothing there and is not marked.
+// Called by whole warps for batch slots kk = threadIdx.x, threadIdx.x + NTH,
+// ... < BATCH; a, b, c are the slot's record (a.x, a.y = mean2D; a.z, a.w,
+// b.x = U; b.y = opacity; c.z, c.w = support half-extents), valid false past
+// the batch's end.  One ballot per target warp and 32 slots.
 template <int TILE, int PPT, int NW, int NWORD>
-__device__ __forceinline__ void overlap_masks(uint32_t (*s_ov)[NWORD], int kk, bool valid, float4 a, float4 c,
-                                              int tile_x0, int tile_y0) {
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
+__device__ __forceinline__ void overlap_masks(uint32_t (*s_ov)[NWORD], int kk, bool valid, float4 a, float4 b,
+                                              float4 c, float alpha_min, int tile_x0, int tile_y0) {
+    constexpr int H = 4 * PPT;
+    const float qcut = valid ? 1.001f * (2.f * __logf(b.y / alpha_min)) + 0.01f : 0.f;
+#pragma unroll 1
+    for (int w = 0; w < NW; ++w) {  // not unrolled: the test's temporaries stay few
         int lx0, ly0;
         tile_pixel<TILE, PPT>(w * 32, 0, lx0, ly0);
         const float wx = (float)(tile_x0 + lx0) + 0.5f, wy = (float)(tile_y0 + ly0) + 0.5f;
-        const uint32_t m = __ballot_sync(0xffffffffu, valid && warp_overlaps<4 * PPT>(a, c, wx, wy));
+        bool hit = valid && warp_overlaps<H>(a, c, wx, wy);
+        if (hit) hit = rect_qmin(a.z, a.w, b.x, wx - a.x, wx + 7.f - a.x, wy - a.y, wy + (H - 1) - a.y) <= qcut;
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if ((threadIdx.x & 31) == 0) s_ov[w][kk >> 5] = m;
     }
 }

@@ -161,18 +161,19 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
         }
         for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
             const bool valid = kk < cnt;
-            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra;
             if (valid) {
                 const uint32_t g = COARSE ? s_g[kk] : ls.vals[b0 + kk];
                 const float4 *r = recv + (int64_t)g * 3;
                 ra = r[0];
+                rb = r[1];
                 rc = r[2];
                 s_a[kk] = ra;
-                s_b[kk] = r[1];
+                s_b[kk] = rb;
                 s_c[kk] = rc;
                 s_g[kk] = g;
             }
-            overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rc, tx * TILE, ty * TILE);
+            overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rb, rc, amin, tx * TILE, ty * TILE);
         }
         for (int kk = threadIdx.x; kk < BATCH * 9; kk += NTH) (&s_acc[0][0])[kk] = 0.f;
         __syncthreads();

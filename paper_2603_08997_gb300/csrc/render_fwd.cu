@@ -168,8 +168,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const floa
         for (int kk = threadIdx.x; kk < BATCH; kk += NTH) {  // whole warps (BATCH, NTH multiples of 32)
             const bool valid = kk < cnt;
             const float4 ra = valid ? s_a[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 rb = valid ? s_b[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 rc = valid ? s_c[buf][kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-            overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rc, tx * TILE, ty * TILE);
+            overlap_masks<TILE, PPT, NW, NWORD>(s_ov, kk, valid, ra, rb, rc, amin, tx * TILE, ty * TILE);
         }
         __syncthreads();
         const float4 *s_a_b = s_a[buf], *s_b_b = s_b[buf], *s_c_b = s_c[buf];
