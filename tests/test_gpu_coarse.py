@@ -356,3 +356,41 @@ def test_projected_single_view_depth_order(depths):
         assert np.array_equal(g, tv[rg[t, 0]:rg[t, 1]]), t
     assert torch.equal(rc.image, rt.image)
 
+
+
+@pytest.mark.parametrize("coarse,ppt", [(True, 2), (False, 2), (True, 1), (False, 4)])
+def test_needles_against_oracle(coarse, ppt):
+    """Long thin rotated footprints (aspect 15 to 40, long-axis sigma 4 to 14
+    px): their support boxes cover many warp pixel blocks that their support
+    ellipses miss, which the compositing kernels do not visit.  Pixels,
+    last-contributor counts and 2D gradients against the oracle, both list
+    forms."""
+    w, h = 160, 120
+    cams = [synth.camera_pinhole(50, 50, w / 2, h / 2, w, h)]
+    rec = synth.projected_records(700, w, h, seed=77, sigma_range=(4.0, 14.0), aniso=(15.0, 40.0))
+    # the case does what it is for: most (record, 8 x 8 block) pairs that a
+    # box reaches lie outside the record's ellipse at 3 sigma
+    c, s = np.cos(rec["theta"]), np.sin(rec["theta"])
+    ex = 3 * np.sqrt((rec["sigma1"] * c) ** 2 + (rec["sigma2"] * s) ** 2)
+    ey = 3 * np.sqrt((rec["sigma1"] * s) ** 2 + (rec["sigma2"] * c) ** 2)
+    assert np.median(4 * ex * ey / (9 * np.pi * rec["sigma1"] * rec["sigma2"])) > 3.0  # box area / ellipse area
+    dev, orc = gpu_util.records([rec], cams, 16)
+    dl = synth.dl_dimage(w, h, seed=5)
+    r = _renderer(cams, 700, coarse, tile=16, ppt=ppt)
+    gpu_util.set_projected(r, dev)
+    r.bin_sort()
+    r.render_fwd()
+    g2d = r.raster_bwd(dL_dimage=torch.from_numpy(dl.ravel()).cuda()).double().cpu().numpy()[0]
+    torch.cuda.synchronize()
+    assert int(r.status.item()) == 0
+    rc = oracle.RasterConfig(tile=16)
+    _, ovals, oranges, toff = oracle.bin_sort(orc, cams, 16)
+    from tests.test_gpu_raster import _compare_images
+    o = oracle.render(orc[0], cams[0], ovals, oranges, rc, 0)
+    _compare_images(r.image_of(0).cpu().numpy(), o["image"], o["margin"])
+    nl = r.n_last[:w * h].view(h, w).cpu().numpy()
+    assert ((nl == o["n_last"]) | o["margin"].astype(bool)).all()
+    og = oracle.raster_bwd(orc[0], cams[0], ovals, oranges, rc, dl.astype(np.float64), 0)
+    for sl in (slice(0, 2), slice(2, 5), slice(5, 6), slice(6, 9)):
+        assert gpu_util.rel_err(g2d[:, sl], og[:, sl]) < 1e-4
+        assert gpu_util.cosine(g2d[:, sl], og[:, sl]) > 0.9999
