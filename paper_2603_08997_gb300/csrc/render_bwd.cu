@@ -71,8 +71,10 @@ __device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane, int
     return d;
 }
 
+// Two pixels per thread (the loop's shape): at most 73 registers, so 7 blocks
+// fit an SM with no spill (left alone the compiler took 64 and spilled).
 template <int TILE, int BATCH, int PPT, bool COARSE>
-__global__ void __launch_bounds__(TILE *TILE / PPT) render_bwd_kernel(
+__global__ void __launch_bounds__(TILE *TILE / PPT, PPT == 2 ? 7 : 1) render_bwd_kernel(
     const float4 *__restrict__ rec, int64_t n, const ListSrc ls, const uint2 *__restrict__ ranges,
     const gs_camera *__restrict__ cams, int n_views, gs_raster_config cfg, const float *__restrict__ T_final,
     const int32_t *__restrict__ n_last, const float *__restrict__ ckpt, int64_t ckpt_slots,
