@@ -25,8 +25,10 @@ using namespace gsr;
 
 namespace {
 
+// One pixel per thread (the loop's shape): 5 resident blocks per SM (48
+// registers) measured faster than the compiler's own 4 (63).
 template <int TILE, int BATCH, int PPT, bool COARSE>
-__global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(const float4 *__restrict__ rec, int64_t n,
+__global__ void __launch_bounds__(TILE *TILE / PPT, PPT == 1 ? 5 : 1) render_fwd_kernel(const float4 *__restrict__ rec, int64_t n,
                                                                        const ListSrc ls,
                                                                        const uint2 *__restrict__ ranges,
                                                                        const gs_camera *__restrict__ cams, int n_views,
