@@ -333,7 +333,7 @@ __device__ __forceinline__ AlphaEval eval_alpha(float4 a, float4 b, float px, fl
 
 // Pixels of thread t in a TILE x TILE tile when each thread owns PPT pixels:
 // each warp covers an 8 x (4 PPT) block (pixel k of a thread is 4k rows below
-// its first), so a warp can skip a Gaussian whose support box misses its block.
+// its first), so a warp can skip a Gaussian whose support misses its block.
 // Pixel k of thread t has the in-tile slot t + k * (TILE * TILE / PPT).
 template <int TILE, int PPT>
 __device__ __forceinline__ void tile_pixel(int t, int k, int &lx, int &ly) {

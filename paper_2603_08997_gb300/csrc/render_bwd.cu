@@ -1,7 +1,7 @@
 // gs_render_bwd: analytic adjoint of gs_render_fwd and gs_project.
 //
 // Raster adjoint (one CTA per tile, PPT = 1, 2 or 4 pixels per thread; each
-// warp walks only the staged records whose support box reaches its pixel
+// warp walks only the staged records whose support ellipse reaches its pixel
 // block, marked per batch with one ballot per warp and 32 records).  With
 // A_k = sum_{j>k} c_j a_j T_j + T_end bg (the colour behind contributor k),
 // Eq. (blend) gives dC/dc_k = a_k T_k and dC/da_k = c_k T_k - A_k / (1 - a_k).

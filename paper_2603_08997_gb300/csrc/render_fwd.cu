@@ -5,7 +5,7 @@
 // consumed `BATCH` Gaussians at a time: the CTA gathers the batch's packed
 // records into shared memory (one 48-byte record per Gaussian, copied
 // asynchronously one batch ahead into a second buffer) and marks, per warp,
-// the records whose support box reaches the warp's pixel block (one ballot
+// the records whose support ellipse reaches the warp's pixel block (one ballot
 // per warp and 32 records); every warp then walks only its marked records,
 // in order.  At the start of every batch but the tile's first (which starts
 // at T = 1) each pixel stores its transmittance into the checkpoint slot
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, PPT == 1 ? 5 : 1) render_fwd
         if (!all_done) {
             bool alive = true;
             for (int wd = 0; wd < NWORD && alive; ++wd) {
-                // only records whose support box reaches the warp's block can have alpha' >= alpha_min there
+                // only records whose support ellipse reaches the warp's block can have alpha' >= alpha_min there
                 uint32_t m = s_ov[warp][wd];
                 while (m) {
                     const int j = wd * 32 + __ffs(m) - 1;
