@@ -355,12 +355,12 @@ __device__ __forceinline__ bool warp_overlaps(float4 a, float4 c, float wx, floa
 // contain dp = 0, else the least of q's minima along the four edges (q is
 // convex with its minimum at 0, so over the rectangle it is least on the
 // boundary); along an edge q is a quadratic in one offset, minimised in closed
-// form and clamped to the edge.
-__device__ __forceinline__ float rect_qmin(float u00, float u01, float u11, float dx0, float dx1, float dy0,
-                                           float dy1) {
+// form and clamped to the edge.  sv = -u00 u01 / (u01^2 + u11^2) and
+// sh = -u01 / u00 (the minimising dy at dx = 1 and dx at dy = 1) depend on the
+// record only and are passed in.
+__device__ __forceinline__ float rect_qmin(float u00, float u01, float u11, float sv, float sh, float dx0,
+                                           float dx1, float dy0, float dy1) {
     if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
-    const float sv = -u00 * u01 / (u01 * u01 + u11 * u11);  // dy minimising q at dx = 1
-    const float sh = -u01 / u00;                            // dx minimising q at dy = 1
     auto at = [&](float dx, float dy) {
         const float z0 = u00 * dx + u01 * dy, z1 = u11 * dy;
         return z0 * z0 + z1 * z1;
@@ -386,13 +386,15 @@ __device__ __forceinline__ void overlap_masks(uint32_t (*s_ov)[NWORD], int kk, b
                                               float4 c, float alpha_min, int tile_x0, int tile_y0) {
     constexpr int H = 4 * PPT;
     const float qcut = valid ? 1.001f * (2.f * __logf(b.y / alpha_min)) + 0.01f : 0.f;
+    const float sv = valid ? -a.z * a.w / (a.w * a.w + b.x * b.x) : 0.f;
+    const float sh = valid ? -a.w / a.z : 0.f;
 #pragma unroll 1
     for (int w = 0; w < NW; ++w) {  // not unrolled: the test's temporaries stay few
         int lx0, ly0;
         tile_pixel<TILE, PPT>(w * 32, 0, lx0, ly0);
         const float wx = (float)(tile_x0 + lx0) + 0.5f, wy = (float)(tile_y0 + ly0) + 0.5f;
         bool hit = valid && warp_overlaps<H>(a, c, wx, wy);
-        if (hit) hit = rect_qmin(a.z, a.w, b.x, wx - a.x, wx + 7.f - a.x, wy - a.y, wy + (H - 1) - a.y) <= qcut;
+        if (hit) hit = rect_qmin(a.z, a.w, b.x, sv, sh, wx - a.x, wx + 7.f - a.x, wy - a.y, wy + (H - 1) - a.y) <= qcut;
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if ((threadIdx.x & 31) == 0) s_ov[w][kk >> 5] = m;
     }
